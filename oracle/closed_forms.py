@@ -1,0 +1,136 @@
+"""Analytic fields the oracle is pinned against (FP64 NumPy).
+
+TEST INFRASTRUCTURE, like the rest of ``oracle/``.
+
+Units follow the general form of the paper's Eqs. E and B: E carries k_e
+(1/(4 pi eps0), the paper's 1/(4 pi)), B carries k_b (mu0/(4 pi)); the fields
+of moving charges below assume the Maxwell-consistent choice k_b = k_e / c^2.
+
+* ``coulomb``        static point charge: E = k_e q D / R^3
+* ``biot_savart``    static current element J dV: B = k_b dV J x D / R^3
+* ``gauss_sphere``   spherical Gaussian charge (Gauss's law with an erf
+                     enclosed charge)
+* ``lienard_wiechert`` point charge in uniform motion, fields at the present
+                     position (Heaviside form)
+* ``gaussian_lw``    the same for a rigidly moving Gaussian blob, by
+                     tensor Gauss-Hermite quadrature of the point field
+* ``hertz_dipole``   oscillating point dipole p(t) z-hat with near,
+                     intermediate and far terms, times the Gaussian form
+                     factor exp(-(omega sigma / c)^2 / 2) of a smeared dipole
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erf
+
+
+def _as_pts(obs):
+    return np.asarray(obs, dtype=np.float64).reshape(-1, 3)
+
+
+def coulomb(q, rs, obs, k_e=1.0):
+    D = _as_pts(obs) - np.asarray(rs, dtype=np.float64)
+    R = np.linalg.norm(D, axis=1)
+    return k_e * q * D / R[:, None] ** 3
+
+
+def biot_savart(Jvec, dV, rs, obs, k_b=1.0):
+    D = _as_pts(obs) - np.asarray(rs, dtype=np.float64)
+    R = np.linalg.norm(D, axis=1)
+    return k_b * dV * np.cross(np.asarray(Jvec, dtype=np.float64)[None, :], D) / R[:, None] ** 3
+
+
+def gauss_sphere(Q, sigma, center, obs, k_e=1.0):
+    """E of a spherical Gaussian charge Q with standard deviation sigma."""
+    D = _as_pts(obs) - np.asarray(center, dtype=np.float64)
+    r = np.linalg.norm(D, axis=1)
+    x = r / sigma
+    q_enc = Q * (erf(x / math.sqrt(2.0)) - math.sqrt(2.0 / math.pi) * x * np.exp(-0.5 * x * x))
+    return k_e * q_enc[:, None] * D / r[:, None] ** 3
+
+
+def lienard_wiechert(q, pos_now, v, obs, c=1.0, k_e=1.0, k_b=None):
+    """Fields of a point charge moving with constant velocity v, located at
+    ``pos_now`` at the observation time (Heaviside's form of the
+    Lienard-Wiechert field).  pos_now may be [3] or [n, 3] (per point)."""
+    if k_b is None:
+        k_b = k_e / (c * c)
+    v = np.asarray(v, dtype=np.float64)
+    P = _as_pts(obs) - np.asarray(pos_now, dtype=np.float64)
+    R = np.linalg.norm(P, axis=1)
+    beta2 = float(v @ v) / (c * c)
+    vn = math.sqrt(float(v @ v))
+    if vn > 0:
+        cos_psi = (P @ v) / (R * vn)
+        sin2 = 1.0 - cos_psi ** 2
+    else:
+        sin2 = np.zeros_like(R)
+    E = k_e * q * (1.0 - beta2) * P / (R[:, None] ** 3 * (1.0 - beta2 * sin2)[:, None] ** 1.5)
+    B = (k_b / k_e) * np.cross(v[None, :], E)
+    return E, B
+
+
+def gaussian_lw(q, sigma, center_now, v, obs, c=1.0, k_e=1.0, k_b=None, n_gh=12):
+    """Fields of a Gaussian charge blob (per-axis standard deviations
+    ``sigma``) moving rigidly with velocity v, centred at ``center_now`` at the
+    observation time: the point field above averaged over the blob by a
+    tensor Gauss-Hermite rule with n_gh nodes per axis."""
+    sig = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (3,))
+    x, w = np.polynomial.hermite.hermgauss(n_gh)
+    nodes = np.sqrt(2.0) * x
+    wts = w / np.sqrt(np.pi)
+    obs = _as_pts(obs)
+    E = np.zeros_like(obs)
+    B = np.zeros_like(obs)
+    cen = np.asarray(center_now, dtype=np.float64)
+    for i in range(n_gh):
+        for j in range(n_gh):
+            for k in range(n_gh):
+                off = np.array([nodes[i] * sig[0], nodes[j] * sig[1], nodes[k] * sig[2]])
+                wt = wts[i] * wts[j] * wts[k]
+                e, b = lienard_wiechert(q, cen + off, v, obs, c=c, k_e=k_e, k_b=k_b)
+                E += wt * e
+                B += wt * b
+    return E, B
+
+
+def hertz_dipole(p0, omega, obs, t, c=1.0, k_e=1.0, k_b=None, sigma=0.0, phase=0.0):
+    """Oscillating dipole p(t) = p0 cos(omega t + phase) z-hat at the origin.
+
+    E = k_e [ (3(p.n)n - p)/r^3 + (3(p'.n)n - p')/(c r^2) + ((p''.n)n - p'')/(c^2 r) ]
+    B = k_b [ p' x n / r^2 + p'' x n / (c r) ]
+    with p, p', p'' taken at t - r/c, times exp(-(omega sigma/c)^2/2) for a
+    dipole smeared by a spherical Gaussian of standard deviation sigma.
+    """
+    if k_b is None:
+        k_b = k_e / (c * c)
+    obs = _as_pts(obs)
+    r = np.linalg.norm(obs, axis=1)
+    n = obs / r[:, None]
+    tr = t - r / c
+    ph = omega * tr + phase
+    p = p0 * np.cos(ph)
+    pd = -p0 * omega * np.sin(ph)
+    pdd = -p0 * omega * omega * np.cos(ph)
+    z = np.array([0.0, 0.0, 1.0])
+    nz = n[:, 2]
+
+    def vec(a):
+        return a[:, None] * z[None, :]
+
+    E = (vec(p) * -1 + 3 * (p * nz)[:, None] * n) / r[:, None] ** 3
+    E += (vec(pd) * -1 + 3 * (pd * nz)[:, None] * n) / (c * r[:, None] ** 2)
+    E += (vec(pdd) * -1 + (pdd * nz)[:, None] * n) / (c * c * r[:, None])
+    B = np.cross(vec(pd), n) / r[:, None] ** 2 + np.cross(vec(pdd), n) / (c * r[:, None])
+    F = math.exp(-0.5 * (omega * sigma / c) ** 2)
+    return k_e * F * E, k_b * F * B
+
+
+def rel_l2(a, b):
+    """Normwise relative L2 error ||a - b|| / ||b||."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a - b))

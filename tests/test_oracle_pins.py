@@ -1,0 +1,435 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the term or rule it pins.  A plausible slip in the oracle --
+a dropped term, a wrong sign or power of R, a missing c, a transposed cross
+product, an x/z-swapped cell index, an off-by-one slice -- fails at least one
+of them.  None of these tests retypes the oracle's own formula as its
+expectation; the expectations are closed forms, exact rational arithmetic
+and invariants.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from workloads import (Blob, Dipole, Grid, MovingGaussians, StepConstant, c1_lienard_wiechert,
+                       shell_points)
+
+RNG = np.random.Generator(np.random.PCG64(1234))
+
+
+def single_cell_history(grid, cell_ijk, n_slices, rho_fn=None, J_fn=None):
+    """History with one non-zero cell; rho_fn(n) / J_fn(n) give its values."""
+    i, j, k = cell_ijk
+    cell = (k * grid.n[1] + j) * grid.n[0] + i
+    rho = np.zeros((n_slices, grid.size))
+    J = np.zeros((n_slices, grid.size, 3))
+    for n in range(n_slices):
+        if rho_fn is not None:
+            rho[n, cell] = rho_fn(n)
+        if J_fn is not None:
+            J[n, cell] = J_fn(n)
+    centre = np.array([grid.lo[a] + (cell_ijk[a] + 0.5) * grid.d[a] for a in range(3)])
+    return rho, J, centre
+
+
+def far_points(centre, n, rmin=2.0, rmax=4.0, seed=5):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v = rng.standard_normal((n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    r = rng.uniform(rmin, rmax, n)
+    return centre + v * r[:, None]
+
+
+def exact_slot(T, R, c, dt):
+    """floor((T - R/c)/dt) in exact rational arithmetic."""
+    u = (Fraction(T) - Fraction(R) / Fraction(c)) / Fraction(dt)
+    return math.floor(u), u
+
+
+# ---------------------------------------------------------------- rho / R^3 (Coulomb)
+def test_coulomb_single_cell_pins_rho_term_and_cell_layout():
+    """Static rho in one cell of a non-cubic grid: E = k_e q D/R^3, B = 0.
+
+    Pins: sign and power of the rho/R^3 term, the k_e and dV prefactors,
+    the cell-centred convention and the x-fastest cell index (an x/z swap
+    moves the charge)."""
+    g = Grid((5, 6, 7), (-0.7, 0.3, -1.1), (0.21, 0.17, 0.13))
+    ijk = (3, 1, 5)
+    rho, J, centre = single_cell_history(g, ijk, 40, rho_fn=lambda n: 2.5)
+    obs = far_points(centre, 64)
+    c, k_e, k_b, dt = 2.5, 0.7, 0.3, 0.1
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, c=c, k_e=k_e, k_b=k_b, dt=dt, t=3.9)
+    Ec = cf.coulomb(2.5 * g.dV, centre, obs, k_e)
+    assert cf.rel_l2(E, Ec) < 1e-14
+    assert np.abs(E - Ec).max() <= 1e-14 * np.abs(Ec).max()
+    # static: the backward difference is exactly zero, so no J, no dJ, no B
+    assert np.all(B == 0.0)
+
+
+# ---------------------------------------------------------------- J / R^3 (Biot-Savart)
+def test_biot_savart_single_cell_pins_J_term_and_cross_order():
+    """Static J in one cell: B = k_b dV J x D / R^3 and E = 0 exactly.
+
+    Pins the sign of the B sum (paper Eq. B has a leading minus with D x J;
+    the result is J x D), the order of the cross product and k_b."""
+    g = Grid((4, 5, 6), (0.1, -0.4, 0.2), (0.25, 0.2, 0.3))
+    Jv = np.array([0.3, -1.2, 0.7])
+    rho, J, centre = single_cell_history(g, (1, 4, 2), 30, J_fn=lambda n: Jv)
+    obs = far_points(centre, 64, seed=6)
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, c=1.7, k_e=0.9, k_b=0.45, dt=0.2, t=5.0)
+    Bc = cf.biot_savart(Jv, g.dV, centre, obs, 0.45)
+    assert cf.rel_l2(B, Bc) < 1e-14
+    assert np.all(E == 0.0)
+
+
+# ---------------------------------------------------------------- d rho/dt / (c R^2)
+def test_charge_ramp_pins_drho_term_and_slot():
+    """rho_n = alpha (n+1) dt in one cell, so the backward difference is alpha
+    for every slice (including n = 0, where f[-1] = 0).  Then exactly
+    E = k_e dV D [rho_n/R^3 + alpha/(c R^2)], B = 0, with n the retarded slot.
+
+    The geometry is dyadic with a Pythagorean distance so the slot is an
+    exact rational floor.  Pins the drho term (sign, power, 1/c), the
+    backward difference and the slot index."""
+    g = Grid((4, 4, 4), (-1.0, -1.0, -1.0), (0.5, 0.5, 0.5))
+    alpha, dt, c, k_e = 0.75, 0.125, 2.0, 1.5
+    rho, J, centre = single_cell_history(g, (1, 2, 3), 200, rho_fn=lambda n: alpha * (n + 1) * dt)
+    # points at Pythagorean offsets (2,3,6)*s -> R = 7 s, (1,4,8)*s -> 9 s
+    offs = np.array([[2, 3, 6], [-2, 3, -6], [1, 4, 8], [8, -1, 4], [4, 4, 7], [-6, 6, 7]], float)
+    Rs = np.array([7, 7, 9, 9, 9, 11], float)
+    s = 0.25
+    obs = centre + offs * s
+    t = 9.8125
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, c=c, k_e=k_e, k_b=1.0, dt=dt, t=t)
+    for p in range(len(obs)):
+        R = Rs[p] * s
+        n, _ = exact_slot(t, R, c, dt)
+        D = offs[p] * s
+        expect = k_e * g.dV * D * (alpha * (n + 1) * dt / R ** 3 + alpha / (c * R ** 2))
+        np.testing.assert_allclose(E[p], expect, rtol=1e-14, atol=0)
+    assert np.all(B == 0.0)
+
+
+# ---------------------------------------------------------------- d J/dt terms
+def test_current_ramp_pins_both_dJ_terms():
+    """J_n = J1 (n+1) dt in one cell: dJ/dt = J1, so exactly
+    E = -k_e dV J1/(c^2 R) and B = k_b dV (J_n/R^3 + J1/(c R^2)) x D.
+
+    Pins the -dJ/(c^2 R) term of E and the dJ/(c R^2) term of B."""
+    g = Grid((3, 4, 5), (0.0, 0.0, 0.0), (0.5, 0.5, 0.5))
+    J1 = np.array([0.5, -0.25, 1.0])
+    dt, c, k_e, k_b = 0.0625, 4.0, 0.8, 0.05
+    rho, J, centre = single_cell_history(g, (2, 0, 3), 400, J_fn=lambda n: J1 * (n + 1) * dt)
+    offs = np.array([[2, 3, 6], [3, -6, 2], [-1, 4, 8], [4, -4, 7]], float)
+    Rs = np.array([7, 7, 9, 9], float)
+    s = 0.5
+    obs = centre + offs * s
+    t = 12.53125
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, c=c, k_e=k_e, k_b=k_b, dt=dt, t=t)
+    for p in range(len(obs)):
+        R = Rs[p] * s
+        n, _ = exact_slot(t, R, c, dt)
+        D = offs[p] * s
+        Jn = J1 * (n + 1) * dt
+        np.testing.assert_allclose(E[p], -k_e * g.dV * J1 / (c * c * R), rtol=1e-14, atol=0)
+        V = Jn / R ** 3 + J1 / (c * R ** 2)
+        np.testing.assert_allclose(B[p], k_b * g.dV * np.cross(V, D), rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- slot rule (Eq. tr-1)
+def test_slot_rule_matches_exact_rational_floor_including_ties():
+    """Slot of Eq. tr-1, n = floor((t - t0 - R/c)/dt), on dyadic pairs where
+    FP64 is exact: ties (u an integer) must give n = u, and every other
+    case the rational floor."""
+    cases = []
+    quads = [((1, 2, 2), 3), ((2, 3, 6), 7), ((1, 4, 8), 9), ((4, 4, 7), 9), ((2, 6, 9), 11),
+             ((6, 6, 7), 11), ((3, 4, 12), 13), ((0, 3, 4), 5), ((0, 0, 1), 1)]
+    for (a, b, cc), m in quads:
+        for s in (0.125, 0.5, 1.0):
+            for c in (1.0, 2.0, 0.5):
+                for dt in (0.125, 0.25, 0.0625):
+                    R = m * s
+                    for k in (3, 10, 57):
+                        T_tie = k * dt + R / c                 # exact tie
+                        for T in (T_tie, T_tie + dt / 4, T_tie - dt / 4):
+                            cases.append(((a * s, b * s, cc * s), R, c, dt, T))
+    xs = np.array([[0.375, -1.25, 2.0]] * len(cases))
+    xo = xs + np.array([cse[0] for cse in cases])
+    got = []
+    for idx, (off, R, c, dt, T) in enumerate(cases):
+        got.append(oracle.pair_slots(xo[idx:idx + 1], xs[idx:idx + 1], t=T + 0.5, t0=0.5, c=c, dt=dt)[0])
+    for (off, R, c, dt, T), n in zip(cases, got):
+        expect, u = exact_slot(T, R, c, dt)
+        assert n == expect, (off, R, c, dt, T, u)
+
+
+def test_slot_rule_non_dyadic_matches_rational_floor_away_from_ties():
+    """Random FP64 pairs with non-dyadic dt and c: where the exact rational u
+    of the FP64 inputs is not within 1e-9 of an integer, the slot is its
+    floor."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    xo = rng.uniform(-5, 5, (4000, 3))
+    xs = rng.uniform(-5, 5, (4000, 3))
+    t, t0, c, dt = 23.3, 0.7, 1.3, 0.1
+    got = oracle.pair_slots(xo, xs, t=t, t0=t0, c=c, dt=dt)
+    checked = 0
+    for k in range(len(xo)):
+        D = [Fraction(float(a)) - Fraction(float(b)) for a, b in zip(xo[k], xs[k])]
+        S = sum(x * x for x in D)
+        # R to high precision via integer square root on a scaled value
+        scale = 10 ** 40
+        R = Fraction(math.isqrt(int(S * scale * scale)), scale)
+        u = (Fraction(t) - Fraction(t0) - R / Fraction(c)) / Fraction(dt)
+        if abs(u - round(u)) < Fraction(1, 10 ** 9):
+            continue
+        checked += 1
+        assert got[k] == math.floor(u)
+    assert checked > 3900
+
+
+# ---------------------------------------------------------------- Gauss's law
+def test_static_gaussian_matches_gauss_law():
+    """Static spherical Gaussian charge (sigma = 3 cells) seen from outside:
+    the midpoint sum is spectrally accurate, so E equals Gauss's law
+    k_e Q_enc(r) r_hat / r^2 to ~1e-9, and B = 0."""
+    g = Grid.cube(40, -2.0, 2.0)
+    sigma = 0.3
+    src = MovingGaussians([Blob(1.0, (sigma,) * 3, (0.0, 0.0, 0.0), (0.0, 0.0, 0.0))])
+    rho, J, _, _ = src.history(g, 30, 0.5)
+    obs = shell_points([2.5, 3.5], 24, seed=9)
+    # t - R_max/c > dt for every pair: no pair sees the turn-on slice 0
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, dt=0.5, t=8.9, k_e=0.25)
+    Eg = cf.gauss_sphere(1.0, sigma, (0, 0, 0), obs, k_e=0.25)
+    assert cf.rel_l2(E, Eg) < 1e-9
+    assert np.all(B == 0.0)
+
+
+# ---------------------------------------------------------------- invariants
+def test_static_history_gives_time_independent_fields():
+    """Any static history: derivative terms vanish exactly (f - f = 0), so E
+    and B are bit-identical at every t once all pairs see a slice, and equal
+    the Coulomb + Biot-Savart superposition."""
+    g = Grid((4, 3, 5), (-0.5, -0.4, -0.6), (0.25, 0.3, 0.22))
+    r0 = RNG.standard_normal(g.size)
+    J0 = RNG.standard_normal((g.size, 3))
+    rho = np.repeat(r0[None], 60, axis=0)
+    J = np.repeat(J0[None], 60, axis=0)
+    obs = far_points(np.zeros(3), 40, 3.0, 4.0, seed=11)
+    outs = [oracle.fields(g.n, g.lo, g.d, obs, rho, J, dt=0.1, t=t, c=1.0) for t in (5.3, 5.6, 5.9)]
+    for E, B in outs[1:]:
+        assert np.array_equal(E, outs[0][0]) and np.array_equal(B, outs[0][1])
+    pts = g.points()
+    Ec = sum(cf.coulomb(r0[i] * g.dV, pts[i], obs) for i in range(g.size))
+    Bc = sum(cf.biot_savart(J0[i], g.dV, pts[i], obs) for i in range(g.size))
+    assert cf.rel_l2(outs[0][0], Ec) < 1e-13
+    assert cf.rel_l2(outs[0][1], Bc) < 1e-13
+
+
+def test_linearity_in_sources():
+    """E[a S1 + b S2] = a E[S1] + b E[S2] (backward differences are linear)."""
+    g = Grid((5, 4, 3), (-0.3, -0.2, -0.1), (0.15, 0.2, 0.25))
+    H = 50
+    r1, r2 = RNG.standard_normal((2, H, g.size))
+    J1, J2 = RNG.standard_normal((2, H, g.size, 3))
+    obs = far_points(np.zeros(3), 30, 1.0, 3.0, seed=12)
+    a, b = 0.7, -1.9
+    kw = dict(dt=0.1, t=4.0, c=1.0)
+    E1, B1 = oracle.fields(g.n, g.lo, g.d, obs, r1, J1, **kw)
+    E2, B2 = oracle.fields(g.n, g.lo, g.d, obs, r2, J2, **kw)
+    E3, B3 = oracle.fields(g.n, g.lo, g.d, obs, a * r1 + b * r2, a * J1 + b * J2, **kw)
+    assert cf.rel_l2(E3, a * E1 + b * E2) < 1e-13
+    assert cf.rel_l2(B3, a * B1 + b * B2) < 1e-13
+
+
+def test_causality_no_field_before_first_signal():
+    """Sources start at t0: for t - t0 < R_min/c every slot is negative and
+    the fields are exactly zero; just after, they are not."""
+    g = Grid.cube(4, -0.5, 0.5)
+    rho = np.ones((40, g.size))
+    J = np.ones((40, g.size, 3))
+    obs = np.array([[3.0, 0.1, -0.2], [2.5, 1.0, 0.0]])
+    pts = g.points()
+    rmin = min(np.linalg.norm(pts - o, axis=1).min() for o in obs)
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, dt=0.1, t0=1.0, t=1.0 + rmin - 1e-9)
+    assert np.all(E == 0) and np.all(B == 0)
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, dt=0.1, t0=1.0, t=1.0 + rmin + 1e-9)
+    assert np.any(E != 0) and np.any(B != 0)
+
+
+def test_step_sources_saturate_after_longest_path():
+    """Paper Sec. 3.1 (Eq. const_sources, 15^3 cells over [-3,3]^3, cell 0.4):
+    with step-on constant sources the fields stop changing once every pair's
+    retarded slot is >= 1, i.e. for t >= R_max/c + dt.  (The paper's bound is
+    printed as 6 cbrt(3) ~ 8.7; the longest centre distance here is
+    6 sqrt(3) (14/15) ~ 9.70.)  Before that they still change."""
+    g = Grid.cube(15, -3.0, 3.0)
+    obs = Grid.cube(15, -3.0, 3.0).points()[::37]
+    dt = 0.05
+    rho, J, _, _ = StepConstant().history(g, 301, dt)
+    pts = g.points()
+    rmax = max(np.linalg.norm(pts - o, axis=1).max() for o in obs)
+    assert rmax < 6 * math.sqrt(3) * 14 / 15 + 1e-12
+    kw = dict(dt=dt, screen=(0.2, 0.2, 0.2))
+    Ea, Ba = oracle.fields(g.n, g.lo, g.d, obs, rho, J, t=rmax + 1.01 * dt, **kw)
+    Eb, Bb = oracle.fields(g.n, g.lo, g.d, obs, rho, J, t=14.9, **kw)
+    assert np.array_equal(Ea, Eb) and np.array_equal(Ba, Bb)
+    Ec, Bc = oracle.fields(g.n, g.lo, g.d, obs, rho, J, t=rmax - 0.5, **kw)
+    assert not np.array_equal(Ec, Eb)
+
+
+def test_mirror_symmetry_of_charge_moving_along_x():
+    """C1 geometry (grids symmetric in y and z), charge moving along x:
+    J || x gives B_x == 0 exactly; E_y, B_z are odd and E_x even under
+    y -> -y."""
+    p = c1_lienard_wiechert()
+    rho, J, _, _ = p.source.history(p.src, p.n_push, p.dt)
+    obs = p.obs()
+    E, B = oracle.fields(p.src.n, p.src.lo, p.src.d, obs, rho, J, dt=p.dt, t=p.times[1])
+    assert np.all(B[:, 0] == 0.0)
+    n = p.obs_grid.n
+    Eg = E.reshape(n[2], n[1], n[0], 3)
+    Bg = B.reshape(n[2], n[1], n[0], 3)
+    scale = np.abs(E).max()
+    assert np.abs(Eg[:, ::-1, :, 1] + Eg[:, :, :, 1]).max() < 1e-12 * scale
+    assert np.abs(Eg[:, ::-1, :, 0] - Eg[:, :, :, 0]).max() < 1e-12 * scale
+    assert np.abs(Bg[:, ::-1, :, 2] + Bg[:, :, :, 2]).max() < 1e-12 * np.abs(B).max()
+
+
+# ---------------------------------------------------------------- screening (Sec. 2.1, Sec. 3)
+def test_screening_box():
+    """A pair with |D_a| <= delta_a on every axis contributes nothing: a
+    charge in the observation point's own cell gives zero field; a
+    neighbour one cell away contributes for delta = d/2 and is screened for
+    delta = d."""
+    g = Grid.cube(3, -0.75, 0.75)             # d = 0.5, centres -0.5, 0, 0.5
+    rho_self, J0, c_self = single_cell_history(g, (1, 1, 1), 20, rho_fn=lambda n: 1.0)
+    obs = np.array([c_self])
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho_self, J0, dt=0.1, t=1.5)
+    assert np.all(E == 0)
+    rho_nb, _, c_nb = single_cell_history(g, (2, 1, 1), 20, rho_fn=lambda n: 1.0)
+    E, _ = oracle.fields(g.n, g.lo, g.d, obs, rho_nb, J0, dt=0.1, t=1.5)
+    np.testing.assert_allclose(E, cf.coulomb(g.dV, c_nb, obs), rtol=1e-15)
+    E, _ = oracle.fields(g.n, g.lo, g.d, obs, rho_nb, J0, dt=0.1, t=1.5, screen=(0.5, 0.5, 0.5))
+    assert np.all(E == 0)
+    # screening is per axis: a diagonal neighbour with delta = (0.5, 0.5, 0.25)
+    rho_d, _, c_d = single_cell_history(g, (2, 2, 2), 20, rho_fn=lambda n: 1.0)
+    E, _ = oracle.fields(g.n, g.lo, g.d, obs, rho_d, J0, dt=0.1, t=1.5, screen=(0.5, 0.5, 0.25))
+    np.testing.assert_allclose(E, cf.coulomb(g.dV, c_d, obs), rtol=1e-15)
+
+
+def test_needs_future_slice_is_an_error():
+    g = Grid.cube(2, 0.0, 1.0)
+    rho = np.ones((5, g.size))
+    J = np.zeros((5, g.size, 3))
+    with pytest.raises(ValueError):
+        oracle.fields(g.n, g.lo, g.d, np.array([[3.0, 0.0, 0.0]]), rho, J, dt=0.1, t=4.0)
+
+
+# ---------------------------------------------------------------- moving charges
+def _lw_error(v, dt, H):
+    p = c1_lienard_wiechert(dt=dt, H=H)
+    tt = p.times[1]
+    tc = tt - 3.0
+    b = Blob(1.0, (0.2, 0.2, 0.2), (-v * tc, 0.0, 0.0), (v, 0.0, 0.0))
+    rho, J, _, _ = MovingGaussians([b]).history(p.src, p.n_push, p.dt)
+    obs = p.obs()
+    E, B = oracle.fields(p.src.n, p.src.lo, p.src.d, obs, rho, J, dt=p.dt, t=tt)
+    Ec, Bc = cf.gaussian_lw(b.q, b.sigma, np.array(b.x0) + np.array(b.v) * tt, b.v, obs)
+    return cf.rel_l2(E, Ec), cf.rel_l2(B, Bc)
+
+
+def test_lienard_wiechert_first_order_convergence():
+    """Gaussian charge at v = 0.1 c (kept well inside the source box): the
+    floor slot and backward difference are first order in dt, so the error
+    against the Lienard-Wiechert field is small and falls ~4x when dt falls
+    4x."""
+    e1, b1 = _lw_error(0.1, 0.0625, 80)
+    e4, b4 = _lw_error(0.1, 0.015625, 320)
+    assert e1 < 5e-3 and b1 < 7e-3
+    assert e4 < e1 / 3.0 and b4 < b1 / 3.0
+
+
+def test_lienard_wiechert_c1_config():
+    """The 16^3 / v = 0.3 c configuration: within physics tolerance (O(dt)
+    lag plus the part of the charge that sits outside the [-1,1]^3 source
+    box at the earliest retarded times)."""
+    p = c1_lienard_wiechert()
+    rho, J, _, _ = p.source.history(p.src, p.n_push, p.dt)
+    b = p.source.blobs[0]
+    obs = p.obs()
+    for tt in (p.times[0], p.times[-1]):
+        E, B = oracle.fields(p.src.n, p.src.lo, p.src.d, obs, rho, J, dt=p.dt, t=tt)
+        Ec, Bc = cf.gaussian_lw(b.q, b.sigma, np.array(b.x0) + np.array(b.v) * tt, b.v, obs)
+        assert cf.rel_l2(E, Ec) < 0.10 and cf.rel_l2(B, Bc) < 0.10
+
+
+@pytest.mark.parametrize("supplied", [True, False])
+def test_hertz_dipole(supplied):
+    """Gaussian-smeared oscillating dipole (sigma = 0.1, omega = 2 pi/8) seen
+    at R = 5 (c = 1) and R = 12 (c = 2): the near, intermediate and far terms
+    of the Hertzian dipole times the form factor exp(-(omega sigma/c)^2/2).
+
+    The floor slot samples each source on average dt/2 before its retarded
+    time, and a backward difference is centred another dt/2 earlier, so the
+    closed form is taken at t - dt/2 (supplied derivatives) or t - dt
+    (backward differences).  A wrong sign or power in any derivative term
+    breaks the far-zone cancellation and fails by orders of magnitude."""
+    g = Grid.cube(20, -0.5, 0.5)
+    model = Dipole(1.0, 2 * math.pi / 8.0, 0.1)
+    dt = 0.005
+    for R, k_e, c, tolE in ((5.0, 1.0, 1.0, 2e-3), (12.0, 0.3, 2.0, 6e-3)):
+        obs = shell_points([R], 16, seed=int(R))
+        rmin, rmax = R - 0.9, R + 0.9
+        t = 3.1
+        t0 = t - rmax / c - 3 * dt
+        n = int((rmax - rmin) / c / dt) + 8
+        rho, J, drho, dJ = model.history(g, n, dt, t0)
+        kw = dict(drho=drho, dJ=dJ) if supplied else {}
+        k_b = k_e / c ** 2
+        E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, dt=dt, t0=t0, t=t, c=c, k_e=k_e,
+                             k_b=k_b, **kw)
+        lag = dt / 2 if supplied else dt
+        Ec, Bc = cf.hertz_dipole(1.0, model.omega, obs, t - lag, c=c, k_e=k_e, k_b=k_b, sigma=0.1)
+        assert cf.rel_l2(E, Ec) < tolE, R
+        assert cf.rel_l2(B, Bc) < 1e-3, R
+
+
+# ---------------------------------------------------------------- cross-check (not a pin)
+def test_bruteforce_python_cross_check_tiny():
+    """Independent pure-Python evaluation (math.fsum) of the same sum on a
+    2x2x3 grid with random histories.  This catches loop/index slips in the
+    C code; the physics pins above are what fix the formula."""
+    g = Grid((2, 2, 3), (-0.2, 0.1, -0.3), (0.3, 0.25, 0.2))
+    H = 30
+    rho = RNG.standard_normal((H, g.size))
+    J = RNG.standard_normal((H, g.size, 3))
+    obs = np.array([[0.9, 0.2, 0.1], [-0.7, 1.1, 0.4], [0.0, 0.35, -0.1]])
+    c, dt, t = 1.5, 0.05, 1.2
+    E, B = oracle.fields(g.n, g.lo, g.d, obs, rho, J, c=c, dt=dt, t=t)
+    pts = g.points()
+    for o in range(len(obs)):
+        te, tb = [[], [], []], [[], [], []]
+        for cell in range(g.size):
+            D = obs[o] - pts[cell]
+            if all(abs(D[a]) <= g.d[a] / 2 for a in range(3)):
+                continue
+            R = math.sqrt(D[0] ** 2 + D[1] ** 2 + D[2] ** 2)
+            n = math.floor((t - R / c) / dt)
+            if n < 0:
+                continue
+            r = rho[n, cell]
+            dr = (r - (rho[n - 1, cell] if n >= 1 else 0.0)) / dt
+            Jn = J[n, cell]
+            dJ = (Jn - (J[n - 1, cell] if n >= 1 else 0.0)) / dt
+            V = Jn / R ** 3 + dJ / (c * R ** 2)
+            bv = np.cross(V, D)
+            for a in range(3):
+                te[a].append(D[a] * (r / R ** 3 + dr / (c * R ** 2)) - dJ[a] / (c * c * R))
+                tb[a].append(bv[a])
+        for a in range(3):
+            assert abs(E[o, a] - g.dV * math.fsum(te[a])) <= 1e-12 * (abs(E[o, a]) + 1e-300) + 1e-14
+            assert abs(B[o, a] - g.dV * math.fsum(tb[a])) <= 1e-12 * (abs(B[o, a]) + 1e-300) + 1e-14
