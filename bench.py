@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark: Jefimenko retarded direct sum on GB300 (pair-interactions per second).
+
+Workload (one "step" = one pass of the whole hot path): the heavy-ion-shaped
+problem -- source and observation grids both 64^3 over [-5,5]^3, two
+Lorentz-contracted Gaussian charges at +-0.995c with 1% seeded noise, a
+128-slice resident history -- push one new source slice, then evaluate E and
+B at 8 times spread over the valid window (one launch).  Pairs per step =
+64^3 * 64^3 * 8 = 5.5e11.  The ring (1.08 GB FP32) is larger than L2, so no
+flush is needed between steps.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the reference arm of this build), on a bounded sample.
+Multi-GPU runs (torchrun) are independent replicas: the path needs no
+exchange, so each rank runs the full workload on its own GPU ("weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s, compensated FP32 vs plain FP64 at 1e-5 err; serving p50/p99"
+UNIT = "pairs/s"
+SUM_FP32_INSTR_PER_PAIR = 31       # canonical FP32 pipe instructions per pair
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+# ---------------------------------------------------------------------------- distributed
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Largest value of x over all ranks (the job is as slow as its slowest rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- workload
+def eval_times(lo, hi, k=8):
+    return [lo + (hi - lo) * (i + 0.5) / k for i in range(k)]
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2104_05426_gb300", "csrc", "jefi_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per sum-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sum_f32c_c2_ncu.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2104_05426_gb300 as jefi
+    from workloads import c2_heavy_ion
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    stream = torch.cuda.current_stream()
+
+    p = c2_heavy_ion()
+    H = p.H
+    n_extra = args.warmup + 2 * args.steps
+    slices = [p.source.sample(p.src, p.t0 + n * p.dt, n) for n in range(H + n_extra)]
+    dev_slices = [(torch.from_numpy(r).to(dev), torch.from_numpy(j).to(dev)) for r, j in slices]
+
+    def make(prec, flags=0):
+        prm = jefi.default_params(c=p.c, k_e=p.k_e, k_b=p.k_b, dt=p.dt, t0=p.t0, history_slots=H,
+                                  precision=prec, flags=flags)
+        return jefi.jefi_create(jefi.grid_from(p.src), obs_grid=jefi.grid_from(p.obs_grid),
+                                params=prm, torch_allocator=True)
+
+    h = make("fp32c", jefi.JEFI_FLAG_STATS)
+    for n in range(H):
+        jefi.jefi_push_sources(h, *dev_slices[n])
+    n_obs = p.n_obs
+    n_src = p.src.size
+    n_t = 8
+    pairs_step = n_obs * n_src * n_t
+    E = torch.empty((n_t, n_obs, 3), dtype=torch.float64, device=dev)
+    B = torch.empty_like(E)
+
+    # first evaluation (untimed): accuracy reference for the oracle sample
+    lo, hi = jefi.jefi_valid_window(h)
+    t_first = eval_times(lo, hi, n_t)
+    jefi.jefi_eval_fields_multi(h, t_first, E, B)
+    E_first, B_first = E.cpu().numpy(), B.cpu().numpy()
+
+    next_slice = H
+
+    def step(host_io=False, E_host=None, B_host=None, pinned=None):
+        nonlocal next_slice
+        if host_io:
+            jefi.jefi_push_sources(h, pinned[next_slice][0], pinned[next_slice][1])
+        else:
+            jefi.jefi_push_sources(h, *dev_slices[next_slice])
+        next_slice += 1
+        lo_, hi_ = jefi.jefi_valid_window(h)
+        ts = eval_times(lo_, hi_, n_t)
+        if host_io:
+            jefi.jefi_eval_fields_multi(h, ts, E_host, B_host)
+        else:
+            jefi.jefi_eval_fields_multi(h, ts, E, B)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    jefi.jefi_reset_stats(h)
+    launches0 = jefi.jefi_get_info(h)["kernel_launches"]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms_local = ev0.elapsed_time(ev1)
+    info = jefi.jefi_get_info(h)
+    launches = info["kernel_launches"] - launches0
+    ms = max_over_ranks(ms_local, world, dev)
+    value = world * pairs_step * args.steps / (ms / 1e3)
+
+    # dominant kernel: the sum kernel, timed by the library's events on this stream
+    sum_ms = info["sum_ms_total"] / max(info["sum_launches"], 1)
+    pairs_launch = pairs_step
+    achieved = pairs_launch * SUM_FP32_INSTR_PER_PAIR / (sum_ms / 1e3) / 1e12
+    peak = N_SM * FP32_LANES_PER_SM * 2070e6 / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "FP32 Tinstr/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic(), "kernel": "sum_f32_kernel<comp>",
+                "kernel_ms": round(sum_ms, 3), "fallback_pairs": info["slot_fallbacks"],
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)"}
+
+    # end to end through the C ABI with pinned host buffers
+    pinned = [(torch.from_numpy(r).pin_memory(), torch.from_numpy(j).pin_memory())
+              for r, j in slices]
+    E_host = torch.empty((n_t, n_obs, 3), dtype=torch.float64).pin_memory()
+    B_host = torch.empty_like(E_host).pin_memory()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(True, E_host, B_host, pinned)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * pairs_step * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": n_src * 4 * 8, "d2h_bytes_per_step": 2 * n_t * n_obs * 3 * 8}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": "heavy-ion 64^3 src x 64^3 obs over [-5,5]^3, 2 Gaussian "
+                                     "charges +-0.995c + 1% noise, H=128, 8 eval times per step",
+                         "precision": "fp32 compensated, fp64 cross-split reduction",
+                         "pairs_per_step": pairs_step, "l2": "inputs larger than L2 (FP32 ring "
+                         f"{n_src * (H + 1) * 32 / 1e9:.2f} GB)", "parallelism": f"replicas x{world}"},
+              "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+
+    if rank == 0 and not args.no_extras:
+        # plain FP64 GPU path on the same workload (one evaluation time)
+        h64 = make("fp64", jefi.JEFI_FLAG_STATS)
+        for n in range(next_slice - H, next_slice):
+            jefi.jefi_push_sources(h64, *dev_slices[n])
+        lo, hi = jefi.jefi_valid_window(h64)
+        tmid = 0.5 * (lo + hi)
+        E64 = torch.empty((1, n_obs, 3), dtype=torch.float64, device=dev)
+        B64 = torch.empty_like(E64)
+        jefi.jefi_eval_fields_multi(h64, [tmid], E64, B64)      # warm-up
+        jefi.jefi_reset_stats(h64)
+        jefi.jefi_eval_fields_multi(h64, [tmid], E64, B64)
+        i64 = jefi.jefi_get_info(h64)
+        ms64 = i64["sum_ms_total"] / max(i64["sum_launches"], 1)
+        jefi.jefi_eval_fields_multi(h, [tmid], E[:1], B[:1])
+        torch.cuda.synchronize()
+        err = {"E": float(torch.linalg.norm(E[0] - E64[0]) / torch.linalg.norm(E64[0])),
+               "B": float(torch.linalg.norm(B[0] - B64[0]) / torch.linalg.norm(B64[0]))}
+        fp32c_kernel_pairs_s = pairs_launch / (sum_ms / 1e3)
+        fp64_pairs_s = n_obs * n_src / (ms64 / 1e3)
+        result["fp64_plain"] = {"value": fp64_pairs_s, "unit": UNIT, "kernel_ms": ms64,
+                                "fp32c_speedup_kernel": fp32c_kernel_pairs_s / fp64_pairs_s,
+                                "rel_l2_fp32c_vs_fp64_all_points": err}
+        jefi.jefi_destroy(h64)
+        if not args.no_cpu_baseline:
+            result["cpu_baseline"], result["oracle_check"] = cpu_baseline(p, slices[:H], t_first,
+                                                                          E_first, B_first)
+    jefi.jefi_destroy(h)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(p, slices, times, E_gpu, B_gpu, stride=512):
+    """FP64 oracle on every `stride`-th observation point, all sources, all 8
+    times (about 1.1e9 pairs), on every host core; also checks the GPU result
+    on that sample."""
+    import oracle
+
+    rho = np.stack([s[0] for s in slices])
+    J = np.stack([s[1] for s in slices])
+    sub = np.arange(0, p.n_obs, stride)
+    obs = p.obs()[sub]
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    errs = {"E": 0.0, "B": 0.0}
+    for i, t in enumerate(times):
+        Er, Br = oracle.fields(p.src.n, p.src.lo, p.src.d, obs, rho, J, dt=p.dt, t0=p.t0, t=t)
+        errs["E"] = max(errs["E"], float(np.linalg.norm(E_gpu[i][sub] - Er) / np.linalg.norm(Er)))
+        errs["B"] = max(errs["B"], float(np.linalg.norm(B_gpu[i][sub] - Br) / np.linalg.norm(Br)))
+    dt_s = time.perf_counter() - t0
+    pairs = len(sub) * p.src.size * len(times)
+    base = {"value": pairs / dt_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"every {stride}th of {p.n_obs} observation points x {p.src.size} sources x "
+                      f"{len(times)} times = {pairs:.3e} pairs, {dt_s:.1f} s"}
+    check = {"max_rel_l2_fp32c_vs_oracle": errs, "points": int(len(sub)), "times": len(times)}
+    return base, check
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from workloads import c2_heavy_ion
+
+    p = c2_heavy_ion()
+    slices = [p.source.sample(p.src, p.t0 + n * p.dt, n) for n in range(p.H)]
+    rho = np.stack([s[0] for s in slices])
+    J = np.stack([s[1] for s in slices])
+    times = p.times
+    stride = 4096
+    sub = np.arange(0, p.n_obs, stride)
+    obs = p.obs()[sub]
+
+    def step():
+        for t in times:
+            oracle.fields(p.src.n, p.src.lo, p.src.d, obs, rho, J, dt=p.dt, t0=p.t0, t=t)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt_s = time.perf_counter() - t0
+    pairs_step = len(sub) * p.src.size * len(times)
+    value = pairs_step * args.steps / dt_s
+    cores = oracle.max_threads()
+    sample = (f"every {stride}th of {p.n_obs} observation points x {p.src.size} sources x "
+              f"{len(times)} times = {pairs_step:.3e} pairs per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "heavy-ion 64^3 src x 64^3 obs over [-5,5]^3, H=128, 8 eval times",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+        flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="jefi", choices=["jefi", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and oracle legs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

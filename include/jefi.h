@@ -1,0 +1,209 @@
+/*
+ * jefi.h -- C ABI of libjefi: Jefimenko field evaluation on one GB300 GPU.
+ *
+ * What the library computes (JefiGPU, Sec. 2.2, Eqs. E-1, B-1, tr-1): for
+ * every observation point r_o and evaluation time t, the midpoint sum over
+ * all source cells r_s of a uniform grid
+ *
+ *   E(r_o,t) = k_e dV sum_s [ D (rho/R^3 + drho/(c R^2)) - dJ/(c^2 R) ]
+ *   B(r_o,t) = k_b dV sum_s [ (J/R^3 + dJ/(c R^2)) x D ]
+ *
+ * with D = r_o - r_s, R = |D| and every source quantity read at the
+ * retarded slice
+ *
+ *   n = floor(((t - t0) - R/c) / dt)                                (Eq. tr-1)
+ *
+ * of a history of source snapshots pushed one slice at a time (slice n
+ * holds the sources at t0 + n dt; sources are zero before slice 0).  Time
+ * derivatives are the backward difference (f[n] - f[n-1])/dt of Eq. E-1
+ * (f[-1] = 0) or are supplied by the caller.  Pairs inside the screening box
+ * |D_a| <= delta_a on all three axes contribute nothing (coarse screening,
+ * Sec. 2.1 and Sec. 3).  The paper's units are k_e = k_b = 1/(4 pi), c = 1
+ * (Eqs. E and B); any positive c and any k_e, k_b are accepted.
+ *
+ * Exactness contract.  Cell centres are x_i = lo + (i + 0.5) d rounded as
+ * written (product, then sum); the slot n is the FP64 value of the formula
+ * above with R = sqrt((Dx*Dx + Dy*Dy) + Dz*Dz), every operation rounded
+ * (no FMA).  Every precision selects exactly that slot for every pair;
+ * screening decisions are made in FP64 the same way.
+ *
+ * Threading and streams.  A handle is not thread-safe; issue all calls for
+ * one handle from one host thread and on one CUDA stream (or serialise the
+ * streams yourself).  `stream` arguments are cudaStream_t values (NULL is the
+ * legacy default stream).
+ *
+ * Errors.  Every call returns a jefi_status; on error nothing has been
+ * enqueued unless the code is JEFI_ECUDA.  jefi_strerror() gives a message.
+ */
+#ifndef JEFI_H
+#define JEFI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JEFI_OK = 0,
+    JEFI_EINVAL = 1,       /* bad argument (NULL, non-finite, size or mode)       */
+    JEFI_ENOMEM = 2,       /* device or host allocation failed                    */
+    JEFI_ENOTYET = 3,      /* t needs a slice that has not been pushed yet        */
+    JEFI_EEVICTED = 4,     /* t needs a slice already overwritten in the ring     */
+    JEFI_ECUDA = 5,        /* a CUDA runtime call failed                          */
+    JEFI_ETIMEOUT = 6,     /* a bounded device wait expired                       */
+    JEFI_EINTERNAL = 7,    /* internal consistency check failed                   */
+    JEFI_EUNSUPPORTED = 8  /* valid request outside what this build supports      */
+} jefi_status;
+
+typedef struct jefi_problem* jefi_handle;
+
+/* Cell-centred uniform grid: centre of cell i on axis a is lo[a] + (i+0.5) d[a].
+ * Arrays over a grid are x fastest: index = (k*n[1] + j)*n[0] + i. */
+typedef struct {
+    int32_t n[3];
+    double lo[3];
+    double d[3];
+} jefi_grid;
+
+typedef enum {
+    JEFI_FP64 = 0,       /* FP64 ring and FP64 arithmetic                          */
+    JEFI_FP32 = 1,       /* FP32 ring, FP32 sums, FP64 cross-block reduction        */
+    JEFI_FP32_COMP = 2   /* as JEFI_FP32 with compensated (Kahan) per-thread sums   */
+} jefi_precision;
+
+typedef enum {
+    JEFI_DERIV_BACKWARD = 0, /* d/dt = (f[n] - f[n-1]) / dt, f[-1] = 0 (Eq. E-1)  */
+    JEFI_DERIV_SUPPLIED = 1  /* caller passes drho/dt and dJ/dt with each slice   */
+} jefi_deriv_mode;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Both
+ * NULL: the library uses cudaMalloc / cudaFree. */
+typedef void* (*jefi_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*jefi_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+    double c;                 /* signal speed, > 0                                  */
+    double k_e;               /* E prefactor (1/(4 pi eps0); paper: 1/(4 pi))       */
+    double k_b;               /* B prefactor (mu0/(4 pi); paper: 1/(4 pi))          */
+    double dt;                /* slice spacing, > 0                                 */
+    double t0;                /* time of slice 0                                    */
+    int32_t history_slots;    /* H: resident slices in the device ring, >= 1        */
+    int32_t precision;        /* jefi_precision                                     */
+    int32_t deriv;            /* jefi_deriv_mode                                    */
+    int32_t flags;            /* JEFI_FLAG_* bits                                   */
+    double screen[3];         /* screening half-widths; < 0 selects d_src/2         */
+    jefi_alloc_fn alloc;
+    jefi_free_fn free;
+    void* alloc_ctx;
+} jefi_params;
+
+#define JEFI_FLAG_STATS 1u    /* count slot fall-backs and time kernels (adds sync points) */
+
+/* Fills p with: c = 1, k_e = k_b = 1, dt = 1, t0 = 0, H = 64, FP32_COMP,
+ * backward differences, default screening, cudaMalloc. */
+void jefi_default_params(jefi_params* p);
+
+/*
+ * Create a problem: a source grid, observation points, and an empty history.
+ *
+ * src         source grid (n[a] >= 0; a zero extent gives zero fields)
+ * obs_grid    observation grid, or NULL when obs_points is given
+ * obs_points  [n_obs][3] FP64 host array of observation points (used when
+ *             obs_grid is NULL); n_obs >= 0
+ * p           parameters (copied)
+ * stream      stream for the initial uploads (the call synchronises it)
+ * out         receives the handle
+ *
+ * Allocates the ring (history_slots+1 slots x padded cells x 8 channels of
+ * FP32 or FP64) and per-point tables on the device.  Host work is
+ * O(N_obs + N_src).
+ */
+int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
+                int64_t n_obs, const jefi_params* p, void* stream, jefi_handle* out);
+
+/*
+ * Append the next slice n_latest+1 of the source history (paper Sec. 2.2:
+ * rho and J stay resident on the device between evaluations).
+ *
+ * rho [N_src], J [N_src][3]: FP64, x-fastest over the source grid.
+ * drho_dt, dJ_dt: same layouts; required iff deriv == JEFI_DERIV_SUPPLIED,
+ *   must be NULL otherwise.
+ * on_device: 1 if the pointers are device memory (read asynchronously on
+ *   `stream`), 0 if host memory (copied before the call returns).
+ * Backward differences use the previously pushed slice.
+ */
+int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const double* drho_dt,
+                      const double* dJ_dt, int on_device, void* stream);
+
+/*
+ * E and B at time t for every observation point (input order).
+ *
+ * E, B: [N_obs][3] FP64.  on_device = 1: device pointers, results written
+ * asynchronously on `stream`.  on_device = 0: host pointers, the call
+ * returns when they are filled.
+ * JEFI_ENOTYET / JEFI_EEVICTED when some pair's retarded slice is not
+ * resident; nothing is written then.
+ */
+int jefi_eval_fields(jefi_handle h, double t, double* E, double* B, int on_device, void* stream);
+
+/*
+ * Several evaluation times in one launch: t[n_t] (host array); E, B are
+ * [n_t][N_obs][3].  Same semantics as n_t calls of jefi_eval_fields.
+ */
+int jefi_eval_fields_multi(jefi_handle h, int32_t n_t, const double* t, double* E, double* B,
+                           int on_device, void* stream);
+
+/*
+ * Interval [t_lo, t_hi] of evaluation times whose every retarded slice is
+ * resident (all slots >= n_latest-H+1 or < 0, all <= n_latest).  Returns
+ * JEFI_ENOTYET if no time qualifies (e.g. nothing pushed yet).
+ */
+int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi);
+
+/* Problem sizes and counters. */
+typedef struct {
+    int64_t n_src;            /* source cells                                      */
+    int64_t n_obs;            /* observation points                                */
+    int64_t n_latest;         /* index of the newest pushed slice (-1 if none)      */
+    int64_t pairs_per_eval;   /* n_src * n_obs                                     */
+    int64_t device_bytes;     /* bytes allocated on the device                     */
+    int64_t kernel_launches;  /* kernels launched by this handle so far            */
+    int64_t slot_fallbacks;   /* pairs whose slot the FP32 path recomputed in FP64  */
+    int64_t sum_launches;     /* timed sum-kernel launches (JEFI_FLAG_STATS)        */
+    double sum_ms_total;      /* their summed device time, ms (JEFI_FLAG_STATS)     */
+    int32_t n_split;          /* source splits per observation tile                */
+    int32_t precision;
+} jefi_info;
+
+/* Fills *out; with JEFI_FLAG_STATS it first waits for the timed launches. */
+int jefi_get_info(jefi_handle h, jefi_info* out);
+
+/* Zeroes the fall-back counter and the kernel timing totals. */
+int jefi_reset_stats(jefi_handle h);
+
+/*
+ * Diagnostic: the retarded slot the evaluation kernel selects for every
+ * pair at time t, through the same code path as jefi_eval_fields.
+ * slots: host array [N_obs][N_src] int32 (source index x fastest);
+ * screened pairs are INT32_MIN.  Intended for small problems.
+ */
+int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream);
+
+/*
+ * Host reference of the exact slot rule above for explicit pairs (no GPU
+ * needed): xo, xs [n][3]; out[n].
+ */
+void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double t, double t0,
+                          double c, double dt, int64_t* out);
+
+/* Release every device and host resource of the handle (synchronises). */
+int jefi_destroy(jefi_handle h);
+
+const char* jefi_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JEFI_H */

@@ -1,0 +1,350 @@
+"""Python binding of libjefi: GB300 Jefimenko field evaluation (JefiGPU, Sec. 2.2).
+
+Thin ctypes layer over the C ABI in ``include/jefi.h``: every function has
+the C name and only marshals arguments (NumPy arrays for host memory, torch
+CUDA tensors for device memory, torch streams).  All computation happens in
+the CUDA kernels of ``libjefi.so``; there is no CPU path.  Importing this
+package never falls back: if the library cannot be built or loaded, ``load``
+raises.
+
+Typical use::
+
+    import paper_2104_05426_gb300 as jefi
+    p = jefi.default_params(dt=0.0625, history_slots=80)
+    h = jefi.jefi_create(jefi.grid((16,16,16), (-1,-1,-1), (0.125,)*3), obs_points=pts, params=p)
+    jefi.jefi_push_sources(h, rho, J)           # numpy (host) or torch CUDA tensors
+    E, B = jefi.eval_fields(h, t)               # torch CUDA tensors [N_obs, 3] FP64
+    jefi.jefi_destroy(h)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+JEFI_OK = 0
+JEFI_EINVAL = 1
+JEFI_ENOMEM = 2
+JEFI_ENOTYET = 3
+JEFI_EEVICTED = 4
+JEFI_ECUDA = 5
+JEFI_ETIMEOUT = 6
+JEFI_EINTERNAL = 7
+JEFI_EUNSUPPORTED = 8
+
+JEFI_FP64 = 0
+JEFI_FP32 = 1
+JEFI_FP32_COMP = 2
+JEFI_DERIV_BACKWARD = 0
+JEFI_DERIV_SUPPLIED = 1
+JEFI_FLAG_STATS = 1
+
+PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
+
+# Every symbol include/jefi.h declares (checked by the CPU test suite).
+EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval_fields",
+           "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info", "jefi_reset_stats",
+           "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror")
+
+
+class JefiError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+
+
+class jefi_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("lo", ctypes.c_double * 3), ("d", ctypes.c_double * 3)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class jefi_params(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("k_e", ctypes.c_double), ("k_b", ctypes.c_double),
+                ("dt", ctypes.c_double), ("t0", ctypes.c_double),
+                ("history_slots", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("deriv", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("screen", ctypes.c_double * 3),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class jefi_info(ctypes.Structure):
+    _fields_ = [("n_src", ctypes.c_int64), ("n_obs", ctypes.c_int64), ("n_latest", ctypes.c_int64),
+                ("pairs_per_eval", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("slot_fallbacks", ctypes.c_int64),
+                ("sum_launches", ctypes.c_int64), ("sum_ms_total", ctypes.c_double),
+                ("n_split", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libjefi.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_needed and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("libjefi.so is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        P, I, I32, I64, D = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int64,
+                             ctypes.c_double)
+        L.jefi_default_params.argtypes = [ctypes.POINTER(jefi_params)]
+        L.jefi_default_params.restype = None
+        L.jefi_create.argtypes = [ctypes.POINTER(jefi_grid), ctypes.POINTER(jefi_grid), P, I64,
+                                  ctypes.POINTER(jefi_params), P, ctypes.POINTER(P)]
+        L.jefi_push_sources.argtypes = [P, P, P, P, P, I, P]
+        L.jefi_eval_fields.argtypes = [P, D, P, P, I, P]
+        L.jefi_eval_fields_multi.argtypes = [P, I32, P, P, P, I, P]
+        L.jefi_valid_window.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.jefi_get_info.argtypes = [P, ctypes.POINTER(jefi_info)]
+        L.jefi_reset_stats.argtypes = [P]
+        L.jefi_debug_slots.argtypes = [P, D, P, P]
+        L.jefi_host_pair_slots.argtypes = [I64, P, P, D, D, D, D, P]
+        L.jefi_host_pair_slots.restype = None
+        L.jefi_destroy.argtypes = [P]
+        L.jefi_strerror.argtypes = [I]
+        L.jefi_strerror.restype = ctypes.c_char_p
+        for name in ("jefi_create", "jefi_push_sources", "jefi_eval_fields",
+                     "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info",
+                     "jefi_reset_stats", "jefi_debug_slots", "jefi_destroy"):
+            getattr(L, name).restype = I
+        _lib = L
+        return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().jefi_strerror(int(code)).decode()
+    except Exception:  # pragma: no cover - only when the library itself is missing
+        return "unknown"
+
+
+def _check(rc: int, what: str):
+    if rc != JEFI_OK:
+        raise JefiError(rc, what)
+
+
+# ---------------------------------------------------------------------------- marshalling
+def grid(n: Sequence[int], lo: Sequence[float], d: Sequence[float]) -> jefi_grid:
+    g = jefi_grid()
+    for a in range(3):
+        g.n[a] = int(n[a])
+        g.lo[a] = float(lo[a])
+        g.d[a] = float(d[a])
+    return g
+
+
+def grid_from(obj) -> jefi_grid:
+    """From any object with ``n``, ``lo`` and ``d`` attributes (e.g. workloads.Grid)."""
+    return grid(obj.n, obj.lo, obj.d)
+
+
+def default_params(**kw) -> jefi_params:
+    p = jefi_params()
+    load().jefi_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if k == "screen":
+            for a in range(3):
+                p.screen[a] = float(v[a])
+            continue
+        setattr(p, k, v)
+    return p
+
+
+class _TorchAllocator:
+    """Device allocations through torch's caching allocator (kept alive by the handle)."""
+
+    def __init__(self):
+        import torch
+
+        self._torch = torch
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes))
+        except Exception:
+            return None
+
+    def _free(self, ptr, ctx):
+        self._torch.cuda.caching_allocator_delete(ptr)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _buf(x, dtype=np.float64):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if x is None:
+        return None, None, None
+    try:
+        import torch
+
+        if isinstance(x, torch.Tensor):
+            if x.dtype != torch.float64 or not x.is_contiguous():
+                raise ValueError("tensors must be contiguous float64")
+            return x.data_ptr(), bool(x.is_cuda), x
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, False, a
+
+
+class Handle:
+    """Owns a jefi_handle plus the Python objects its callbacks need."""
+
+    def __init__(self, ptr, keep):
+        self.ptr = ptr
+        self._keep = keep
+        self.n_obs = 0
+        self.n_src = 0
+
+    @property
+    def value(self):
+        return self.ptr.value
+
+
+# ---------------------------------------------------------------------------- C names
+def jefi_create(src: jefi_grid, obs_grid: Optional[jefi_grid] = None, obs_points=None,
+                params: Optional[jefi_params] = None, stream=None, torch_allocator: bool = False):
+    L = load()
+    if params is None:
+        params = default_params()
+    keep = []
+    if torch_allocator:
+        ta = _TorchAllocator()
+        params.alloc = ta.alloc
+        params.free = ta.free
+        keep.append(ta)
+    pts_ptr, n_obs = None, 0
+    if obs_grid is None:
+        pts = np.ascontiguousarray(obs_points, dtype=np.float64).reshape(-1, 3)
+        pts_ptr, n_obs = pts.ctypes.data, pts.shape[0]
+        keep.append(pts)
+    out = ctypes.c_void_p()
+    rc = L.jefi_create(ctypes.byref(src), ctypes.byref(obs_grid) if obs_grid is not None else None,
+                       pts_ptr, n_obs, ctypes.byref(params), _stream_ptr(stream), ctypes.byref(out))
+    _check(rc, "jefi_create")
+    keep.append(params)
+    h = Handle(out, keep)
+    info = jefi_get_info(h)
+    h.n_obs = int(info["n_obs"])
+    h.n_src = int(info["n_src"])
+    return h
+
+
+def jefi_push_sources(h: Handle, rho, J, drho_dt=None, dJ_dt=None, stream=None):
+    r, on_dev, k1 = _buf(rho)
+    j, on_dev_j, k2 = _buf(J)
+    dr, _, k3 = _buf(drho_dt)
+    dj, _, k4 = _buf(dJ_dt)
+    if on_dev_j is not None and on_dev is not None and on_dev != on_dev_j:
+        raise ValueError("rho and J must both be host or both device buffers")
+    rc = load().jefi_push_sources(h.ptr, r, j, dr, dj, 1 if on_dev else 0, _stream_ptr(stream))
+    _check(rc, "jefi_push_sources")
+
+
+def jefi_eval_fields(h: Handle, t: float, E, B, stream=None):
+    e, on_dev, ke = _buf(E)
+    b, _, kb = _buf(B)
+    if not on_dev and (ke is not E or kb is not B):
+        raise ValueError("host outputs must be contiguous float64 numpy arrays")
+    rc = load().jefi_eval_fields(h.ptr, float(t), e, b, 1 if on_dev else 0, _stream_ptr(stream))
+    _check(rc, "jefi_eval_fields")
+
+
+def jefi_eval_fields_multi(h: Handle, times, E, B, stream=None):
+    ts = np.ascontiguousarray(times, dtype=np.float64).reshape(-1)
+    e, on_dev, ke = _buf(E)
+    b, _, kb = _buf(B)
+    if not on_dev and (ke is not E or kb is not B):
+        raise ValueError("host outputs must be contiguous float64 numpy arrays")
+    rc = load().jefi_eval_fields_multi(h.ptr, ts.shape[0], ts.ctypes.data, e, b,
+                                       1 if on_dev else 0, _stream_ptr(stream))
+    _check(rc, "jefi_eval_fields_multi")
+
+
+def jefi_valid_window(h: Handle):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    rc = load().jefi_valid_window(h.ptr, ctypes.byref(lo), ctypes.byref(hi))
+    _check(rc, "jefi_valid_window")
+    return lo.value, hi.value
+
+
+def jefi_get_info(h: Handle) -> dict:
+    info = jefi_info()
+    _check(load().jefi_get_info(h.ptr, ctypes.byref(info)), "jefi_get_info")
+    return info.as_dict()
+
+
+def jefi_reset_stats(h: Handle):
+    _check(load().jefi_reset_stats(h.ptr), "jefi_reset_stats")
+
+
+def jefi_debug_slots(h: Handle, t: float, stream=None) -> np.ndarray:
+    out = np.empty((h.n_obs, h.n_src), dtype=np.int32)
+    rc = load().jefi_debug_slots(h.ptr, float(t), out.ctypes.data, _stream_ptr(stream))
+    _check(rc, "jefi_debug_slots")
+    return out
+
+
+def jefi_host_pair_slots(xo, xs, t, t0, c, dt) -> np.ndarray:
+    xo = np.ascontiguousarray(xo, dtype=np.float64).reshape(-1, 3)
+    xs = np.ascontiguousarray(xs, dtype=np.float64).reshape(-1, 3)
+    out = np.empty(xo.shape[0], dtype=np.int64)
+    load().jefi_host_pair_slots(xo.shape[0], xo.ctypes.data, xs.ctypes.data, float(t), float(t0),
+                                float(c), float(dt), out.ctypes.data)
+    return out
+
+
+def jefi_destroy(h: Handle):
+    if h.ptr:
+        rc = load().jefi_destroy(h.ptr)
+        h.ptr = ctypes.c_void_p()
+        _check(rc, "jefi_destroy")
+
+
+# ---------------------------------------------------------------------------- conveniences
+def eval_fields(h: Handle, t, stream=None):
+    """E, B at time t (or times) as new torch CUDA tensors, FP64 [.., N_obs, 3]."""
+    import torch
+
+    if np.ndim(t) == 0:
+        E = torch.empty((h.n_obs, 3), dtype=torch.float64, device="cuda")
+        B = torch.empty_like(E)
+        jefi_eval_fields(h, float(t), E, B, stream)
+    else:
+        ts = np.asarray(t, dtype=np.float64)
+        E = torch.empty((ts.shape[0], h.n_obs, 3), dtype=torch.float64, device="cuda")
+        B = torch.empty_like(E)
+        jefi_eval_fields_multi(h, ts, E, B, stream)
+    return E, B

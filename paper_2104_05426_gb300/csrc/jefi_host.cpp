@@ -1,0 +1,905 @@
+// jefi_host.cpp -- host side of libjefi: problem set-up, exact slot tables,
+// validity checks and the C ABI declared in include/jefi.h.
+//
+// Built with -ffp-contract=off: the FP64 slot rule below must round every
+// operation exactly as written (no fused multiply-add).
+#include "jefi.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "jefi_internal.h"
+
+using namespace jefi;
+
+namespace {
+
+constexpr int kTimeChunk = 8;      // evaluation times per sum launch
+constexpr int kTablePad = 3;       // candidate-table margin on each side (slots)
+constexpr double kSafety = 2.0;    // factor on the FP32 squared-distance error bound
+constexpr int kMaxEventPairs = 4096;
+
+// ---------------------------------------------------------------- exact FP64 rules
+// Cell centre lo + (i + 0.5) d (product, then sum).
+inline double center(double lo, double d, int64_t i) {
+    double off = ((double)i + 0.5) * d;
+    return lo + off;
+}
+
+// Retarded slot of Eq. tr-1 from the squared distance S; T = t - t0.
+inline int64_t slot_of(double S, double T, double c, double dt) {
+    double R = std::sqrt(S);
+    double q = R / c;
+    double u = (T - q) / dt;
+    double f = std::floor(u);
+    if (!(f > -4e18)) return INT64_MIN / 2;   // far past (or NaN): below any table
+    if (!(f < 4e18)) return INT64_MAX / 2;
+    return (int64_t)f;
+}
+
+inline double sq_sum(double sx, double sy, double sz) {
+    double sxy = sx + sy;
+    return sxy + sz;
+}
+
+// Largest S >= 0 with slot_of(S) >= k; -1 if none, +inf if every S.
+double threshold(int64_t k, double T, double c, double dt) {
+    if (slot_of(0.0, T, c, dt) < k) return -1.0;
+    if (slot_of(DBL_MAX, T, c, dt) >= k) return INFINITY;
+    auto bits = [](double x) { int64_t b; std::memcpy(&b, &x, 8); return b; };
+    auto from = [](int64_t b) { double x; std::memcpy(&x, &b, 8); return x; };
+    int64_t lo = 0, hi = bits(DBL_MAX);  // slot(lo) >= k, slot(hi) < k
+    // narrow the bracket around the analytic boundary ((T - k dt) c)^2
+    double g = (T - (double)k * dt) * c;
+    if (g > 0 && std::isfinite(g * g)) {
+        double s = g * g;
+        for (double w = 1e-12; w < 1.0; w *= 1e3) {
+            double a = s * (1.0 - w), b = s * (1.0 + w);
+            if (!std::isfinite(b)) break;
+            if (slot_of(a, T, c, dt) >= k && slot_of(b, T, c, dt) < k) {
+                lo = bits(a);
+                hi = bits(b);
+                break;
+            }
+        }
+    }
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (slot_of(from(mid), T, c, dt) >= k)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return from(lo);
+}
+
+float round_down_f32(double x) {
+    if (std::isnan(x)) return -INFINITY;
+    float f = (float)x;
+    if ((double)f > x) f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+float round_up_f32(double x) {
+    if (std::isnan(x)) return INFINITY;
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+struct AxisInfo {
+    double far_sq, near_sq, near_out_sq;  // extremes of fl(D^2) along one axis
+    int32_t rlo, rhi;                      // screening index range (rlo > rhi: empty)
+};
+
+// Per-axis extremes of one observation coordinate against source centres
+// j in [0, nlim) (monotone: D(j) = xo - x_j is non-increasing in j).
+AxisInfo axis_info(double xo, double lo, double d, int64_t nlim, int64_t npad, double delta) {
+    AxisInfo r;
+    auto D = [&](int64_t j) { return xo - center(lo, d, j); };
+    // screening range over the padded index space [0, npad)
+    int64_t a = 0, b = npad;  // first j with D(j) <= delta
+    while (a < b) {
+        int64_t m = (a + b) / 2;
+        if (D(m) <= delta) b = m; else a = m + 1;
+    }
+    int64_t first = a;
+    a = -1;
+    b = npad - 1;  // last j with D(j) >= -delta
+    while (a < b) {
+        int64_t m = b - (b - a) / 2;
+        if (D(m) >= -delta) a = m; else b = m - 1;
+    }
+    int64_t last = a;
+    if (first <= last) {
+        r.rlo = (int32_t)first;
+        r.rhi = (int32_t)last;
+    } else {
+        r.rlo = INT32_MAX;
+        r.rhi = INT32_MIN;
+    }
+    auto sq = [&](int64_t j) { double v = D(j); return v * v; };
+    r.far_sq = std::max(sq(0), sq(nlim - 1));
+    // nearest centre: first j with D(j) <= 0 and its left neighbour
+    a = 0;
+    b = nlim;
+    while (a < b) {
+        int64_t m = (a + b) / 2;
+        if (D(m) <= 0) b = m; else a = m + 1;
+    }
+    r.near_sq = INFINITY;
+    for (int64_t j = a - 1; j <= a; ++j)
+        if (j >= 0 && j < nlim) r.near_sq = std::min(r.near_sq, sq(j));
+    if (first > last) {
+        r.near_out_sq = r.near_sq;
+    } else {
+        r.near_out_sq = INFINITY;
+        if (first - 1 >= 0 && first - 1 < nlim) r.near_out_sq = std::min(r.near_out_sq, sq(first - 1));
+        if (last + 1 < nlim) r.near_out_sq = std::min(r.near_out_sq, sq(last + 1));
+    }
+    return r;
+}
+
+struct Extremes {
+    double s_min = INFINITY;  // over unscreened pairs
+    double s_max = -INFINITY;
+};
+
+void fold(Extremes& e, const AxisInfo (&ax)[3]) {
+    double smax = sq_sum(ax[0].far_sq, ax[1].far_sq, ax[2].far_sq);
+    double s0 = sq_sum(ax[0].near_out_sq, ax[1].near_sq, ax[2].near_sq);
+    double s1 = sq_sum(ax[0].near_sq, ax[1].near_out_sq, ax[2].near_sq);
+    double s2 = sq_sum(ax[0].near_sq, ax[1].near_sq, ax[2].near_out_sq);
+    e.s_min = std::min(e.s_min, std::min(s0, std::min(s1, s2)));
+    e.s_max = std::max(e.s_max, smax);
+}
+
+// Morton key of a point quantised to 21 bits per axis inside [lo, hi].
+uint64_t morton(const double* p, const double* lo, const double* hi) {
+    uint64_t key = 0;
+    uint32_t q[3];
+    for (int a = 0; a < 3; ++a) {
+        double span = hi[a] - lo[a];
+        double f = span > 0 ? (p[a] - lo[a]) / span : 0.0;
+        f = std::min(std::max(f, 0.0), 1.0);
+        q[a] = (uint32_t)(f * 2097151.0);
+    }
+    for (int bit = 20; bit >= 0; --bit)
+        for (int a = 2; a >= 0; --a) key = (key << 1) | ((q[a] >> bit) & 1u);
+    return key;
+}
+
+bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+}  // namespace
+
+// ============================================================================ handle
+struct jefi_problem {
+    jefi_params prm{};
+    jefi_grid src{};
+    bool fp64 = false;
+    int32_t nbx = 0, nby = 0, nbz = 0, n_bricks = 0, npx = 0, npy = 0, npz = 0;
+    int64_t n_src = 0, n_obs = 0;
+    int32_t n_slots = 0, n_tiles = 0;
+    int32_t H = 0, Hp = 0;
+    double screen[3] = {0, 0, 0};
+    int64_t n_latest = -1;
+    int32_t n_split = 1, bricks_per_split = 0;
+    int32_t K = 0;                 // candidate-table length per time
+    // exact squared-distance extremes over unscreened pairs
+    Extremes real, pad;
+    bool any_pairs = false;
+    // FP32 error model: |S32 - S64| <= err_rel*S + err_lin*sqrt(S) + err_abs
+    double err_rel = 0, err_lin = 0, err_abs = 0;
+    // host tables
+    std::vector<int32_t> inv_perm;   // observation -> tile slot
+    std::vector<int32_t> slot_obs;   // tile slot -> observation (-1: padding)
+    // device memory
+    void* ring = nullptr;
+    double* obs_xyz = nullptr;
+    int32_t* obs_scr = nullptr;
+    int32_t* d_inv_perm = nullptr;
+    double* prev = nullptr;
+    double* stage_in = nullptr;      // host pushes: rho, J, drho, dJ
+    double* partials = nullptr;      // [kTimeChunk][n_split][6][n_slots]
+    double* out_stage = nullptr;     // host outputs: E, B for kTimeChunk times
+    float4* tab32 = nullptr;
+    double* theta = nullptr;
+    TimeParams* times = nullptr;
+    unsigned long long* fallbacks = nullptr;
+    std::vector<std::pair<void*, size_t>> allocs;
+    int64_t device_bytes = 0;
+    // host staging for the per-eval tables
+    std::vector<float4> h_tab;
+    std::vector<double> h_theta;
+    std::vector<TimeParams> h_times;
+    // statistics
+    int64_t launches = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
+    int64_t sum_launches = 0;
+    double sum_ms = 0;
+};
+
+namespace {
+
+#define JEFI_CUDA(x)                                     \
+    do {                                                 \
+        cudaError_t _e = (x);                            \
+        if (_e != cudaSuccess) return JEFI_ECUDA;        \
+    } while (0)
+
+void* dev_alloc(jefi_problem* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (h->prm.alloc) {
+        p = h->prm.alloc(bytes, h->prm.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        h->allocs.emplace_back(p, bytes);
+        h->device_bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+void release_all(jefi_problem* h) {
+    for (auto& a : h->allocs) {
+        if (h->prm.free)
+            h->prm.free(a.first, h->prm.alloc_ctx);
+        else
+            cudaFree(a.first);
+    }
+    h->allocs.clear();
+    for (auto& e : h->ev_pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    for (auto& e : h->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    h->ev_pending.clear();
+    h->ev_free.clear();
+}
+
+int64_t phys_slot(const jefi_problem* h, int64_t k) {
+    if (k < 0 || k > h->n_latest || k < h->n_latest - h->H + 1) return h->H;  // zero slot
+    return k % h->H;
+}
+
+// Range of slots [n_lo, n_hi] needed at time t by real unscreened pairs.
+void needed_range(const jefi_problem* h, double T, int64_t* n_lo, int64_t* n_hi) {
+    *n_lo = slot_of(h->real.s_max, T, h->prm.c, h->prm.dt);
+    *n_hi = slot_of(h->real.s_min, T, h->prm.c, h->prm.dt);
+}
+
+int check_time(const jefi_problem* h, double t) {
+    if (!std::isfinite(t)) return JEFI_EINVAL;
+    if (!h->any_pairs) return JEFI_OK;
+    const double T = t - h->prm.t0;
+    const double c = h->prm.c, dt = h->prm.dt;
+    // |u| must stay well inside int64 and the FP32 candidate range
+    const double umax = (std::fabs(T) + std::sqrt(h->pad.s_max) / c) / dt;
+    if (!(umax < 1e15)) return JEFI_EUNSUPPORTED;
+    int64_t lo, hi;
+    needed_range(h, T, &lo, &hi);
+    if (hi < 0) return JEFI_OK;                      // all sources still in the future
+    if (hi > h->n_latest) return JEFI_ENOTYET;
+    const int64_t oldest = h->n_latest - h->H + 1;
+    if (std::max<int64_t>(lo, 0) < oldest) return JEFI_EEVICTED;
+    return JEFI_OK;
+}
+
+// Build the candidate tables of one evaluation time into slot ti of the staging arrays.
+void build_tables(jefi_problem* h, int ti, double t) {
+    const double T = t - h->prm.t0;
+    const double c = h->prm.c, dt = h->prm.dt;
+    const int64_t n_lo = slot_of(h->pad.s_max, T, c, dt);
+    const int64_t k0 = n_lo - kTablePad;
+    const int K = h->K;
+    double* th = h->h_theta.data() + (size_t)ti * (K + 1);
+    for (int i = 0; i <= K; ++i) th[i] = threshold(k0 + i, T, c, dt);
+    float4* tab = h->h_tab.data() + (size_t)ti * K;
+    auto err = [&](double S) { return h->err_rel * S + h->err_lin * std::sqrt(S) + h->err_abs; };
+    for (int i = 0; i < K; ++i) {
+        const double hi_t = th[i], lo_t = th[i + 1];
+        float hi, lo;
+        if (hi_t < 0) hi = -INFINITY;
+        else if (std::isinf(hi_t)) hi = INFINITY;
+        else hi = round_down_f32(hi_t - err(hi_t));
+        if (lo_t < 0) lo = -INFINITY;
+        else if (std::isinf(lo_t)) lo = INFINITY;
+        else lo = round_up_f32(lo_t + err(lo_t));
+        int32_t ps = (int32_t)phys_slot(h, k0 + i);
+        float psf;
+        std::memcpy(&psf, &ps, 4);
+        tab[i] = make_float4(hi, lo, psf, 0.f);
+    }
+    TimeParams tp;
+    tp.A = (float)(T / dt - (double)k0);
+    tp.pad = 0;
+    tp.k0 = k0;
+    h->h_times[ti] = tp;
+}
+
+int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B, cudaStream_t s,
+                 int32_t* debug_slots) {
+    for (int i = 0; i < n_t; ++i) build_tables(h, i, t[i]);
+    const int K = h->K;
+    JEFI_CUDA(cudaMemcpyAsync(h->tab32, h->h_tab.data(), sizeof(float4) * K * n_t,
+                              cudaMemcpyHostToDevice, s));
+    JEFI_CUDA(cudaMemcpyAsync(h->theta, h->h_theta.data(), sizeof(double) * (K + 1) * n_t,
+                              cudaMemcpyHostToDevice, s));
+    JEFI_CUDA(cudaMemcpyAsync(h->times, h->h_times.data(), sizeof(TimeParams) * n_t,
+                              cudaMemcpyHostToDevice, s));
+    SumParams p{};
+    p.nbx = h->nbx; p.nby = h->nby; p.nbz = h->nbz; p.n_bricks = h->n_bricks;
+    p.npx = h->npx; p.npy = h->npy; p.npz = h->npz;
+    for (int a = 0; a < 3; ++a) {
+        p.lo[a] = h->src.lo[a];
+        p.d[a] = h->src.d[a];
+        p.d32[a] = (float)h->src.d[a];
+    }
+    p.n_slots = h->n_slots;
+    p.n_tiles = h->n_tiles;
+    p.obs_xyz = h->obs_xyz;
+    p.obs_scr = h->obs_scr;
+    p.ring = h->ring;
+    p.Hp = h->Hp;
+    p.zero_slot = h->H;
+    p.tab32 = h->tab32;
+    p.theta = h->theta;
+    p.times = h->times;
+    p.n_t = n_t;
+    p.K = K;
+    p.K32 = (float)(1.0 / (h->prm.c * h->prm.dt));
+    p.n_split = h->n_split;
+    p.bricks_per_split = h->bricks_per_split;
+    p.partials = h->partials;
+    p.fallbacks = h->fallbacks;
+    p.debug_slots = debug_slots;
+    if (sum_smem_bytes(p) > 200 * 1024) return JEFI_EUNSUPPORTED;
+
+    const bool timed = (h->prm.flags & JEFI_FLAG_STATS) != 0 && !debug_slots;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (timed && (int)h->ev_pending.size() < kMaxEventPairs) {
+        if (!h->ev_free.empty()) {
+            ev = h->ev_free.back();
+            h->ev_free.pop_back();
+        } else {
+            JEFI_CUDA(cudaEventCreate(&ev.first));
+            JEFI_CUDA(cudaEventCreate(&ev.second));
+        }
+        JEFI_CUDA(cudaEventRecord(ev.first, s));
+    }
+    cudaError_t e = h->fp64 ? launch_sum_f64(p, s)
+                            : launch_sum_f32(p, h->prm.precision == JEFI_FP32_COMP, s);
+    if (e != cudaSuccess) return JEFI_ECUDA;
+    h->launches++;
+    if (ev.first) {
+        JEFI_CUDA(cudaEventRecord(ev.second, s));
+        h->ev_pending.push_back(ev);
+    }
+    if (debug_slots) return JEFI_OK;
+    ReduceParams r{};
+    r.n_obs = (int32_t)h->n_obs;
+    r.n_slots = h->n_slots;
+    r.n_split = h->n_split;
+    r.n_t = n_t;
+    r.inv_perm = h->d_inv_perm;
+    r.partials = h->partials;
+    r.e_scale = h->prm.k_e * (h->src.d[0] * h->src.d[1] * h->src.d[2]) / h->prm.c;
+    r.b_scale = h->prm.k_b * (h->src.d[0] * h->src.d[1] * h->src.d[2]);
+    r.E = E;
+    r.B = B;
+    JEFI_CUDA(launch_reduce(r, s));
+    h->launches++;
+    return JEFI_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+void jefi_default_params(jefi_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->c = 1.0;
+    p->k_e = 1.0;
+    p->k_b = 1.0;
+    p->dt = 1.0;
+    p->t0 = 0.0;
+    p->history_slots = 64;
+    p->precision = JEFI_FP32_COMP;
+    p->deriv = JEFI_DERIV_BACKWARD;
+    p->screen[0] = p->screen[1] = p->screen[2] = -1.0;
+}
+
+const char* jefi_strerror(int code) {
+    switch (code) {
+        case JEFI_OK: return "ok";
+        case JEFI_EINVAL: return "invalid argument";
+        case JEFI_ENOMEM: return "out of memory";
+        case JEFI_ENOTYET: return "evaluation time needs a slice that has not been pushed";
+        case JEFI_EEVICTED: return "evaluation time needs a slice that was evicted from the ring";
+        case JEFI_ECUDA: return "CUDA runtime error";
+        case JEFI_ETIMEOUT: return "bounded device wait expired";
+        case JEFI_EINTERNAL: return "internal consistency check failed";
+        case JEFI_EUNSUPPORTED: return "request outside what this build supports";
+        default: return "unknown jefi status";
+    }
+}
+
+void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double t, double t0,
+                          double c, double dt, int64_t* out) {
+    const double T = t - t0;
+    for (int64_t k = 0; k < n; ++k) {
+        double dx = xo[3 * k] - xs[3 * k];
+        double dy = xo[3 * k + 1] - xs[3 * k + 1];
+        double dz = xo[3 * k + 2] - xs[3 * k + 2];
+        out[k] = slot_of(sq_sum(dx * dx, dy * dy, dz * dz), T, c, dt);
+    }
+}
+
+int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
+                int64_t n_obs_in, const jefi_params* p, void* stream, jefi_handle* out) {
+    if (!src || !p || !out) return JEFI_EINVAL;
+    *out = nullptr;
+    if (!(p->c > 0) || !std::isfinite(p->c) || !(p->dt > 0) || !std::isfinite(p->dt) ||
+        !std::isfinite(p->t0) || !std::isfinite(p->k_e) || !std::isfinite(p->k_b) ||
+        p->history_slots < 1 || p->precision < 0 || p->precision > 2 || p->deriv < 0 ||
+        p->deriv > 1 || (p->alloc == nullptr) != (p->free == nullptr))
+        return JEFI_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        if (src->n[a] < 0 || !(src->d[a] > 0) || !std::isfinite(src->d[a]) ||
+            !std::isfinite(src->lo[a]) || !std::isfinite(p->screen[a]))
+            return JEFI_EINVAL;
+    }
+    int64_t n_obs = 0;
+    if (obs_grid) {
+        for (int a = 0; a < 3; ++a)
+            if (obs_grid->n[a] < 0 || !(obs_grid->d[a] > 0) || !std::isfinite(obs_grid->d[a]) ||
+                !std::isfinite(obs_grid->lo[a]))
+                return JEFI_EINVAL;
+        n_obs = (int64_t)obs_grid->n[0] * obs_grid->n[1] * obs_grid->n[2];
+    } else {
+        if (n_obs_in < 0 || (n_obs_in > 0 && !obs_points)) return JEFI_EINVAL;
+        n_obs = n_obs_in;
+        for (int64_t i = 0; i < n_obs; ++i)
+            if (!finite3(obs_points + 3 * i)) return JEFI_EINVAL;
+    }
+    if (n_obs > (int64_t)1 << 28) return JEFI_EUNSUPPORTED;
+
+    jefi_problem* h = new (std::nothrow) jefi_problem();
+    if (!h) return JEFI_ENOMEM;
+    h->prm = *p;
+    h->src = *src;
+    h->fp64 = p->precision == JEFI_FP64;
+    h->H = p->history_slots;
+    h->Hp = h->H + kZeroPadSlots;
+    for (int a = 0; a < 3; ++a) h->screen[a] = p->screen[a] < 0 ? src->d[a] / 2 : p->screen[a];
+    h->n_src = (int64_t)src->n[0] * src->n[1] * src->n[2];
+    h->n_obs = n_obs;
+    h->nbx = (src->n[0] + 3) / 4;
+    h->nby = (src->n[1] + 3) / 4;
+    h->nbz = (src->n[2] + 3) / 4;
+    h->npx = 4 * h->nbx;
+    h->npy = 4 * h->nby;
+    h->npz = 4 * h->nbz;
+    const int64_t n_bricks = (int64_t)h->nbx * h->nby * h->nbz;
+    const int64_t n_cells = n_bricks * kBrickCells;
+    if (n_bricks > INT32_MAX / 2 || (double)n_cells * h->Hp > 4e11) {
+        delete h;
+        return JEFI_EUNSUPPORTED;
+    }
+    h->n_bricks = (int32_t)n_bricks;
+
+    // ---------------------------------------------------------------- observation tiles
+    std::vector<double> pts((size_t)n_obs * 3);
+    std::vector<int64_t> order;  // tile slot -> observation index (-1 padding)
+    if (obs_grid) {
+        const int gx = obs_grid->n[0], gy = obs_grid->n[1], gz = obs_grid->n[2];
+        for (int64_t o = 0; o < n_obs; ++o) {
+            const int64_t i = o % gx, j = (o / gx) % gy, k = o / ((int64_t)gx * gy);
+            pts[3 * o + 0] = center(obs_grid->lo[0], obs_grid->d[0], i);
+            pts[3 * o + 1] = center(obs_grid->lo[1], obs_grid->d[1], j);
+            pts[3 * o + 2] = center(obs_grid->lo[2], obs_grid->d[2], k);
+        }
+        if (n_obs > 0) {
+            const int tx = (gx + 7) / 8, ty = (gy + 7) / 8, tz = (gz + 3) / 4;
+            order.assign((size_t)tx * ty * tz * kTileThreads, -1);
+            for (int64_t tile = 0; tile < (int64_t)tx * ty * tz; ++tile) {
+                const int64_t bx = tile % tx, by = (tile / tx) % ty, bz = tile / ((int64_t)tx * ty);
+                for (int tid = 0; tid < kTileThreads; ++tid) {
+                    const int w = tid >> 5, l = tid & 31;
+                    const int64_t i = 8 * bx + 4 * (w & 1) + (l & 3);
+                    const int64_t j = 8 * by + 4 * ((w >> 1) & 1) + ((l >> 2) & 3);
+                    const int64_t k = 4 * bz + 2 * (w >> 2) + (l >> 4);
+                    if (i < gx && j < gy && k < gz)
+                        order[tile * kTileThreads + tid] = (k * gy + j) * gx + i;
+                }
+            }
+        }
+    } else {
+        std::memcpy(pts.data(), obs_points, sizeof(double) * 3 * (size_t)n_obs);
+        if (n_obs > 0) {
+            double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int64_t o = 0; o < n_obs; ++o)
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = std::min(lo[a], pts[3 * o + a]);
+                    hi[a] = std::max(hi[a], pts[3 * o + a]);
+                }
+            std::vector<std::pair<uint64_t, int64_t>> keys((size_t)n_obs);
+            for (int64_t o = 0; o < n_obs; ++o) keys[o] = {morton(&pts[3 * o], lo, hi), o};
+            std::sort(keys.begin(), keys.end());
+            const int64_t n_tiles = (n_obs + kTileThreads - 1) / kTileThreads;
+            order.assign((size_t)n_tiles * kTileThreads, -1);
+            for (int64_t o = 0; o < n_obs; ++o) order[o] = keys[o].second;
+        }
+    }
+    h->n_slots = (int32_t)order.size();
+    h->n_tiles = h->n_slots / kTileThreads;
+    h->slot_obs.resize(order.size());
+    h->inv_perm.resize((size_t)n_obs);
+    std::vector<double> slot_xyz((size_t)h->n_slots * 3);
+    std::vector<int32_t> scr((size_t)6 * h->n_slots);
+    double O[3] = {0, 0, 0}, Xmax = 0;
+    const int64_t npad_axis[3] = {h->npx, h->npy, h->npz};
+    for (int a = 0; a < 3; ++a) {
+        Xmax = std::max(Xmax, std::fabs(src->lo[a]));
+        Xmax = std::max(Xmax, std::fabs(center(src->lo[a], src->d[a], npad_axis[a])));
+    }
+    for (int64_t tile = 0; tile < h->n_tiles; ++tile) {
+        // padding slots repeat the last real point of their tile (or the first)
+        int64_t fill = -1;
+        for (int tid = 0; tid < kTileThreads; ++tid)
+            if (order[tile * kTileThreads + tid] >= 0) fill = order[tile * kTileThreads + tid];
+        for (int tid = 0; tid < kTileThreads; ++tid) {
+            const int64_t s = tile * kTileThreads + tid;
+            const int64_t o = order[s];
+            h->slot_obs[s] = (int32_t)o;
+            if (o >= 0) h->inv_perm[o] = (int32_t)s;
+            const int64_t src_o = o >= 0 ? o : fill;
+            for (int a = 0; a < 3; ++a) slot_xyz[3 * s + a] = pts[3 * src_o + a];
+        }
+        // the anchor of the FP32 kernel is the tile's first slot
+        for (int tid = 0; tid < kTileThreads; ++tid) {
+            const int64_t s = tile * kTileThreads + tid;
+            for (int a = 0; a < 3; ++a) {
+                O[a] = std::max(O[a], std::fabs(slot_xyz[3 * s + a] - slot_xyz[3 * tile * kTileThreads + a]));
+                Xmax = std::max(Xmax, std::fabs(slot_xyz[3 * s + a]));
+            }
+        }
+    }
+
+    // ---------------------------------------------------------------- screening and extremes
+    const int64_t nlim[3] = {src->n[0], src->n[1], src->n[2]};
+    const int64_t npad[3] = {h->npx, h->npy, h->npz};
+    if (h->n_src > 0) {
+        for (int64_t s = 0; s < h->n_slots; ++s) {
+            AxisInfo real_ax[3], pad_ax[3];
+            for (int a = 0; a < 3; ++a) {
+                pad_ax[a] = axis_info(slot_xyz[3 * s + a], src->lo[a], src->d[a], npad[a], npad[a],
+                                      h->screen[a]);
+                real_ax[a] = axis_info(slot_xyz[3 * s + a], src->lo[a], src->d[a], nlim[a], npad[a],
+                                       h->screen[a]);
+                scr[(2 * a) * h->n_slots + s] = pad_ax[a].rlo;
+                scr[(2 * a + 1) * h->n_slots + s] = pad_ax[a].rhi;
+            }
+            fold(h->pad, pad_ax);
+            if (h->slot_obs[s] >= 0) fold(h->real, real_ax);
+        }
+    }
+    h->any_pairs = h->n_src > 0 && n_obs > 0 && std::isfinite(h->real.s_min);
+    if (h->any_pairs && !h->fp64 && !(h->pad.s_min > 1e-30)) {
+        delete h;
+        return JEFI_EUNSUPPORTED;  // unscreened pairs closer than FP32 can square
+    }
+
+    // ---------------------------------------------------------------- FP32 error model
+    {
+        const double u = std::ldexp(1.0, -24);
+        double G2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double G = u * (2 * O[a] + 12 * src->d[a]) + 4 * std::ldexp(1.0, -53) * Xmax;
+            G2 += G * G;
+        }
+        const double G = std::sqrt(G2) * (1 + 1e-6);
+        h->err_rel = kSafety * (9.1 * u + 1e-15);
+        h->err_lin = kSafety * 2 * G;
+        h->err_abs = kSafety * G * G;
+    }
+
+    // ---------------------------------------------------------------- table size, splits
+    if (h->any_pairs) {
+        const double span = (std::sqrt(h->pad.s_max) - std::sqrt(h->pad.s_min)) / (p->c * p->dt);
+        const double K = std::ceil(span) + 4 + 2 * kTablePad;
+        if (!(K < 8192)) {
+            delete h;
+            return JEFI_EUNSUPPORTED;
+        }
+        h->K = (int32_t)K;
+    } else {
+        h->K = 1;
+    }
+    {
+        const int64_t target = 2 * 152 * 2;  // two waves of two CTAs per SM
+        int64_t ns = std::max<int64_t>(1, (target + h->n_tiles - 1) / std::max<int32_t>(h->n_tiles, 1));
+        ns = std::min<int64_t>(ns, std::max<int32_t>(h->n_bricks, 1));
+        h->bricks_per_split = (int32_t)((h->n_bricks + ns - 1) / ns);
+        if (h->bricks_per_split < 1) h->bricks_per_split = 1;
+        h->n_split = (int32_t)((h->n_bricks + h->bricks_per_split - 1) / h->bricks_per_split);
+        if (h->n_split < 1) h->n_split = 1;
+    }
+
+    // ---------------------------------------------------------------- device buffers
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t esz = h->fp64 ? sizeof(double) : sizeof(float);
+    const size_t ring_bytes = (size_t)n_cells * h->Hp * 8 * esz;
+    h->ring = dev_alloc(h, ring_bytes);
+    h->obs_xyz = (double*)dev_alloc(h, sizeof(double) * slot_xyz.size());
+    h->obs_scr = (int32_t*)dev_alloc(h, sizeof(int32_t) * scr.size());
+    h->d_inv_perm = (int32_t*)dev_alloc(h, sizeof(int32_t) * std::max<size_t>(1, h->inv_perm.size()));
+    h->prev = (double*)dev_alloc(h, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src));
+    h->stage_in = (double*)dev_alloc(h, sizeof(double) * 8 * std::max<int64_t>(1, h->n_src));
+    h->partials = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * h->n_split * 6 * std::max<int32_t>(1, h->n_slots));
+    h->out_stage = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * 6 * std::max<int64_t>(1, n_obs));
+    h->tab32 = (float4*)dev_alloc(h, sizeof(float4) * kTimeChunk * h->K);
+    h->theta = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * (h->K + 1));
+    h->times = (TimeParams*)dev_alloc(h, sizeof(TimeParams) * kTimeChunk);
+    h->fallbacks = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
+    if (!h->ring || !h->obs_xyz || !h->obs_scr || !h->d_inv_perm || !h->prev || !h->stage_in ||
+        !h->partials || !h->out_stage || !h->tab32 || !h->theta || !h->times || !h->fallbacks) {
+        release_all(h);
+        delete h;
+        return JEFI_ENOMEM;
+    }
+    h->h_tab.resize((size_t)kTimeChunk * h->K);
+    h->h_theta.resize((size_t)kTimeChunk * (h->K + 1));
+    h->h_times.resize(kTimeChunk);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->prev, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->fallbacks, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess && !slot_xyz.empty())
+        e = cudaMemcpyAsync(h->obs_xyz, slot_xyz.data(), sizeof(double) * slot_xyz.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !scr.empty())
+        e = cudaMemcpyAsync(h->obs_scr, scr.data(), sizeof(int32_t) * scr.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !h->inv_perm.empty())
+        e = cudaMemcpyAsync(h->d_inv_perm, h->inv_perm.data(), sizeof(int32_t) * h->inv_perm.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        release_all(h);
+        delete h;
+        return JEFI_ECUDA;
+    }
+    *out = h;
+    return JEFI_OK;
+}
+
+int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const double* drho,
+                      const double* dJ, int on_device, void* stream) {
+    if (!h) return JEFI_EINVAL;
+    const bool supplied = h->prm.deriv == JEFI_DERIV_SUPPLIED;
+    if (h->n_src > 0 && (!rho || !J)) return JEFI_EINVAL;
+    if (supplied != (drho != nullptr) || supplied != (dJ != nullptr)) return JEFI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = h->n_src;
+    const double *r = rho, *j = J, *dr = drho, *dj = dJ;
+    if (!on_device && n > 0) {
+        double* st = h->stage_in;
+        JEFI_CUDA(cudaMemcpyAsync(st, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        JEFI_CUDA(cudaMemcpyAsync(st + n, J, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+        r = st;
+        j = st + n;
+        if (supplied) {
+            JEFI_CUDA(cudaMemcpyAsync(st + 4 * n, drho, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            JEFI_CUDA(cudaMemcpyAsync(st + 5 * n, dJ, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+            dr = st + 4 * n;
+            dj = st + 5 * n;
+        }
+    }
+    const int64_t next = h->n_latest + 1;
+    PushParams p{};
+    p.nx = h->src.n[0];
+    p.ny = h->src.n[1];
+    p.nz = h->src.n[2];
+    p.nbx = h->nbx;
+    p.nby = h->nby;
+    p.n_src = n;
+    p.Hp = h->Hp;
+    p.slot = (int32_t)(next % h->H);
+    p.supplied = supplied;
+    p.fp64 = h->fp64;
+    p.c = h->prm.c;
+    p.inv_c = 1.0 / h->prm.c;
+    p.dt = h->prm.dt;
+    p.rho = r;
+    p.J = j;
+    p.drho = dr;
+    p.dJ = dj;
+    p.prev = h->prev;
+    p.ring = h->ring;
+    JEFI_CUDA(launch_push(p, s));
+    if (n > 0) h->launches++;
+    h->n_latest = next;
+    return JEFI_OK;
+}
+
+static int eval_impl(jefi_handle h, int32_t n_t, const double* t, double* E, double* B,
+                     int on_device, void* stream) {
+    if (!h || n_t < 0 || (n_t > 0 && !t)) return JEFI_EINVAL;
+    if (n_t == 0 || h->n_obs == 0) return JEFI_OK;
+    if (!E || !B) return JEFI_EINVAL;
+    for (int i = 0; i < n_t; ++i) {
+        const int rc = check_time(h, t[i]);
+        if (rc != JEFI_OK) return rc;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t per_t = (size_t)h->n_obs * 3;
+    for (int base = 0; base < n_t; base += kTimeChunk) {
+        const int m = std::min(kTimeChunk, n_t - base);
+        double* Ed = on_device ? E + base * per_t : h->out_stage;
+        double* Bd = on_device ? B + base * per_t : h->out_stage + kTimeChunk * per_t;
+        if (!h->any_pairs) {
+            JEFI_CUDA(cudaMemsetAsync(Ed, 0, sizeof(double) * per_t * m, s));
+            JEFI_CUDA(cudaMemsetAsync(Bd, 0, sizeof(double) * per_t * m, s));
+        } else {
+            const int rc = launch_chunk(h, m, t + base, Ed, Bd, s, nullptr);
+            if (rc != JEFI_OK) return rc;
+        }
+        if (!on_device) {
+            JEFI_CUDA(cudaMemcpyAsync(E + base * per_t, Ed, sizeof(double) * per_t * m, cudaMemcpyDeviceToHost, s));
+            JEFI_CUDA(cudaMemcpyAsync(B + base * per_t, Bd, sizeof(double) * per_t * m, cudaMemcpyDeviceToHost, s));
+            JEFI_CUDA(cudaStreamSynchronize(s));
+        }
+    }
+    return JEFI_OK;
+}
+
+int jefi_eval_fields(jefi_handle h, double t, double* E, double* B, int on_device, void* stream) {
+    return eval_impl(h, 1, &t, E, B, on_device, stream);
+}
+
+int jefi_eval_fields_multi(jefi_handle h, int32_t n_t, const double* t, double* E, double* B,
+                           int on_device, void* stream) {
+    return eval_impl(h, n_t, t, E, B, on_device, stream);
+}
+
+int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream) {
+    if (!h || !slots) return JEFI_EINVAL;
+    const int rc = check_time(h, t);
+    if (rc != JEFI_OK) return rc;
+    if (h->n_obs == 0 || h->n_src == 0) return JEFI_OK;
+    const int64_t n_cells = (int64_t)h->n_bricks * kBrickCells;
+    const int64_t total = (int64_t)h->n_slots * n_cells;
+    if (total > ((int64_t)1 << 30)) return JEFI_EUNSUPPORTED;
+    if (!h->any_pairs) {
+        for (int64_t i = 0; i < h->n_obs * h->n_src; ++i) slots[i] = INT32_MIN;
+        return JEFI_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t* d = nullptr;
+    JEFI_CUDA(cudaMalloc(&d, sizeof(int32_t) * total));
+    std::vector<int32_t> host((size_t)total);
+    int r = launch_chunk(h, 1, &t, nullptr, nullptr, s, d);
+    if (r == JEFI_OK) {
+        cudaError_t e = cudaMemcpyAsync(host.data(), d, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) r = JEFI_ECUDA;
+    }
+    cudaFree(d);
+    if (r != JEFI_OK) return r;
+    const int nx = h->src.n[0], ny = h->src.n[1];
+    for (int64_t o = 0; o < h->n_obs; ++o) {
+        const int64_t slot = h->inv_perm[o];
+        for (int64_t g = 0; g < h->n_src; ++g) {
+            const int64_t ix = g % nx, iy = (g / nx) % ny, iz = g / ((int64_t)nx * ny);
+            const int64_t brick = ((iz >> 2) * h->nby + (iy >> 2)) * h->nbx + (ix >> 2);
+            const int64_t cell = brick * kBrickCells + ((iz & 3) * 16 + (iy & 3) * 4 + (ix & 3));
+            slots[o * h->n_src + g] = host[(size_t)(slot * n_cells + cell)];
+        }
+    }
+    return JEFI_OK;
+}
+
+int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi) {
+    if (!h || !t_lo || !t_hi) return JEFI_EINVAL;
+    if (h->n_latest < 0) return JEFI_ENOTYET;
+    if (!h->any_pairs) {
+        *t_lo = -INFINITY;
+        *t_hi = INFINITY;
+        return JEFI_OK;
+    }
+    const double c = h->prm.c, dt = h->prm.dt, t0 = h->prm.t0;
+    const double rmin = std::sqrt(h->real.s_min), rmax = std::sqrt(h->real.s_max);
+    auto ok_hi = [&](double t) { return slot_of(h->real.s_min, t - t0, c, dt) <= h->n_latest; };
+    // monotone in t: the farthest pair's slot has not yet fallen out of the ring
+    auto ok_lo = [&](double t) {
+        const int64_t oldest = h->n_latest - h->H + 1;
+        return slot_of(h->real.s_max, t - t0, c, dt) >= oldest;
+    };
+    // t_hi: largest t with ok_hi, found from the estimate by exact stepping/bisection
+    auto refine = [&](double guess, auto pred, bool want_max) {
+        double a = guess, b = guess;
+        double step = std::max(std::fabs(guess) * 1e-12, 1e-300);
+        if (want_max) {
+            while (!pred(a)) { a -= step; step *= 2; }
+            step = std::max(std::fabs(guess) * 1e-12, 1e-300);
+            while (pred(b)) { b += step; step *= 2; }
+        } else {
+            while (!pred(b)) { b += step; step *= 2; }
+            step = std::max(std::fabs(guess) * 1e-12, 1e-300);
+            while (pred(a)) { a -= step; step *= 2; }
+        }
+        // invariant: want_max: pred(a) && !pred(b); else: !pred(a) && pred(b)
+        for (int it = 0; it < 200; ++it) {
+            double m = a + (b - a) / 2;
+            if (m == a || m == b) break;
+            if (pred(m) == want_max) a = m; else b = m;
+        }
+        return want_max ? a : b;
+    };
+    *t_hi = refine(t0 + (double)(h->n_latest + 1) * dt + rmin / c, ok_hi, true);
+    if (h->n_latest - h->H + 1 <= 0) {
+        *t_lo = -INFINITY;
+    } else {
+        *t_lo = refine(t0 + (double)(h->n_latest - h->H + 1) * dt + rmax / c, ok_lo, false);
+    }
+    if (*t_lo > *t_hi) return JEFI_ENOTYET;
+    return JEFI_OK;
+}
+
+int jefi_get_info(jefi_handle h, jefi_info* out) {
+    if (!h || !out) return JEFI_EINVAL;
+    for (auto& ev : h->ev_pending) {
+        float ms = 0;
+        JEFI_CUDA(cudaEventSynchronize(ev.second));
+        JEFI_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+        h->sum_ms += ms;
+        h->sum_launches++;
+        h->ev_free.push_back(ev);
+    }
+    h->ev_pending.clear();
+    unsigned long long fb = 0;
+    JEFI_CUDA(cudaMemcpy(&fb, h->fallbacks, sizeof(fb), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    out->n_src = h->n_src;
+    out->n_obs = h->n_obs;
+    out->n_latest = h->n_latest;
+    out->pairs_per_eval = h->n_src * h->n_obs;
+    out->device_bytes = h->device_bytes;
+    out->kernel_launches = h->launches;
+    out->slot_fallbacks = (int64_t)fb;
+    out->sum_launches = h->sum_launches;
+    out->sum_ms_total = h->sum_ms;
+    out->n_split = h->n_split;
+    out->precision = h->prm.precision;
+    return JEFI_OK;
+}
+
+int jefi_reset_stats(jefi_handle h) {
+    if (!h) return JEFI_EINVAL;
+    jefi_info tmp;
+    int rc = jefi_get_info(h, &tmp);
+    if (rc != JEFI_OK) return rc;
+    h->sum_ms = 0;
+    h->sum_launches = 0;
+    JEFI_CUDA(cudaMemset(h->fallbacks, 0, sizeof(unsigned long long)));
+    return JEFI_OK;
+}
+
+int jefi_destroy(jefi_handle h) {
+    if (!h) return JEFI_EINVAL;
+    cudaDeviceSynchronize();
+    release_all(h);
+    delete h;
+    return JEFI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// jefi_internal.h -- structures shared by the libjefi host code and its kernels.
+//
+// Device data layout (all owned by one problem handle):
+//
+//   ring      [cell][Hp][8]  FP32 or FP64, Hp = H + 1.  Cells are in brick
+//             order: brick b = (bz*nby + by)*nbx + bx covers the 4x4x4 source
+//             cells (4bx+i, 4by+j, 4bz+k); cell = b*64 + (k*16 + j*4 + i).
+//             Grid extents are padded up to whole bricks with cells whose
+//             channels stay zero.  Physical slot H is a permanent zero slot
+//             (sources before slice 0).  Slice n lives in slot n mod H.
+//             Channels: c*rho, Jx, Jy, Jz, drho/dt, dJx/dt/c, dJy/dt/c, dJz/dt/c.
+//             With these, per pair
+//               E' += D (ch0/R^3 + ch4/R^2) - ch5..7/R   ->  E = (k_e dV / c) E'
+//               B  += (ch1..3/R^3 + ch5..7/R^2) x D      ->  B = k_b dV B
+//             which is Eqs. E-1 and B-1 with the constants factored out.
+//   obs_xyz   [n_slots][3] FP64 observation points in tile order (256 per
+//             tile); padding slots repeat a real point.
+//   obs_scr   [6][n_slots] int32 per-axis source-index ranges [lo, hi] of
+//             the screening box of each observation point (FP64 decision).
+//   tab32     [n_t][K] float4 {hi, lo, phys_slot (int bits), 0} per candidate
+//             slot k = k0 + i: S32 in (lo, hi] proves slot k exactly.
+//   theta     [n_t][K+1] FP64 exact thresholds: slot(S) >= k0+i iff S <= theta[i].
+//   partials  [n_t][n_split][6][n_slots] FP64 per-split sums.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jefi {
+
+constexpr int kTileThreads = 256;   // observation points per tile (one per thread)
+constexpr int kBrick = 4;           // source brick edge (cells)
+constexpr int kBrickCells = 64;
+constexpr int kZeroPadSlots = 1;    // the zero slot after the H ring slots
+
+struct TimeParams {
+    float A;        // fp32(T/dt - k0): candidate index = floor(A - R/(c dt))
+    int32_t pad;
+    int64_t k0;     // table origin slot
+};
+
+struct SumParams {
+    // source geometry
+    int32_t nbx, nby, nbz, n_bricks;
+    int32_t npx, npy, npz;          // padded grid extents (4 * nb)
+    double lo[3], d[3];             // source grid, FP64
+    float d32[3];
+    // observation tiles
+    int32_t n_slots;                // padded observation count
+    int32_t n_tiles;
+    const double* obs_xyz;
+    const int32_t* obs_scr;
+    // history ring
+    const void* ring;
+    int32_t Hp;                     // slots per cell including the zero slot
+    int32_t zero_slot;              // == H
+    // per-time tables
+    const float4* tab32;
+    const double* theta;
+    const TimeParams* times;
+    int32_t n_t;
+    int32_t K;                      // candidate slots per time
+    float K32;                      // fp32(1 / (c dt))
+    // work split
+    int32_t n_split;
+    int32_t bricks_per_split;
+    // outputs
+    double* partials;
+    unsigned long long* fallbacks;  // warp-level slot fall-back counter
+    int32_t* debug_slots;           // NULL, or [n_slots][n_cells] logical slot per pair
+};
+
+struct PushParams {
+    int32_t nx, ny, nz;
+    int32_t nbx, nby;
+    int64_t n_src;
+    int32_t Hp;
+    int32_t slot;                   // physical slot to write
+    int32_t supplied;
+    int32_t fp64;
+    double c, inv_c, dt;
+    const double* rho;
+    const double* J;
+    const double* drho;
+    const double* dJ;
+    double* prev;                   // [n_src][4] previous slice (backward differences)
+    void* ring;
+};
+
+struct ReduceParams {
+    int32_t n_obs, n_slots, n_split, n_t;
+    const int32_t* inv_perm;        // [n_obs] observation index -> tile slot
+    const double* partials;
+    double e_scale, b_scale;
+    double* E;                      // [n_t][n_obs][3]
+    double* B;
+};
+
+cudaError_t launch_push(const PushParams& p, cudaStream_t s);
+cudaError_t launch_sum_f32(const SumParams& p, bool compensated, cudaStream_t s);
+cudaError_t launch_sum_f64(const SumParams& p, cudaStream_t s);
+cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t s);
+size_t sum_smem_bytes(const SumParams& p);
+
+}  // namespace jefi

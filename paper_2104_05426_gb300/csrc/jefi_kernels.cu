@@ -1,0 +1,545 @@
+// jefi_kernels.cu -- sm_103a kernels of libjefi.
+//
+//   push_kernel      one source slice -> ring slot (brick order, 8 channels),
+//                    backward differences of Eq. E-1 formed in FP64
+//   sum_f32_kernel   retarded direct sum of Eqs. E-1/B-1 (FP32 arithmetic,
+//                    optional Kahan compensation per thread, FP64 partials)
+//   sum_f64_kernel   the same sum in FP64
+//   reduce_kernel    deterministic FP64 sum over source splits, scaling,
+//                    scatter to input order
+//
+// Work decomposition of the sums: one CTA = one tile of 256 observation
+// points (one per thread; a warp holds a compact 4x4x2 block for grids) x
+// one contiguous range of source bricks.  All threads of a warp visit the
+// same source cell at the same time, so the ring gathers of a warp hit a few
+// neighbouring slots of one cell.  The retarded slot of every pair is exact
+// (Eq. tr-1 in FP64): the FP64 kernel compares its exact squared distance
+// with exact thresholds, the FP32 kernel proves its slot with error-bounded
+// thresholds and recomputes the rare undecided pairs in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jefi_internal.h"
+
+namespace jefi {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: rd(u + M) has floor(u) in its low bits
+constexpr int kMagicBits = 0x4B400000;
+
+// Cell centre x_i = lo + (i + 0.5) d, product then sum, each rounded.
+__device__ __forceinline__ double cell_center(double lo, double d, int i) {
+    return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), d));
+}
+
+// Spec squared distance (Dx*Dx + Dy*Dy) + Dz*Dz, every operation rounded.
+__device__ __forceinline__ double spec_s64(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Table index whose threshold interval (theta[i+1], theta[i]] holds S.
+// Thresholds are non-increasing; the exact slot always lies strictly
+// inside the table, so both walks stop there.
+__device__ __forceinline__ int theta_search(const double* th, int K, int i, double S) {
+    i = i < 0 ? 0 : (i > K - 1 ? K - 1 : i);
+    while (i > 0 && S > th[i]) --i;
+    while (i < K - 1 && S <= th[i + 1]) ++i;
+    return i;
+}
+
+// Exact slot of one pair from scratch in FP64 (the rare undecided case of
+// the FP32 kernel).  Returns the table index.
+__device__ __noinline__ int slot_fallback_f32(const double* obs_xyz, int slot, double lox,
+                                              double loy, double loz, double dx_, double dy_,
+                                              double dz_, int ix, int iy, int iz,
+                                              const double* th, int K, int guess,
+                                              unsigned long long* counter) {
+    const double xo = obs_xyz[3 * slot + 0];
+    const double yo = obs_xyz[3 * slot + 1];
+    const double zo = obs_xyz[3 * slot + 2];
+    const double S = spec_s64(__dsub_rn(xo, cell_center(lox, dx_, ix)),
+                              __dsub_rn(yo, cell_center(loy, dy_, iy)),
+                              __dsub_rn(zo, cell_center(loz, dz_, iz)));
+    if (counter) atomicAdd(counter, 1ull);
+    return theta_search(th, K, guess, S);
+}
+
+__device__ __forceinline__ unsigned candidate_index(float S, float ri, float K32, float A, int K) {
+    const float R = S * ri;
+    const float u = fmaf(-R, K32, A);
+    const int bits = __float_as_int(__fadd_rd(u, kMagic));
+    const unsigned idx = (unsigned)(bits - kMagicBits);
+    return min(idx, (unsigned)(K - 1));
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Accumulate one pair (FP32).  v0 = (c rho, J), v1 = (drho, dJ/c).
+__device__ __forceinline__ void pair_f32(float dx, float dy, float dz, float ri, const float4& v0,
+                                         const float4& v1, float (&pe)[3], float (&pb)[3]) {
+    const float r2 = ri * ri;
+    const float r3 = r2 * ri;
+    const float q = fmaf(v1.x, r2, v0.x * r3);
+    pe[0] = fmaf(dx, q, pe[0]);
+    pe[1] = fmaf(dy, q, pe[1]);
+    pe[2] = fmaf(dz, q, pe[2]);
+    pe[0] = fmaf(-v1.y, ri, pe[0]);
+    pe[1] = fmaf(-v1.z, ri, pe[1]);
+    pe[2] = fmaf(-v1.w, ri, pe[2]);
+    const float vx = fmaf(v1.y, r2, v0.y * r3);
+    const float vy = fmaf(v1.z, r2, v0.z * r3);
+    const float vz = fmaf(v1.w, r2, v0.w * r3);
+    pb[0] = fmaf(vy, dz, pb[0]);
+    pb[1] = fmaf(vz, dx, pb[1]);
+    pb[2] = fmaf(vx, dy, pb[2]);
+    pb[0] = fmaf(-vz, dy, pb[0]);
+    pb[1] = fmaf(-vx, dz, pb[1]);
+    pb[2] = fmaf(-vy, dx, pb[2]);
+}
+
+struct ThreadCtx {
+    int slot;
+    int rlo[3], rhi[3];   // screening index ranges
+};
+
+}  // namespace
+
+// ============================================================================ FP32
+// Shared memory: tab32[K] float4 | theta[K+1] double | D[nbx+nby+nbz] float
+template <bool COMP, bool DEBUG>
+__global__ void __launch_bounds__(kTileThreads, 2) sum_f32_kernel(const SumParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = p.K;
+    float4* s_tab = reinterpret_cast<float4*>(smem);
+    double* s_th = reinterpret_cast<double*>(s_tab + K);
+    float* s_D = reinterpret_cast<float*>(s_th + K + 1);
+
+    const int tile = blockIdx.x;
+    const int split = blockIdx.y;
+    const int ti = blockIdx.z;
+    const int tid = threadIdx.x;
+
+    const float4* g_tab = p.tab32 + (size_t)ti * K;
+    const double* g_th = p.theta + (size_t)ti * (K + 1);
+    for (int i = tid; i < K; i += kTileThreads) s_tab[i] = g_tab[i];
+    for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
+
+    // Anchor: the tile's first point.  D[b] = fp32(anchor - centre of the
+    // brick's first cell) per axis, so that P = (x_o - anchor) + D is small
+    // and well rounded for every pair of a brick.
+    const double* txyz = p.obs_xyz + (size_t)tile * kTileThreads * 3;
+    const double cox = txyz[0], coy = txyz[1], coz = txyz[2];
+    const int nbxy = p.nbx + p.nby;
+    for (int i = tid; i < nbxy + p.nbz; i += kTileThreads) {
+        int a = i < p.nbx ? 0 : (i < nbxy ? 1 : 2);
+        int b = a == 0 ? i : (a == 1 ? i - p.nbx : i - nbxy);
+        double co = a == 0 ? cox : (a == 1 ? coy : coz);
+        s_D[i] = __double2float_rn(__dsub_rn(co, cell_center(p.lo[a], p.d[a], kBrick * b)));
+    }
+    __syncthreads();
+
+    ThreadCtx ctx;
+    ctx.slot = tile * kTileThreads + tid;
+    const double xo = txyz[3 * tid + 0], yo = txyz[3 * tid + 1], zo = txyz[3 * tid + 2];
+    const float oox = __double2float_rn(__dsub_rn(xo, cox));
+    const float ooy = __double2float_rn(__dsub_rn(yo, coy));
+    const float ooz = __double2float_rn(__dsub_rn(zo, coz));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ctx.rlo[a] = p.obs_scr[(2 * a) * p.n_slots + ctx.slot];
+        ctx.rhi[a] = p.obs_scr[(2 * a + 1) * p.n_slots + ctx.slot];
+    }
+    const TimeParams tp = p.times[ti];
+    const float A = tp.A;
+    const float K32 = p.K32;
+    const float d32x = p.d32[0], d32y = p.d32[1], d32z = p.d32[2];
+    const int Hp = p.Hp;
+    const float4* ring = reinterpret_cast<const float4*>(p.ring);
+    const size_t n_cells = (size_t)p.n_bricks * kBrickCells;
+
+    float se[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
+    float ce[3] = {0.f, 0.f, 0.f}, cb[3] = {0.f, 0.f, 0.f};
+
+    const int b_begin = split * p.bricks_per_split;
+    const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
+    for (int b = b_begin; b < b_end; ++b) {
+        const int bx = b % p.nbx;
+        const int rest = b / p.nbx;
+        const int by = rest % p.nby;
+        const int bz = rest / p.nby;
+        const float Px = oox + s_D[bx];
+        const float Py = ooy + s_D[p.nbx + by];
+        const float Pz = ooz + s_D[nbxy + bz];
+        const float4* cbase = ring + (size_t)b * kBrickCells * Hp * 2;
+        float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
+
+        const bool near = (ctx.rlo[0] <= kBrick * bx + 3) & (ctx.rhi[0] >= kBrick * bx) &
+                          (ctx.rlo[1] <= kBrick * by + 3) & (ctx.rhi[1] >= kBrick * by) &
+                          (ctx.rlo[2] <= kBrick * bz + 3) & (ctx.rhi[2] >= kBrick * bz);
+        if (__any_sync(kFull, near)) {
+            // Bricks that may hold screened pairs: rolled loop with the
+            // per-pair screening test (rare: only bricks next to the tile).
+            for (int cl = 0; cl < kBrickCells; ++cl) {
+                const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+                const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
+                const float dx = fmaf(-(float)i, d32x, Px);
+                const float dy = fmaf(-(float)j, d32y, Py);
+                const float dz = fmaf(-(float)k, d32z, Pz);
+                const float S = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
+                                          __fmul_rn(dz, dz));
+                const bool scr = (ix >= ctx.rlo[0]) & (ix <= ctx.rhi[0]) & (iy >= ctx.rlo[1]) &
+                                 (iy <= ctx.rhi[1]) & (iz >= ctx.rlo[2]) & (iz <= ctx.rhi[2]);
+                float ri = rsqrtf(S);
+                unsigned idx = candidate_index(S, ri, K32, A, K);
+                float4 e = s_tab[idx];
+                bool ok = scr | ((S <= e.x) & (S > e.y));
+                if (__any_sync(kFull, !ok)) {
+                    if (!ok) {
+                        idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2],
+                                                p.d[0], p.d[1], p.d[2], ix, iy, iz, s_th, K,
+                                                (int)idx, p.fallbacks);
+                        e = s_tab[idx];
+                    }
+                }
+                const int ps = scr ? p.zero_slot : __float_as_int(e.z);
+                if (scr) ri = 0.f;
+                if (DEBUG) {
+                    p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
+                        scr ? INT32_MIN : (int)(tp.k0 + idx);
+                }
+                const float4* q = cbase + (cl * Hp + ps) * 2;
+                const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+            }
+        } else {
+            // Far bricks: every squared distance from per-axis squares.
+            float ddx[4], ddy[4], ddz[4], sqx[4], sqy[4], sqz[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                ddx[i] = fmaf(-(float)i, d32x, Px);
+                ddy[i] = fmaf(-(float)i, d32y, Py);
+                ddz[i] = fmaf(-(float)i, d32z, Pz);
+                sqx[i] = __fmul_rn(ddx[i], ddx[i]);
+                sqy[i] = __fmul_rn(ddy[i], ddy[i]);
+                sqz[i] = __fmul_rn(ddz[i], ddz[i]);
+            }
+            float sxy[16];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sxy[j * 4 + i] = __fadd_rn(sqx[i], sqy[j]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int cl = k * 16 + j * 4 + i;
+                        const float S = __fadd_rn(sxy[j * 4 + i], sqz[k]);
+                        const float ri = rsqrtf(S);
+                        unsigned idx = candidate_index(S, ri, K32, A, K);
+                        float4 e = s_tab[idx];
+                        const bool ok = (S <= e.x) & (S > e.y);
+                        if (__any_sync(kFull, !ok)) {
+                            if (!ok) {
+                                idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1],
+                                                        p.lo[2], p.d[0], p.d[1], p.d[2],
+                                                        kBrick * bx + i, kBrick * by + j,
+                                                        kBrick * bz + k, s_th, K, (int)idx,
+                                                        p.fallbacks);
+                                e = s_tab[idx];
+                            }
+                        }
+                        if (DEBUG) {
+                            p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells +
+                                          cl] = (int)(tp.k0 + idx);
+                        }
+                        const float4* q = cbase + (cl * Hp + __float_as_int(e.z)) * 2;
+                        const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                        pair_f32(ddx[i], ddy[j], ddz[k], ri, v0, v1, pe, pb);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (COMP) {
+                kahan_add(se[a], ce[a], pe[a]);
+                kahan_add(sb[a], cb[a], pb[a]);
+            } else {
+                se[a] += pe[a];
+                sb[a] += pb[a];
+            }
+        }
+    }
+
+    double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        // s - c: the Kahan compensation holds the negated lost low part
+        out[(size_t)a * p.n_slots] = COMP ? (double)se[a] - (double)ce[a] : (double)se[a];
+        out[(size_t)(3 + a) * p.n_slots] = COMP ? (double)sb[a] - (double)cb[a] : (double)sb[a];
+    }
+}
+
+// ============================================================================ FP64
+// Shared memory: tab32[K] float4 | theta[K+1] double | xs[npx] ys[npy] zs[npz] double
+__device__ __forceinline__ void pair_f64(double dx, double dy, double dz, double ri,
+                                         const double2& a0, const double2& a1, const double2& a2,
+                                         const double2& a3, double (&pe)[3], double (&pb)[3]) {
+    // a0 = (c rho, Jx), a1 = (Jy, Jz), a2 = (drho, dJx/c), a3 = (dJy/c, dJz/c)
+    const double r2 = ri * ri;
+    const double r3 = r2 * ri;
+    const double q = fma(a2.x, r2, a0.x * r3);
+    pe[0] = fma(dx, q, pe[0]);
+    pe[1] = fma(dy, q, pe[1]);
+    pe[2] = fma(dz, q, pe[2]);
+    pe[0] = fma(-a2.y, ri, pe[0]);
+    pe[1] = fma(-a3.x, ri, pe[1]);
+    pe[2] = fma(-a3.y, ri, pe[2]);
+    const double vx = fma(a2.y, r2, a0.y * r3);
+    const double vy = fma(a3.x, r2, a1.x * r3);
+    const double vz = fma(a3.y, r2, a1.y * r3);
+    pb[0] = fma(vy, dz, pb[0]);
+    pb[1] = fma(vz, dx, pb[1]);
+    pb[2] = fma(vx, dy, pb[2]);
+    pb[0] = fma(-vz, dy, pb[0]);
+    pb[1] = fma(-vx, dz, pb[1]);
+    pb[2] = fma(-vy, dx, pb[2]);
+}
+
+template <bool DEBUG>
+__global__ void __launch_bounds__(kTileThreads, 1) sum_f64_kernel(const SumParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = p.K;
+    float4* s_tab = reinterpret_cast<float4*>(smem);
+    double* s_th = reinterpret_cast<double*>(s_tab + K);
+    double* s_xs = s_th + K + 1;
+    double* s_ys = s_xs + p.npx;
+    double* s_zs = s_ys + p.npy;
+
+    const int tile = blockIdx.x;
+    const int split = blockIdx.y;
+    const int ti = blockIdx.z;
+    const int tid = threadIdx.x;
+    const float4* g_tab = p.tab32 + (size_t)ti * K;
+    const double* g_th = p.theta + (size_t)ti * (K + 1);
+    for (int i = tid; i < K; i += kTileThreads) s_tab[i] = g_tab[i];
+    for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
+    for (int i = tid; i < p.npx; i += kTileThreads) s_xs[i] = cell_center(p.lo[0], p.d[0], i);
+    for (int i = tid; i < p.npy; i += kTileThreads) s_ys[i] = cell_center(p.lo[1], p.d[1], i);
+    for (int i = tid; i < p.npz; i += kTileThreads) s_zs[i] = cell_center(p.lo[2], p.d[2], i);
+    __syncthreads();
+
+    ThreadCtx ctx;
+    ctx.slot = tile * kTileThreads + tid;
+    const double xo = p.obs_xyz[3 * ctx.slot + 0];
+    const double yo = p.obs_xyz[3 * ctx.slot + 1];
+    const double zo = p.obs_xyz[3 * ctx.slot + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ctx.rlo[a] = p.obs_scr[(2 * a) * p.n_slots + ctx.slot];
+        ctx.rhi[a] = p.obs_scr[(2 * a + 1) * p.n_slots + ctx.slot];
+    }
+    const TimeParams tp = p.times[ti];
+    const float A = tp.A;
+    const float K32 = p.K32;
+    const int Hp = p.Hp;
+    const double2* ring = reinterpret_cast<const double2*>(p.ring);
+    const size_t n_cells = (size_t)p.n_bricks * kBrickCells;
+
+    double se[3] = {0, 0, 0}, sb[3] = {0, 0, 0};
+    const int b_begin = split * p.bricks_per_split;
+    const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
+    for (int b = b_begin; b < b_end; ++b) {
+        const int bx = b % p.nbx;
+        const int rest = b / p.nbx;
+        const int by = rest % p.nby;
+        const int bz = rest / p.nby;
+        double ddx[4], ddy[4], ddz[4], sqx[4], sqy[4], sqz[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ddx[i] = __dsub_rn(xo, s_xs[kBrick * bx + i]);
+            ddy[i] = __dsub_rn(yo, s_ys[kBrick * by + i]);
+            ddz[i] = __dsub_rn(zo, s_zs[kBrick * bz + i]);
+            sqx[i] = __dmul_rn(ddx[i], ddx[i]);
+            sqy[i] = __dmul_rn(ddy[i], ddy[i]);
+            sqz[i] = __dmul_rn(ddz[i], ddz[i]);
+        }
+        double sxy[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sxy[j * 4 + i] = __dadd_rn(sqx[i], sqy[j]);
+        const bool near = (ctx.rlo[0] <= kBrick * bx + 3) & (ctx.rhi[0] >= kBrick * bx) &
+                          (ctx.rlo[1] <= kBrick * by + 3) & (ctx.rhi[1] >= kBrick * by) &
+                          (ctx.rlo[2] <= kBrick * bz + 3) & (ctx.rhi[2] >= kBrick * bz);
+        const bool any_near = __any_sync(kFull, near);
+        const double2* cbase = ring + (size_t)b * kBrickCells * Hp * 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int cl = k * 16 + j * 4 + i;
+                    const double S = __dadd_rn(sxy[j * 4 + i], sqz[k]);
+                    bool scr = false;
+                    if (any_near) {
+                        const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
+                        scr = (ix >= ctx.rlo[0]) & (ix <= ctx.rhi[0]) & (iy >= ctx.rlo[1]) &
+                              (iy <= ctx.rhi[1]) & (iz >= ctx.rlo[2]) & (iz <= ctx.rhi[2]);
+                    }
+                    const float Sf = __double2float_rn(S);
+                    int it = (int)candidate_index(Sf, rsqrtf(Sf), K32, A, K);
+                    if (!scr) {
+                        if (!((S <= s_th[it]) & (S > s_th[it + 1]))) it = theta_search(s_th, K, it, S);
+                    }
+                    const int ps = scr ? p.zero_slot : __float_as_int(s_tab[it].z);
+                    if (DEBUG) {
+                        p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
+                            scr ? INT32_MIN : (int)(tp.k0 + it);
+                    }
+                    const double ri = scr ? 0.0 : rsqrt(S);
+                    const double2* q = cbase + (cl * Hp + ps) * 4;
+                    const double2 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2),
+                                  a3 = __ldg(q + 3);
+                    pair_f64(ddx[i], ddy[j], ddz[k], ri, a0, a1, a2, a3, se, sb);
+                }
+            }
+        }
+    }
+    double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out[(size_t)a * p.n_slots] = se[a];
+        out[(size_t)(3 + a) * p.n_slots] = sb[a];
+    }
+}
+
+// ============================================================================ push
+__global__ void push_kernel(const PushParams p) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= p.n_src) return;
+    const int ix = (int)(g % p.nx);
+    const int64_t r = g / p.nx;
+    const int iy = (int)(r % p.ny);
+    const int iz = (int)(r / p.ny);
+    const int64_t brick = ((int64_t)(iz >> 2) * p.nby + (iy >> 2)) * p.nbx + (ix >> 2);
+    const int64_t cell = brick * kBrickCells + ((iz & 3) * 16 + (iy & 3) * 4 + (ix & 3));
+
+    const double rho = p.rho[g];
+    const double j0 = p.J[3 * g + 0], j1 = p.J[3 * g + 1], j2 = p.J[3 * g + 2];
+    double dr, dj0, dj1, dj2;
+    if (p.supplied) {
+        dr = p.drho[g];
+        dj0 = p.dJ[3 * g + 0];
+        dj1 = p.dJ[3 * g + 1];
+        dj2 = p.dJ[3 * g + 2];
+    } else {
+        // backward difference (f[n] - f[n-1]) / dt, Eq. E-1
+        double* pv = p.prev + 4 * g;
+        dr = __ddiv_rn(__dsub_rn(rho, pv[0]), p.dt);
+        dj0 = __ddiv_rn(__dsub_rn(j0, pv[1]), p.dt);
+        dj1 = __ddiv_rn(__dsub_rn(j1, pv[2]), p.dt);
+        dj2 = __ddiv_rn(__dsub_rn(j2, pv[3]), p.dt);
+        pv[0] = rho;
+        pv[1] = j0;
+        pv[2] = j1;
+        pv[3] = j2;
+    }
+    const double ch[8] = {__dmul_rn(p.c, rho), j0, j1, j2, dr, __ddiv_rn(dj0, p.c),
+                          __ddiv_rn(dj1, p.c), __ddiv_rn(dj2, p.c)};
+    const size_t off = ((size_t)cell * p.Hp + p.slot) * 8;
+    if (p.fp64) {
+        double2* dst = reinterpret_cast<double2*>(static_cast<double*>(p.ring) + off);
+        dst[0] = make_double2(ch[0], ch[1]);
+        dst[1] = make_double2(ch[2], ch[3]);
+        dst[2] = make_double2(ch[4], ch[5]);
+        dst[3] = make_double2(ch[6], ch[7]);
+    } else {
+        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(p.ring) + off);
+        dst[0] = make_float4(__double2float_rn(ch[0]), __double2float_rn(ch[1]),
+                             __double2float_rn(ch[2]), __double2float_rn(ch[3]));
+        dst[1] = make_float4(__double2float_rn(ch[4]), __double2float_rn(ch[5]),
+                             __double2float_rn(ch[6]), __double2float_rn(ch[7]));
+    }
+}
+
+// ============================================================================ reduce
+__global__ void reduce_kernel(const ReduceParams p) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)p.n_t * p.n_obs;
+    if (gid >= total) return;
+    const int ti = (int)(gid / p.n_obs);
+    const int o = (int)(gid % p.n_obs);
+    const int slot = p.inv_perm[o];
+    const double* base = p.partials + (size_t)ti * p.n_split * 6 * p.n_slots + slot;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < p.n_split; ++s) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += base[((size_t)s * 6 + c) * p.n_slots];
+    }
+    double* E = p.E + (size_t)gid * 3;
+    double* B = p.B + (size_t)gid * 3;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        E[a] = acc[a] * p.e_scale;
+        B[a] = acc[3 + a] * p.b_scale;
+    }
+}
+
+// ============================================================================ launchers
+size_t sum_smem_bytes(const SumParams& p) {
+    size_t b = (size_t)p.K * sizeof(float4) + (size_t)(p.K + 1) * sizeof(double);
+    return b + (size_t)(p.npx + p.npy + p.npz) * sizeof(double);
+}
+
+cudaError_t launch_sum_f32(const SumParams& p, bool compensated, cudaStream_t s) {
+    const dim3 grid(p.n_tiles, p.n_split, p.n_t);
+    const size_t smem = sum_smem_bytes(p);
+    void (*k)(SumParams);
+    if (p.debug_slots)
+        k = compensated ? sum_f32_kernel<true, true> : sum_f32_kernel<false, true>;
+    else
+        k = compensated ? sum_f32_kernel<true, false> : sum_f32_kernel<false, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kTileThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_f64(const SumParams& p, cudaStream_t s) {
+    const dim3 grid(p.n_tiles, p.n_split, p.n_t);
+    const size_t smem = sum_smem_bytes(p);
+    void (*k)(SumParams) = p.debug_slots ? sum_f64_kernel<true> : sum_f64_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kTileThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_push(const PushParams& p, cudaStream_t s) {
+    if (p.n_src == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (p.n_src + threads - 1) / threads;
+    push_kernel<<<(unsigned)blocks, threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t s) {
+    const int64_t total = (int64_t)p.n_t * p.n_obs;
+    if (total == 0) return cudaSuccess;
+    const int threads = 256;
+    reduce_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace jefi

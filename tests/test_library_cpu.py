@@ -1,0 +1,88 @@
+"""CPU checks of libjefi: it builds, loads, exports every declared symbol, and
+its host-side exact slot rule agrees with the oracle's (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2104_05426_gb300 as jefi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(jefi_\w+)\s*\(", text, flags=re.M):
+                names.add(m.group(1))
+    return names
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = jefi._build.build()
+    L = jefi.load()
+    declared = declared_functions()
+    assert declared, "no declarations found"
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (jefi_\w+)", out))
+    missing = declared - exported
+    assert not missing, missing
+    for name in declared:
+        getattr(L, name)
+    assert set(jefi.EXPORTS) == declared
+
+
+def test_strerror_and_defaults():
+    assert jefi.strerror(0) == "ok"
+    assert "pushed" in jefi.strerror(jefi.JEFI_ENOTYET)
+    p = jefi.default_params()
+    assert p.c == 1.0 and p.history_slots == 64 and p.precision == jefi.JEFI_FP32_COMP
+    assert list(p.screen) == [-1.0, -1.0, -1.0]
+
+
+def test_host_slot_rule_matches_oracle_random_pairs():
+    rng = np.random.Generator(np.random.PCG64(3))
+    for c, dt, t, t0 in ((1.0, 0.0625, 7.3, 0.0), (2.7, 0.1, 31.1, -4.2), (0.3, 0.013, 3.0, 1.0)):
+        xo = rng.uniform(-6, 6, (20000, 3))
+        xs = rng.uniform(-6, 6, (20000, 3))
+        a = jefi.jefi_host_pair_slots(xo, xs, t, t0, c, dt)
+        b = oracle.pair_slots(xo, xs, t=t, t0=t0, c=c, dt=dt)
+        assert np.array_equal(a, b)
+
+
+def test_host_slot_rule_matches_oracle_on_ties():
+    """Dyadic pairs whose u is an exact integer, and their neighbours."""
+    offs = np.array([[1, 2, 2], [2, 3, 6], [1, 4, 8], [0, 3, 4], [6, 6, 7]], float)
+    rs = np.array([3, 7, 9, 5, 11], float)
+    xs = np.tile([[0.25, -0.5, 1.0]], (len(offs), 1))
+    for s in (0.125, 0.5):
+        xo = xs + offs * s
+        for dt in (0.0625, 0.125):
+            for k in (0, 5, 40):
+                for eps in (0.0, dt / 8, -dt / 8):
+                    t = k * dt + rs * s
+                    for i in range(len(offs)):
+                        a = jefi.jefi_host_pair_slots(xo[i:i + 1], xs[i:i + 1], t[i] + eps, 0.0, 1.0, dt)
+                        b = oracle.pair_slots(xo[i:i + 1], xs[i:i + 1], t=t[i] + eps, t0=0.0, c=1.0, dt=dt)
+                        assert a[0] == b[0]
+
+
+def test_handle_creation_without_gpu_fails_cleanly():
+    """Without a CUDA device the library reports an error code instead of
+    falling back to anything."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    g = jefi.grid((4, 4, 4), (0, 0, 0), (0.25,) * 3)
+    with pytest.raises(jefi.JefiError) as e:
+        jefi.jefi_create(g, obs_points=np.zeros((5, 3)) + 3.0,
+                         params=jefi.default_params(dt=0.1, history_slots=8), stream=0)
+    assert e.value.code in (jefi.JEFI_ENOMEM, jefi.JEFI_ECUDA)
