@@ -99,7 +99,8 @@ typedef struct {
     void* alloc_ctx;
 } jefi_params;
 
-#define JEFI_FLAG_STATS 1u    /* count slot fall-backs and time kernels (adds sync points) */
+#define JEFI_FLAG_STATS 1u    /* time the sum kernel with CUDA events on the call's stream */
+#define JEFI_FLAG_DIRECT_GATHER 2u  /* FP32: never use the TMA-staged kernel (for comparisons) */
 
 /* Fills p with: c = 1, k_e = k_b = 1, dt = 1, t0 = 0, H = 64, FP32_COMP,
  * backward differences, default screening, cudaMalloc. */
@@ -175,9 +176,14 @@ typedef struct {
     double sum_ms_total;      /* their summed device time, ms (JEFI_FLAG_STATS)     */
     int32_t n_split;          /* source splits per observation tile                */
     int32_t precision;
+    int32_t device_status;    /* first error a kernel reported (0 = none), sticky  */
+    int32_t staged_band;      /* FP32 sum kernel: history rows staged per cell by
+                                 TMA, or 0 for the direct-gather kernel            */
 } jefi_info;
 
-/* Fills *out; with JEFI_FLAG_STATS it first waits for the timed launches. */
+/* Fills *out (waits for the handle's outstanding work).  Kernel-side errors
+ * (a bounded wait that expired, a failed internal check) are reported in
+ * device_status; calls with host outputs also return them directly. */
 int jefi_get_info(jefi_handle h, jefi_info* out);
 
 /* Zeroes the fall-back counter and the kernel timing totals. */

@@ -43,6 +43,7 @@ JEFI_FP32_COMP = 2
 JEFI_DERIV_BACKWARD = 0
 JEFI_DERIV_SUPPLIED = 1
 JEFI_FLAG_STATS = 1
+JEFI_FLAG_DIRECT_GATHER = 2
 
 PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 
@@ -80,7 +81,8 @@ class jefi_info(ctypes.Structure):
                 ("pairs_per_eval", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("slot_fallbacks", ctypes.c_int64),
                 ("sum_launches", ctypes.c_int64), ("sum_ms_total", ctypes.c_double),
-                ("n_split", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("n_split", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("device_status", ctypes.c_int32), ("staged_band", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

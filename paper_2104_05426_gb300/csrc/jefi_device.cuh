@@ -1,0 +1,99 @@
+// jefi_device.cuh -- device helpers shared by the libjefi kernels: the exact
+// FP64 cell-centre and squared-distance rules, the threshold search, the FP32
+// slot candidate, compensated addition and the per-pair FP32 accumulation of
+// Eqs. E-1 and B-1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jefi {
+namespace dev {
+
+static constexpr unsigned kFull = 0xffffffffu;
+static constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: rd(u + M) has floor(u) in its low bits
+static constexpr int kMagicBits = 0x4B400000;
+
+// Cell centre x_i = lo + (i + 0.5) d, product then sum, each rounded.
+static __device__ __forceinline__ double cell_center(double lo, double d, int i) {
+    return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), d));
+}
+
+// Spec squared distance (Dx*Dx + Dy*Dy) + Dz*Dz, every operation rounded.
+static __device__ __forceinline__ double spec_s64(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Table index whose threshold interval (theta[i+1], theta[i]] holds S.
+// Thresholds are non-increasing; the exact slot always lies strictly
+// inside the table, so both walks stop there.
+static __device__ __forceinline__ int theta_search(const double* th, int K, int i, double S) {
+    i = i < 0 ? 0 : (i > K - 1 ? K - 1 : i);
+    while (i > 0 && S > th[i]) --i;
+    while (i < K - 1 && S <= th[i + 1]) ++i;
+    return i;
+}
+
+// Exact slot of one pair from scratch in FP64 (the rare undecided case of
+// the FP32 kernel).  Returns the table index.
+static __device__ __noinline__ int slot_fallback_f32(const double* obs_xyz, int slot, double lox,
+                                              double loy, double loz, double dx_, double dy_,
+                                              double dz_, int ix, int iy, int iz,
+                                              const double* th, int K, int guess,
+                                              unsigned long long* counter) {
+    const double xo = obs_xyz[3 * slot + 0];
+    const double yo = obs_xyz[3 * slot + 1];
+    const double zo = obs_xyz[3 * slot + 2];
+    const double S = spec_s64(__dsub_rn(xo, cell_center(lox, dx_, ix)),
+                              __dsub_rn(yo, cell_center(loy, dy_, iy)),
+                              __dsub_rn(zo, cell_center(loz, dz_, iz)));
+    if (counter) atomicAdd(counter, 1ull);
+    return theta_search(th, K, guess, S);
+}
+
+static __device__ __forceinline__ unsigned candidate_index(float S, float ri, float K32, float A, int K) {
+    const float R = S * ri;
+    const float u = fmaf(-R, K32, A);
+    const int bits = __float_as_int(__fadd_rd(u, kMagic));
+    const unsigned idx = (unsigned)(bits - kMagicBits);
+    return min(idx, (unsigned)(K - 1));
+}
+
+static __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Accumulate one pair (FP32).  v0 = (c rho, J), v1 = (drho, dJ/c).
+static __device__ __forceinline__ void pair_f32(float dx, float dy, float dz, float ri, const float4& v0,
+                                         const float4& v1, float (&pe)[3], float (&pb)[3]) {
+    const float r2 = ri * ri;
+    const float r3 = r2 * ri;
+    const float q = fmaf(v1.x, r2, v0.x * r3);
+    pe[0] = fmaf(dx, q, pe[0]);
+    pe[1] = fmaf(dy, q, pe[1]);
+    pe[2] = fmaf(dz, q, pe[2]);
+    pe[0] = fmaf(-v1.y, ri, pe[0]);
+    pe[1] = fmaf(-v1.z, ri, pe[1]);
+    pe[2] = fmaf(-v1.w, ri, pe[2]);
+    const float vx = fmaf(v1.y, r2, v0.y * r3);
+    const float vy = fmaf(v1.z, r2, v0.z * r3);
+    const float vz = fmaf(v1.w, r2, v0.w * r3);
+    pb[0] = fmaf(vy, dz, pb[0]);
+    pb[1] = fmaf(vz, dx, pb[1]);
+    pb[2] = fmaf(vx, dy, pb[2]);
+    pb[0] = fmaf(-vz, dy, pb[0]);
+    pb[1] = fmaf(-vx, dz, pb[1]);
+    pb[2] = fmaf(-vy, dx, pb[2]);
+}
+
+struct ThreadCtx {
+    int slot;
+    int rlo[3], rhi[3];   // screening index ranges
+};
+
+}  // namespace dev
+
+}  // namespace jefi

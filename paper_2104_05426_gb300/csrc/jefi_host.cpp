@@ -5,7 +5,9 @@
 // operation exactly as written (no fused multiply-add).
 #include "jefi.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cfloat>
@@ -141,9 +143,13 @@ AxisInfo axis_info(double xo, double lo, double d, int64_t nlim, int64_t npad, d
     if (first > last) {
         r.near_out_sq = r.near_sq;
     } else {
+        // nearest real index on each side of the screening range (the range
+        // may lie partly or wholly outside [0, nlim))
         r.near_out_sq = INFINITY;
-        if (first - 1 >= 0 && first - 1 < nlim) r.near_out_sq = std::min(r.near_out_sq, sq(first - 1));
-        if (last + 1 < nlim) r.near_out_sq = std::min(r.near_out_sq, sq(last + 1));
+        const int64_t left = std::min(first - 1, nlim - 1);
+        const int64_t right = std::max<int64_t>(last + 1, 0);
+        if (left >= 0) r.near_out_sq = std::min(r.near_out_sq, sq(left));
+        if (right < nlim) r.near_out_sq = std::min(r.near_out_sq, sq(right));
     }
     return r;
 }
@@ -178,6 +184,41 @@ uint64_t morton(const double* p, const double* lo, const double* hi) {
 }
 
 bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// True when every observation coordinate, every (padded) source centre and the
+// source spacing are integer multiples of one power of two q, small enough that
+// the FP32 kernel's squared-distance chain (anchor offsets, brick offsets,
+// differences, squares and their sums) is exact: then S32 == S64 for every pair.
+bool exact_lattice(const std::vector<double>& obs_xyz, const jefi_grid& src, const int64_t* npad) {
+    std::vector<double> vals(obs_xyz);
+    double lo[3], hi[3], olo[3] = {INFINITY, INFINITY, INFINITY}, ohi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (size_t i = 0; i < obs_xyz.size(); ++i) {
+        olo[i % 3] = std::min(olo[i % 3], obs_xyz[i]);
+        ohi[i % 3] = std::max(ohi[i % 3], obs_xyz[i]);
+    }
+    for (int a = 0; a < 3; ++a) {
+        vals.push_back(src.d[a]);
+        for (int64_t j = 0; j < npad[a]; ++j) vals.push_back(center(src.lo[a], src.d[a], j));
+        lo[a] = center(src.lo[a], src.d[a], 0);
+        hi[a] = center(src.lo[a], src.d[a], npad[a] - 1);
+    }
+    int e = -40;
+    for (; e <= 60; ++e) {
+        bool ok = true;
+        for (double v : vals) {
+            const double w = std::ldexp(v, e);
+            if (w != std::floor(w) || std::fabs(w) >= 1048576.0) { ok = false; break; }
+        }
+        if (ok) break;
+    }
+    if (e > 60) return false;
+    // largest |D| along any axis, in units of q; three squares must fit 24 bits
+    double m = 0;
+    for (int a = 0; a < 3; ++a)
+        m = std::max(m, std::max(std::fabs(ohi[a] - lo[a]), std::fabs(hi[a] - olo[a])));
+    const double M = std::ldexp(m, e);
+    return 3.0 * M * M < 16777216.0;
+}
 
 }  // namespace
 
@@ -221,6 +262,16 @@ struct jefi_problem {
     std::vector<float4> h_tab;
     std::vector<double> h_theta;
     std::vector<TimeParams> h_times;
+    // staged FP32 kernel (0 = direct-gather kernel)
+    int32_t band = 0;
+    int32_t mirror = 0;              // M: mirrored ring slots
+    bool exact = false;              // lattice geometry: S32 == S64
+    double g_bias = 0;               // bound on the FP32 candidate error (slots)
+    float* tile_box = nullptr;
+    float2* tab2 = nullptr;
+    std::vector<float2> h_tab2;
+    alignas(64) CUtensorMap tmap;
+    int32_t* status = nullptr;
     // statistics
     int64_t launches = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -267,7 +318,7 @@ void release_all(jefi_problem* h) {
 }
 
 int64_t phys_slot(const jefi_problem* h, int64_t k) {
-    if (k < 0 || k > h->n_latest || k < h->n_latest - h->H + 1) return h->H;  // zero slot
+    if (k < 0 || k > h->n_latest || k < h->n_latest - h->H + 1) return h->H + h->mirror;  // zero slot
     return k % h->H;
 }
 
@@ -319,11 +370,61 @@ void build_tables(jefi_problem* h, int ti, double t) {
         std::memcpy(&psf, &ps, 4);
         tab[i] = make_float4(hi, lo, psf, 0.f);
     }
+    if (h->band > 0) {
+        // staged kernel: (T_hi, T_lo) of Theta_k for k = k0 - guard ... k0 + K + guard - 1
+        const int KT = K + 2 * kTabGuard;
+        float2* t2 = h->h_tab2.data() + (size_t)ti * KT;
+        for (int e = 0; e < KT; ++e) {
+            const int i = e - kTabGuard;
+            if (i < 0 || i >= K) {
+                t2[e] = make_float2(-INFINITY, INFINITY);   // never reached; undecided if it were
+                continue;
+            }
+            const double th_k = th[i];
+            float thi, tlo;
+            if (th_k < 0) thi = tlo = -INFINITY;
+            else if (std::isinf(th_k)) thi = tlo = INFINITY;
+            else if (h->exact) thi = tlo = round_down_f32(th_k);
+            else {
+                thi = round_down_f32(th_k - err(th_k));
+                tlo = round_up_f32(th_k + err(th_k));
+            }
+            t2[e] = make_float2(thi, tlo);
+        }
+    }
     TimeParams tp;
-    tp.A = (float)(T / dt - (double)k0);
+    const double A = T / dt - (double)k0;
+    tp.A = (float)A;
+    const double w_max = std::sqrt(h->pad.s_max) / (c * dt);
+    tp.Ag = (float)(A + h->g_bias + 8 * std::ldexp(1.0, -53) * (std::fabs(T / dt) + w_max + 1));
+    // Before the ring wraps, pairs may need slots < 0 (sources not yet on):
+    // the band may then start below 0 and read zeros there.  Once slices have
+    // been evicted, no valid pair needs a slot older than the oldest resident.
+    const int64_t oldest = h->n_latest - h->H + 1;
+    const int64_t oldest_rel = oldest > 0 ? oldest - k0 : (int64_t)(INT32_MIN / 2);
+    tp.oldest_rel = (int32_t)std::max<int64_t>(std::min<int64_t>(oldest_rel, INT32_MAX / 2), INT32_MIN / 2);
     tp.pad = 0;
     tp.k0 = k0;
     h->h_times[ti] = tp;
+}
+
+// TMA descriptor over the FP32 ring [cells][Hp][8]: box = 8 channels x band
+// slots x one brick of 64 cells.
+int make_tensor_map(jefi_problem* h) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess)
+        return JEFI_ECUDA;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    const cuuint64_t dims[3] = {8, (cuuint64_t)h->Hp, (cuuint64_t)h->n_bricks * kBrickCells};
+    const cuuint64_t strides[2] = {8 * sizeof(float), (cuuint64_t)h->Hp * 8 * sizeof(float)};
+    const cuuint32_t box[3] = {8, (cuuint32_t)h->band, kBrickCells};
+    const cuuint32_t elem[3] = {1, 1, 1};
+    const CUresult r = encode(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ring, dims, strides, box,
+                              elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? JEFI_OK : JEFI_ECUDA;
 }
 
 int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B, cudaStream_t s,
@@ -336,6 +437,9 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
                               cudaMemcpyHostToDevice, s));
     JEFI_CUDA(cudaMemcpyAsync(h->times, h->h_times.data(), sizeof(TimeParams) * n_t,
                               cudaMemcpyHostToDevice, s));
+    if (h->band > 0)
+        JEFI_CUDA(cudaMemcpyAsync(h->tab2, h->h_tab2.data(),
+                                  sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
     SumParams p{};
     p.nbx = h->nbx; p.nby = h->nby; p.nbz = h->nbz; p.n_bricks = h->n_bricks;
     p.npx = h->npx; p.npy = h->npy; p.npz = h->npz;
@@ -350,7 +454,15 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
     p.obs_scr = h->obs_scr;
     p.ring = h->ring;
     p.Hp = h->Hp;
-    p.zero_slot = h->H;
+    p.zero_slot = h->H + h->mirror;
+    p.H = h->H;
+    p.status = h->status;
+    p.tab2 = h->tab2;
+    p.tile_box = h->tile_box;
+    for (int a = 0; a < 3; ++a) {
+        p.n_src_axis[a] = h->src.n[a];
+        p.nfull[a] = h->src.n[a] / kBrick;
+    }
     p.tab32 = h->tab32;
     p.theta = h->theta;
     p.times = h->times;
@@ -362,7 +474,7 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
     p.partials = h->partials;
     p.fallbacks = h->fallbacks;
     p.debug_slots = debug_slots;
-    if (sum_smem_bytes(p) > 200 * 1024) return JEFI_EUNSUPPORTED;
+    if (h->band == 0 && sum_smem_bytes(p) > 200 * 1024) return JEFI_EUNSUPPORTED;
 
     const bool timed = (h->prm.flags & JEFI_FLAG_STATS) != 0 && !debug_slots;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -376,8 +488,19 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
         }
         JEFI_CUDA(cudaEventRecord(ev.first, s));
     }
-    cudaError_t e = h->fp64 ? launch_sum_f64(p, s)
-                            : launch_sum_f32(p, h->prm.precision == JEFI_FP32_COMP, s);
+    cudaError_t e;
+    if (h->fp64) {
+        e = launch_sum_f64(p, s);
+    } else if (h->band > 0) {
+        StagedConfig sc;
+        sc.band = h->band;
+        sc.exact = h->exact;
+        sc.compensated = h->prm.precision == JEFI_FP32_COMP;
+        sc.tensor_map = &h->tmap;
+        e = launch_sum_f32_staged(p, sc, s);
+    } else {
+        e = launch_sum_f32(p, h->prm.precision == JEFI_FP32_COMP, s);
+    }
     if (e != cudaSuccess) return JEFI_ECUDA;
     h->launches++;
     if (ev.first) {
@@ -481,7 +604,6 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
     h->src = *src;
     h->fp64 = p->precision == JEFI_FP64;
     h->H = p->history_slots;
-    h->Hp = h->H + kZeroPadSlots;
     for (int a = 0; a < 3; ++a) h->screen[a] = p->screen[a] < 0 ? src->d[a] / 2 : p->screen[a];
     h->n_src = (int64_t)src->n[0] * src->n[1] * src->n[2];
     h->n_obs = n_obs;
@@ -493,7 +615,7 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
     h->npz = 4 * h->nbz;
     const int64_t n_bricks = (int64_t)h->nbx * h->nby * h->nbz;
     const int64_t n_cells = n_bricks * kBrickCells;
-    if (n_bricks > INT32_MAX / 2 || (double)n_cells * h->Hp > 4e11) {
+    if (n_bricks > INT32_MAX / 2 || (double)n_cells * (h->H + 64.0) > 4e11) {
         delete h;
         return JEFI_EUNSUPPORTED;
     }
@@ -602,7 +724,10 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
     }
 
     // ---------------------------------------------------------------- FP32 error model
-    {
+    h->exact = exact_lattice(slot_xyz, *src, npad);
+    if (h->exact) {
+        h->err_rel = h->err_lin = h->err_abs = 0.0;   // S32 == S64 exactly
+    } else {
         const double u = std::ldexp(1.0, -24);
         double G2 = 0;
         for (int a = 0; a < 3; ++a) {
@@ -637,6 +762,60 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
         if (h->n_split < 1) h->n_split = 1;
     }
 
+    // ---------------------------------------------------------------- staged FP32 kernel
+    // The TMA-staged kernel needs every (tile, brick) slot band to fit one of
+    // the compiled band heights, and a candidate bias g with 2g < 1.
+    std::vector<float> tile_box((size_t)h->n_tiles * 6);
+    if (!h->fp64 && h->any_pairs && !(p->flags & JEFI_FLAG_DIRECT_GATHER)) {
+        double diag_max = 0;
+        for (int64_t tile = 0; tile < h->n_tiles; ++tile) {
+            double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+            const double* anchor = &slot_xyz[3 * tile * kTileThreads];
+            for (int tid = 0; tid < kTileThreads; ++tid) {
+                const double* x = &slot_xyz[3 * (tile * kTileThreads + tid)];
+                for (int a = 0; a < 3; ++a) {
+                    mn[a] = std::min(mn[a], x[a] - anchor[a]);
+                    mx[a] = std::max(mx[a], x[a] - anchor[a]);
+                }
+            }
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                tile_box[tile * 6 + a] = round_down_f32(mn[a]);
+                tile_box[tile * 6 + 3 + a] = round_up_f32(mx[a]);
+                d2 += (mx[a] - mn[a]) * (mx[a] - mn[a]);
+            }
+            diag_max = std::max(diag_max, std::sqrt(d2));
+        }
+        double db2 = 0;
+        for (int a = 0; a < 3; ++a) db2 += 9.0 * src->d[a] * src->d[a];
+        const double Kd = 1.0 / (p->c * p->dt);
+        const double need = std::ceil((diag_max + std::sqrt(db2)) * Kd * (1 + 1e-4) + 1e-3) + 7;
+        const int bands[4] = {16, 24, 32, 48};
+        int band = 0;
+        for (int b : bands)
+            if (need <= b) { band = b; break; }
+        // candidate bias: bound on |floor argument in FP32 - FP64 rule| (slots),
+        // without the |T/dt| term that each evaluation adds
+        const double u = std::ldexp(1.0, -24);
+        const double eps_rsqrt = std::ldexp(1.0, -22);   // measured max 2^-22.93 over all normals
+        const double eps_S = h->exact ? 0.0
+                                      : h->err_rel + h->err_lin / std::sqrt(h->pad.s_min) + h->err_abs / h->pad.s_min;
+        const double w_max = std::sqrt(h->pad.s_max) * Kd;
+        const double A_max = h->K + 2.0;
+        h->g_bias = 2.0 * (u * (2 * A_max + 2) + w_max * (eps_S / 2 + eps_rsqrt + 4 * u) +
+                           u * (A_max + w_max + 2));
+        if (band > 0 && 2 * (h->g_bias + 1e-3) < 1.0) {
+            SumParams probe{};
+            probe.K = h->K;
+            probe.nbx = h->nbx;
+            probe.nby = h->nby;
+            probe.nbz = h->nbz;
+            if (staged_smem_bytes(probe, band) <= 220 * 1024) h->band = band;
+        }
+    }
+    h->mirror = h->band;
+    h->Hp = h->H + h->mirror + kZeroPadSlots;
+
     // ---------------------------------------------------------------- device buffers
     cudaStream_t s = (cudaStream_t)stream;
     const size_t esz = h->fp64 ? sizeof(double) : sizeof(float);
@@ -653,8 +832,16 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
     h->theta = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * (h->K + 1));
     h->times = (TimeParams*)dev_alloc(h, sizeof(TimeParams) * kTimeChunk);
     h->fallbacks = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
+    h->status = (int32_t*)dev_alloc(h, sizeof(int32_t));
+    if (h->band > 0) {
+        h->tile_box = (float*)dev_alloc(h, sizeof(float) * tile_box.size());
+        h->tab2 = (float2*)dev_alloc(h, sizeof(float2) * kTimeChunk * (h->K + 2 * kTabGuard));
+        if (!h->tile_box || !h->tab2) h->status = nullptr;
+        h->h_tab2.resize((size_t)kTimeChunk * (h->K + 2 * kTabGuard));
+    }
     if (!h->ring || !h->obs_xyz || !h->obs_scr || !h->d_inv_perm || !h->prev || !h->stage_in ||
-        !h->partials || !h->out_stage || !h->tab32 || !h->theta || !h->times || !h->fallbacks) {
+        !h->partials || !h->out_stage || !h->tab32 || !h->theta || !h->times || !h->fallbacks ||
+        !h->status) {
         release_all(h);
         delete h;
         return JEFI_ENOMEM;
@@ -666,6 +853,10 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->prev, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fallbacks, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess && h->band > 0)
+        e = cudaMemcpyAsync(h->tile_box, tile_box.data(), sizeof(float) * tile_box.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h->band > 0 && make_tensor_map(h) != JEFI_OK) e = cudaErrorInvalidValue;
     if (e == cudaSuccess && !slot_xyz.empty())
         e = cudaMemcpyAsync(h->obs_xyz, slot_xyz.data(), sizeof(double) * slot_xyz.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !scr.empty())
@@ -714,6 +905,7 @@ int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const d
     p.n_src = n;
     p.Hp = h->Hp;
     p.slot = (int32_t)(next % h->H);
+    p.mirror_slot = p.slot < h->mirror ? p.slot + h->H : -1;
     p.supplied = supplied;
     p.fp64 = h->fp64;
     p.c = h->prm.c;
@@ -756,7 +948,10 @@ static int eval_impl(jefi_handle h, int32_t n_t, const double* t, double* E, dou
         if (!on_device) {
             JEFI_CUDA(cudaMemcpyAsync(E + base * per_t, Ed, sizeof(double) * per_t * m, cudaMemcpyDeviceToHost, s));
             JEFI_CUDA(cudaMemcpyAsync(B + base * per_t, Bd, sizeof(double) * per_t * m, cudaMemcpyDeviceToHost, s));
+            int32_t st = 0;
+            JEFI_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, s));
             JEFI_CUDA(cudaStreamSynchronize(s));
+            if (st != 0) return st;
         }
     }
     return JEFI_OK;
@@ -880,6 +1075,10 @@ int jefi_get_info(jefi_handle h, jefi_info* out) {
     out->sum_ms_total = h->sum_ms;
     out->n_split = h->n_split;
     out->precision = h->prm.precision;
+    int32_t st = 0;
+    JEFI_CUDA(cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+    out->device_status = st;
+    out->staged_band = h->band;
     return JEFI_OK;
 }
 

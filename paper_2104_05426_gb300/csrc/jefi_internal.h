@@ -2,12 +2,14 @@
 //
 // Device data layout (all owned by one problem handle):
 //
-//   ring      [cell][Hp][8]  FP32 or FP64, Hp = H + 1.  Cells are in brick
+//   ring      [cell][Hp][8]  FP32 or FP64, Hp = H + M + 1.  Cells are in brick
 //             order: brick b = (bz*nby + by)*nbx + bx covers the 4x4x4 source
 //             cells (4bx+i, 4by+j, 4bz+k); cell = b*64 + (k*16 + j*4 + i).
 //             Grid extents are padded up to whole bricks with cells whose
-//             channels stay zero.  Physical slot H is a permanent zero slot
-//             (sources before slice 0).  Slice n lives in slot n mod H.
+//             channels stay zero.  Slice n lives in slot n mod H; slots
+//             [H, H+M) mirror slots [0, M) so that any M consecutive slots are
+//             one contiguous TMA box; slot H+M is a permanent zero slot
+//             (sources before slice 0).  M = 0 unless the staged kernel is used.
 //             Channels: c*rho, Jx, Jy, Jz, drho/dt, dJx/dt/c, dJy/dt/c, dJz/dt/c.
 //             With these, per pair
 //               E' += D (ch0/R^3 + ch4/R^2) - ch5..7/R   ->  E = (k_e dV / c) E'
@@ -34,10 +36,14 @@ constexpr int kBrickCells = 64;
 constexpr int kZeroPadSlots = 1;    // the zero slot after the H ring slots
 
 struct TimeParams {
-    float A;        // fp32(T/dt - k0): candidate index = floor(A - R/(c dt))
+    float A;            // fp32(T/dt - k0): candidate index ~ floor(A - R/(c dt))
+    float Ag;           // A + g, g >= |error of the FP32 candidate|: floor(Ag - R K) in {n-k0, n-k0+1}
+    int32_t oldest_rel; // oldest resident slot - k0 (clamped to int32)
     int32_t pad;
-    int64_t k0;     // table origin slot
+    int64_t k0;         // table origin slot
 };
+
+constexpr int kTabGuard = 32;       // guard entries on each side of the staged kernel's table
 
 struct SumParams {
     // source geometry
@@ -53,7 +59,7 @@ struct SumParams {
     // history ring
     const void* ring;
     int32_t Hp;                     // slots per cell including the zero slot
-    int32_t zero_slot;              // == H
+    int32_t zero_slot;              // == H + M
     // per-time tables
     const float4* tab32;
     const double* theta;
@@ -66,8 +72,15 @@ struct SumParams {
     int32_t bricks_per_split;
     // outputs
     double* partials;
-    unsigned long long* fallbacks;  // warp-level slot fall-back counter
+    unsigned long long* fallbacks;  // pairs whose slot was recomputed in FP64
     int32_t* debug_slots;           // NULL, or [n_slots][n_cells] logical slot per pair
+    int32_t* status;                // device error word (0 = ok, else a jefi_status)
+    // staged kernel only
+    const float2* tab2;             // [n_t][K + 2 kTabGuard] {T_hi, T_lo} per candidate slot
+    const float* tile_box;          // [n_tiles][6] min xyz, max xyz of (x_o - anchor), fp32 outward
+    int32_t n_src_axis[3];          // real source cells per axis
+    int32_t nfull[3];               // whole bricks per axis (bricks past them hold padding cells)
+    int32_t H;                      // ring period (physical slot of slice n is n mod H)
 };
 
 struct PushParams {
@@ -78,6 +91,7 @@ struct PushParams {
     int32_t slot;                   // physical slot to write
     int32_t supplied;
     int32_t fp64;
+    int32_t mirror_slot;            // also write the slice here (the ring's mirror copy), or -1
     double c, inv_c, dt;
     const double* rho;
     const double* J;
@@ -96,7 +110,17 @@ struct ReduceParams {
     double* B;
 };
 
+struct StagedConfig {
+    int32_t band;                   // slot rows staged per cell (a compiled variant)
+    bool exact;                     // FP32 squared distances are exact (lattice geometry)
+    bool compensated;
+    const void* tensor_map;         // CUtensorMap over the FP32 ring
+};
+
 cudaError_t launch_push(const PushParams& p, cudaStream_t s);
+cudaError_t launch_sum_f32_staged(const SumParams& p, const StagedConfig& c, cudaStream_t s);
+size_t staged_smem_bytes(const SumParams& p, int band);
+bool staged_band_supported(int band);
 cudaError_t launch_sum_f32(const SumParams& p, bool compensated, cudaStream_t s);
 cudaError_t launch_sum_f64(const SumParams& p, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t s);

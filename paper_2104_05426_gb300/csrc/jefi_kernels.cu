@@ -19,97 +19,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "jefi_device.cuh"
 #include "jefi_internal.h"
 
 namespace jefi {
 
-namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-constexpr float kMagic = 12582912.0f;      // 1.5 * 2^23: rd(u + M) has floor(u) in its low bits
-constexpr int kMagicBits = 0x4B400000;
-
-// Cell centre x_i = lo + (i + 0.5) d, product then sum, each rounded.
-__device__ __forceinline__ double cell_center(double lo, double d, int i) {
-    return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), d));
-}
-
-// Spec squared distance (Dx*Dx + Dy*Dy) + Dz*Dz, every operation rounded.
-__device__ __forceinline__ double spec_s64(double dx, double dy, double dz) {
-    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-}
-
-// Table index whose threshold interval (theta[i+1], theta[i]] holds S.
-// Thresholds are non-increasing; the exact slot always lies strictly
-// inside the table, so both walks stop there.
-__device__ __forceinline__ int theta_search(const double* th, int K, int i, double S) {
-    i = i < 0 ? 0 : (i > K - 1 ? K - 1 : i);
-    while (i > 0 && S > th[i]) --i;
-    while (i < K - 1 && S <= th[i + 1]) ++i;
-    return i;
-}
-
-// Exact slot of one pair from scratch in FP64 (the rare undecided case of
-// the FP32 kernel).  Returns the table index.
-__device__ __noinline__ int slot_fallback_f32(const double* obs_xyz, int slot, double lox,
-                                              double loy, double loz, double dx_, double dy_,
-                                              double dz_, int ix, int iy, int iz,
-                                              const double* th, int K, int guess,
-                                              unsigned long long* counter) {
-    const double xo = obs_xyz[3 * slot + 0];
-    const double yo = obs_xyz[3 * slot + 1];
-    const double zo = obs_xyz[3 * slot + 2];
-    const double S = spec_s64(__dsub_rn(xo, cell_center(lox, dx_, ix)),
-                              __dsub_rn(yo, cell_center(loy, dy_, iy)),
-                              __dsub_rn(zo, cell_center(loz, dz_, iz)));
-    if (counter) atomicAdd(counter, 1ull);
-    return theta_search(th, K, guess, S);
-}
-
-__device__ __forceinline__ unsigned candidate_index(float S, float ri, float K32, float A, int K) {
-    const float R = S * ri;
-    const float u = fmaf(-R, K32, A);
-    const int bits = __float_as_int(__fadd_rd(u, kMagic));
-    const unsigned idx = (unsigned)(bits - kMagicBits);
-    return min(idx, (unsigned)(K - 1));
-}
-
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-    const float y = x - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
-
-// Accumulate one pair (FP32).  v0 = (c rho, J), v1 = (drho, dJ/c).
-__device__ __forceinline__ void pair_f32(float dx, float dy, float dz, float ri, const float4& v0,
-                                         const float4& v1, float (&pe)[3], float (&pb)[3]) {
-    const float r2 = ri * ri;
-    const float r3 = r2 * ri;
-    const float q = fmaf(v1.x, r2, v0.x * r3);
-    pe[0] = fmaf(dx, q, pe[0]);
-    pe[1] = fmaf(dy, q, pe[1]);
-    pe[2] = fmaf(dz, q, pe[2]);
-    pe[0] = fmaf(-v1.y, ri, pe[0]);
-    pe[1] = fmaf(-v1.z, ri, pe[1]);
-    pe[2] = fmaf(-v1.w, ri, pe[2]);
-    const float vx = fmaf(v1.y, r2, v0.y * r3);
-    const float vy = fmaf(v1.z, r2, v0.z * r3);
-    const float vz = fmaf(v1.w, r2, v0.w * r3);
-    pb[0] = fmaf(vy, dz, pb[0]);
-    pb[1] = fmaf(vz, dx, pb[1]);
-    pb[2] = fmaf(vx, dy, pb[2]);
-    pb[0] = fmaf(-vz, dy, pb[0]);
-    pb[1] = fmaf(-vx, dz, pb[1]);
-    pb[2] = fmaf(-vy, dx, pb[2]);
-}
-
-struct ThreadCtx {
-    int slot;
-    int rlo[3], rhi[3];   // screening index ranges
-};
-
-}  // namespace
+using namespace dev;
 
 // ============================================================================ FP32
 // Shared memory: tab32[K] float4 | theta[K+1] double | D[nbx+nby+nbz] float
@@ -457,19 +372,23 @@ __global__ void push_kernel(const PushParams p) {
     }
     const double ch[8] = {__dmul_rn(p.c, rho), j0, j1, j2, dr, __ddiv_rn(dj0, p.c),
                           __ddiv_rn(dj1, p.c), __ddiv_rn(dj2, p.c)};
-    const size_t off = ((size_t)cell * p.Hp + p.slot) * 8;
-    if (p.fp64) {
-        double2* dst = reinterpret_cast<double2*>(static_cast<double*>(p.ring) + off);
-        dst[0] = make_double2(ch[0], ch[1]);
-        dst[1] = make_double2(ch[2], ch[3]);
-        dst[2] = make_double2(ch[4], ch[5]);
-        dst[3] = make_double2(ch[6], ch[7]);
-    } else {
-        float4* dst = reinterpret_cast<float4*>(static_cast<float*>(p.ring) + off);
-        dst[0] = make_float4(__double2float_rn(ch[0]), __double2float_rn(ch[1]),
-                             __double2float_rn(ch[2]), __double2float_rn(ch[3]));
-        dst[1] = make_float4(__double2float_rn(ch[4]), __double2float_rn(ch[5]),
-                             __double2float_rn(ch[6]), __double2float_rn(ch[7]));
+    const int n_copies = p.mirror_slot >= 0 ? 2 : 1;
+    for (int copy = 0; copy < n_copies; ++copy) {
+        const int slot = copy == 0 ? p.slot : p.mirror_slot;
+        const size_t off = ((size_t)cell * p.Hp + slot) * 8;
+        if (p.fp64) {
+            double2* dst = reinterpret_cast<double2*>(static_cast<double*>(p.ring) + off);
+            dst[0] = make_double2(ch[0], ch[1]);
+            dst[1] = make_double2(ch[2], ch[3]);
+            dst[2] = make_double2(ch[4], ch[5]);
+            dst[3] = make_double2(ch[6], ch[7]);
+        } else {
+            float4* dst = reinterpret_cast<float4*>(static_cast<float*>(p.ring) + off);
+            dst[0] = make_float4(__double2float_rn(ch[0]), __double2float_rn(ch[1]),
+                                 __double2float_rn(ch[2]), __double2float_rn(ch[3]));
+            dst[1] = make_float4(__double2float_rn(ch[4]), __double2float_rn(ch[5]),
+                                 __double2float_rn(ch[6]), __double2float_rn(ch[7]));
+        }
     }
 }
 

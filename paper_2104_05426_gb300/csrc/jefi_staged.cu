@@ -1,0 +1,430 @@
+// jefi_staged.cu -- FP32 retarded direct sum (Eqs. E-1, B-1, tr-1) with the
+// history band of every source brick staged in shared memory by TMA.
+//
+// One CTA = one tile of 256 observation points x a contiguous range of source
+// bricks.  For each brick one thread computes, from the tile's and the brick's
+// bounding boxes, the band of slots [lo, lo + BAND) that any pair of the two
+// can retard into, and one cp.async.bulk.tensor copies the 64 cells x BAND
+// slots x 8 channels of the ring into a shared-memory buffer (two buffers,
+// the next brick's copy overlaps the current brick's arithmetic; completion
+// through an mbarrier, waits bounded in time).
+//
+// Slot selection per pair, exact with respect to the FP64 rule of Eq. tr-1:
+//   k' = floor(A + g - R32/(c dt)), g bounding the FP32 error of the
+//   candidate, so that k' is n or n+1; one threshold entry (T_hi, T_lo) of
+//   Theta_k' (largest S64 whose slot is >= k') decides: S32 > T_lo -> n = k'-1,
+//   S32 <= T_hi -> n = k'.  On exact-lattice geometry S32 == S64 and
+//   T_hi == T_lo == Theta_k' rounded down, so every pair is decided without a
+//   branch.  Otherwise the rare pairs between T_hi and T_lo contribute nothing
+//   in the unrolled loop and are redone after the brick with their slot
+//   recomputed in FP64.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "jefi_device.cuh"
+#include "jefi_internal.h"
+
+namespace jefi {
+using namespace dev;
+
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // a bounded wait gives up after 2 s
+constexpr int kStatusTimeout = 6;                    // JEFI_ETIMEOUT
+constexpr int kStatusInternal = 7;                   // JEFI_EINTERNAL
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity; false if it has not completed
+// after kWaitLimitNs.
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
+    if (mbar_try_wait(a, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; it != 0; ++it) {
+        if (mbar_try_wait(a, parity)) return true;
+        if ((it & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+
+template <int BAND>
+struct Layout {
+    static constexpr uint32_t kRowBytes = 32;                          // 8 FP32 channels
+    static constexpr uint32_t kCellBytes = BAND * kRowBytes;
+    static constexpr uint32_t kBufBytes = kBrickCells * kCellBytes;
+    static constexpr uint32_t kCtrl = 2 * kBufBytes;                   // mbarriers, band origins
+    static constexpr uint32_t kTab = kCtrl + 64;                        // float2 table
+};
+
+}  // namespace
+
+template <int BAND, bool EXACT, bool DEBUG>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p, const int comp) {
+    using L = Layout<BAND>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int K = p.K;
+    const int KT = K + 2 * kTabGuard;
+    uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + L::kCtrl);
+    int* s_band = reinterpret_cast<int*>(smem + L::kCtrl + 16);
+    float2* s_tab = reinterpret_cast<float2*>(smem + L::kTab);
+    double* s_th = reinterpret_cast<double*>(smem + L::kTab + (size_t)KT * sizeof(float2));
+    float* s_D = reinterpret_cast<float*>(s_th + K + 1);
+
+    const int tile = blockIdx.x;
+    const int split = blockIdx.y;
+    const int ti = blockIdx.z;
+    const int tid = threadIdx.x;
+
+    const float2* g_tab = p.tab2 + (size_t)ti * KT;
+    for (int i = tid; i < KT; i += kTileThreads) s_tab[i] = g_tab[i];
+    const double* g_th = p.theta + (size_t)ti * (K + 1);
+    for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
+    const double* txyz = p.obs_xyz + (size_t)tile * kTileThreads * 3;
+    const double cox = txyz[0], coy = txyz[1], coz = txyz[2];
+    const int nbxy = p.nbx + p.nby;
+    for (int i = tid; i < nbxy + p.nbz; i += kTileThreads) {
+        const int a = i < p.nbx ? 0 : (i < nbxy ? 1 : 2);
+        const int b = a == 0 ? i : (a == 1 ? i - p.nbx : i - nbxy);
+        const double co = a == 0 ? cox : (a == 1 ? coy : coz);
+        s_D[i] = __double2float_rn(__dsub_rn(co, cell_center(p.lo[a], p.d[a], kBrick * b)));
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&s_mbar[0]), 1);
+        mbar_init(smem_u32(&s_mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    ThreadCtx ctx;
+    ctx.slot = tile * kTileThreads + tid;
+    const double xo = txyz[3 * tid + 0], yo = txyz[3 * tid + 1], zo = txyz[3 * tid + 2];
+    const float oox = __double2float_rn(__dsub_rn(xo, cox));
+    const float ooy = __double2float_rn(__dsub_rn(yo, coy));
+    const float ooz = __double2float_rn(__dsub_rn(zo, coz));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ctx.rlo[a] = p.obs_scr[(2 * a) * p.n_slots + ctx.slot];
+        ctx.rhi[a] = p.obs_scr[(2 * a + 1) * p.n_slots + ctx.slot];
+    }
+    const TimeParams tp = p.times[ti];
+    const float K32 = p.K32;
+    const float Ag = tp.Ag;
+    const float d32x = p.d32[0], d32y = p.d32[1], d32z = p.d32[2];
+    const size_t n_cells = (size_t)p.n_bricks * kBrickCells;
+    const uint32_t mbar_u32[2] = {smem_u32(&s_mbar[0]), smem_u32(&s_mbar[1])};
+    const uint32_t buf_u32[2] = {smem_u32(smem), smem_u32(smem + L::kBufBytes)};
+
+    // Producer (thread 0): slot band of (this tile, brick b) and its TMA copy.
+    float tbox[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) tbox[a] = tid == 0 ? p.tile_box[(size_t)tile * 6 + a] : 0.f;
+    auto issue = [&](int b, int bufi) {
+        const int bx = b % p.nbx;
+        const int rest = b / p.nbx;
+        const int by = rest % p.nby;
+        const int bz = rest / p.nby;
+        const float cb[3] = {-s_D[bx], -s_D[p.nbx + by], -s_D[nbxy + bz]};
+        const float dd[3] = {d32x, d32y, d32z};
+        float mn2 = 0.f, mx2 = 0.f, span = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // pair offsets D = x_o - x_s span [box_lo - (cb + 3d), box_hi - cb]
+            const float lo = tbox[a] - (cb[a] + 3.f * dd[a]);
+            const float hi = tbox[3 + a] - cb[a];
+            const float mn = lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
+            const float mx = fmaxf(fabsf(lo), fabsf(hi));
+            mn2 = fmaf(mn, mn, mn2);
+            mx2 = fmaf(mx, mx, mx2);
+            span += fabsf(cb[a]) + fabsf(tbox[a]) + fabsf(tbox[3 + a]) + 3.f * dd[a];
+        }
+        const float slack = 1e-5f * span;
+        const float rmin = fmaxf(sqrtf(mn2) * (1.f - 1e-5f) - slack, 0.f);
+        const float rmax = sqrtf(mx2) * (1.f + 1e-5f) + slack;
+        const int hi_rel = (int)floorf(tp.A - rmin * K32) + 2;
+        const int lo_rel = (int)floorf(tp.A - rmax * K32) - 2;
+        const int band_rel = max(lo_rel, tp.oldest_rel);
+        if (hi_rel - band_rel + 1 > BAND) atomicExch(p.status, kStatusInternal);
+        s_band[bufi] = band_rel;
+        const long long band_abs = tp.k0 + band_rel;
+        int y0;
+        if (band_abs >= 0)
+            y0 = (int)(band_abs % p.H);
+        else
+            y0 = band_abs < -(1ll << 30) ? -(1 << 30) : (int)band_abs;   // rows < 0 read as zero
+        // the buffer was last read through the generic proxy: order those
+        // reads before the async-proxy write
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(mbar_u32[bufi], L::kBufBytes);
+        tma_load_3d(buf_u32[bufi], &tmap, 0, y0, b * kBrickCells, mbar_u32[bufi]);
+    };
+
+    float se[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
+    float ce[3] = {0.f, 0.f, 0.f}, cb[3] = {0.f, 0.f, 0.f};
+    const int b_begin = split * p.bricks_per_split;
+    const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
+    const uint32_t tbase = L::kTab + (uint32_t)(kTabGuard - kMagicBits) * 8u;
+
+    if (tid == 0 && b_begin < b_end) issue(b_begin, 0);
+    int aborted_at = -1;
+    for (int b = b_begin; b < b_end; ++b) {
+        const int it = b - b_begin;
+        const int buf = it & 1;
+        if (tid == 0 && b + 1 < b_end) issue(b + 1, buf ^ 1);
+        const bool ready = mbar_wait_bounded(mbar_u32[buf], (it >> 1) & 1);
+        if (ready) {
+            const int bx = b % p.nbx;
+            const int rest = b / p.nbx;
+            const int by = rest % p.nby;
+            const int bz = rest / p.nby;
+            const int band_rel = s_band[buf];
+            const float Px = oox + s_D[bx];
+            const float Py = ooy + s_D[p.nbx + by];
+            const float Pz = ooz + s_D[nbxy + bz];
+            const uint32_t gbase = (uint32_t)buf * L::kBufBytes -
+                                   (uint32_t)(kMagicBits + band_rel) * L::kRowBytes;
+            const bool full = (bx < p.nfull[0]) & (by < p.nfull[1]) & (bz < p.nfull[2]);
+            const bool near = (ctx.rlo[0] <= kBrick * bx + 3) & (ctx.rhi[0] >= kBrick * bx) &
+                              (ctx.rlo[1] <= kBrick * by + 3) & (ctx.rhi[1] >= kBrick * by) &
+                              (ctx.rlo[2] <= kBrick * bz + 3) & (ctx.rhi[2] >= kBrick * bz);
+            float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
+            if (full && !__any_sync(kFull, near)) {
+                float ddx[4], ddy[4], ddz[4], sqx[4], sqy[4], sqz[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    ddx[i] = fmaf(-(float)i, d32x, Px);
+                    ddy[i] = fmaf(-(float)i, d32y, Py);
+                    ddz[i] = fmaf(-(float)i, d32z, Pz);
+                    sqx[i] = __fmul_rn(ddx[i], ddx[i]);
+                    sqy[i] = __fmul_rn(ddy[i], ddy[i]);
+                    sqz[i] = __fmul_rn(ddz[i], ddz[i]);
+                }
+                uint32_t m_lo = 0u, m_hi = 0u;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float syz = __fadd_rn(sqy[j], sqz[k]);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int cl = k * 16 + j * 4 + i;
+                            const float S = __fadd_rn(sqx[i], syz);
+                            float ri = rsqrtf(S);
+                            const float u = fmaf(-(S * ri), K32, Ag);
+                            const uint32_t bits = __float_as_uint(__fadd_rd(u, kMagic));
+                            const float2 th = *reinterpret_cast<const float2*>(smem + (tbase + bits * 8u));
+                            const bool lower = S > th.y;
+                            if (!EXACT) {
+                                if (!(S <= th.x) && !lower) {   // undecided: redo after the brick
+                                    if (cl < 32) m_lo |= 1u << cl; else m_hi |= 1u << (cl - 32);
+                                    ri = 0.f;
+                                }
+                            }
+                            if (DEBUG) {
+                                p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
+                                    (int)(tp.k0 + (int)(bits - kMagicBits) - (lower ? 1 : 0));
+                            }
+                            const uint32_t off = gbase + bits * L::kRowBytes +
+                                                 (uint32_t)cl * L::kCellBytes - (lower ? L::kRowBytes : 0u);
+                            const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
+                            const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                            pair_f32(ddx[i], ddy[j], ddz[k], ri, v0, v1, pe, pb);
+                        }
+                    }
+                }
+                if (!EXACT) {
+                    if (__any_sync(kFull, (m_lo | m_hi) != 0u)) {
+                        uint64_t mask = ((uint64_t)m_hi << 32) | m_lo;
+                        while (mask) {
+                            const int cl = __ffsll((long long)mask) - 1;
+                            mask &= mask - 1;
+                            const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+                            const float dx = fmaf(-(float)i, d32x, Px);
+                            const float dy = fmaf(-(float)j, d32y, Py);
+                            const float dz = fmaf(-(float)k, d32z, Pz);
+                            const float S = __fadd_rn(__fmul_rn(dx, dx),
+                                                      __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+                            const float ri = rsqrtf(S);
+                            const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
+                            const int idx = slot_fallback_f32(
+                                p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
+                                kBrick * bx + i, kBrick * by + j, kBrick * bz + k, s_th, K,
+                                (int)(bits - kMagicBits), p.fallbacks);
+                            int row = idx - band_rel;
+                            if (row < 0 || row >= BAND) {
+                                atomicExch(p.status, kStatusInternal);
+                                row = row < 0 ? 0 : BAND - 1;
+                            }
+                            if (DEBUG) {
+                                p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
+                                    (int)(tp.k0 + idx);
+                            }
+                            const uint32_t off = (uint32_t)buf * L::kBufBytes + (uint32_t)cl * L::kCellBytes +
+                                                 (uint32_t)row * L::kRowBytes;
+                            const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
+                            const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                            pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+                        }
+                    }
+                }
+            } else {
+                // Bricks with padding cells or screened pairs: rolled loop with
+                // per-pair checks and clamped indices.
+                for (int cl = 0; cl < kBrickCells; ++cl) {
+                    const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+                    const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
+                    const bool real = (ix < p.n_src_axis[0]) & (iy < p.n_src_axis[1]) & (iz < p.n_src_axis[2]);
+                    const bool scr = (ix >= ctx.rlo[0]) & (ix <= ctx.rhi[0]) & (iy >= ctx.rlo[1]) &
+                                     (iy <= ctx.rhi[1]) & (iz >= ctx.rlo[2]) & (iz <= ctx.rhi[2]);
+                    const bool use = real & !scr;
+                    const float dx = fmaf(-(float)i, d32x, Px);
+                    const float dy = fmaf(-(float)j, d32y, Py);
+                    const float dz = fmaf(-(float)k, d32z, Pz);
+                    const float S = __fadd_rn(__fmul_rn(dx, dx),
+                                              __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+                    float ri = rsqrtf(S);
+                    const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
+                    const uint32_t tix = min(bits - (uint32_t)kMagicBits + (uint32_t)kTabGuard, (uint32_t)(KT - 1));
+                    const float2 th = s_tab[tix];
+                    const bool lower = S > th.y;
+                    int idx = (int)tix - kTabGuard - (lower ? 1 : 0);
+                    if (use && !(S <= th.x) && !lower) {
+                        idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
+                                                p.d[1], p.d[2], ix, iy, iz, s_th, K, idx, p.fallbacks);
+                    }
+                    int row = idx - band_rel;
+                    if (!use) {
+                        ri = 0.f;
+                        row = 0;
+                    } else if (row < 0 || row >= BAND) {
+                        atomicExch(p.status, kStatusInternal);
+                        row = row < 0 ? 0 : BAND - 1;
+                    }
+                    if (DEBUG) {
+                        p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
+                            scr ? INT32_MIN : (int)(tp.k0 + idx);
+                    }
+                    const uint32_t off = (uint32_t)buf * L::kBufBytes + (uint32_t)cl * L::kCellBytes +
+                                         (uint32_t)row * L::kRowBytes;
+                    const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
+                    const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                    pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (comp) {
+                    kahan_add(se[a], ce[a], pe[a]);
+                    kahan_add(sb[a], cb[a], pb[a]);
+                } else {
+                    se[a] += pe[a];
+                    sb[a] += pb[a];
+                }
+            }
+        }
+        // every thread is done with this buffer before it is refilled
+        if (__syncthreads_or(!ready)) {
+            aborted_at = it;
+            break;
+        }
+    }
+    if (aborted_at >= 0) {
+        // a copy did not complete in time: report, then wait (bounded) for
+        // the copies still in flight before the shared memory goes away
+        if (tid == 0) {
+            atomicExch(p.status, kStatusTimeout);
+            mbar_wait_bounded(mbar_u32[aborted_at & 1], (aborted_at >> 1) & 1);
+            if (b_begin + aborted_at + 1 < b_end)
+                mbar_wait_bounded(mbar_u32[(aborted_at + 1) & 1], ((aborted_at + 1) >> 1) & 1);
+        }
+        __syncthreads();
+    }
+
+    double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        out[(size_t)a * p.n_slots] = comp ? (double)se[a] - (double)ce[a] : (double)se[a];
+        out[(size_t)(3 + a) * p.n_slots] = comp ? (double)sb[a] - (double)cb[a] : (double)sb[a];
+    }
+}
+
+bool staged_band_supported(int band) { return band == 16 || band == 24 || band == 32 || band == 48; }
+
+size_t staged_smem_bytes(const SumParams& p, int band) {
+    const size_t buf = (size_t)kBrickCells * band * 32;
+    size_t b = 2 * buf + 64;
+    b += (size_t)(p.K + 2 * kTabGuard) * sizeof(float2);
+    b += (size_t)(p.K + 1) * sizeof(double);
+    b += (size_t)(p.nbx + p.nby + p.nbz) * sizeof(float);
+    return b;
+}
+
+template <int BAND, bool EXACT, bool DEBUG>
+static cudaError_t launch_variant(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
+    const dim3 grid(p.n_tiles, p.n_split, p.n_t);
+    const size_t smem = staged_smem_bytes(p, BAND);
+    auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tensor_map);
+    k<<<grid, kTileThreads, smem, s>>>(*tm, p, c.compensated ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int BAND>
+static cudaError_t launch_band(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
+    const bool dbg = p.debug_slots != nullptr;
+    if (c.exact) return dbg ? launch_variant<BAND, true, true>(p, c, s) : launch_variant<BAND, true, false>(p, c, s);
+    return dbg ? launch_variant<BAND, false, true>(p, c, s) : launch_variant<BAND, false, false>(p, c, s);
+}
+
+cudaError_t launch_sum_f32_staged(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
+    switch (c.band) {
+        case 16: return launch_band<16>(p, c, s);
+        case 24: return launch_band<24>(p, c, s);
+        case 32: return launch_band<32>(p, c, s);
+        case 48: return launch_band<48>(p, c, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace jefi

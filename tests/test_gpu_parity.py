@@ -41,6 +41,10 @@ def test_c1_fields_match_oracle(gpu, c1, prec, tol):
     for i in range(len(p.times)):
         assert rel_l2(E[i], ref[i][0]) <= tol, (prec, i, rel_l2(E[i], ref[i][0]))
         assert rel_l2(B[i], ref[i][1]) <= tol, (prec, i, rel_l2(B[i], ref[i][1]))
+    info = jefi.jefi_get_info(h)
+    assert info["device_status"] == 0
+    if prec != "fp64":
+        assert info["staged_band"] > 0          # 16^3 lattice grids take the staged kernel
     jefi.jefi_destroy(h)
 
 
@@ -110,6 +114,7 @@ def test_ragged_grids_with_screening(gpu, coincide):
             assert np.all(got[sc] == np.iinfo(np.int32).min)
             if coincide:
                 assert sc.sum() >= prob.n_obs       # every point screens its own cell
+        assert jefi.jefi_get_info(h)["device_status"] == 0
         jefi.jefi_destroy(h)
 
 
@@ -290,3 +295,51 @@ def test_c2_full_size_sampled(gpu):
     assert rel_l2(E32[0], E64[0]) <= FP32C_TOL and rel_l2(B32[0], B64[0]) <= FP32C_TOL
     jefi.jefi_destroy(h32)
     jefi.jefi_destroy(h64)
+
+
+@pytest.mark.parametrize("lattice", [True, False])
+def test_staged_kernel_matches_direct_gather(gpu, lattice):
+    """The TMA-staged FP32 kernel and the direct-gather FP32 kernel are two
+    implementations of the same sum: identical slots for every pair, fields
+    equal to FP32 rounding, both within tolerance of the oracle.  On an exact
+    lattice the staged kernel decides every slot without an FP64 fall-back."""
+    if lattice:
+        src = Grid.cube(16, -1.0, 1.0)
+        obs = Grid.box((16, 16, 8), (1.5, -1.0, -0.5), (3.5, 1.0, 0.5))
+        dt = 0.0625
+    else:
+        src = Grid((16, 16, 16), (-0.731, -0.683, -0.802), (0.0931, 0.0877, 0.1013))
+        obs = Grid((16, 16, 8), (1.113, -0.917, -0.419), (0.1207, 0.1133, 0.1049))
+        dt = 0.0517
+    blob = Blob(1.0, (0.25, 0.2, 0.3), (-0.2, 0.05, 0.0), (0.2, 0.1, -0.05))
+    H = 120
+    prob = Problem("st", src, obs, None, dt, H, H, [], MovingGaussians([blob], noise=0.02, seed=3))
+    hist = history(prob)
+    handles = {}
+    for name, flags in (("staged", jefi.JEFI_FLAG_STATS),
+                        ("direct", jefi.JEFI_FLAG_STATS | jefi.JEFI_FLAG_DIRECT_GATHER)):
+        h = create(prob, "fp32c", flags=flags)
+        push_all(h, hist)
+        handles[name] = h
+    info_s = jefi.jefi_get_info(handles["staged"])
+    info_d = jefi.jefi_get_info(handles["direct"])
+    assert info_s["staged_band"] > 0 and info_d["staged_band"] == 0
+    lo, hi = jefi.jefi_valid_window(handles["staged"])
+    times = [hi - 0.4, hi - 0.02]
+    ref = oracle_fields(prob, hist, times)
+    out = {k: gpu_fields(h, times) for k, h in handles.items()}
+    for i, t in enumerate(times):
+        s_st = jefi.jefi_debug_slots(handles["staged"], t)
+        s_di = jefi.jefi_debug_slots(handles["direct"], t)
+        assert np.array_equal(s_st, s_di)
+        for k in out:
+            assert rel_l2(out[k][0][i], ref[i][0]) <= FP32C_TOL
+            assert rel_l2(out[k][1][i], ref[i][1]) <= FP32C_TOL
+        assert rel_l2(out["staged"][0][i], out["direct"][0][i]) <= 2e-6
+        assert rel_l2(out["staged"][1][i], out["direct"][1][i]) <= 2e-6
+    info_s = jefi.jefi_get_info(handles["staged"])
+    assert info_s["device_status"] == 0
+    if lattice:
+        assert info_s["slot_fallbacks"] == 0
+    for h in handles.values():
+        jefi.jefi_destroy(h)
