@@ -204,6 +204,41 @@ int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream);
 void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double t, double t0,
                           double c, double dt, int64_t* out);
 
+/*
+ * One-shot FP64 evaluation that allocates no device memory.  The paper has
+ * no counterpart: it is for callers that cannot allocate device memory when
+ * they need fields -- a host application whose own pool allocator owns the
+ * device memory and forbids other cudaMalloc calls, or a time-critical loop
+ * where cudaMalloc/cudaFree would synchronise the device.
+ *
+ * Computes the same sum as jefi_eval_fields with precision JEFI_FP64 and
+ * backward differences, for one time t, from the caller's device buffers:
+ *   src        source grid (host struct)
+ *   obs        device [n_obs][3] FP64 observation points (any order)
+ *   rho, J     device [n_slices][N_src] and [n_slices][N_src][3] FP64: the
+ *              whole history, slice n at time p->t0 + n*p->dt, cells x fastest
+ *   p          uses c, k_e, k_b, dt, t0 and screen; other fields are ignored
+ *   E, B       device [n_obs][3] FP64 outputs
+ * The call is synchronous on `stream` (it returns after E and B are written).
+ *
+ * Working memory is one file-scope device array of JEFI_NOALLOC_SCRATCH_BYTES
+ * per GPU that loads the library, held until the process exits.  The first
+ * call on a device, with that device current, finds the array's address
+ * (cudaGetSymbolAddress, which also loads the module): make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents; calls that overlap on the GPU race on it, so callers
+ * on several streams or threads must serialise them.
+ *
+ * Limits: ceil(n_obs/256)*256 <= (JEFI_NOALLOC_SCRATCH_BYTES - 256)/48 (that
+ * is n_obs <= 698880), and 4*(ceil(nx/4)+ceil(ny/4)+ceil(nz/4)) <= 6144;
+ * larger requests return JEFI_EUNSUPPORTED without touching the GPU.
+ * JEFI_ENOTYET if some pair needs a slice >= n_slices (E, B then incomplete).
+ */
+#define JEFI_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int jefi_eval_fields_noalloc(const jefi_grid* src, const double* obs, int64_t n_obs,
+                             const double* rho, const double* J, int64_t n_slices,
+                             const jefi_params* p, double t, double* E, double* B, void* stream);
+
 /* Release every device and host resource of the handle (synchronises). */
 int jefi_destroy(jefi_handle h);
 

@@ -50,7 +50,10 @@ PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 # Every symbol include/jefi.h declares (checked by the CPU test suite).
 EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval_fields",
            "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info", "jefi_reset_stats",
-           "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror")
+           "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror",
+           "jefi_eval_fields_noalloc")
+
+JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class JefiError(RuntimeError):
@@ -123,6 +126,9 @@ def load(build_if_needed: bool = True):
         L.jefi_host_pair_slots.argtypes = [I64, P, P, D, D, D, D, P]
         L.jefi_host_pair_slots.restype = None
         L.jefi_destroy.argtypes = [P]
+        L.jefi_eval_fields_noalloc.argtypes = [ctypes.POINTER(jefi_grid), P, I64, P, P, I64,
+                                               ctypes.POINTER(jefi_params), D, P, P, P]
+        L.jefi_eval_fields_noalloc.restype = I
         L.jefi_strerror.argtypes = [I]
         L.jefi_strerror.restype = ctypes.c_char_p
         for name in ("jefi_create", "jefi_push_sources", "jefi_eval_fields",
@@ -350,3 +356,23 @@ def eval_fields(h: Handle, t, stream=None):
         B = torch.empty_like(E)
         jefi_eval_fields_multi(h, ts, E, B, stream)
     return E, B
+
+
+def jefi_eval_fields_noalloc(src: jefi_grid, obs, rho, J, params: jefi_params, t: float, E, B,
+                             stream=None):
+    """FP64 fields at time t with no device allocation by the library.
+
+    For callers that cannot allocate device memory at this point (see
+    include/jefi.h): every buffer is the caller's own -- obs [N_obs, 3],
+    rho [n_slices, N_src], J [n_slices, N_src, 3], E and B [N_obs, 3], all
+    contiguous float64 CUDA tensors.  Synchronous on `stream`.
+    """
+    bufs = [_buf(x) for x in (obs, rho, J, E, B)]
+    if not all(b[1] for b in bufs):
+        raise ValueError("jefi_eval_fields_noalloc takes device (CUDA) tensors only")
+    n_obs = int(obs.shape[0]) if obs.dim() == 2 else int(obs.numel() // 3)
+    n_slices = int(rho.shape[0])
+    rc = load().jefi_eval_fields_noalloc(ctypes.byref(src), bufs[0][0], n_obs, bufs[1][0], bufs[2][0],
+                                         n_slices, ctypes.byref(params), float(t), bufs[3][0],
+                                         bufs[4][0], _stream_ptr(stream))
+    _check(rc, "jefi_eval_fields_noalloc")

@@ -26,7 +26,7 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
              "-I" + INCLUDE, "-I" + CSRC, "-I" + os.path.join(CUDA_HOME, "include")]
 
-CU_SOURCES = ["jefi_kernels.cu", "jefi_staged.cu"]
+CU_SOURCES = ["jefi_kernels.cu", "jefi_staged.cu", "jefi_noalloc.cu"]
 CXX_SOURCES = ["jefi_host.cpp"]
 HEADERS = ["jefi_internal.h", "jefi_device.cuh"]
 _lock = threading.Lock()
