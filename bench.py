@@ -134,8 +134,11 @@ def eval_times(lo, hi, k=8):
 
 
 def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_2104_05426_gb300", "csrc", "jefi_kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """Hash of the sources of the dominant kernel (the staged FP32 sum)."""
+    h = hashlib.sha256()
+    for f in ("jefi_staged.cu", "jefi_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2104_05426_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():

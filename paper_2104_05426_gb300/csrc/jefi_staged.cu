@@ -228,25 +228,37 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                               (ctx.rlo[2] <= kBrick * bz + 3) & (ctx.rhi[2] >= kBrick * bz);
             float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
             if (full && !__any_sync(kFull, near)) {
-                float ddx[4], ddy[4], ddz[4], sqx[4], sqy[4], sqz[4];
+                // Per-axis offsets and squares of the brick's 4 columns; the
+                // z slabs are a rolled loop (keeps the hot body small), the
+                // 16 cells of a slab are unrolled.
+                float ddx[4], ddy[4], sqx[4], sqy[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     ddx[i] = fmaf(-(float)i, d32x, Px);
                     ddy[i] = fmaf(-(float)i, d32y, Py);
-                    ddz[i] = fmaf(-(float)i, d32z, Pz);
                     sqx[i] = __fmul_rn(ddx[i], ddx[i]);
                     sqy[i] = __fmul_rn(ddy[i], ddy[i]);
-                    sqz[i] = __fmul_rn(ddz[i], ddz[i]);
                 }
-                uint32_t m_lo = 0u, m_hi = 0u;
-#pragma unroll
+                uint64_t mask = 0;
+                float2 acc_eyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
+                float acc_ex = 0.f, acc_bz = 0.f;
+#pragma unroll 1
                 for (int k = 0; k < 4; ++k) {
+                    const float dz = fmaf(-(float)k, d32z, Pz);
+                    const float sqz = __fmul_rn(dz, dz);
+                    const uint32_t gk = gbase + (uint32_t)(k * 16) * L::kCellBytes;
+                    float2 dyz[4], dzx[4];      // (dy_j, dz) and (dz, dx_i) operand pairs
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        dyz[i] = make_float2(ddy[i], dz);
+                        dzx[i] = make_float2(dz, ddx[i]);
+                    }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const float syz = __fadd_rn(sqy[j], sqz[k]);
+                        const float syz = __fadd_rn(sqy[j], sqz);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
-                            const int cl = k * 16 + j * 4 + i;
+                            const int c16 = j * 4 + i;
                             const float S = __fadd_rn(sqx[i], syz);
                             float ri = rsqrtf(S);
                             const float u = fmaf(-(S * ri), K32, Ag);
@@ -255,22 +267,50 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                             const bool lower = S > th.y;
                             if (!EXACT) {
                                 if (!(S <= th.x) && !lower) {   // undecided: redo after the brick
-                                    if (cl < 32) m_lo |= 1u << cl; else m_hi |= 1u << (cl - 32);
+                                    mask |= 1ull << (k * 16 + c16);
                                     ri = 0.f;
                                 }
                             }
                             if (DEBUG) {
-                                p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
+                                p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + k * 16 + c16] =
                                     (int)(tp.k0 + (int)(bits - kMagicBits) - (lower ? 1 : 0));
                             }
-                            const uint32_t off = gbase + bits * L::kRowBytes +
-                                                 (uint32_t)cl * L::kCellBytes - (lower ? L::kRowBytes : 0u);
+                            const uint32_t off = gk + bits * L::kRowBytes + (uint32_t)c16 * L::kCellBytes -
+                                                 (lower ? L::kRowBytes : 0u);
                             const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
                             const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
-                            pair_f32(ddx[i], ddy[j], ddz[k], ri, v0, v1, pe, pb);
+                            // Eqs. E-1/B-1 with packed pairs:
+                            //   (q, Vx) = (drho, dJx/c) r^-2 + (c rho, Jx) r^-3,  q the D-term of E
+                            //   (Vy, Vz) = (dJy, dJz)/c r^-2 + (Jy, Jz) r^-3
+                            const float2 ri2 = make_float2(ri, ri);
+                            const float2 r2 = __fmul2_rn(ri2, ri2);
+                            const float2 r3 = __fmul2_rn(r2, ri2);
+                            const float2 qvx = __ffma2_rn(make_float2(v1.x, v1.y), r2,
+                                                          __fmul2_rn(make_float2(v0.x, v0.y), r3));
+                            const float2 vyz = __ffma2_rn(make_float2(v1.z, v1.w), r2,
+                                                          __fmul2_rn(make_float2(v0.z, v0.w), r3));
+                            const float q = qvx.x, vx = qvx.y;
+                            // E' += D q - (dJ/c) / R
+                            acc_ex = fmaf(ddx[i], q, acc_ex);
+                            acc_ex = fmaf(-v1.y, ri, acc_ex);
+                            acc_eyz = __ffma2_rn(dyz[j], make_float2(q, q), acc_eyz);
+                            acc_eyz = __ffma2_rn(make_float2(-v1.z, -v1.w), ri2, acc_eyz);
+                            // B += V x D
+                            acc_bxy = __ffma2_rn(vyz, dzx[i], acc_bxy);          // (Vy dz, Vz dx)
+                            acc_bxy.x = fmaf(-vyz.y, ddy[j], acc_bxy.x);         // - Vz dy
+                            acc_bxy.y = fmaf(-vx, dz, acc_bxy.y);                // - Vx dz
+                            acc_bz = fmaf(vx, ddy[j], acc_bz);
+                            acc_bz = fmaf(-vyz.x, ddx[i], acc_bz);
                         }
                     }
                 }
+                pe[0] += acc_ex;
+                pe[1] += acc_eyz.x;
+                pe[2] += acc_eyz.y;
+                pb[0] += acc_bxy.x;
+                pb[1] += acc_bxy.y;
+                pb[2] += acc_bz;
+                const uint32_t m_lo = (uint32_t)mask, m_hi = (uint32_t)(mask >> 32);
                 if (!EXACT) {
                     if (__any_sync(kFull, (m_lo | m_hi) != 0u)) {
                         uint64_t mask = ((uint64_t)m_hi << 32) | m_lo;
