@@ -157,6 +157,22 @@ int jefi_eval_fields_multi(jefi_handle h, int32_t n_t, const double* t, double* 
                            int on_device, void* stream);
 
 /*
+ * Several problems, each at its own time, in one persistent launch per
+ * kernel variant present (problems sharing precision and staging share a
+ * launch) plus one reduction launch: the many-problem form of
+ * jefi_eval_fields (Eqs. E-1, B-1, tr-1 for every problem).
+ *
+ * hs[n], t[n]: problem i is evaluated at time t[i] (a handle may appear up
+ *   to 8 times).  E[i], B[i]: device [N_obs_i][3] FP64 outputs.
+ * Asynchronous on `stream`.  Every problem's result is bit-identical to
+ * jefi_eval_fields on the same handle and time: the work items run the same
+ * code in the same order whatever else is in the batch.  Batches issued on
+ * different streams are serialised on the device.
+ */
+int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, double* const* B,
+                    int32_t n, void* stream);
+
+/*
  * Interval [t_lo, t_hi] of evaluation times whose every retarded slice is
  * resident (all slots >= n_latest-H+1 or < 0, all <= n_latest).  Returns
  * JEFI_ENOTYET if no time qualifies (e.g. nothing pushed yet).

@@ -51,7 +51,7 @@ PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval_fields",
            "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info", "jefi_reset_stats",
            "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror",
-           "jefi_eval_fields_noalloc")
+           "jefi_eval_fields_noalloc", "jefi_eval_batch")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -126,6 +126,8 @@ def load(build_if_needed: bool = True):
         L.jefi_host_pair_slots.argtypes = [I64, P, P, D, D, D, D, P]
         L.jefi_host_pair_slots.restype = None
         L.jefi_destroy.argtypes = [P]
+        L.jefi_eval_batch.argtypes = [P, P, P, P, I32, P]
+        L.jefi_eval_batch.restype = I
         L.jefi_eval_fields_noalloc.argtypes = [ctypes.POINTER(jefi_grid), P, I64, P, P, I64,
                                                ctypes.POINTER(jefi_params), D, P, P, P]
         L.jefi_eval_fields_noalloc.restype = I
@@ -376,3 +378,25 @@ def jefi_eval_fields_noalloc(src: jefi_grid, obs, rho, J, params: jefi_params, t
                                          n_slices, ctypes.byref(params), float(t), bufs[3][0],
                                          bufs[4][0], _stream_ptr(stream))
     _check(rc, "jefi_eval_fields_noalloc")
+
+
+def jefi_eval_batch(handles, times, E_list, B_list, stream=None):
+    """Evaluate handles[i] at times[i] into E_list[i], B_list[i] (CUDA float64
+    tensors [N_obs_i, 3]) in one batched launch."""
+    n = len(handles)
+    if not (len(times) == len(E_list) == len(B_list) == n):
+        raise ValueError("handles, times and outputs must have the same length")
+    hs = (ctypes.c_void_p * n)(*[h.ptr.value for h in handles])
+    ts = (ctypes.c_double * n)(*[float(x) for x in times])
+    es, bs = [], []
+    for E, B in zip(E_list, B_list):
+        e, on_e, _ = _buf(E)
+        b, on_b, _ = _buf(B)
+        if not (on_e and on_b):
+            raise ValueError("jefi_eval_batch writes device (CUDA) tensors only")
+        es.append(e)
+        bs.append(b)
+    ep = (ctypes.c_void_p * n)(*es)
+    bp = (ctypes.c_void_p * n)(*bs)
+    rc = load().jefi_eval_batch(hs, ts, ep, bp, n, _stream_ptr(stream))
+    _check(rc, "jefi_eval_batch")

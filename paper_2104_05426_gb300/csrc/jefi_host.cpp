@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -427,19 +429,10 @@ int make_tensor_map(jefi_problem* h) {
     return r == CUDA_SUCCESS ? JEFI_OK : JEFI_ECUDA;
 }
 
-int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B, cudaStream_t s,
-                 int32_t* debug_slots) {
-    for (int i = 0; i < n_t; ++i) build_tables(h, i, t[i]);
+// Kernel parameters of handle h for n_t evaluation times whose tables sit in
+// table slots [slot0, slot0 + n_t) of the handle's device buffers.
+SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_slots) {
     const int K = h->K;
-    JEFI_CUDA(cudaMemcpyAsync(h->tab32, h->h_tab.data(), sizeof(float4) * K * n_t,
-                              cudaMemcpyHostToDevice, s));
-    JEFI_CUDA(cudaMemcpyAsync(h->theta, h->h_theta.data(), sizeof(double) * (K + 1) * n_t,
-                              cudaMemcpyHostToDevice, s));
-    JEFI_CUDA(cudaMemcpyAsync(h->times, h->h_times.data(), sizeof(TimeParams) * n_t,
-                              cudaMemcpyHostToDevice, s));
-    if (h->band > 0)
-        JEFI_CUDA(cudaMemcpyAsync(h->tab2, h->h_tab2.data(),
-                                  sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
     SumParams p{};
     p.nbx = h->nbx; p.nby = h->nby; p.nbz = h->nbz; p.n_bricks = h->n_bricks;
     p.npx = h->npx; p.npy = h->npy; p.npz = h->npz;
@@ -457,23 +450,50 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
     p.zero_slot = h->H + h->mirror;
     p.H = h->H;
     p.status = h->status;
-    p.tab2 = h->tab2;
+    p.tab2 = h->tab2 ? h->tab2 + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
     p.tile_box = h->tile_box;
     for (int a = 0; a < 3; ++a) {
         p.n_src_axis[a] = h->src.n[a];
         p.nfull[a] = h->src.n[a] / kBrick;
     }
-    p.tab32 = h->tab32;
-    p.theta = h->theta;
-    p.times = h->times;
+    p.tab32 = h->tab32 + (size_t)slot0 * K;
+    p.theta = h->theta + (size_t)slot0 * (K + 1);
+    p.times = h->times + slot0;
     p.n_t = n_t;
     p.K = K;
     p.K32 = (float)(1.0 / (h->prm.c * h->prm.dt));
     p.n_split = h->n_split;
     p.bricks_per_split = h->bricks_per_split;
-    p.partials = h->partials;
+    p.partials = h->partials + (size_t)slot0 * h->n_split * 6 * h->n_slots;
     p.fallbacks = h->fallbacks;
     p.debug_slots = debug_slots;
+    p.comp = h->prm.precision == JEFI_FP32_COMP ? 1 : 0;
+    return p;
+}
+
+// Upload the tables built in host slots [0, n_t) to the device.
+int upload_tables(jefi_problem* h, int n_t, cudaStream_t s) {
+    const int K = h->K;
+    JEFI_CUDA(cudaMemcpyAsync(h->tab32, h->h_tab.data(), sizeof(float4) * K * n_t,
+                              cudaMemcpyHostToDevice, s));
+    JEFI_CUDA(cudaMemcpyAsync(h->theta, h->h_theta.data(), sizeof(double) * (K + 1) * n_t,
+                              cudaMemcpyHostToDevice, s));
+    JEFI_CUDA(cudaMemcpyAsync(h->times, h->h_times.data(), sizeof(TimeParams) * n_t,
+                              cudaMemcpyHostToDevice, s));
+    if (h->band > 0)
+        JEFI_CUDA(cudaMemcpyAsync(h->tab2, h->h_tab2.data(),
+                                  sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
+    return JEFI_OK;
+}
+
+int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B, cudaStream_t s,
+                 int32_t* debug_slots) {
+    for (int i = 0; i < n_t; ++i) build_tables(h, i, t[i]);
+    {
+        const int rc = upload_tables(h, n_t, s);
+        if (rc != JEFI_OK) return rc;
+    }
+    SumParams p = make_params(h, n_t, 0, debug_slots);
     if (h->band == 0 && sum_smem_bytes(p) > 200 * 1024) return JEFI_EUNSUPPORTED;
 
     const bool timed = (h->prm.flags & JEFI_FLAG_STATS) != 0 && !debug_slots;
@@ -521,6 +541,45 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
     r.B = B;
     JEFI_CUDA(launch_reduce(r, s));
     h->launches++;
+    return JEFI_OK;
+}
+
+// ---------------------------------------------------------------- batched launches
+// Device memory for the metadata of batched launches, one arena per device.
+// A batch waits (on its stream) for the previous batch that used the arena
+// before overwriting it.
+struct BatchArena {
+    std::mutex lock;
+    void* dev = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    int n_sm = 0;
+};
+BatchArena g_arena[64];
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int arena_reserve(BatchArena& a, size_t bytes) {
+    if (!a.done) {
+        JEFI_CUDA(cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming));
+        int dev = 0;
+        JEFI_CUDA(cudaGetDevice(&dev));
+        JEFI_CUDA(cudaDeviceGetAttribute(&a.n_sm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    if (a.cap >= bytes) return JEFI_OK;
+    if (a.dev) {
+        JEFI_CUDA(cudaEventSynchronize(a.done));
+        cudaFree(a.dev);
+        a.dev = nullptr;
+        a.cap = 0;
+    }
+    const size_t cap = std::max<size_t>(bytes, 1 << 20);
+    if (cudaMalloc(&a.dev, cap) != cudaSuccess) {
+        cudaGetLastError();
+        a.dev = nullptr;
+        return JEFI_ENOMEM;
+    }
+    a.cap = cap;
     return JEFI_OK;
 }
 
@@ -964,6 +1023,161 @@ int jefi_eval_fields(jefi_handle h, double t, double* E, double* B, int on_devic
 int jefi_eval_fields_multi(jefi_handle h, int32_t n_t, const double* t, double* E, double* B,
                            int on_device, void* stream) {
     return eval_impl(h, n_t, t, E, B, on_device, stream);
+}
+
+int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, double* const* B, int32_t n,
+                    void* stream) {
+    if (n < 0 || (n > 0 && (!hs || !t || !E || !B))) return JEFI_EINVAL;
+    if (n == 0) return JEFI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> occ(n);
+    std::map<jefi_problem*, int> count;
+    for (int i = 0; i < n; ++i) {
+        jefi_problem* h = hs[i];
+        if (!h) return JEFI_EINVAL;
+        if (h->n_obs > 0 && (!E[i] || !B[i])) return JEFI_EINVAL;
+        const int rc = check_time(h, t[i]);
+        if (rc != JEFI_OK) return rc;
+        occ[i] = count[h]++;
+        if (occ[i] >= kTimeChunk) return JEFI_EUNSUPPORTED;   // a handle at most 8 times per batch
+    }
+    for (int i = 0; i < n; ++i)
+        if (hs[i]->any_pairs && hs[i]->n_obs > 0) build_tables(hs[i], occ[i], t[i]);
+    for (auto& kv : count)
+        if (kv.first->any_pairs && kv.first->n_obs > 0) {
+            const int rc = upload_tables(kv.first, kv.second, s);
+            if (rc != JEFI_OK) return rc;
+        }
+
+    // Group the problems by kernel variant: one persistent launch per group.
+    struct Group {
+        int kind;           // 0 FP64, 1 FP32 direct, 2 FP32 staged
+        int comp, band;
+        bool exact;
+        std::vector<int> members;
+    };
+    std::vector<Group> groups;
+    std::vector<ReduceItem> ritems;
+    std::vector<int64_t> rstart(1, 0);
+    for (int i = 0; i < n; ++i) {
+        jefi_problem* h = hs[i];
+        if (h->n_obs == 0) continue;
+        if (!h->any_pairs) {
+            JEFI_CUDA(cudaMemsetAsync(E[i], 0, sizeof(double) * 3 * h->n_obs, s));
+            JEFI_CUDA(cudaMemsetAsync(B[i], 0, sizeof(double) * 3 * h->n_obs, s));
+            continue;
+        }
+        Group key{h->fp64 ? 0 : (h->band > 0 ? 2 : 1), h->prm.precision == JEFI_FP32_COMP ? 1 : 0, h->band,
+                  h->exact, {}};
+        if (key.kind != 1) key.comp = 0;
+        if (key.kind != 2) { key.band = 0; key.exact = false; }
+        Group* g = nullptr;
+        for (auto& x : groups)
+            if (x.kind == key.kind && x.comp == key.comp && x.band == key.band && x.exact == key.exact &&
+                (x.kind != 2 || (int)x.members.size() < kMaxBatchMaps))
+                g = &x;
+        if (!g) {
+            groups.push_back(key);
+            g = &groups.back();
+        }
+        g->members.push_back(i);
+        ReduceItem r{};
+        r.inv_perm = h->d_inv_perm;
+        r.partials = h->partials + (size_t)occ[i] * h->n_split * 6 * h->n_slots;
+        r.n_obs = (int32_t)h->n_obs;
+        r.n_slots = h->n_slots;
+        r.n_split = h->n_split;
+        r.e_scale = h->prm.k_e * (h->src.d[0] * h->src.d[1] * h->src.d[2]) / h->prm.c;
+        r.b_scale = h->prm.k_b * (h->src.d[0] * h->src.d[1] * h->src.d[2]);
+        r.E = E[i];
+        r.B = B[i];
+        ritems.push_back(r);
+        rstart.push_back(rstart.back() + h->n_obs);
+    }
+    if (groups.empty()) return JEFI_OK;
+
+    // Arena layout: per group [params | item_start | counter], then [reduce items | starts].
+    std::vector<size_t> off_params(groups.size()), off_start(groups.size()), off_counter(groups.size());
+    size_t bytes = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        off_params[g] = bytes;
+        bytes = align256(bytes + sizeof(SumParams) * groups[g].members.size());
+        off_start[g] = bytes;
+        bytes = align256(bytes + sizeof(int32_t) * (groups[g].members.size() + 1));
+        off_counter[g] = bytes;
+        bytes = align256(bytes + sizeof(unsigned int));
+    }
+    const size_t off_ritems = bytes;
+    bytes = align256(bytes + sizeof(ReduceItem) * ritems.size());
+    const size_t off_rstart = bytes;
+    bytes = align256(bytes + sizeof(int64_t) * rstart.size());
+
+    int dev = 0;
+    JEFI_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return JEFI_EUNSUPPORTED;
+    BatchArena& arena = g_arena[dev];
+    std::lock_guard<std::mutex> guard(arena.lock);
+    {
+        const int rc = arena_reserve(arena, bytes);
+        if (rc != JEFI_OK) return rc;
+    }
+    std::vector<unsigned char> host(bytes, 0);
+    std::vector<int> n_items(groups.size());
+    std::vector<size_t> smem(groups.size(), 0);
+    for (size_t g = 0; g < groups.size(); ++g) {
+        SumParams* prm = reinterpret_cast<SumParams*>(host.data() + off_params[g]);
+        int32_t* start = reinterpret_cast<int32_t*>(host.data() + off_start[g]);
+        int32_t acc = 0;
+        for (size_t m = 0; m < groups[g].members.size(); ++m) {
+            const int i = groups[g].members[m];
+            jefi_problem* h = hs[i];
+            prm[m] = make_params(h, 1, occ[i], nullptr);
+            start[m] = acc;
+            acc += h->n_tiles * h->n_split;
+            smem[g] = std::max(smem[g], groups[g].kind == 2 ? staged_smem_bytes(prm[m], groups[g].band)
+                                                             : sum_smem_bytes(prm[m]));
+        }
+        start[groups[g].members.size()] = acc;
+        n_items[g] = acc;
+        if (smem[g] > 220 * 1024) return JEFI_EUNSUPPORTED;
+    }
+    std::memcpy(host.data() + off_ritems, ritems.data(), sizeof(ReduceItem) * ritems.size());
+    std::memcpy(host.data() + off_rstart, rstart.data(), sizeof(int64_t) * rstart.size());
+
+    unsigned char* d = static_cast<unsigned char*>(arena.dev);
+    JEFI_CUDA(cudaStreamWaitEvent(s, arena.done, 0));
+    JEFI_CUDA(cudaMemcpyAsync(d, host.data(), bytes, cudaMemcpyHostToDevice, s));
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const int per_sm = groups[g].kind == 0 ? 1 : (smem[g] > 110 * 1024 ? 1 : 2);
+        const int grid = std::max(1, std::min(n_items[g], per_sm * arena.n_sm));
+        cudaError_t e;
+        if (groups[g].kind == 2) {
+            StagedBatchArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
+            a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
+            a.n = (int32_t)groups[g].members.size();
+            a.n_items = n_items[g];
+            a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
+            for (size_t m = 0; m < groups[g].members.size(); ++m) a.maps[m] = hs[groups[g].members[m]]->tmap;
+            e = launch_sum_f32_staged_batch(a, groups[g].band, groups[g].exact, smem[g], grid, s);
+        } else {
+            BatchArgs a;
+            a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
+            a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
+            a.n = (int32_t)groups[g].members.size();
+            a.n_items = n_items[g];
+            a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
+            e = groups[g].kind == 0 ? launch_sum_f64_batch(a, smem[g], grid, s)
+                                    : launch_sum_f32_batch(a, groups[g].comp != 0, smem[g], grid, s);
+        }
+        if (e != cudaSuccess) return JEFI_ECUDA;
+    }
+    JEFI_CUDA(launch_reduce_batch(reinterpret_cast<const ReduceItem*>(d + off_ritems),
+                                  reinterpret_cast<const int64_t*>(d + off_rstart), (int)ritems.size(),
+                                  rstart.back(), s));
+    JEFI_CUDA(cudaEventRecord(arena.done, s));
+    return JEFI_OK;
 }
 
 int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream) {

@@ -81,6 +81,17 @@ struct SumParams {
     int32_t n_src_axis[3];          // real source cells per axis
     int32_t nfull[3];               // whole bricks per axis (bricks past them hold padding cells)
     int32_t H;                      // ring period (physical slot of slice n is n mod H)
+    int32_t comp;                   // FP32: compensated (Kahan) per-thread sums
+};
+
+// Persistent batched launches: problem i owns items [item_start[i], item_start[i+1]),
+// item = (time, split, tile) in that order of significance.
+struct BatchArgs {
+    const SumParams* params;        // [n] device
+    const int32_t* item_start;      // [n+1] device
+    int32_t n;
+    int32_t n_items;
+    unsigned int* counter;          // device, zero at launch
 };
 
 struct PushParams {
@@ -109,6 +120,35 @@ struct ReduceParams {
     double* E;                      // [n_t][n_obs][3]
     double* B;
 };
+
+constexpr int kMaxBatchMaps = 224;  // tensor maps per staged batched launch (kernel-parameter space)
+
+#ifdef CUDA_VERSION
+struct StagedBatchArgs {
+    const SumParams* params;
+    const int32_t* item_start;
+    int32_t n;
+    int32_t n_items;
+    unsigned int* counter;
+    CUtensorMap maps[kMaxBatchMaps];
+};
+cudaError_t launch_sum_f32_staged_batch(const StagedBatchArgs& a, int band, bool exact, size_t smem,
+                                        int grid, cudaStream_t s);
+#endif
+
+struct ReduceItem {
+    const int32_t* inv_perm;
+    const double* partials;         // this item's [n_split][6][n_slots]
+    int32_t n_obs, n_slots, n_split, pad;
+    double e_scale, b_scale;
+    double* E;
+    double* B;
+};
+
+cudaError_t launch_sum_f32_batch(const BatchArgs& a, bool compensated, size_t smem, int grid, cudaStream_t s);
+cudaError_t launch_sum_f64_batch(const BatchArgs& a, size_t smem, int grid, cudaStream_t s);
+cudaError_t launch_reduce_batch(const ReduceItem* items, const int64_t* out_start, int n, int64_t total,
+                                cudaStream_t s);
 
 struct StagedConfig {
     int32_t band;                   // slot rows staged per cell (a compiled variant)

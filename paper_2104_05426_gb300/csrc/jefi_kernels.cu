@@ -29,16 +29,13 @@ using namespace dev;
 // ============================================================================ FP32
 // Shared memory: tab32[K] float4 | theta[K+1] double | D[nbx+nby+nbz] float
 template <bool COMP, bool DEBUG>
-__global__ void __launch_bounds__(kTileThreads, 2) sum_f32_kernel(const SumParams p) {
+__device__ __forceinline__ void direct_f32_item(const SumParams& p, const int tile, const int split,
+                                                const int ti) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K;
     float4* s_tab = reinterpret_cast<float4*>(smem);
     double* s_th = reinterpret_cast<double*>(s_tab + K);
     float* s_D = reinterpret_cast<float*>(s_th + K + 1);
-
-    const int tile = blockIdx.x;
-    const int split = blockIdx.y;
-    const int ti = blockIdx.z;
     const int tid = threadIdx.x;
 
     const float4* g_tab = p.tab32 + (size_t)ti * K;
@@ -204,6 +201,42 @@ __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_kernel(const SumParam
     }
 }
 
+template <bool COMP, bool DEBUG>
+__global__ void __launch_bounds__(kTileThreads, 2) sum_f32_kernel(const SumParams p) {
+    direct_f32_item<COMP, DEBUG>(p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Take the next item of a persistent batched launch; false when the queue is empty.
+__device__ __forceinline__ bool next_item(const BatchArgs& a, int* s_item, int* pr, int* tile, int* split, int* ti) {
+    if (threadIdx.x == 0) *s_item = (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int item = *s_item;
+    __syncthreads();
+    if (item >= a.n_items) return false;
+    int lo = 0, hi = a.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.item_start[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const SumParams& p = a.params[lo];
+    const int local = item - a.item_start[lo];
+    const int per_t = p.n_tiles * p.n_split;
+    *pr = lo;
+    *ti = local / per_t;
+    const int r = local - *ti * per_t;
+    *split = r / p.n_tiles;
+    *tile = r - *split * p.n_tiles;
+    return true;
+}
+
+template <bool COMP>
+__global__ void __launch_bounds__(kTileThreads, 2) sum_f32_batch(const BatchArgs a) {
+    __shared__ int s_item;
+    int pr, tile, split, ti;
+    while (next_item(a, &s_item, &pr, &tile, &split, &ti))
+        direct_f32_item<COMP, false>(a.params[pr], tile, split, ti);
+}
+
 // ============================================================================ FP64
 // Shared memory: tab32[K] float4 | theta[K+1] double | xs[npx] ys[npy] zs[npz] double
 __device__ __forceinline__ void pair_f64(double dx, double dy, double dz, double ri,
@@ -231,7 +264,7 @@ __device__ __forceinline__ void pair_f64(double dx, double dy, double dz, double
 }
 
 template <bool DEBUG>
-__global__ void __launch_bounds__(kTileThreads, 1) sum_f64_kernel(const SumParams p) {
+__device__ __forceinline__ void f64_item(const SumParams& p, const int tile, const int split, const int ti) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K;
     float4* s_tab = reinterpret_cast<float4*>(smem);
@@ -240,9 +273,6 @@ __global__ void __launch_bounds__(kTileThreads, 1) sum_f64_kernel(const SumParam
     double* s_ys = s_xs + p.npx;
     double* s_zs = s_ys + p.npy;
 
-    const int tile = blockIdx.x;
-    const int split = blockIdx.y;
-    const int ti = blockIdx.z;
     const int tid = threadIdx.x;
     const float4* g_tab = p.tab32 + (size_t)ti * K;
     const double* g_th = p.theta + (size_t)ti * (K + 1);
@@ -339,6 +369,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) sum_f64_kernel(const SumParam
     }
 }
 
+template <bool DEBUG>
+__global__ void __launch_bounds__(kTileThreads, 1) sum_f64_kernel(const SumParams p) {
+    f64_item<DEBUG>(p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+__global__ void __launch_bounds__(kTileThreads, 1) sum_f64_batch(const BatchArgs a) {
+    __shared__ int s_item;
+    int pr, tile, split, ti;
+    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) f64_item<false>(a.params[pr], tile, split, ti);
+}
+
 // ============================================================================ push
 __global__ void push_kernel(const PushParams p) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -415,7 +456,53 @@ __global__ void reduce_kernel(const ReduceParams p) {
     }
 }
 
+// Batched reduction: output point `gid` of the concatenation of all items.
+__global__ void reduce_batch_kernel(const ReduceItem* items, const int64_t* out_start, int n, int64_t total) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (out_start[mid] <= gid) lo = mid; else hi = mid - 1;
+    }
+    const ReduceItem it = items[lo];
+    const int o = (int)(gid - out_start[lo]);
+    const double* base = it.partials + it.inv_perm[o];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < it.n_split; ++s) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[c] += base[((size_t)s * 6 + c) * it.n_slots];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        it.E[(size_t)o * 3 + a] = acc[a] * it.e_scale;
+        it.B[(size_t)o * 3 + a] = acc[3 + a] * it.b_scale;
+    }
+}
+
 // ============================================================================ launchers
+cudaError_t launch_sum_f32_batch(const BatchArgs& a, bool compensated, size_t smem, int grid, cudaStream_t s) {
+    void (*k)(BatchArgs) = compensated ? sum_f32_batch<true> : sum_f32_batch<false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kTileThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_f64_batch(const BatchArgs& a, size_t smem, int grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(sum_f64_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sum_f64_batch<<<grid, kTileThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_batch(const ReduceItem* items, const int64_t* out_start, int n, int64_t total,
+                                cudaStream_t s) {
+    if (total == 0) return cudaSuccess;
+    reduce_batch_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(items, out_start, n, total);
+    return cudaGetLastError();
+}
+
 size_t sum_smem_bytes(const SumParams& p) {
     size_t b = (size_t)p.K * sizeof(float4) + (size_t)(p.K + 1) * sizeof(double);
     return b + (size_t)(p.npx + p.npy + p.npz) * sizeof(double);

@@ -97,9 +97,27 @@ struct Layout {
 
 }  // namespace
 
+// Both staged kernels initialise the two mbarriers once per CTA.
+template <int BAND>
+__device__ __forceinline__ void staged_init_barriers() {
+    using L = Layout<BAND>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    if (threadIdx.x == 0) {
+        uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + L::kCtrl);
+        mbar_init(smem_u32(&s_mbar[0]), 1);
+        mbar_init(smem_u32(&s_mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// One work item: observation tile `tile` x source split `split` at time
+// index `ti` of problem p.  g_it counts the CTA's staged bricks across items
+// (it selects the buffer and the mbarrier phase).  Returns false if a copy
+// did not complete in time (the caller stops).
 template <int BAND, bool EXACT, bool DEBUG>
-__global__ void __launch_bounds__(kTileThreads, 2)
-    sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p, const int comp) {
+__device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const int comp,
+                                            const int tile, const int split, const int ti, uint32_t& g_it) {
     using L = Layout<BAND>;
     extern __shared__ __align__(1024) unsigned char smem[];
     const int K = p.K;
@@ -110,9 +128,6 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     double* s_th = reinterpret_cast<double*>(smem + L::kTab + (size_t)KT * sizeof(float2));
     float* s_D = reinterpret_cast<float*>(s_th + K + 1);
 
-    const int tile = blockIdx.x;
-    const int split = blockIdx.y;
-    const int ti = blockIdx.z;
     const int tid = threadIdx.x;
 
     const float2* g_tab = p.tab2 + (size_t)ti * KT;
@@ -127,11 +142,6 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         const int b = a == 0 ? i : (a == 1 ? i - p.nbx : i - nbxy);
         const double co = a == 0 ? cox : (a == 1 ? coy : coz);
         s_D[i] = __double2float_rn(__dsub_rn(co, cell_center(p.lo[a], p.d[a], kBrick * b)));
-    }
-    if (tid == 0) {
-        mbar_init(smem_u32(&s_mbar[0]), 1);
-        mbar_init(smem_u32(&s_mbar[1]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         // reads before the async-proxy write
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(mbar_u32[bufi], L::kBufBytes);
-        tma_load_3d(buf_u32[bufi], &tmap, 0, y0, b * kBrickCells, mbar_u32[bufi]);
+        tma_load_3d(buf_u32[bufi], tmap_ptr, 0, y0, b * kBrickCells, mbar_u32[bufi]);
     };
 
     float se[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
@@ -204,10 +214,10 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
     const uint32_t tbase = L::kTab + (uint32_t)(kTabGuard - kMagicBits) * 8u;
 
-    if (tid == 0 && b_begin < b_end) issue(b_begin, 0);
-    int aborted_at = -1;
+    if (tid == 0 && b_begin < b_end) issue(b_begin, g_it & 1);
+    int64_t aborted_at = -1;
     for (int b = b_begin; b < b_end; ++b) {
-        const int it = b - b_begin;
+        const uint32_t it = g_it + (uint32_t)(b - b_begin);
         const int buf = it & 1;
         if (tid == 0 && b + 1 < b_end) issue(b + 1, buf ^ 1);
         const bool ready = mbar_wait_bounded(mbar_u32[buf], (it >> 1) & 1);
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         }
         // every thread is done with this buffer before it is refilled
         if (__syncthreads_or(!ready)) {
-            aborted_at = it;
+            aborted_at = b - b_begin;
             break;
         }
     }
@@ -411,13 +421,14 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         // a copy did not complete in time: report, then wait (bounded) for
         // the copies still in flight before the shared memory goes away
         if (tid == 0) {
+            const uint32_t it = g_it + (uint32_t)aborted_at;
             atomicExch(p.status, kStatusTimeout);
-            mbar_wait_bounded(mbar_u32[aborted_at & 1], (aborted_at >> 1) & 1);
-            if (b_begin + aborted_at + 1 < b_end)
-                mbar_wait_bounded(mbar_u32[(aborted_at + 1) & 1], ((aborted_at + 1) >> 1) & 1);
+            mbar_wait_bounded(mbar_u32[it & 1], (it >> 1) & 1);
+            if (b_begin + aborted_at + 1 < b_end) mbar_wait_bounded(mbar_u32[(it + 1) & 1], ((it + 1) >> 1) & 1);
         }
         __syncthreads();
     }
+    g_it += (uint32_t)(b_end > b_begin ? b_end - b_begin : 0);
 
     double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
 #pragma unroll
@@ -425,13 +436,54 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         out[(size_t)a * p.n_slots] = comp ? (double)se[a] - (double)ce[a] : (double)se[a];
         out[(size_t)(3 + a) * p.n_slots] = comp ? (double)sb[a] - (double)cb[a] : (double)sb[a];
     }
+    return aborted_at < 0;
+}
+
+template <int BAND, bool EXACT, bool DEBUG>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p) {
+    staged_init_barriers<BAND>();
+    uint32_t g_it = 0;
+    staged_item<BAND, EXACT, DEBUG>(&tmap, p, p.comp, blockIdx.x, blockIdx.y, blockIdx.z, g_it);
+}
+
+// Persistent batched kernel: CTAs take (problem, time, split, tile) items
+// from a queue until it is empty; each item runs the same code as the
+// single-problem kernel, so a problem's result does not depend on the batch.
+template <int BAND, bool EXACT>
+__global__ void __launch_bounds__(kTileThreads, 2) sum_f32_staged_batch(const __grid_constant__ StagedBatchArgs a) {
+    using L = Layout<BAND>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    int* s_item = reinterpret_cast<int*>(smem + L::kCtrl + 32);
+    staged_init_barriers<BAND>();
+    uint32_t g_it = 0;
+    for (;;) {
+        if (threadIdx.x == 0) *s_item = (int)atomicAdd(a.counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= a.n_items) break;
+        int lo = 0, hi = a.n - 1;                 // problem: last start <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.item_start[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const SumParams& p = a.params[lo];
+        const int local = item - a.item_start[lo];
+        const int per_t = p.n_tiles * p.n_split;
+        const int ti = local / per_t;
+        const int r = local - ti * per_t;
+        const int split = r / p.n_tiles;
+        const int tile = r - split * p.n_tiles;
+        if (!staged_item<BAND, EXACT, false>(&a.maps[lo], p, p.comp, tile, split, ti, g_it)) break;
+    }
 }
 
 bool staged_band_supported(int band) { return band == 16 || band == 24 || band == 32 || band == 48; }
 
 size_t staged_smem_bytes(const SumParams& p, int band) {
     const size_t buf = (size_t)kBrickCells * band * 32;
-    size_t b = 2 * buf + 64;
+    size_t b = 2 * buf + 64;                 // two buffers, mbarriers / band origins / item
     b += (size_t)(p.K + 2 * kTabGuard) * sizeof(float2);
     b += (size_t)(p.K + 1) * sizeof(double);
     b += (size_t)(p.nbx + p.nby + p.nbz) * sizeof(float);
@@ -446,8 +498,28 @@ static cudaError_t launch_variant(const SumParams& p, const StagedConfig& c, cud
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tensor_map);
-    k<<<grid, kTileThreads, smem, s>>>(*tm, p, c.compensated ? 1 : 0);
+    k<<<grid, kTileThreads, smem, s>>>(*tm, p);
     return cudaGetLastError();
+}
+
+template <int BAND, bool EXACT>
+static cudaError_t launch_batch_variant(const StagedBatchArgs& a, size_t smem, int grid, cudaStream_t s) {
+    auto k = sum_f32_staged_batch<BAND, EXACT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kTileThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_f32_staged_batch(const StagedBatchArgs& a, int band, bool exact, size_t smem,
+                                        int grid, cudaStream_t s) {
+    switch (band) {
+        case 16: return exact ? launch_batch_variant<16, true>(a, smem, grid, s) : launch_batch_variant<16, false>(a, smem, grid, s);
+        case 24: return exact ? launch_batch_variant<24, true>(a, smem, grid, s) : launch_batch_variant<24, false>(a, smem, grid, s);
+        case 32: return exact ? launch_batch_variant<32, true>(a, smem, grid, s) : launch_batch_variant<32, false>(a, smem, grid, s);
+        case 48: return exact ? launch_batch_variant<48, true>(a, smem, grid, s) : launch_batch_variant<48, false>(a, smem, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int BAND>

@@ -293,3 +293,41 @@ def c3_dipole(side: int = 32, per_shell: int = 1024, radii=(5.0, 10.0, 20.0, 40.
     assert span + 3 < H
     return Problem("C3", src, None, pts, dt, H, n_push, times,
                    Dipole(1.0, 2.0 * math.pi / 8.0, sigma), t0=t0)
+
+
+def c4_batch(n_problems: int = 256, seed: int = 4, src_sides=(8, 48), obs_sides=(8, 32),
+             H_range=(32, 128)) -> List[Problem]:
+    """Independent problems of uneven sizes: cubic source grids of side
+    uniform in src_sides over [-1,1]^3, cubic observation grids of side
+    uniform in obs_sides over [-2,2]^3 (overlapping, so screening applies),
+    1-4 moving Gaussian charges (speed uniform in [0, 0.9]c, random
+    direction, sigma in [0.1, 0.4]), H uniform in H_range and
+    dt = (R_max - R_min)/(c (H - 3)) so each history just covers its pairs;
+    one evaluation time per problem, inside its window."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(n_problems):
+        ns = int(rng.integers(src_sides[0], src_sides[1] + 1))
+        no = int(rng.integers(obs_sides[0], obs_sides[1] + 1))
+        H = int(rng.integers(H_range[0], H_range[1] + 1))
+        src = Grid.cube(ns, -1.0, 1.0)
+        obs = Grid.cube(no, -2.0, 2.0)
+        blobs = []
+        for _ in range(int(rng.integers(1, 5))):
+            v = rng.standard_normal(3)
+            v *= rng.uniform(0.0, 0.9) / np.linalg.norm(v)
+            sig = float(rng.uniform(0.1, 0.4))
+            x0 = rng.uniform(-0.3, 0.3, 3)
+            blobs.append(Blob(float(rng.choice([-1.0, 1.0])), (sig, sig, sig), tuple(x0), tuple(v)))
+        rmax = float(np.linalg.norm(np.array(obs.lo) - (np.array(src.lo) + np.array(src.d) * (np.array(src.n) - 0.5)))) + 1e-9
+        rmin = min(src.d[0], obs.d[0]) * 0.25
+        dt = (rmax - rmin) / (H - 3)
+        # window: slots between 1 and H-1 for every pair; shift the charges so
+        # they sit near the origin at the evaluation time
+        t_eval = rmax + 1.5 * dt
+        t0 = 0.0
+        moved = [Blob(b.q, b.sigma, tuple(np.asarray(b.x0) - np.asarray(b.v) * (t_eval - 1.0)), b.v)
+                 for b in blobs]
+        out.append(Problem(f"C4-{k}", src, obs, None, dt, H, H, [t_eval], MovingGaussians(moved),
+                           t0=t0))
+    return out
