@@ -308,6 +308,8 @@ def run_gpu(args):
                                 "fp32c_speedup_kernel": fp32c_kernel_pairs_s / fp64_pairs_s,
                                 "rel_l2_fp32c_vs_fp64_all_points": err}
         jefi.jefi_destroy(h64)
+        if not args.no_serving:
+            result["serving"] = serving_leg()
         if not args.no_cpu_baseline:
             result["cpu_baseline"], result["oracle_check"] = cpu_baseline(p, slices[:H], t_first,
                                                                           E_first, B_first)
@@ -316,6 +318,34 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving_leg(n_problems=16, n_requests=600, seed=11, tick_s=0.02):
+    """Continuous batching of Poisson-arriving requests against resident
+    problems (source sides 16-48, histories 64-128 slices, observation sides
+    8-48, one slice pushed to every problem per tick): saturated throughput
+    first (all requests at once), then p50/p99 latency at 0.8x that rate."""
+    from paper_2104_05426_gb300.serving import ServingEngine, make_problems, poisson_requests
+
+    probs = make_problems(n_problems, seed, sides=(16, 48), H_range=(64, 128))
+    sides = [8, 16, 24, 32, 40, 48]
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=4, max_batch=32, tick_s=None)
+    sat = eng.run(poisson_requests(n_requests, rate=1e9, n_problems=n_problems, seed=seed + 1,
+                                   side_choices=sides))
+    rate = 0.8 * sat.requests_per_s
+    eng.tick_s = tick_s
+    st = eng.run(poisson_requests(n_requests, rate=rate, n_problems=n_problems, seed=seed + 2,
+                                  side_choices=sides))
+    eng.close()
+    return {"p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+            "offered_requests_per_s": rate, "requests_per_s": st.requests_per_s,
+            "pairs_per_s": st.pairs_per_s, "saturated_requests_per_s": sat.requests_per_s,
+            "saturated_pairs_per_s": sat.pairs_per_s, "completed": st.completed,
+            "rejected": st.rejected, "mean_batch": st.mean_batch, "max_batch": st.max_batch,
+            "peak_device_bytes": st.peak_bytes,
+            "workload": f"{n_problems} resident problems, {n_requests} Poisson requests at 0.8x "
+                        f"saturation, obs sides {sides}, slice push every {tick_s * 1e3:.0f} ms, "
+                        "compensated FP32"}
 
 
 def cpu_baseline(p, slices, times, E_gpu, B_gpu, stride=512):
@@ -397,6 +427,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="jefi", choices=["jefi", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and oracle legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--side", type=int, default=64,
                     help="grid side of the heavy-ion workload (64 = the benchmark; smaller "
                          "sides only for profiler captures)")

@@ -101,6 +101,7 @@ typedef struct {
 
 #define JEFI_FLAG_STATS 1u    /* time the sum kernel with CUDA events on the call's stream */
 #define JEFI_FLAG_DIRECT_GATHER 2u  /* FP32: never use the TMA-staged kernel (for comparisons) */
+#define JEFI_FLAG_SHARED_RING 4u    /* FP32: size the ring's mirror for views of any staged band */
 
 /* Fills p with: c = 1, k_e = k_b = 1, dt = 1, t0 = 0, H = 64, FP32_COMP,
  * backward differences, default screening, cudaMalloc. */
@@ -123,6 +124,21 @@ void jefi_default_params(jefi_params* p);
  */
 int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
                 int64_t n_obs, const jefi_params* p, void* stream, jefi_handle* out);
+
+/*
+ * A second set of observation points over the same resident source history:
+ * the view shares `base`'s ring, parameters and pushed slices (pushes go to
+ * the base; a view always sees the latest), and has its own tiles, tables
+ * and scratch.  The paper keeps rho and J resident across calls (Sec. 2.2);
+ * views let many observation regions use one resident history.
+ * obs_grid / obs_points / n_obs as in jefi_create.  Destroy every view of a
+ * base before the base (jefi_destroy of a base with live views returns
+ * JEFI_EINVAL).  Pushing to a view returns JEFI_EINVAL.  A view uses the
+ * staged kernel only if its band fits the base ring's mirror (create the
+ * base with JEFI_FLAG_SHARED_RING).
+ */
+int jefi_create_view(jefi_handle base, const jefi_grid* obs_grid, const double* obs_points,
+                     int64_t n_obs, void* stream, jefi_handle* out);
 
 /*
  * Append the next slice n_latest+1 of the source history (paper Sec. 2.2:
@@ -167,7 +183,8 @@ int jefi_eval_fields_multi(jefi_handle h, int32_t n_t, const double* t, double* 
  * Asynchronous on `stream`.  Every problem's result is bit-identical to
  * jefi_eval_fields on the same handle and time: the work items run the same
  * code in the same order whatever else is in the batch.  Batches issued on
- * different streams are serialised on the device.
+ * different streams may run concurrently (each stream has its own batch
+ * metadata); a handle must not be in two batches in flight at once.
  */
 int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, double* const* B,
                     int32_t n, void* stream);

@@ -44,6 +44,7 @@ JEFI_DERIV_BACKWARD = 0
 JEFI_DERIV_SUPPLIED = 1
 JEFI_FLAG_STATS = 1
 JEFI_FLAG_DIRECT_GATHER = 2
+JEFI_FLAG_SHARED_RING = 4
 
 PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 
@@ -51,7 +52,7 @@ PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval_fields",
            "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info", "jefi_reset_stats",
            "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror",
-           "jefi_eval_fields_noalloc", "jefi_eval_batch")
+           "jefi_eval_fields_noalloc", "jefi_eval_batch", "jefi_create_view")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -127,6 +128,8 @@ def load(build_if_needed: bool = True):
         L.jefi_host_pair_slots.restype = None
         L.jefi_destroy.argtypes = [P]
         L.jefi_eval_batch.argtypes = [P, P, P, P, I32, P]
+        L.jefi_create_view.argtypes = [P, ctypes.POINTER(jefi_grid), P, I64, P, ctypes.POINTER(P)]
+        L.jefi_create_view.restype = I
         L.jefi_eval_batch.restype = I
         L.jefi_eval_fields_noalloc.argtypes = [ctypes.POINTER(jefi_grid), P, I64, P, P, I64,
                                                ctypes.POINTER(jefi_params), D, P, P, P]
@@ -400,3 +403,22 @@ def jefi_eval_batch(handles, times, E_list, B_list, stream=None):
     bp = (ctypes.c_void_p * n)(*bs)
     rc = load().jefi_eval_batch(hs, ts, ep, bp, n, _stream_ptr(stream))
     _check(rc, "jefi_eval_batch")
+
+
+def jefi_create_view(base: Handle, obs_grid: Optional[jefi_grid] = None, obs_points=None, stream=None):
+    """Observation view over base's resident history (see include/jefi.h)."""
+    keep = [base]
+    pts_ptr, n_obs = None, 0
+    if obs_grid is None:
+        pts = np.ascontiguousarray(obs_points, dtype=np.float64).reshape(-1, 3)
+        pts_ptr, n_obs = pts.ctypes.data, pts.shape[0]
+        keep.append(pts)
+    out = ctypes.c_void_p()
+    rc = load().jefi_create_view(base.ptr, ctypes.byref(obs_grid) if obs_grid is not None else None,
+                                 pts_ptr, n_obs, _stream_ptr(stream), ctypes.byref(out))
+    _check(rc, "jefi_create_view")
+    h = Handle(out, keep)
+    info = jefi_get_info(h)
+    h.n_obs = int(info["n_obs"])
+    h.n_src = int(info["n_src"])
+    return h

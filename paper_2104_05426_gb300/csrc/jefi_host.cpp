@@ -274,6 +274,9 @@ struct jefi_problem {
     std::vector<float2> h_tab2;
     alignas(64) CUtensorMap tmap;
     int32_t* status = nullptr;
+    // observation views share a base handle's ring and pushes
+    jefi_problem* base = nullptr;
+    int32_t n_views = 0;
     // statistics
     int64_t launches = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -555,7 +558,15 @@ struct BatchArena {
     cudaEvent_t done = nullptr;
     int n_sm = 0;
 };
-BatchArena g_arena[64];
+std::mutex g_arena_lock;
+std::map<std::pair<int, cudaStream_t>, BatchArena*> g_arenas;   // per (device, stream)
+
+BatchArena& arena_for(int dev, cudaStream_t s) {
+    std::lock_guard<std::mutex> guard(g_arena_lock);
+    BatchArena*& a = g_arenas[{dev, s}];
+    if (!a) a = new BatchArena();
+    return *a;
+}
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -628,8 +639,9 @@ void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double 
     }
 }
 
-int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
-                int64_t n_obs_in, const jefi_params* p, void* stream, jefi_handle* out) {
+static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
+                       int64_t n_obs_in, const jefi_params* p, void* stream, jefi_problem* base,
+                       jefi_handle* out) {
     if (!src || !p || !out) return JEFI_EINVAL;
     *out = nullptr;
     if (!(p->c > 0) || !std::isfinite(p->c) || !(p->dt > 0) || !std::isfinite(p->dt) ||
@@ -659,6 +671,7 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
 
     jefi_problem* h = new (std::nothrow) jefi_problem();
     if (!h) return JEFI_ENOMEM;
+    h->base = base;
     h->prm = *p;
     h->src = *src;
     h->fp64 = p->precision == JEFI_FP64;
@@ -762,13 +775,22 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
     const int64_t nlim[3] = {src->n[0], src->n[1], src->n[2]};
     const int64_t npad[3] = {h->npx, h->npy, h->npz};
     if (h->n_src > 0) {
+        // Per-axis results depend on one coordinate only; observation grids
+        // repeat each coordinate many times, so memoise them per axis.
+        std::map<double, std::pair<AxisInfo, AxisInfo>> memo[3];
         for (int64_t s = 0; s < h->n_slots; ++s) {
             AxisInfo real_ax[3], pad_ax[3];
             for (int a = 0; a < 3; ++a) {
-                pad_ax[a] = axis_info(slot_xyz[3 * s + a], src->lo[a], src->d[a], npad[a], npad[a],
-                                      h->screen[a]);
-                real_ax[a] = axis_info(slot_xyz[3 * s + a], src->lo[a], src->d[a], nlim[a], npad[a],
-                                       h->screen[a]);
+                const double x = slot_xyz[3 * s + a];
+                auto it = obs_grid ? memo[a].find(x) : memo[a].end();
+                if (it != memo[a].end()) {
+                    pad_ax[a] = it->second.first;
+                    real_ax[a] = it->second.second;
+                } else {
+                    pad_ax[a] = axis_info(x, src->lo[a], src->d[a], npad[a], npad[a], h->screen[a]);
+                    real_ax[a] = axis_info(x, src->lo[a], src->d[a], nlim[a], npad[a], h->screen[a]);
+                    if (obs_grid) memo[a][x] = {pad_ax[a], real_ax[a]};
+                }
                 scr[(2 * a) * h->n_slots + s] = pad_ax[a].rlo;
                 scr[(2 * a + 1) * h->n_slots + s] = pad_ax[a].rhi;
             }
@@ -863,6 +885,7 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
         const double A_max = h->K + 2.0;
         h->g_bias = 2.0 * (u * (2 * A_max + 2) + w_max * (eps_S / 2 + eps_rsqrt + 4 * u) +
                            u * (A_max + w_max + 2));
+        if (base && band > base->mirror) band = 0;      // a view fits the base ring's mirror
         if (band > 0 && 2 * (h->g_bias + 1e-3) < 1.0) {
             SumParams probe{};
             probe.K = h->K;
@@ -872,19 +895,25 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
             if (staged_smem_bytes(probe, band) <= 220 * 1024) h->band = band;
         }
     }
-    h->mirror = h->band;
+    if (base) {
+        h->mirror = base->mirror;
+    } else if (!h->fp64 && (p->flags & JEFI_FLAG_SHARED_RING)) {
+        h->mirror = 48;                                  // room for the widest staged band of any view
+    } else {
+        h->mirror = h->band;
+    }
     h->Hp = h->H + h->mirror + kZeroPadSlots;
 
     // ---------------------------------------------------------------- device buffers
     cudaStream_t s = (cudaStream_t)stream;
     const size_t esz = h->fp64 ? sizeof(double) : sizeof(float);
     const size_t ring_bytes = (size_t)n_cells * h->Hp * 8 * esz;
-    h->ring = dev_alloc(h, ring_bytes);
+    h->ring = base ? base->ring : dev_alloc(h, ring_bytes);
     h->obs_xyz = (double*)dev_alloc(h, sizeof(double) * slot_xyz.size());
     h->obs_scr = (int32_t*)dev_alloc(h, sizeof(int32_t) * scr.size());
     h->d_inv_perm = (int32_t*)dev_alloc(h, sizeof(int32_t) * std::max<size_t>(1, h->inv_perm.size()));
-    h->prev = (double*)dev_alloc(h, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src));
-    h->stage_in = (double*)dev_alloc(h, sizeof(double) * 8 * std::max<int64_t>(1, h->n_src));
+    h->prev = base ? base->prev : (double*)dev_alloc(h, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src));
+    h->stage_in = base ? base->stage_in : (double*)dev_alloc(h, sizeof(double) * 8 * std::max<int64_t>(1, h->n_src));
     h->partials = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * h->n_split * 6 * std::max<int32_t>(1, h->n_slots));
     h->out_stage = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * 6 * std::max<int64_t>(1, n_obs));
     h->tab32 = (float4*)dev_alloc(h, sizeof(float4) * kTimeChunk * h->K);
@@ -909,8 +938,9 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
     h->h_theta.resize((size_t)kTimeChunk * (h->K + 1));
     h->h_times.resize(kTimeChunk);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->prev, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
+    if (e == cudaSuccess && !base) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
+    if (e == cudaSuccess && !base)
+        e = cudaMemsetAsync(h->prev, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fallbacks, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && h->band > 0)
@@ -928,13 +958,29 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
         delete h;
         return JEFI_ECUDA;
     }
+    if (base) {
+        base->n_views++;
+        h->n_latest = base->n_latest;
+    }
     *out = h;
     return JEFI_OK;
 }
 
+int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
+                int64_t n_obs, const jefi_params* p, void* stream, jefi_handle* out) {
+    return create_impl(src, obs_grid, obs_points, n_obs, p, stream, nullptr, out);
+}
+
+int jefi_create_view(jefi_handle base, const jefi_grid* obs_grid, const double* obs_points,
+                     int64_t n_obs, void* stream, jefi_handle* out) {
+    if (!base || !out) return JEFI_EINVAL;
+    if (base->base) return JEFI_EINVAL;                  // views of views are not supported
+    return create_impl(&base->src, obs_grid, obs_points, n_obs, &base->prm, stream, base, out);
+}
+
 int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const double* drho,
                       const double* dJ, int on_device, void* stream) {
-    if (!h) return JEFI_EINVAL;
+    if (!h || h->base) return JEFI_EINVAL;               // views read the base's history
     const bool supplied = h->prm.deriv == JEFI_DERIV_SUPPLIED;
     if (h->n_src > 0 && (!rho || !J)) return JEFI_EINVAL;
     if (supplied != (drho != nullptr) || supplied != (dJ != nullptr)) return JEFI_EINVAL;
@@ -982,9 +1028,14 @@ int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const d
     return JEFI_OK;
 }
 
+static void sync_view(jefi_problem* h) {
+    if (h && h->base) h->n_latest = h->base->n_latest;
+}
+
 static int eval_impl(jefi_handle h, int32_t n_t, const double* t, double* E, double* B,
                      int on_device, void* stream) {
     if (!h || n_t < 0 || (n_t > 0 && !t)) return JEFI_EINVAL;
+    sync_view(h);
     if (n_t == 0 || h->n_obs == 0) return JEFI_OK;
     if (!E || !B) return JEFI_EINVAL;
     for (int i = 0; i < n_t; ++i) {
@@ -1035,6 +1086,7 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
     for (int i = 0; i < n; ++i) {
         jefi_problem* h = hs[i];
         if (!h) return JEFI_EINVAL;
+        sync_view(h);
         if (h->n_obs > 0 && (!E[i] || !B[i])) return JEFI_EINVAL;
         const int rc = check_time(h, t[i]);
         if (rc != JEFI_OK) return rc;
@@ -1114,8 +1166,7 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
 
     int dev = 0;
     JEFI_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return JEFI_EUNSUPPORTED;
-    BatchArena& arena = g_arena[dev];
+    BatchArena& arena = arena_for(dev, s);
     std::lock_guard<std::mutex> guard(arena.lock);
     {
         const int rc = arena_reserve(arena, bytes);
@@ -1182,6 +1233,7 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
 
 int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream) {
     if (!h || !slots) return JEFI_EINVAL;
+    sync_view(h);
     const int rc = check_time(h, t);
     if (rc != JEFI_OK) return rc;
     if (h->n_obs == 0 || h->n_src == 0) return JEFI_OK;
@@ -1219,6 +1271,7 @@ int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream) {
 
 int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi) {
     if (!h || !t_lo || !t_hi) return JEFI_EINVAL;
+    sync_view(h);
     if (h->n_latest < 0) return JEFI_ENOTYET;
     if (!h->any_pairs) {
         *t_lo = -INFINITY;
@@ -1266,6 +1319,7 @@ int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi) {
 
 int jefi_get_info(jefi_handle h, jefi_info* out) {
     if (!h || !out) return JEFI_EINVAL;
+    sync_view(h);
     for (auto& ev : h->ev_pending) {
         float ms = 0;
         JEFI_CUDA(cudaEventSynchronize(ev.second));
@@ -1309,7 +1363,9 @@ int jefi_reset_stats(jefi_handle h) {
 
 int jefi_destroy(jefi_handle h) {
     if (!h) return JEFI_EINVAL;
+    if (h->n_views > 0) return JEFI_EINVAL;              // destroy the views first
     cudaDeviceSynchronize();
+    if (h->base) h->base->n_views--;
     release_all(h);
     delete h;
     return JEFI_OK;

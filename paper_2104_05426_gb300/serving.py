@@ -1,0 +1,385 @@
+"""Continuous-batching serving loop for field-evaluation requests.
+
+A request asks for E and B on an observation grid at a time t, against one of
+several source problems whose histories stay resident on the GPU (the paper
+keeps rho and J on the device between calls, Sec. 2.2; here many problems and
+many requests share the device).  The loop:
+
+* keeps one base handle per source problem (FP32 compensated ring, sized for
+  views of any staged band) and pushes one new slice to every problem per
+  tick, generated on the device;
+* serves each request through an observation view of its problem (cached per
+  observation grid; a view is never in two batches at once);
+* admits arrived requests first-in first-out while the device memory of their
+  views and outputs fits the budget;
+* launches admitted requests as they come, as one jefi_eval_batch per stream,
+  on a small pool of streams, so batches that arrive while others run are
+  admitted and overlap them on the device (continuous batching);
+* orders every slice push after the in-flight batches that read the same ring
+  and every later batch after that push (CUDA events);
+* records arrival, launch and completion times; latency = completion - arrival.
+
+Every step of the field evaluation runs in libjefi's kernels; this module is
+host-side scheduling only.
+"""
+from __future__ import annotations
+
+import math
+import time
+from collections import deque
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import (JEFI_FLAG_SHARED_RING, JefiError, default_params, grid, jefi_create,
+               jefi_create_view, jefi_destroy, jefi_eval_batch, jefi_get_info, jefi_push_sources,
+               jefi_valid_window)
+
+
+@dataclass
+class Blob:
+    q: float
+    sigma: float
+    x0: Tuple[float, float, float]
+    v: Tuple[float, float, float]
+
+
+class ServedProblem:
+    """A resident source problem: a cube grid of Gaussian charges moving at constant
+    velocity, its base handle and a device-side slice generator."""
+
+    def __init__(self, side: int, half_width: float, H: int, dt: float, blobs: List[Blob],
+                 device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.side = side
+        self.L = half_width
+        self.H = H
+        self.dt = dt
+        self.blobs = blobs
+        d = 2.0 * half_width / side
+        self.grid = grid((side,) * 3, (-half_width,) * 3, (d,) * 3)
+        prm = default_params(dt=dt, history_slots=H, precision="fp32c", flags=JEFI_FLAG_SHARED_RING)
+        self.handle = jefi_create(self.grid, obs_points=np.zeros((0, 3)), params=prm, stream=stream)
+        ax = -half_width + (torch.arange(side, dtype=torch.float64, device=self.device) + 0.5) * d
+        z, y, x = torch.meshgrid(ax, ax, ax, indexing="ij")
+        self.pts = torch.stack([x.reshape(-1), y.reshape(-1), z.reshape(-1)], dim=1)
+        self.n_pushed = 0
+        self.last_push = None               # event after the latest push
+        self.readers: List = []             # events of batches reading the ring
+
+    def slice_at(self, t: float):
+        torch = self.torch
+        rho = torch.zeros(self.pts.shape[0], dtype=torch.float64, device=self.device)
+        J = torch.zeros((self.pts.shape[0], 3), dtype=torch.float64, device=self.device)
+        for b in self.blobs:
+            c = torch.tensor([b.x0[a] + b.v[a] * t for a in range(3)], dtype=torch.float64,
+                             device=self.device)
+            r2 = ((self.pts - c) ** 2).sum(dim=1)
+            g = b.q / ((2.0 * math.pi) ** 1.5 * b.sigma ** 3) * torch.exp(-0.5 * r2 / b.sigma ** 2)
+            rho += g
+            J += g[:, None] * torch.tensor(b.v, dtype=torch.float64, device=self.device)[None, :]
+        return rho, J
+
+    def push_next(self, stream):
+        """Push the next slice on `stream` after every batch still reading the ring."""
+        torch = self.torch
+        for ev in self.readers:
+            stream.wait_event(ev)
+        self.readers = []
+        with torch.cuda.stream(stream):
+            rho, J = self.slice_at(self.n_pushed * self.dt)
+            jefi_push_sources(self.handle, rho, J, stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.last_push = ev
+        self.n_pushed += 1
+
+
+@dataclass
+class Request:
+    rid: int
+    problem: int
+    obs_side: int
+    frac: float                      # position of t inside the valid window
+    arrival: float                   # seconds after the start of the run
+    t: float = math.nan
+    launch: float = math.nan
+    done: float = math.nan
+    error: int = 0
+    E: object = None
+    B: object = None
+    view: object = None
+    pairs: int = 0
+
+
+@dataclass
+class ServingStats:
+    completed: int
+    rejected: int
+    wall_s: float
+    p50_ms: float
+    p99_ms: float
+    mean_ms: float
+    requests_per_s: float
+    pairs_per_s: float
+    max_batch: int
+    mean_batch: float
+    peak_bytes: int
+    views_created: int
+    latencies_ms: List[float] = field(default_factory=list)
+
+    def as_dict(self):
+        d = dict(self.__dict__)
+        d.pop("latencies_ms")
+        return d
+
+
+class ServingEngine:
+    def __init__(self, problems: List[ServedProblem], obs_half_width: float, n_streams: int = 4,
+                 memory_budget: float = 64e9, max_batch: int = 64, tick_s: Optional[float] = None,
+                 keep_outputs: bool = False):
+        import torch
+
+        self.torch = torch
+        self.problems = problems
+        self.obs_half_width = obs_half_width
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.push_stream = torch.cuda.Stream()
+        self.memory_budget = memory_budget
+        self.max_batch = max_batch
+        self.tick_s = tick_s
+        self.keep_outputs = keep_outputs
+        self.views: Dict[Tuple[int, int], List] = {}     # (problem, side) -> [[view, busy, bytes]]
+        self.resident_bytes = sum(jefi_get_info(p.handle)["device_bytes"] for p in problems)
+        self.used_bytes = self.resident_bytes
+        self.peak_bytes = self.used_bytes
+        self.views_created = 0
+
+    # ------------------------------------------------------------------ views
+    def _acquire_view(self, req: Request):
+        key = (req.problem, req.obs_side)
+        for entry in self.views.setdefault(key, []):
+            if not entry[1]:
+                entry[1] = True
+                return entry
+        p = self.problems[req.problem]
+        s = req.obs_side
+        d = 2.0 * self.obs_half_width / s
+        g = grid((s,) * 3, (-self.obs_half_width,) * 3, (d,) * 3)
+        view = jefi_create_view(p.handle, obs_grid=g)
+        nbytes = jefi_get_info(view)["device_bytes"]
+        entry = [view, True, nbytes]
+        self.views[key].append(entry)
+        self.used_bytes += nbytes
+        self.views_created += 1
+        return entry
+
+    def _evict_idle(self, need: int):
+        """Destroy cached views that no batch is using until `need` bytes are freed."""
+        freed = 0
+        for key in list(self.views.keys()):
+            keep = []
+            for e in self.views[key]:
+                if freed < need and not e[1]:
+                    jefi_destroy(e[0])
+                    self.used_bytes -= e[2]
+                    freed += e[2]
+                else:
+                    keep.append(e)
+            self.views[key] = keep
+            if freed >= need:
+                break
+
+    def _output_bytes(self, side):
+        return side ** 3 * 6 * 8
+
+    # ------------------------------------------------------------------ run
+    def run(self, requests: List[Request]) -> ServingStats:
+        torch = self.torch
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        queue: deque = deque()
+        admitted: List[Request] = []
+        inflight: List[Tuple[object, int, List[Request]]] = []
+        free_streams = list(range(len(self.streams)))
+        done: List[Request] = []
+        batch_sizes: List[int] = []
+        rejected = 0
+        torch.cuda.synchronize()
+        start = time.perf_counter()
+        next_tick = self.tick_s if self.tick_s else math.inf
+        while pending or queue or admitted or inflight:
+            now = time.perf_counter() - start
+            progressed = False
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.popleft())
+                progressed = True
+            if now >= next_tick:
+                for p in self.problems:
+                    p.push_next(self.push_stream)
+                next_tick += self.tick_s
+                progressed = True
+            # admission, first in first out, by device memory
+            while queue:
+                req = queue[0]
+                need = self._output_bytes(req.obs_side)
+                key = (req.problem, req.obs_side)
+                has_free = any(not e[1] for e in self.views.get(key, []))
+                if not has_free:
+                    need += self._estimate_view_bytes(req)
+                if self.used_bytes + need > self.memory_budget:
+                    self._evict_idle(self.used_bytes + need - self.memory_budget)
+                if self.used_bytes + need > self.memory_budget:
+                    if not inflight and not admitted:
+                        queue.popleft()          # can never fit: reject
+                        req.error = -1
+                        rejected += 1
+                        progressed = True
+                        continue
+                    break
+                queue.popleft()
+                entry = self._acquire_view(req)
+                req.view = entry
+                req.E = torch.empty((req.obs_side ** 3, 3), dtype=torch.float64, device="cuda")
+                req.B = torch.empty_like(req.E)
+                self.used_bytes += self._output_bytes(req.obs_side)
+                self.peak_bytes = max(self.peak_bytes, self.used_bytes)
+                p = self.problems[req.problem]
+                lo, hi = jefi_valid_window(entry[0])
+                if not math.isfinite(lo):
+                    lo = hi - 4 * p.dt
+                req.t = lo + (hi - lo) * req.frac
+                req.pairs = p.side ** 3 * req.obs_side ** 3
+                admitted.append(req)
+                progressed = True
+            # launch: one batch per free stream
+            while admitted and free_streams:
+                si = free_streams.pop()
+                stream = self.streams[si]
+                batch = admitted[: self.max_batch]
+                del admitted[: len(batch)]
+                for p_idx in {r.problem for r in batch}:
+                    if self.problems[p_idx].last_push is not None:
+                        stream.wait_event(self.problems[p_idx].last_push)
+                t_launch = time.perf_counter() - start
+                try:
+                    jefi_eval_batch([r.view[0] for r in batch], [r.t for r in batch],
+                                    [r.E for r in batch], [r.B for r in batch], stream=stream)
+                    ok = True
+                except JefiError as e:
+                    ok = False
+                    for r in batch:
+                        r.error = e.code
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                for r in batch:
+                    r.launch = t_launch
+                    self.problems[r.problem].readers.append(ev)
+                inflight.append((ev, si, batch))
+                batch_sizes.append(len(batch))
+                progressed = True
+            # completion
+            still = []
+            for ev, si, batch in inflight:
+                if ev.query():
+                    t_done = time.perf_counter() - start
+                    for r in batch:
+                        r.done = t_done
+                        r.view[1] = False
+                        self.used_bytes -= self._output_bytes(r.obs_side)
+                        if r.error:
+                            rejected += 1
+                        else:
+                            done.append(r)
+                        if not self.keep_outputs:
+                            r.E = r.B = None
+                    free_streams.append(si)
+                    progressed = True
+                else:
+                    still.append((ev, si, batch))
+            inflight = still
+            if not progressed:
+                time.sleep(50e-6)
+        wall = time.perf_counter() - start
+        lat = sorted((r.done - r.arrival) * 1e3 for r in done)
+        pairs = sum(r.pairs for r in done)
+
+        def pct(q):
+            if not lat:
+                return math.nan
+            return float(np.percentile(np.asarray(lat), q))
+
+        return ServingStats(completed=len(done), rejected=rejected, wall_s=wall, p50_ms=pct(50),
+                            p99_ms=pct(99), mean_ms=float(np.mean(lat)) if lat else math.nan,
+                            requests_per_s=len(done) / wall, pairs_per_s=pairs / wall,
+                            max_batch=max(batch_sizes) if batch_sizes else 0,
+                            mean_batch=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+                            peak_bytes=int(self.peak_bytes), views_created=self.views_created,
+                            latencies_ms=lat)
+
+    def _estimate_view_bytes(self, req: Request) -> int:
+        # partial sums dominate: 8 time slots x splits x 6 x points x 8 B, splits ~ 2 waves / tiles
+        n = req.obs_side ** 3
+        tiles = max(1, (n + 255) // 256)
+        splits = max(1, min(608 // tiles, 64))
+        return int(8 * splits * 6 * tiles * 256 * 8 + n * 3 * 8 * 2 + (1 << 20))
+
+    def close(self):
+        self.torch.cuda.synchronize()
+        for entries in self.views.values():
+            for e in entries:
+                jefi_destroy(e[0])
+        self.views = {}
+        for p in self.problems:
+            jefi_destroy(p.handle)
+
+
+def make_problems(n: int, seed: int, sides=(16, 64), H_range=(64, 256), half_width=1.0,
+                  obs_half_width=2.0, stream=None) -> List[ServedProblem]:
+    """Seeded resident problems: cubic source grids over [-L,L]^3 with 1-4
+    moving Gaussian charges; dt chosen so H slices just cover the pairs of an
+    observation grid over [-2L,2L]^3.  Pushes H slices into each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(n):
+        side = int(rng.integers(sides[0], sides[1] + 1))
+        H = int(rng.integers(H_range[0], H_range[1] + 1))
+        rmax = math.sqrt(3.0) * (half_width + obs_half_width)
+        dt = rmax / (H - 8)
+        blobs = []
+        for _ in range(int(rng.integers(1, 5))):
+            v = rng.standard_normal(3)
+            v *= rng.uniform(0.0, 0.5) / np.linalg.norm(v)
+            blobs.append(Blob(float(rng.choice([-1.0, 1.0])), float(rng.uniform(0.15, 0.35)),
+                              tuple(rng.uniform(-0.2, 0.2, 3) - v * H * dt * 0.5), tuple(v)))
+        p = ServedProblem(side, half_width, H, dt, blobs)
+        out.append(p)
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    for p in out:
+        for _ in range(p.H + 1):          # one past the ring: the oldest slice is evicted
+            p.push_next(s)
+    torch.cuda.synchronize()
+    return out
+
+
+def poisson_requests(n: int, rate: float, n_problems: int, obs_sides=(8, 48), seed: int = 7,
+                     side_choices: Optional[List[int]] = None) -> List[Request]:
+    """Seeded Poisson arrivals at `rate` per second; uniform problem, side and
+    position in the valid window."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, n)
+    arrivals = np.cumsum(gaps)
+    reqs = []
+    for i in range(n):
+        if side_choices:
+            side = int(side_choices[int(rng.integers(0, len(side_choices)))])
+        else:
+            side = int(rng.integers(obs_sides[0], obs_sides[1] + 1))
+        reqs.append(Request(i, int(rng.integers(0, n_problems)), side, float(rng.uniform(0.05, 0.95)),
+                            float(arrivals[i])))
+    return reqs

@@ -1,0 +1,46 @@
+"""Serving loop: continuous batching of field-evaluation requests against
+resident source problems.  Each result is bit-identical to evaluating the same
+view at the same time alone; admission respects the memory budget; pushes
+interleave safely with in-flight batches."""
+import numpy as np
+import pytest
+
+import paper_2104_05426_gb300 as jefi
+from paper_2104_05426_gb300.serving import ServingEngine, make_problems, poisson_requests
+
+pytestmark = pytest.mark.gpu
+
+
+def test_served_results_equal_single_evaluations(gpu):
+    import torch
+
+    probs = make_problems(3, seed=1, sides=(8, 14), H_range=(40, 56))
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=3, max_batch=8, tick_s=None,
+                        keep_outputs=True)
+    reqs = poisson_requests(48, rate=5000.0, n_problems=3, seed=3, side_choices=[4, 6, 8, 9])
+    stats = eng.run(reqs)
+    assert stats.completed == len(reqs) and stats.rejected == 0
+    assert stats.max_batch > 1                       # requests were batched together
+    for r in reqs:
+        E = torch.empty_like(r.E)
+        B = torch.empty_like(r.B)
+        jefi.jefi_eval_fields(r.view[0], r.t, E, B)
+        torch.cuda.synchronize()
+        assert torch.equal(E, r.E) and torch.equal(B, r.B), r.rid
+        assert jefi.jefi_get_info(r.view[0])["device_status"] == 0
+    eng.close()
+
+
+def test_serving_with_pushes_and_memory_budget(gpu):
+    probs = make_problems(3, seed=2, sides=(8, 12), H_range=(40, 48))
+    resident = sum(jefi.jefi_get_info(p.handle)["device_bytes"] for p in probs)
+    budget = resident + 24 * (1 << 20)               # room for a few views at a time
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=2, max_batch=6, tick_s=0.003,
+                        memory_budget=budget)
+    reqs = poisson_requests(60, rate=800.0, n_problems=3, seed=4, side_choices=[4, 6, 8])
+    stats = eng.run(reqs)
+    assert stats.completed + stats.rejected == len(reqs)
+    assert stats.completed >= len(reqs) // 2
+    assert stats.peak_bytes <= budget
+    assert np.isfinite(stats.p50_ms) and stats.p99_ms >= stats.p50_ms
+    eng.close()
