@@ -133,7 +133,8 @@ int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* o
  * views let many observation regions use one resident history.
  * obs_grid / obs_points / n_obs as in jefi_create.  Destroy every view of a
  * base before the base (jefi_destroy of a base with live views returns
- * JEFI_EINVAL).  Pushing to a view returns JEFI_EINVAL.  A view uses the
+ * JEFI_EINVAL).  Pushing to a view returns JEFI_EINVAL.  A view keeps
+ * scratch for 2 evaluation times per launch (a base handle for 8).  A view uses the
  * staged kernel only if its band fits the base ring's mirror (create the
  * base with JEFI_FLAG_SHARED_RING).
  */
@@ -179,7 +180,8 @@ int jefi_eval_fields_multi(jefi_handle h, int32_t n_t, const double* t, double* 
  * jefi_eval_fields (Eqs. E-1, B-1, tr-1 for every problem).
  *
  * hs[n], t[n]: problem i is evaluated at time t[i] (a handle may appear up
- *   to 8 times).  E[i], B[i]: device [N_obs_i][3] FP64 outputs.
+ *   to 8 times, a view up to 2 times).  E[i], B[i]: device [N_obs_i][3]
+ *   FP64 outputs.
  * Asynchronous on `stream`.  Every problem's result is bit-identical to
  * jefi_eval_fields on the same handle and time: the work items run the same
  * code in the same order whatever else is in the batch.  Batches issued on
@@ -229,6 +231,15 @@ int jefi_reset_stats(jefi_handle h);
  * screened pairs are INT32_MIN.  Intended for small problems.
  */
 int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream);
+
+/*
+ * Diagnostic of the bounded device waits: launches a kernel that waits on a
+ * barrier nothing completes, with the same bounded wait the staged sum
+ * kernel uses for its TMA copies, limited to limit_s seconds (0 < limit_s
+ * <= 10).  Returns JEFI_ETIMEOUT when the wait expired and was reported
+ * (the expected outcome), JEFI_OK if it did not expire.
+ */
+int jefi_debug_wait_timeout(double limit_s, void* stream);
 
 /*
  * Host reference of the exact slot rule above for explicit pairs (no GPU

@@ -52,7 +52,8 @@ PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval_fields",
            "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info", "jefi_reset_stats",
            "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror",
-           "jefi_eval_fields_noalloc", "jefi_eval_batch", "jefi_create_view")
+           "jefi_eval_fields_noalloc", "jefi_eval_batch", "jefi_create_view",
+           "jefi_debug_wait_timeout")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -130,6 +131,8 @@ def load(build_if_needed: bool = True):
         L.jefi_eval_batch.argtypes = [P, P, P, P, I32, P]
         L.jefi_create_view.argtypes = [P, ctypes.POINTER(jefi_grid), P, I64, P, ctypes.POINTER(P)]
         L.jefi_create_view.restype = I
+        L.jefi_debug_wait_timeout.argtypes = [D, P]
+        L.jefi_debug_wait_timeout.restype = I
         L.jefi_eval_batch.restype = I
         L.jefi_eval_fields_noalloc.argtypes = [ctypes.POINTER(jefi_grid), P, I64, P, P, I64,
                                                ctypes.POINTER(jefi_params), D, P, P, P]
@@ -422,3 +425,8 @@ def jefi_create_view(base: Handle, obs_grid: Optional[jefi_grid] = None, obs_poi
     h.n_obs = int(info["n_obs"])
     h.n_src = int(info["n_src"])
     return h
+
+
+def jefi_debug_wait_timeout(limit_s: float, stream=None) -> int:
+    """Status of a bounded device wait that nothing completes (JEFI_ETIMEOUT expected)."""
+    return int(load().jefi_debug_wait_timeout(float(limit_s), _stream_ptr(stream)))

@@ -26,7 +26,8 @@ using namespace jefi;
 
 namespace {
 
-constexpr int kTimeChunk = 8;      // evaluation times per sum launch
+constexpr int kTimeChunk = 8;      // evaluation times per sum launch (base handles)
+constexpr int kViewTimeChunk = 2;  // views keep scratch for fewer times
 constexpr int kTablePad = 3;       // candidate-table margin on each side (slots)
 constexpr double kSafety = 2.0;    // factor on the FP32 squared-distance error bound
 constexpr int kMaxEventPairs = 4096;
@@ -252,8 +253,9 @@ struct jefi_problem {
     int32_t* d_inv_perm = nullptr;
     double* prev = nullptr;
     double* stage_in = nullptr;      // host pushes: rho, J, drho, dJ
-    double* partials = nullptr;      // [kTimeChunk][n_split][6][n_slots]
-    double* out_stage = nullptr;     // host outputs: E, B for kTimeChunk times
+    int32_t time_chunk = kTimeChunk; // evaluation times per launch (scratch slots)
+    double* partials = nullptr;      // [time_chunk][n_split][6][n_slots]
+    double* out_stage = nullptr;     // host outputs: E, B for time_chunk times
     float4* tab32 = nullptr;
     double* theta = nullptr;
     TimeParams* times = nullptr;
@@ -672,6 +674,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     jefi_problem* h = new (std::nothrow) jefi_problem();
     if (!h) return JEFI_ENOMEM;
     h->base = base;
+    h->time_chunk = base ? kViewTimeChunk : kTimeChunk;
     h->prm = *p;
     h->src = *src;
     h->fp64 = p->precision == JEFI_FP64;
@@ -914,18 +917,18 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->d_inv_perm = (int32_t*)dev_alloc(h, sizeof(int32_t) * std::max<size_t>(1, h->inv_perm.size()));
     h->prev = base ? base->prev : (double*)dev_alloc(h, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src));
     h->stage_in = base ? base->stage_in : (double*)dev_alloc(h, sizeof(double) * 8 * std::max<int64_t>(1, h->n_src));
-    h->partials = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * h->n_split * 6 * std::max<int32_t>(1, h->n_slots));
-    h->out_stage = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * 6 * std::max<int64_t>(1, n_obs));
-    h->tab32 = (float4*)dev_alloc(h, sizeof(float4) * kTimeChunk * h->K);
-    h->theta = (double*)dev_alloc(h, sizeof(double) * kTimeChunk * (h->K + 1));
-    h->times = (TimeParams*)dev_alloc(h, sizeof(TimeParams) * kTimeChunk);
+    h->partials = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * h->n_split * 6 * std::max<int32_t>(1, h->n_slots));
+    h->out_stage = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * 6 * std::max<int64_t>(1, n_obs));
+    h->tab32 = (float4*)dev_alloc(h, sizeof(float4) * h->time_chunk * h->K);
+    h->theta = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * (h->K + 1));
+    h->times = (TimeParams*)dev_alloc(h, sizeof(TimeParams) * h->time_chunk);
     h->fallbacks = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
     h->status = (int32_t*)dev_alloc(h, sizeof(int32_t));
     if (h->band > 0) {
         h->tile_box = (float*)dev_alloc(h, sizeof(float) * tile_box.size());
-        h->tab2 = (float2*)dev_alloc(h, sizeof(float2) * kTimeChunk * (h->K + 2 * kTabGuard));
+        h->tab2 = (float2*)dev_alloc(h, sizeof(float2) * h->time_chunk * (h->K + 2 * kTabGuard));
         if (!h->tile_box || !h->tab2) h->status = nullptr;
-        h->h_tab2.resize((size_t)kTimeChunk * (h->K + 2 * kTabGuard));
+        h->h_tab2.resize((size_t)h->time_chunk * (h->K + 2 * kTabGuard));
     }
     if (!h->ring || !h->obs_xyz || !h->obs_scr || !h->d_inv_perm || !h->prev || !h->stage_in ||
         !h->partials || !h->out_stage || !h->tab32 || !h->theta || !h->times || !h->fallbacks ||
@@ -934,9 +937,9 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         delete h;
         return JEFI_ENOMEM;
     }
-    h->h_tab.resize((size_t)kTimeChunk * h->K);
-    h->h_theta.resize((size_t)kTimeChunk * (h->K + 1));
-    h->h_times.resize(kTimeChunk);
+    h->h_tab.resize((size_t)h->time_chunk * h->K);
+    h->h_theta.resize((size_t)h->time_chunk * (h->K + 1));
+    h->h_times.resize(h->time_chunk);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess && !base) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
     if (e == cudaSuccess && !base)
@@ -1044,10 +1047,10 @@ static int eval_impl(jefi_handle h, int32_t n_t, const double* t, double* E, dou
     }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t per_t = (size_t)h->n_obs * 3;
-    for (int base = 0; base < n_t; base += kTimeChunk) {
-        const int m = std::min(kTimeChunk, n_t - base);
+    for (int base = 0; base < n_t; base += h->time_chunk) {
+        const int m = std::min(h->time_chunk, n_t - base);
         double* Ed = on_device ? E + base * per_t : h->out_stage;
-        double* Bd = on_device ? B + base * per_t : h->out_stage + kTimeChunk * per_t;
+        double* Bd = on_device ? B + base * per_t : h->out_stage + h->time_chunk * per_t;
         if (!h->any_pairs) {
             JEFI_CUDA(cudaMemsetAsync(Ed, 0, sizeof(double) * per_t * m, s));
             JEFI_CUDA(cudaMemsetAsync(Bd, 0, sizeof(double) * per_t * m, s));
@@ -1091,7 +1094,7 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
         const int rc = check_time(h, t[i]);
         if (rc != JEFI_OK) return rc;
         occ[i] = count[h]++;
-        if (occ[i] >= kTimeChunk) return JEFI_EUNSUPPORTED;   // a handle at most 8 times per batch
+        if (occ[i] >= h->time_chunk) return JEFI_EUNSUPPORTED;   // scratch slots per handle
     }
     for (int i = 0; i < n; ++i)
         if (hs[i]->any_pairs && hs[i]->n_obs > 0) build_tables(hs[i], occ[i], t[i]);
@@ -1267,6 +1270,21 @@ int jefi_debug_slots(jefi_handle h, double t, int32_t* slots, void* stream) {
         }
     }
     return JEFI_OK;
+}
+
+int jefi_debug_wait_timeout(double limit_s, void* stream) {
+    if (!(limit_s > 0) || !(limit_s <= 10.0)) return JEFI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t* d = nullptr;
+    JEFI_CUDA(cudaMalloc(&d, sizeof(int32_t)));
+    int32_t st = -1;
+    cudaError_t e = cudaMemsetAsync(d, 0xff, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_wait_timeout_probe(d, (uint64_t)(limit_s * 1e9), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return JEFI_ECUDA;
+    return st;
 }
 
 int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi) {

@@ -66,13 +66,13 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wait for the phase with the given parity; false if it has not completed
-// after kWaitLimitNs.
-__device__ __noinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
+// after limit_ns.
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(a, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 1; it != 0; ++it) {
         if (mbar_try_wait(a, parity)) return true;
-        if ((it & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+        if ((it & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -477,6 +477,24 @@ __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_staged_batch(const __
         const int tile = r - split * p.n_tiles;
         if (!staged_item<BAND, EXACT, false>(&a.maps[lo], p, p.comp, tile, split, ti, g_it)) break;
     }
+}
+
+// Diagnostic: wait on an mbarrier that nothing arrives at, with the same
+// bounded wait as the staged kernel, and report the outcome in *status.
+__global__ void wait_timeout_probe(int32_t* status, uint64_t limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(smem_u32(&bar), 0, limit_ns);
+    if (threadIdx.x == 0) *status = ok ? 0 : kStatusTimeout;
+}
+
+cudaError_t launch_wait_timeout_probe(int32_t* status, uint64_t limit_ns, cudaStream_t s) {
+    wait_timeout_probe<<<1, 32, 0, s>>>(status, limit_ns);
+    return cudaGetLastError();
 }
 
 bool staged_band_supported(int band) { return band == 16 || band == 24 || band == 32 || band == 48; }

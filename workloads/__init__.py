@@ -331,3 +331,20 @@ def c4_batch(n_problems: int = 256, seed: int = 4, src_sides=(8, 48), obs_sides=
         out.append(Problem(f"C4-{k}", src, obs, None, dt, H, H, [t_eval], MovingGaussians(moved),
                            t0=t0))
     return out
+
+
+def e1_constant(H: int = 256, n_push: int = 160) -> Problem:
+    """Paper Sec. 3.1: step-on constant sources rho = 1, J = (1,1,1) for t >= 0;
+    15^3 source and observation cells over [-3,3]^3 (cell 0.4), screening
+    half-width 0.2 (half a cell), snapshots t = 2.5, 5, 7.5, dt = 0.05."""
+    g = Grid.cube(15, -3.0, 3.0)
+    return Problem("E1", g, g, None, 0.05, H, n_push, [2.5, 5.0, 7.5], StepConstant())
+
+
+def e2_sinusoidal(H: int = 300, n_push: int = 200) -> Problem:
+    """Paper Sec. 3.2: rho = 3(cos t - 1) cos(x+y+z), J_a = sin(x+y+z) sin t for
+    t >= 0; sources 15^3 over [-3,3]^3, observers 15^3 over [-3,3]^2 x [10,16],
+    dt = 0.05."""
+    src = Grid.cube(15, -3.0, 3.0)
+    obs = Grid.box((15, 15, 15), (-3.0, -3.0, 10.0), (3.0, 3.0, 16.0))
+    return Problem("E2", src, obs, None, 0.05, H, n_push, [10.0, 12.5, 15.0], Sinusoidal())
