@@ -407,7 +407,7 @@ def run_reference(args):
     sample = (f"every {stride}th of {p.n_obs} observation points x {p.src.size} sources x "
               f"{len(times)} times = {pairs_step:.3e} pairs per step")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_s * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",

@@ -168,11 +168,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     float tbox[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) tbox[a] = tid == 0 ? p.tile_box[(size_t)tile * 6 + a] : 0.f;
-    auto issue = [&](int b, int bufi) {
-        const int bx = b % p.nbx;
-        const int rest = b / p.nbx;
-        const int by = rest % p.nby;
-        const int bz = rest / p.nby;
+    auto issue = [&](int bx, int by, int bz, int b, int bufi) {
         const float cb[3] = {-s_D[bx], -s_D[p.nbx + by], -s_D[nbxy + bz]};
         const float dd[3] = {d32x, d32y, d32z};
         float mn2 = 0.f, mx2 = 0.f, span = 0.f;
@@ -214,18 +210,32 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
     const uint32_t tbase = L::kTab + (uint32_t)(kTabGuard - kMagicBits) * 8u;
 
-    if (tid == 0 && b_begin < b_end) issue(b_begin, g_it & 1);
+    if (tid == 0 && b_begin < b_end) {
+        const int rest = b_begin / p.nbx;
+        issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, g_it & 1);
+    }
     int64_t aborted_at = -1;
+    // brick coordinates of b, advanced incrementally (no division per brick)
+    int bx = 0, by = 0, bz = 0;
+    if (b_begin < b_end) {
+        bx = b_begin % p.nbx;
+        const int rest = b_begin / p.nbx;
+        by = rest % p.nby;
+        bz = rest / p.nby;
+    }
     for (int b = b_begin; b < b_end; ++b) {
         const uint32_t it = g_it + (uint32_t)(b - b_begin);
         const int buf = it & 1;
-        if (tid == 0 && b + 1 < b_end) issue(b + 1, buf ^ 1);
+        if (tid == 0 && b + 1 < b_end) {
+            int nx = bx + 1, ny = by, nz = bz;
+            if (nx == p.nbx) {
+                nx = 0;
+                if (++ny == p.nby) { ny = 0; ++nz; }
+            }
+            issue(nx, ny, nz, b + 1, buf ^ 1);
+        }
         const bool ready = mbar_wait_bounded(mbar_u32[buf], (it >> 1) & 1);
         if (ready) {
-            const int bx = b % p.nbx;
-            const int rest = b / p.nbx;
-            const int by = rest % p.nby;
-            const int bz = rest / p.nby;
             const int band_rel = s_band[buf];
             const float Px = oox + s_D[bx];
             const float Py = ooy + s_D[p.nbx + by];
@@ -273,20 +283,25 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                             float ri = rsqrtf(S);
                             const float u = fmaf(-(S * ri), K32, Ag);
                             const uint32_t bits = __float_as_uint(__fadd_rd(u, kMagic));
-                            const float2 th = *reinterpret_cast<const float2*>(smem + (tbase + bits * 8u));
-                            const bool lower = S > th.y;
-                            if (!EXACT) {
+                            bool lower;
+                            if (EXACT) {
+                                // T_hi == T_lo: one 32-bit threshold decides
+                                const float th = *reinterpret_cast<const float*>(smem + (tbase + 4u + bits * 8u));
+                                lower = S > th;
+                            } else {
+                                const float2 th = *reinterpret_cast<const float2*>(smem + (tbase + bits * 8u));
+                                lower = S > th.y;
                                 if (!(S <= th.x) && !lower) {   // undecided: redo after the brick
                                     mask |= 1ull << (k * 16 + c16);
                                     ri = 0.f;
                                 }
                             }
+                            const uint32_t sel = bits - (lower ? 1u : 0u);   // candidate slot k' or k'-1
                             if (DEBUG) {
                                 p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + k * 16 + c16] =
-                                    (int)(tp.k0 + (int)(bits - kMagicBits) - (lower ? 1 : 0));
+                                    (int)(tp.k0 + (int)(sel - kMagicBits));
                             }
-                            const uint32_t off = gk + bits * L::kRowBytes + (uint32_t)c16 * L::kCellBytes -
-                                                 (lower ? L::kRowBytes : 0u);
+                            const uint32_t off = gk + sel * L::kRowBytes + (uint32_t)c16 * L::kCellBytes;
                             const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
                             const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
                             // Eqs. E-1/B-1 with packed pairs:
@@ -410,6 +425,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     sb[a] += pb[a];
                 }
             }
+        }
+        if (++bx == p.nbx) {
+            bx = 0;
+            if (++by == p.nby) { by = 0; ++bz; }
         }
         // every thread is done with this buffer before it is refilled
         if (__syncthreads_or(!ready)) {
