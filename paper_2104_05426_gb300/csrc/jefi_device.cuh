@@ -59,6 +59,16 @@ static __device__ __forceinline__ unsigned candidate_index(float S, float ri, fl
     return min(idx, (unsigned)(K - 1));
 }
 
+// 1/sqrt(x) by rsqrt.approx.ftz.f32.  For normal x it returns what rsqrtf
+// returns; it leaves out rsqrtf's rescaling of subnormal inputs.  The FP32
+// kernels only see S >= 1e-30 (jefi_create rejects FP32 problems with closer
+// unscreened pairs) or S = 0 on screened pairs, whose result is discarded.
+static __device__ __forceinline__ float rsqrt_ftz(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 static __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     const float y = x - c;
     const float t = s + y;

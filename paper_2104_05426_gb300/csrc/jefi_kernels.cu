@@ -108,7 +108,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                                           __fmul_rn(dz, dz));
                 const bool scr = (ix >= ctx.rlo[0]) & (ix <= ctx.rhi[0]) & (iy >= ctx.rlo[1]) &
                                  (iy <= ctx.rhi[1]) & (iz >= ctx.rlo[2]) & (iz <= ctx.rhi[2]);
-                float ri = rsqrtf(S);
+                float ri = rsqrt_ftz(S);
                 unsigned idx = candidate_index(S, ri, K32, A, K);
                 float4 e = s_tab[idx];
                 bool ok = scr | ((S <= e.x) & (S > e.y));
@@ -155,7 +155,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                     for (int i = 0; i < 4; ++i) {
                         const int cl = k * 16 + j * 4 + i;
                         const float S = __fadd_rn(sxy[j * 4 + i], sqz[k]);
-                        const float ri = rsqrtf(S);
+                        const float ri = rsqrt_ftz(S);
                         unsigned idx = candidate_index(S, ri, K32, A, K);
                         float4 e = s_tab[idx];
                         const bool ok = (S <= e.x) & (S > e.y);

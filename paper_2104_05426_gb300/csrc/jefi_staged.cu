@@ -280,7 +280,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         for (int i = 0; i < 4; ++i) {
                             const int c16 = j * 4 + i;
                             const float S = __fadd_rn(sqx[i], syz);
-                            float ri = rsqrtf(S);
+                            float ri = rsqrt_ftz(S);
                             const float u = fmaf(-(S * ri), K32, Ag);
                             const uint32_t bits = __float_as_uint(__fadd_rd(u, kMagic));
                             bool lower;
@@ -348,7 +348,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                             const float dz = fmaf(-(float)k, d32z, Pz);
                             const float S = __fadd_rn(__fmul_rn(dx, dx),
                                                       __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-                            const float ri = rsqrtf(S);
+                            const float ri = rsqrt_ftz(S);
                             const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
                             const int idx = slot_fallback_f32(
                                 p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
@@ -386,7 +386,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     const float dz = fmaf(-(float)k, d32z, Pz);
                     const float S = __fadd_rn(__fmul_rn(dx, dx),
                                               __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-                    float ri = rsqrtf(S);
+                    float ri = rsqrt_ftz(S);
                     const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
                     const uint32_t tix = min(bits - (uint32_t)kMagicBits + (uint32_t)kTabGuard, (uint32_t)(KT - 1));
                     const float2 th = s_tab[tix];
