@@ -77,6 +77,13 @@ __device__ __noinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity, uint
     return false;
 }
 
+// ~0u if a > b, else 0 (false for NaN operands)
+__device__ __forceinline__ uint32_t gt_mask(float a, float b) {
+    uint32_t r;
+    asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             int c2, uint32_t mbar) {
     asm volatile(
@@ -283,37 +290,38 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                             float ri = rsqrt_ftz(S);
                             const float u = fmaf(-(S * ri), K32, Ag);
                             const uint32_t bits = __float_as_uint(__fadd_rd(u, kMagic));
-                            bool lower;
+                            // row of candidate k' (bits), moved down one row when S is past
+                            // the threshold: lower = 0 or ~0u
+                            const uint32_t row_hi = gk + bits * L::kRowBytes;
+                            uint32_t lower;
                             if (EXACT) {
                                 // T_hi == T_lo: one 32-bit threshold decides
                                 const float th = *reinterpret_cast<const float*>(smem + (tbase + 4u + bits * 8u));
-                                lower = S > th;
+                                lower = gt_mask(S, th);
                             } else {
                                 const float2 th = *reinterpret_cast<const float2*>(smem + (tbase + bits * 8u));
-                                lower = S > th.y;
-                                if (!(S <= th.x) && !lower) {   // undecided: redo after the brick
+                                lower = gt_mask(S, th.y);
+                                if (!(S <= th.x) && lower == 0u) {   // undecided: redo after the brick
                                     mask |= 1ull << (k * 16 + c16);
                                     ri = 0.f;
                                 }
                             }
-                            const uint32_t sel = bits - (lower ? 1u : 0u);   // candidate slot k' or k'-1
                             if (DEBUG) {
                                 p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + k * 16 + c16] =
-                                    (int)(tp.k0 + (int)(sel - kMagicBits));
+                                    (int)(tp.k0 + (int)(bits + lower - kMagicBits));
                             }
-                            const uint32_t off = gk + sel * L::kRowBytes + (uint32_t)c16 * L::kCellBytes;
+                            const uint32_t off = row_hi + lower * L::kRowBytes + (uint32_t)c16 * L::kCellBytes;
                             const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
                             const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
-                            // Eqs. E-1/B-1 with packed pairs:
-                            //   (q, Vx) = (drho, dJx/c) r^-2 + (c rho, Jx) r^-3,  q the D-term of E
-                            //   (Vy, Vz) = (dJy, dJz)/c r^-2 + (Jy, Jz) r^-3
+                            // Eqs. E-1/B-1 with packed pairs, r^-2 factored out:
+                            //   (q, Vx) = ((drho, dJx/c) + (c rho, Jx) r^-1) r^-2,  q the D-term of E
+                            //   (Vy, Vz) = ((dJy, dJz)/c + (Jy, Jz) r^-1) r^-2
                             const float2 ri2 = make_float2(ri, ri);
                             const float2 r2 = __fmul2_rn(ri2, ri2);
-                            const float2 r3 = __fmul2_rn(r2, ri2);
-                            const float2 qvx = __ffma2_rn(make_float2(v1.x, v1.y), r2,
-                                                          __fmul2_rn(make_float2(v0.x, v0.y), r3));
-                            const float2 vyz = __ffma2_rn(make_float2(v1.z, v1.w), r2,
-                                                          __fmul2_rn(make_float2(v0.z, v0.w), r3));
+                            const float2 qvx = __fmul2_rn(__ffma2_rn(make_float2(v0.x, v0.y), ri2,
+                                                                     make_float2(v1.x, v1.y)), r2);
+                            const float2 vyz = __fmul2_rn(__ffma2_rn(make_float2(v0.z, v0.w), ri2,
+                                                                     make_float2(v1.z, v1.w)), r2);
                             const float q = qvx.x, vx = qvx.y;
                             // E' += D q - (dJ/c) / R
                             acc_ex = fmaf(ddx[i], q, acc_ex);
