@@ -53,6 +53,9 @@ def _load():
             lib.oracle_fields.restype = ctypes.c_int
             lib.oracle_fields.argtypes = [P, P, P, I64, P, I64, P, P, P, P,
                                           D, D, D, D, D, P, D, P, P, P, P, P, ctypes.c_int]
+            lib.oracle_fields_interp.restype = ctypes.c_int
+            lib.oracle_fields_interp.argtypes = [P, P, P, I64, P, I64, P, P, P, P,
+                                                 D, D, D, D, D, P, D, P, P, ctypes.c_int]
             lib.oracle_all_slots.restype = None
             lib.oracle_all_slots.argtypes = [P, P, P, I64, P, D, D, D, P, D, P, ctypes.c_int]
             lib.oracle_pair_slots.restype = None
@@ -132,6 +135,45 @@ def fields(src_n, src_lo, src_d, obs, rho, J, *, c=1.0, k_e=1.0, k_b=1.0, dt, t0
     if with_slots:
         out.append((int(sr[0]), int(sr[1])))
     return tuple(out)
+
+
+def fields_interp(src_n, src_lo, src_d, obs, rho, J, *, c=1.0, k_e=1.0, k_b=1.0, dt, t0=0.0,
+                  screen=None, t, drho=None, dJ=None, threads=0):
+    """Second-order variant of ``fields``: sources linearly interpolated
+    between slices n and n+1 at the retarded time, derivatives supplied or
+    central differences (f[k+1] - f[k-1]) / (2 dt), both interpolated; slices
+    before the first are zero.  Needs slices up to n+1 (supplied) or n+2
+    (central); raises ``ValueError`` otherwise.
+    """
+    lib = _load()
+    src_n = np.ascontiguousarray(src_n, dtype=np.int32).reshape(3)
+    src_lo = _f64(src_lo, (3,))
+    src_d = _f64(src_d, (3,))
+    obs = _f64(obs, (-1, 3))
+    Ns = int(np.prod(src_n))
+    rho = _f64(rho, (-1, Ns))
+    n_slices = rho.shape[0]
+    J = _f64(J, (n_slices, Ns, 3))
+    if (drho is None) != (dJ is None):
+        raise ValueError("supply both drho and dJ, or neither")
+    if drho is not None:
+        drho = _f64(drho, (n_slices, Ns))
+        dJ = _f64(dJ, (n_slices, Ns, 3))
+    if screen is None:
+        screen = src_d / 2.0
+    screen = _f64(screen, (3,))
+    n_obs = obs.shape[0]
+    E = np.zeros((n_obs, 3))
+    B = np.zeros((n_obs, 3))
+    rc = lib.oracle_fields_interp(_ptr(src_n), _ptr(src_lo), _ptr(src_d), n_obs, _ptr(obs),
+                                  n_slices, _ptr(rho), _ptr(J), _ptr(drho), _ptr(dJ),
+                                  float(c), float(k_e), float(k_b), float(dt), float(t0),
+                                  _ptr(screen), float(t), _ptr(E), _ptr(B), int(threads))
+    if rc == ENOTYET:
+        raise ValueError("oracle: time t needs a slice beyond the history")
+    if rc != 0:
+        raise ValueError(f"oracle: invalid arguments (code {rc})")
+    return E, B
 
 
 def all_slots(src_n, src_lo, src_d, obs, *, c=1.0, dt, t0=0.0, screen=None, t, threads=0):

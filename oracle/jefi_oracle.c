@@ -233,6 +233,130 @@ int oracle_fields(const int32_t* src_n, const double* src_lo, const double* src_
 }
 
 /*
+ * Second-order variant (opt-in in the library): the same sum, with the
+ * sources read at the retarded time itself instead of at the slice it falls
+ * in.  With u = ((t - t0) - R/c) / dt (the floor argument above, same FP64
+ * sequence), n = floor(u) and w = u - n:
+ *
+ *   f(t_r)  = (1 - w) f[n] + w f[n+1]                  linear interpolation
+ *   f'(t_r) = (1 - w) f'[n] + w f'[n+1]
+ *
+ * where f'[k] is the supplied derivative or the central difference
+ * (f[k+1] - f[k-1]) / (2 dt).  Slices before the first are zero, values and
+ * derivatives alike: f[k] = f'[k] = 0 for k < 0 (so f'[0] = f[1] / (2 dt)).
+ * Linear interpolation and the central difference are both exact for
+ * sources linear in time, and the interpolated central difference is exact
+ * for sources quadratic in time.
+ *
+ * Needs slices up to n+1 (supplied) or n+2 (central); returns
+ * ORACLE_ENOTYET otherwise.  Arguments as oracle_fields.
+ */
+static double hist_at(const double* f, int64_t stride, int64_t k, int64_t cell, int comp) {
+    return k < 0 ? 0.0 : f[(k * stride + cell) * (comp < 0 ? 1 : 3) + (comp < 0 ? 0 : comp)];
+}
+
+int oracle_fields_interp(const int32_t* src_n, const double* src_lo, const double* src_d,
+                         int64_t n_obs, const double* obs,
+                         int64_t n_slices, const double* rho, const double* J,
+                         const double* drho, const double* dJ,
+                         double c, double k_e, double k_b, double dt, double t0,
+                         const double* screen, double t,
+                         double* E, double* B, int nthreads) {
+    if (!(c > 0.0) || !(dt > 0.0) || n_slices < 0) return ORACLE_EINVAL;
+    const int64_t nx = src_n[0], ny = src_n[1], nz = src_n[2];
+    const int64_t Ns = nx * ny * nz;
+    const double dV = src_d[0] * src_d[1] * src_d[2];
+    const double T = t - t0;
+    const int supplied = drho != NULL && dJ != NULL;
+    const int64_t need_ahead = supplied ? 1 : 2;   /* last slice read beyond n */
+    int err = ORACLE_OK;
+
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int64_t o = 0; o < n_obs; ++o) {
+        const double xo = obs[3 * o + 0], yo = obs[3 * o + 1], zo = obs[3 * o + 2];
+        nsum e[3] = {{0, 0}, {0, 0}, {0, 0}};
+        nsum b[3] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int64_t k = 0; k < nz; ++k) {
+            const double dz = zo - oracle_cell_center(src_lo[2], src_d[2], k);
+            for (int64_t j = 0; j < ny; ++j) {
+                const double dy = yo - oracle_cell_center(src_lo[1], src_d[1], j);
+                for (int64_t i = 0; i < nx; ++i) {
+                    const double dx = xo - oracle_cell_center(src_lo[0], src_d[0], i);
+                    if (fabs(dx) <= screen[0] && fabs(dy) <= screen[1] && fabs(dz) <= screen[2])
+                        continue;
+                    const double S = sq_dist(dx, dy, dz);
+                    const double R = sqrt(S);
+                    const double u = (T - R / c) / dt;
+                    const double fl = floor(u);
+                    const int64_t n = (int64_t)fl;
+                    const double w = u - fl;
+                    if (n + 1 < 0) continue; /* both slices before the first */
+                    if (n + need_ahead >= n_slices) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                        err = ORACLE_ENOTYET;
+                        continue;
+                    }
+                    const int64_t cell = (k * ny + j) * nx + i;
+                    /* source values and derivatives at slices n and n+1 */
+                    double r2[2], j2[2][3], dr2[2], dj2[2][3];
+                    for (int s = 0; s < 2; ++s) {
+                        const int64_t m = n + s;
+                        r2[s] = hist_at(rho, Ns, m, cell, -1);
+                        for (int a = 0; a < 3; ++a) j2[s][a] = hist_at(J, Ns, m, cell, a);
+                        if (m < 0) {
+                            dr2[s] = 0.0;
+                            for (int a = 0; a < 3; ++a) dj2[s][a] = 0.0;
+                        } else if (supplied) {
+                            dr2[s] = hist_at(drho, Ns, m, cell, -1);
+                            for (int a = 0; a < 3; ++a) dj2[s][a] = hist_at(dJ, Ns, m, cell, a);
+                        } else {
+                            dr2[s] = (hist_at(rho, Ns, m + 1, cell, -1) - hist_at(rho, Ns, m - 1, cell, -1)) /
+                                     (2.0 * dt);
+                            for (int a = 0; a < 3; ++a)
+                                dj2[s][a] = (hist_at(J, Ns, m + 1, cell, a) - hist_at(J, Ns, m - 1, cell, a)) /
+                                            (2.0 * dt);
+                        }
+                    }
+                    const double r_n = (1.0 - w) * r2[0] + w * r2[1];
+                    const double dr = (1.0 - w) * dr2[0] + w * dr2[1];
+                    double Jn[3], dj[3];
+                    for (int a = 0; a < 3; ++a) {
+                        Jn[a] = (1.0 - w) * j2[0][a] + w * j2[1][a];
+                        dj[a] = (1.0 - w) * dj2[0][a] + w * dj2[1][a];
+                    }
+                    const double R2 = R * R;
+                    const double R3 = R2 * R;
+                    const double D[3] = {dx, dy, dz};
+                    const double sc = r_n / R3 + dr / (c * R2);
+                    double V[3], te[3], tb[3];
+                    for (int a = 0; a < 3; ++a) {
+                        te[a] = D[a] * sc - dj[a] / (c * c * R);
+                        V[a] = Jn[a] / R3 + dj[a] / (c * R2);
+                    }
+                    tb[0] = V[1] * D[2] - V[2] * D[1];
+                    tb[1] = V[2] * D[0] - V[0] * D[2];
+                    tb[2] = V[0] * D[1] - V[1] * D[0];
+                    for (int a = 0; a < 3; ++a) {
+                        nadd(&e[a], te[a]);
+                        nadd(&b[a], tb[a]);
+                    }
+                }
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            E[3 * o + a] = k_e * dV * nval(&e[a]);
+            B[3 * o + a] = k_b * dV * nval(&b[a]);
+        }
+    }
+    return err;
+}
+
+/*
  * Every pair's slot for a small problem: out[n_obs][Ns] (cell index x
  * fastest); screened pairs get INT64_MIN.  Used to check slot selection
  * pair by pair.
