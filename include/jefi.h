@@ -102,6 +102,21 @@ typedef struct {
 #define JEFI_FLAG_STATS 1u    /* time the sum kernel with CUDA events on the call's stream */
 #define JEFI_FLAG_DIRECT_GATHER 2u  /* FP32: never use the TMA-staged kernel (for comparisons) */
 #define JEFI_FLAG_SHARED_RING 4u    /* FP32: size the ring's mirror for views of any staged band */
+/* Second-order retarded time (opt-in; the default floor rule of Eq. tr-1 is
+ * the parity contract).  With u = ((t - t0) - R/c)/dt, n = floor(u) (the same
+ * exact slot as the floor rule) and w = u - n, every source channel is read as
+ *   f = (1 - w) f[n] + w f[n+1],
+ * derivatives included: supplied derivatives are interpolated as given;
+ * with JEFI_DERIV_BACKWARD the library stores central differences
+ * (f[k+1] - f[k-1]) / (2 dt) instead, one slice late (slice k's derivative is
+ * written when slice k+1 is pushed).  Slices before the first are zero,
+ * values and derivatives alike.  An evaluation needs slices up to n+1
+ * (supplied) or n+2 (central) to be pushed: the valid window ends one or two
+ * slices earlier than with the floor rule.  Every single-handle path
+ * (FP64, FP32 staged and direct gather) supports it; jefi_eval_batch returns
+ * JEFI_EUNSUPPORTED for such handles; a view inherits the setting of its
+ * base. */
+#define JEFI_FLAG_INTERP 8u
 
 /* Fills p with: c = 1, k_e = k_b = 1, dt = 1, t0 = 0, H = 64, FP32_COMP,
  * backward differences, default screening, cudaMalloc. */

@@ -45,6 +45,7 @@ JEFI_DERIV_SUPPLIED = 1
 JEFI_FLAG_STATS = 1
 JEFI_FLAG_DIRECT_GATHER = 2
 JEFI_FLAG_SHARED_RING = 4
+JEFI_FLAG_INTERP = 8
 
 PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 

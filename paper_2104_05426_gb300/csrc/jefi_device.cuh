@@ -99,6 +99,32 @@ static __device__ __forceinline__ void pair_f32(float dx, float dy, float dz, fl
     pb[2] = fmaf(-vy, dx, pb[2]);
 }
 
+// Second-order retarded time: weight w = u - n of slot n+1, u = (T/dt - k0)
+// - R/(c dt) (Eq. tr-1 without the floor), n relative to k0.  A + A_lo and
+// K + K_lo carry T/dt - k0 and 1/(c dt) beyond FP32 and R gets one Newton
+// correction, so the weight's error is a few roundings of numbers of order
+// one rather than a rounding of u itself (a bias shared by every pair).
+static __device__ __forceinline__ float interp_weight(float S, float ri, float nrel, float A, float A_lo, float K,
+                                               float K_lo) {
+    float R = S * ri;
+    R = fmaf(0.5f * fmaf(-R, R, S), ri, R);
+    const float t1 = fmaf(-R, K, A - nrel);   // A - nrel is exact
+    const float t2 = fmaf(-R, K_lo, A_lo);
+    return t1 + t2;
+}
+
+// (1 - w) a + w b for the 8 channels, packed.
+static __device__ __forceinline__ void lerp8(float4& v0, float4& v1, const float4& u0, const float4& u1, float w) {
+    const float2 w2 = make_float2(w, w), nw2 = make_float2(-w, -w);
+    auto l = [&](float a0, float a1, float b0, float b1) {
+        return __ffma2_rn(w2, make_float2(b0, b1), __ffma2_rn(nw2, make_float2(a0, a1), make_float2(a0, a1)));
+    };
+    const float2 p0 = l(v0.x, v0.y, u0.x, u0.y), p1 = l(v0.z, v0.w, u0.z, u0.w);
+    const float2 p2 = l(v1.x, v1.y, u1.x, u1.y), p3 = l(v1.z, v1.w, u1.z, u1.w);
+    v0 = make_float4(p0.x, p0.y, p1.x, p1.y);
+    v1 = make_float4(p2.x, p2.y, p3.x, p3.y);
+}
+
 struct ThreadCtx {
     int slot;
     int rlo[3], rhi[3];   // screening index ranges

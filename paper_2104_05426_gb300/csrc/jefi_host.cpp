@@ -252,7 +252,11 @@ struct jefi_problem {
     int32_t* obs_scr = nullptr;
     int32_t* d_inv_perm = nullptr;
     double* prev = nullptr;
+    double* prev2 = nullptr;         // slice n-2 (central differences only)
     double* stage_in = nullptr;      // host pushes: rho, J, drho, dJ
+    // second-order retarded time (JEFI_FLAG_INTERP); central: the ring's
+    // derivative channels hold central differences, written one slice late
+    bool interp = false, central = false;
     int32_t time_chunk = kTimeChunk; // evaluation times per launch (scratch slots)
     double* partials = nullptr;      // [time_chunk][n_split][6][n_slots]
     double* out_stage = nullptr;     // host outputs: E, B for time_chunk times
@@ -329,6 +333,10 @@ int64_t phys_slot(const jefi_problem* h, int64_t k) {
     return k % h->H;
 }
 
+// Slices past a pair's slot n that an evaluation reads: 0 (floor rule),
+// 1 (interpolation), 2 (interpolation of central differences).
+int64_t slices_ahead(const jefi_problem* h) { return h->interp ? (h->central ? 2 : 1) : 0; }
+
 // Range of slots [n_lo, n_hi] needed at time t by real unscreened pairs.
 void needed_range(const jefi_problem* h, double T, int64_t* n_lo, int64_t* n_hi) {
     *n_lo = slot_of(h->real.s_max, T, h->prm.c, h->prm.dt);
@@ -345,8 +353,10 @@ int check_time(const jefi_problem* h, double t) {
     if (!(umax < 1e15)) return JEFI_EUNSUPPORTED;
     int64_t lo, hi;
     needed_range(h, T, &lo, &hi);
-    if (hi < 0) return JEFI_OK;                      // all sources still in the future
-    if (hi > h->n_latest) return JEFI_ENOTYET;
+    // interpolation also reads slice n+1, and n+2 through a central difference
+    const int64_t ahead = slices_ahead(h);
+    if (hi + (h->interp ? 1 : 0) < 0) return JEFI_OK;   // all sources still in the future
+    if (hi + ahead > h->n_latest) return JEFI_ENOTYET;
     const int64_t oldest = h->n_latest - h->H + 1;
     if (std::max<int64_t>(lo, 0) < oldest) return JEFI_EEVICTED;
     return JEFI_OK;
@@ -410,8 +420,9 @@ void build_tables(jefi_problem* h, int ti, double t) {
     const int64_t oldest = h->n_latest - h->H + 1;
     const int64_t oldest_rel = oldest > 0 ? oldest - k0 : (int64_t)(INT32_MIN / 2);
     tp.oldest_rel = (int32_t)std::max<int64_t>(std::min<int64_t>(oldest_rel, INT32_MAX / 2), INT32_MIN / 2);
-    tp.pad = 0;
+    tp.A_lo = (float)(A - (double)tp.A);
     tp.k0 = k0;
+    tp.A64 = A;
     h->h_times[ti] = tp;
 }
 
@@ -467,6 +478,9 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     p.n_t = n_t;
     p.K = K;
     p.K32 = (float)(1.0 / (h->prm.c * h->prm.dt));
+    p.K64 = 1.0 / (h->prm.c * h->prm.dt);
+    p.K32_lo = (float)(p.K64 - (double)p.K32);
+    p.interp = h->interp ? 1 : 0;
     p.n_split = h->n_split;
     p.bricks_per_split = h->bricks_per_split;
     p.partials = h->partials + (size_t)slot0 * h->n_split * 6 * h->n_slots;
@@ -678,6 +692,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->prm = *p;
     h->src = *src;
     h->fp64 = p->precision == JEFI_FP64;
+    h->interp = (p->flags & JEFI_FLAG_INTERP) != 0;
+    h->central = h->interp && p->deriv == JEFI_DERIV_BACKWARD;
     h->H = p->history_slots;
     for (int a = 0; a < 3; ++a) h->screen[a] = p->screen[a] < 0 ? src->d[a] / 2 : p->screen[a];
     h->n_src = (int64_t)src->n[0] * src->n[1] * src->n[2];
@@ -916,6 +932,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->obs_scr = (int32_t*)dev_alloc(h, sizeof(int32_t) * scr.size());
     h->d_inv_perm = (int32_t*)dev_alloc(h, sizeof(int32_t) * std::max<size_t>(1, h->inv_perm.size()));
     h->prev = base ? base->prev : (double*)dev_alloc(h, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src));
+    if (h->central)
+        h->prev2 = base ? base->prev2 : (double*)dev_alloc(h, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src));
     h->stage_in = base ? base->stage_in : (double*)dev_alloc(h, sizeof(double) * 8 * std::max<int64_t>(1, h->n_src));
     h->partials = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * h->n_split * 6 * std::max<int32_t>(1, h->n_slots));
     h->out_stage = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * 6 * std::max<int64_t>(1, n_obs));
@@ -944,6 +962,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     if (e == cudaSuccess && !base) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
     if (e == cudaSuccess && !base)
         e = cudaMemsetAsync(h->prev, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
+        if (e == cudaSuccess && h->prev2)
+            e = cudaMemsetAsync(h->prev2, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fallbacks, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && h->band > 0)
@@ -1025,6 +1045,14 @@ int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const d
     p.dJ = dj;
     p.prev = h->prev;
     p.ring = h->ring;
+    p.central = h->central ? 1 : 0;
+    p.prev2 = h->prev2;
+    p.prev_slot = -1;
+    p.prev_mirror_slot = -1;
+    if (h->central && next >= 1) {
+        p.prev_slot = (int32_t)((next - 1) % h->H);
+        p.prev_mirror_slot = p.prev_slot < h->mirror ? p.prev_slot + h->H : -1;
+    }
     JEFI_CUDA(launch_push(p, s));
     if (n > 0) h->launches++;
     h->n_latest = next;
@@ -1089,6 +1117,7 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
     for (int i = 0; i < n; ++i) {
         jefi_problem* h = hs[i];
         if (!h) return JEFI_EINVAL;
+        if (h->interp) return JEFI_EUNSUPPORTED;   // batched kernels run the floor rule only
         sync_view(h);
         if (h->n_obs > 0 && (!E[i] || !B[i])) return JEFI_EINVAL;
         const int rc = check_time(h, t[i]);
@@ -1298,7 +1327,8 @@ int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi) {
     }
     const double c = h->prm.c, dt = h->prm.dt, t0 = h->prm.t0;
     const double rmin = std::sqrt(h->real.s_min), rmax = std::sqrt(h->real.s_max);
-    auto ok_hi = [&](double t) { return slot_of(h->real.s_min, t - t0, c, dt) <= h->n_latest; };
+    const int64_t ahead = slices_ahead(h);
+    auto ok_hi = [&](double t) { return slot_of(h->real.s_min, t - t0, c, dt) + ahead <= h->n_latest; };
     // monotone in t: the farthest pair's slot has not yet fallen out of the ring
     auto ok_lo = [&](double t) {
         const int64_t oldest = h->n_latest - h->H + 1;
@@ -1325,7 +1355,7 @@ int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi) {
         }
         return want_max ? a : b;
     };
-    *t_hi = refine(t0 + (double)(h->n_latest + 1) * dt + rmin / c, ok_hi, true);
+    *t_hi = refine(t0 + (double)(h->n_latest + 1 - ahead) * dt + rmin / c, ok_hi, true);
     if (h->n_latest - h->H + 1 <= 0) {
         *t_lo = -INFINITY;
     } else {

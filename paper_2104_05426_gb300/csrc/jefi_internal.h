@@ -39,8 +39,9 @@ struct TimeParams {
     float A;            // fp32(T/dt - k0): candidate index ~ floor(A - R/(c dt))
     float Ag;           // A + g, g >= |error of the FP32 candidate|: floor(Ag - R K) in {n-k0, n-k0+1}
     int32_t oldest_rel; // oldest resident slot - k0 (clamped to int32)
-    int32_t pad;
+    float A_lo;         // fp32(T/dt - k0 - A): A + A_lo carries T/dt - k0 to ~2^-48 (interpolation weights)
     int64_t k0;         // table origin slot
+    double A64;         // T/dt - k0 in FP64 (interpolation weight of the FP64 kernel)
 };
 
 constexpr int kTabGuard = 32;       // guard entries on each side of the staged kernel's table
@@ -82,6 +83,10 @@ struct SumParams {
     int32_t nfull[3];               // whole bricks per axis (bricks past them hold padding cells)
     int32_t H;                      // ring period (physical slot of slice n is n mod H)
     int32_t comp;                   // FP32: compensated (Kahan) per-thread sums
+    // second-order retarded time: sources interpolated between slots n and n+1
+    int32_t interp;
+    float K32_lo;                   // fp32(1/(c dt) - K32)
+    double K64;                     // 1 / (c dt)
 };
 
 // Persistent batched launches: problem i owns items [item_start[i], item_start[i+1]),
@@ -110,6 +115,12 @@ struct PushParams {
     const double* dJ;
     double* prev;                   // [n_src][4] previous slice (backward differences)
     void* ring;
+    // central differences: also rewrite the derivative channels of slice n-1
+    // as (f[n] - f[n-2]) / (2 dt)
+    int32_t central;
+    int32_t prev_slot;              // physical slot of slice n-1, or -1 (n = 0)
+    int32_t prev_mirror_slot;       // its mirror copy, or -1
+    double* prev2;                  // [n_src][4] slice n-2
 };
 
 struct ReduceParams {

@@ -28,7 +28,7 @@ using namespace dev;
 
 // ============================================================================ FP32
 // Shared memory: tab32[K] float4 | theta[K+1] double | D[nbx+nby+nbz] float
-template <bool COMP, bool DEBUG>
+template <bool COMP, bool DEBUG, bool INTERP>
 __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int tile, const int split,
                                                 const int ti) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -71,6 +71,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
     const TimeParams tp = p.times[ti];
     const float A = tp.A;
     const float K32 = p.K32;
+    const float A_lo = tp.A_lo, K32_lo = p.K32_lo;   // interpolation weights only
     const float d32x = p.d32[0], d32y = p.d32[1], d32z = p.d32[2];
     const int Hp = p.Hp;
     const float4* ring = reinterpret_cast<const float4*>(p.ring);
@@ -127,7 +128,13 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                         scr ? INT32_MIN : (int)(tp.k0 + idx);
                 }
                 const float4* q = cbase + (cl * Hp + ps) * 2;
-                const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                if (INTERP) {   // slot n+1: the next candidate's physical slot
+                    const int ps1 = scr ? p.zero_slot : __float_as_int(s_tab[idx + 1].z);
+                    const float4* q1 = cbase + (cl * Hp + ps1) * 2;
+                    lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1),
+                          interp_weight(S, ri, (float)(int)idx, A, A_lo, K32, K32_lo));
+                }
                 pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
             }
         } else {
@@ -174,7 +181,12 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                                           cl] = (int)(tp.k0 + idx);
                         }
                         const float4* q = cbase + (cl * Hp + __float_as_int(e.z)) * 2;
-                        const float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                        float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                        if (INTERP) {
+                            const float4* q1 = cbase + (cl * Hp + __float_as_int(s_tab[idx + 1].z)) * 2;
+                            lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1),
+                                  interp_weight(S, ri, (float)(int)idx, A, A_lo, K32, K32_lo));
+                        }
                         pair_f32(ddx[i], ddy[j], ddz[k], ri, v0, v1, pe, pb);
                     }
                 }
@@ -201,9 +213,9 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
     }
 }
 
-template <bool COMP, bool DEBUG>
+template <bool COMP, bool DEBUG, bool INTERP>
 __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_kernel(const SumParams p) {
-    direct_f32_item<COMP, DEBUG>(p, blockIdx.x, blockIdx.y, blockIdx.z);
+    direct_f32_item<COMP, DEBUG, INTERP>(p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Take the next item of a persistent batched launch; false when the queue is empty.
@@ -234,7 +246,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_batch(const BatchArgs
     __shared__ int s_item;
     int pr, tile, split, ti;
     while (next_item(a, &s_item, &pr, &tile, &split, &ti))
-        direct_f32_item<COMP, false>(a.params[pr], tile, split, ti);
+        direct_f32_item<COMP, false, false>(a.params[pr], tile, split, ti);
 }
 
 // ============================================================================ FP64
@@ -263,7 +275,13 @@ __device__ __forceinline__ void pair_f64(double dx, double dy, double dz, double
     pb[2] = fma(-vy, dx, pb[2]);
 }
 
-template <bool DEBUG>
+// Second-order retarded time: the channels of slot n moved toward those of
+// slot n+1 by the weight w = u - n, u = (T - R/c)/dt (Eq. tr-1 without the floor).
+__device__ __forceinline__ double2 lerp2(const double2& a, const double2& b, double w) {
+    return make_double2(fma(w, b.x - a.x, a.x), fma(w, b.y - a.y, a.y));
+}
+
+template <bool DEBUG, bool INTERP>
 __device__ __forceinline__ void f64_item(const SumParams& p, const int tile, const int split, const int ti) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K;
@@ -354,8 +372,17 @@ __device__ __forceinline__ void f64_item(const SumParams& p, const int tile, con
                     }
                     const double ri = scr ? 0.0 : rsqrt(S);
                     const double2* q = cbase + (cl * Hp + ps) * 4;
-                    const double2 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2),
-                                  a3 = __ldg(q + 3);
+                    double2 a0 = __ldg(q), a1 = __ldg(q + 1), a2 = __ldg(q + 2), a3 = __ldg(q + 3);
+                    if (INTERP) {
+                        const int ps1 = scr ? p.zero_slot : __float_as_int(s_tab[it + 1].z);
+                        const double2* q1 = cbase + (cl * Hp + ps1) * 4;
+                        // w = (T/dt - k0) - R/(c dt) - (n - k0), R = S / sqrt(S)
+                        const double w = fma(-(S * ri), p.K64, tp.A64) - (double)it;
+                        a0 = lerp2(a0, __ldg(q1), w);
+                        a1 = lerp2(a1, __ldg(q1 + 1), w);
+                        a2 = lerp2(a2, __ldg(q1 + 2), w);
+                        a3 = lerp2(a3, __ldg(q1 + 3), w);
+                    }
                     pair_f64(ddx[i], ddy[j], ddz[k], ri, a0, a1, a2, a3, se, sb);
                 }
             }
@@ -369,15 +396,15 @@ __device__ __forceinline__ void f64_item(const SumParams& p, const int tile, con
     }
 }
 
-template <bool DEBUG>
+template <bool DEBUG, bool INTERP>
 __global__ void __launch_bounds__(kTileThreads, 1) sum_f64_kernel(const SumParams p) {
-    f64_item<DEBUG>(p, blockIdx.x, blockIdx.y, blockIdx.z);
+    f64_item<DEBUG, INTERP>(p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 __global__ void __launch_bounds__(kTileThreads, 1) sum_f64_batch(const BatchArgs a) {
     __shared__ int s_item;
     int pr, tile, split, ti;
-    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) f64_item<false>(a.params[pr], tile, split, ti);
+    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) f64_item<false, false>(a.params[pr], tile, split, ti);
 }
 
 // ============================================================================ push
@@ -393,6 +420,39 @@ __global__ void push_kernel(const PushParams p) {
 
     const double rho = p.rho[g];
     const double j0 = p.J[3 * g + 0], j1 = p.J[3 * g + 1], j2 = p.J[3 * g + 2];
+    if (p.central && p.prev_slot >= 0) {
+        // slice n-1 now has both neighbours: its derivative channels become
+        // the central difference (f[n] - f[n-2]) / (2 dt), f[-1] = 0
+        double* p2 = p.prev2 + 4 * g;
+        const double two_dt = __dmul_rn(2.0, p.dt);
+        const double cd[4] = {__ddiv_rn(__dsub_rn(rho, p2[0]), two_dt),
+                              __ddiv_rn(__ddiv_rn(__dsub_rn(j0, p2[1]), two_dt), p.c),
+                              __ddiv_rn(__ddiv_rn(__dsub_rn(j1, p2[2]), two_dt), p.c),
+                              __ddiv_rn(__ddiv_rn(__dsub_rn(j2, p2[3]), two_dt), p.c)};
+        const int n_cp = p.prev_mirror_slot >= 0 ? 2 : 1;
+        for (int copy = 0; copy < n_cp; ++copy) {
+            const int slot = copy == 0 ? p.prev_slot : p.prev_mirror_slot;
+            const size_t off = ((size_t)cell * p.Hp + slot) * 8 + 4;
+            if (p.fp64) {
+                double2* dst = reinterpret_cast<double2*>(static_cast<double*>(p.ring) + off);
+                dst[0] = make_double2(cd[0], cd[1]);
+                dst[1] = make_double2(cd[2], cd[3]);
+            } else {
+                float4* dst = reinterpret_cast<float4*>(static_cast<float*>(p.ring) + off);
+                dst[0] = make_float4(__double2float_rn(cd[0]), __double2float_rn(cd[1]),
+                                     __double2float_rn(cd[2]), __double2float_rn(cd[3]));
+            }
+        }
+    }
+    if (p.central) {
+        // slice n-1 (still in prev, updated below) becomes slice n-2
+        double* p2 = p.prev2 + 4 * g;
+        const double* pv = p.prev + 4 * g;
+        p2[0] = pv[0];
+        p2[1] = pv[1];
+        p2[2] = pv[2];
+        p2[3] = pv[3];
+    }
     double dr, dj0, dj1, dj2;
     if (p.supplied) {
         dr = p.drho[g];
@@ -513,9 +573,11 @@ cudaError_t launch_sum_f32(const SumParams& p, bool compensated, cudaStream_t s)
     const size_t smem = sum_smem_bytes(p);
     void (*k)(SumParams);
     if (p.debug_slots)
-        k = compensated ? sum_f32_kernel<true, true> : sum_f32_kernel<false, true>;
+        k = compensated ? sum_f32_kernel<true, true, false> : sum_f32_kernel<false, true, false>;
+    else if (p.interp)
+        k = compensated ? sum_f32_kernel<true, false, true> : sum_f32_kernel<false, false, true>;
     else
-        k = compensated ? sum_f32_kernel<true, false> : sum_f32_kernel<false, false>;
+        k = compensated ? sum_f32_kernel<true, false, false> : sum_f32_kernel<false, false, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kTileThreads, smem, s>>>(p);
@@ -525,7 +587,8 @@ cudaError_t launch_sum_f32(const SumParams& p, bool compensated, cudaStream_t s)
 cudaError_t launch_sum_f64(const SumParams& p, cudaStream_t s) {
     const dim3 grid(p.n_tiles, p.n_split, p.n_t);
     const size_t smem = sum_smem_bytes(p);
-    void (*k)(SumParams) = p.debug_slots ? sum_f64_kernel<true> : sum_f64_kernel<false>;
+    void (*k)(SumParams) = p.debug_slots ? sum_f64_kernel<true, false>
+                           : (p.interp ? sum_f64_kernel<false, true> : sum_f64_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kTileThreads, smem, s>>>(p);

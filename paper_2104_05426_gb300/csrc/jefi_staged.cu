@@ -122,7 +122,7 @@ __device__ __forceinline__ void staged_init_barriers() {
 // index `ti` of problem p.  g_it counts the CTA's staged bricks across items
 // (it selects the buffer and the mbarrier phase).  Returns false if a copy
 // did not complete in time (the caller stops).
-template <int BAND, bool EXACT, bool DEBUG>
+template <int BAND, bool EXACT, bool DEBUG, bool INTERP>
 __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const int comp,
                                             const int tile, const int split, const int ti, uint32_t& g_it) {
     using L = Layout<BAND>;
@@ -166,6 +166,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     const TimeParams tp = p.times[ti];
     const float K32 = p.K32;
     const float Ag = tp.Ag;
+    const float A = tp.A, A_lo = tp.A_lo, K32_lo = p.K32_lo;   // interpolation weights only
     const float d32x = p.d32[0], d32y = p.d32[1], d32z = p.d32[2];
     const size_t n_cells = (size_t)p.n_bricks * kBrickCells;
     const uint32_t mbar_u32[2] = {smem_u32(&s_mbar[0]), smem_u32(&s_mbar[1])};
@@ -311,8 +312,14 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                     (int)(tp.k0 + (int)(bits + lower - kMagicBits));
                             }
                             const uint32_t off = row_hi + lower * L::kRowBytes + (uint32_t)c16 * L::kCellBytes;
-                            const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
-                            const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                            float4 v0 = *reinterpret_cast<const float4*>(smem + off);
+                            float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                            if (INTERP) {   // slot n+1 is the next row of the same cell
+                                const float4 u0 = *reinterpret_cast<const float4*>(smem + off + 32u);
+                                const float4 u1 = *reinterpret_cast<const float4*>(smem + off + 48u);
+                                const float nrel = __uint_as_float(bits + lower) - kMagic;
+                                lerp8(v0, v1, u0, u1, interp_weight(S, ri, nrel, A, A_lo, K32, K32_lo));
+                            }
                             // Eqs. E-1/B-1 with packed pairs, r^-2 factored out:
                             //   (q, Vx) = ((drho, dJx/c) + (c rho, Jx) r^-1) r^-2,  q the D-term of E
                             //   (Vy, Vz) = ((dJy, dJz)/c + (Jy, Jz) r^-1) r^-2
@@ -373,8 +380,13 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                             }
                             const uint32_t off = (uint32_t)buf * L::kBufBytes + (uint32_t)cl * L::kCellBytes +
                                                  (uint32_t)row * L::kRowBytes;
-                            const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
-                            const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                            float4 v0 = *reinterpret_cast<const float4*>(smem + off);
+                            float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                            if (INTERP) {
+                                const float4 u0 = *reinterpret_cast<const float4*>(smem + off + 32u);
+                                const float4 u1 = *reinterpret_cast<const float4*>(smem + off + 48u);
+                                lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
+                            }
                             pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
                         }
                     }
@@ -418,8 +430,13 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     }
                     const uint32_t off = (uint32_t)buf * L::kBufBytes + (uint32_t)cl * L::kCellBytes +
                                          (uint32_t)row * L::kRowBytes;
-                    const float4 v0 = *reinterpret_cast<const float4*>(smem + off);
-                    const float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                    float4 v0 = *reinterpret_cast<const float4*>(smem + off);
+                    float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
+                    if (INTERP) {   // row + 1 < BAND: the band covers slot n+1 of every pair
+                        const float4 u0 = *reinterpret_cast<const float4*>(smem + off + 32u);
+                        const float4 u1 = *reinterpret_cast<const float4*>(smem + off + 48u);
+                        lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
+                    }
                     pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
                 }
             }
@@ -466,12 +483,21 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     return aborted_at < 0;
 }
 
-template <int BAND, bool EXACT, bool DEBUG>
+template <int BAND, bool EXACT, bool DEBUG, bool INTERP>
 __global__ void __launch_bounds__(kTileThreads, 2)
     sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p) {
     staged_init_barriers<BAND>();
     uint32_t g_it = 0;
-    staged_item<BAND, EXACT, DEBUG>(&tmap, p, p.comp, blockIdx.x, blockIdx.y, blockIdx.z, g_it);
+    staged_item<BAND, EXACT, DEBUG, INTERP>(&tmap, p, p.comp, blockIdx.x, blockIdx.y, blockIdx.z, g_it);
+}
+
+// One item of the batched kernel as a call of its own: the item body gets
+// the register budget of the single-problem kernel instead of sharing it
+// with the queue loop (the call happens once per item, thousands of pairs).
+template <int BAND, bool EXACT>
+__device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int split,
+                                               int ti, uint32_t& g_it) {
+    return staged_item<BAND, EXACT, false, false>(map, p, p.comp, tile, split, ti, g_it);
 }
 
 // Persistent batched kernel: CTAs take (problem, time, split, tile) items
@@ -482,6 +508,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_staged_batch(const __
     using L = Layout<BAND>;
     extern __shared__ __align__(1024) unsigned char smem[];
     int* s_item = reinterpret_cast<int*>(smem + L::kCtrl + 32);
+    __shared__ SumParams s_par;
     staged_init_barriers<BAND>();
     uint32_t g_it = 0;
     for (;;) {
@@ -495,14 +522,24 @@ __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_staged_batch(const __
             const int mid = (lo + hi + 1) >> 1;
             if (a.item_start[mid] <= item) lo = mid; else hi = mid - 1;
         }
-        const SumParams& p = a.params[lo];
+        // The item's parameters go to shared memory: read through a dynamic
+        // index into global memory, their loop invariants would be held in
+        // registers (the single-problem kernel reads them from the constant
+        // bank) and the batched kernel would spill.
+        {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.params[lo]);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&s_par);
+            for (int w = threadIdx.x; w < (int)(sizeof(SumParams) / 4); w += kTileThreads) dst[w] = src[w];
+        }
+        __syncthreads();
+        const SumParams& p = s_par;
         const int local = item - a.item_start[lo];
         const int per_t = p.n_tiles * p.n_split;
         const int ti = local / per_t;
         const int r = local - ti * per_t;
         const int split = r / p.n_tiles;
         const int tile = r - split * p.n_tiles;
-        if (!staged_item<BAND, EXACT, false>(&a.maps[lo], p, p.comp, tile, split, ti, g_it)) break;
+        if (!staged_batch_item<BAND, EXACT>(&a.maps[lo], p, tile, split, ti, g_it)) break;
     }
 }
 
@@ -535,11 +572,11 @@ size_t staged_smem_bytes(const SumParams& p, int band) {
     return b;
 }
 
-template <int BAND, bool EXACT, bool DEBUG>
+template <int BAND, bool EXACT, bool DEBUG, bool INTERP = false>
 static cudaError_t launch_variant(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
     const dim3 grid(p.n_tiles, p.n_split, p.n_t);
     const size_t smem = staged_smem_bytes(p, BAND);
-    auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG>;
+    auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG, INTERP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tensor_map);
@@ -570,6 +607,10 @@ cudaError_t launch_sum_f32_staged_batch(const StagedBatchArgs& a, int band, bool
 template <int BAND>
 static cudaError_t launch_band(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
     const bool dbg = p.debug_slots != nullptr;
+    // the slot of every pair is the same with and without interpolation, so
+    // the slot-recording kernels exist only in the floor-rule form
+    if (!dbg && p.interp)
+        return c.exact ? launch_variant<BAND, true, false, true>(p, c, s) : launch_variant<BAND, false, false, true>(p, c, s);
     if (c.exact) return dbg ? launch_variant<BAND, true, true>(p, c, s) : launch_variant<BAND, true, false>(p, c, s);
     return dbg ? launch_variant<BAND, false, true>(p, c, s) : launch_variant<BAND, false, false>(p, c, s);
 }

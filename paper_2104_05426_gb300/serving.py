@@ -383,3 +383,62 @@ def poisson_requests(n: int, rate: float, n_problems: int, obs_sides=(8, 48), se
         reqs.append(Request(i, int(rng.integers(0, n_problems)), side, float(rng.uniform(0.05, 0.95)),
                             float(arrivals[i])))
     return reqs
+
+
+def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0), sides=(16, 64),
+            H_range=(64, 256), obs_sides=(8, 48), seed: int = 11, tick_s: float = 0.02,
+            n_streams: int = 4, max_batch: int = 32) -> dict:
+    """Latency of Poisson-arriving requests against resident problems.
+
+    First the saturated throughput (every request arrives at once), then, for
+    each load factor f, a fresh stream of requests arriving at f times that
+    rate, with one slice pushed to every problem per tick.  Returns the
+    percentiles per load and the resident memory."""
+    import torch
+
+    probs = make_problems(n_problems, seed, sides=sides, H_range=H_range)
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=n_streams, max_batch=max_batch, tick_s=None)
+    sat = eng.run(poisson_requests(n_requests, rate=1e9, n_problems=n_problems, obs_sides=obs_sides,
+                                   seed=seed + 1))
+    out = {"problems": n_problems, "requests_per_load": n_requests, "source_sides": list(sides),
+           "history_slices": list(H_range), "obs_sides": list(obs_sides),
+           "resident_ring_bytes": int(eng.resident_bytes),
+           "saturated": {"requests_per_s": sat.requests_per_s, "pairs_per_s": sat.pairs_per_s,
+                         "mean_batch": sat.mean_batch}, "loads": []}
+    eng.tick_s = tick_s
+    for i, f in enumerate(loads):
+        rate = f * sat.requests_per_s
+        st = eng.run(poisson_requests(n_requests, rate=rate, n_problems=n_problems, obs_sides=obs_sides,
+                                      seed=seed + 2 + i))
+        out["loads"].append({"load": f, "offered_requests_per_s": rate, "p50_ms": st.p50_ms,
+                             "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+                             "requests_per_s": st.requests_per_s, "pairs_per_s": st.pairs_per_s,
+                             "completed": st.completed, "rejected": st.rejected,
+                             "mean_batch": st.mean_batch, "peak_device_bytes": st.peak_bytes})
+    eng.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="Serving latency of jefi field requests (p50/p99 per load).")
+    ap.add_argument("--problems", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=10000, help="requests per load level")
+    ap.add_argument("--loads", default="0.5,0.8,1.0", help="fractions of the saturated request rate")
+    ap.add_argument("--sides", default="16,64", help="source grid side range")
+    ap.add_argument("--history", default="64,256", help="resident history length range")
+    ap.add_argument("--obs-sides", default="8,48", help="observation grid side range")
+    ap.add_argument("--seed", type=int, default=11)
+    ap.add_argument("--tick-ms", type=float, default=20.0, help="one slice pushed per problem per tick")
+    a = ap.parse_args(argv)
+    pair = lambda s: tuple(int(x) for x in s.split(","))
+    res = measure(a.problems, a.requests, tuple(float(x) for x in a.loads.split(",")), pair(a.sides),
+                  pair(a.history), pair(a.obs_sides), a.seed, a.tick_ms / 1e3)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
