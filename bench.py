@@ -308,6 +308,28 @@ def run_gpu(args):
                                 "fp32c_speedup_kernel": fp32c_kernel_pairs_s / fp64_pairs_s,
                                 "rel_l2_fp32c_vs_fp64_all_points": err}
         jefi.jefi_destroy(h64)
+        # second-order retarded time (opt-in) on the same workload, 8 times per
+        # launch: central differences read two slices past the slot, so the
+        # handle holds two more slices and the times sit two slices back
+        prm_i = jefi.default_params(c=p.c, k_e=p.k_e, k_b=p.k_b, dt=p.dt,
+                                    t0=p.t0 + (next_slice - H - 2) * p.dt, history_slots=H + 2,
+                                    precision="fp32c", flags=jefi.JEFI_FLAG_STATS | jefi.JEFI_FLAG_INTERP)
+        hi2 = jefi.jefi_create(jefi.grid_from(p.src), obs_grid=jefi.grid_from(p.obs_grid), params=prm_i,
+                               torch_allocator=True)
+        for n in range(next_slice - H - 2, next_slice):
+            jefi.jefi_push_sources(hi2, *dev_slices[n])
+        ts_i = times_now(next_slice - 3)
+        jefi.jefi_eval_fields_multi(hi2, ts_i, E, B)      # warm-up
+        jefi.jefi_reset_stats(hi2)
+        jefi.jefi_eval_fields_multi(hi2, ts_i, E, B)
+        ii = jefi.jefi_get_info(hi2)
+        ms_i = ii["sum_ms_total"] / max(ii["sum_launches"], 1)
+        result["interp_fp32c"] = {"value": pairs_launch / (ms_i / 1e3), "unit": UNIT, "kernel_ms": ms_i,
+                                  "vs_floor_rule_kernel": sum_ms / ms_i,
+                                  "device_status": ii["device_status"],
+                                  "note": "JEFI_FLAG_INTERP: sources interpolated at the retarded "
+                                          "time, central differences; same 8-time launch"}
+        jefi.jefi_destroy(hi2)
         if not args.no_serving:
             result["serving"] = serving_leg()
         if not args.no_cpu_baseline:
@@ -367,9 +389,18 @@ def cpu_baseline(p, slices, times, E_gpu, B_gpu, stride=512):
         errs["B"] = max(errs["B"], float(np.linalg.norm(B_gpu[i][sub] - Br) / np.linalg.norm(Br)))
     dt_s = time.perf_counter() - t0
     pairs = len(sub) * p.src.size * len(times)
+    # one core, for comparison with single-threaded figures
+    sub1 = np.arange(0, p.n_obs, 16 * stride)
+    t1 = time.perf_counter()
+    oracle.fields(p.src.n, p.src.lo, p.src.d, p.obs()[sub1], rho, J, dt=p.dt, t0=p.t0, t=times[0],
+                  threads=1)
+    dt1 = time.perf_counter() - t1
     base = {"value": pairs / dt_s, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"every {stride}th of {p.n_obs} observation points x {p.src.size} sources x "
-                      f"{len(times)} times = {pairs:.3e} pairs, {dt_s:.1f} s"}
+                      f"{len(times)} times = {pairs:.3e} pairs, {dt_s:.1f} s",
+            "single_core_value": len(sub1) * p.src.size / dt1,
+            "single_core_sample": f"every {16 * stride}th observation point x {p.src.size} sources x "
+                                  f"1 time = {len(sub1) * p.src.size:.3e} pairs, {dt1:.1f} s, 1 thread"}
     check = {"max_rel_l2_fp32c_vs_oracle": errs, "points": int(len(sub)), "times": len(times)}
     return base, check
 

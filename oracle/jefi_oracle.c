@@ -144,8 +144,8 @@ int oracle_fields(const int32_t* src_n, const double* src_lo, const double* src_
     for (int64_t i = 0; i < nz; ++i) zs[i] = oracle_cell_center(src_lo[2], src_d[2], i);
 
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4) reduction(min : gmin) reduction(max : gmax)
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : gmin) reduction(max : gmax) \
+    num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
     for (int64_t o = 0; o < n_obs; ++o) {
         const double xo = obs[3 * o + 0], yo = obs[3 * o + 1], zo = obs[3 * o + 2];
@@ -272,8 +272,7 @@ int oracle_fields_interp(const int32_t* src_n, const double* src_lo, const doubl
     int err = ORACLE_OK;
 
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
     for (int64_t o = 0; o < n_obs; ++o) {
         const double xo = obs[3 * o + 0], yo = obs[3 * o + 1], zo = obs[3 * o + 2];
@@ -368,8 +367,7 @@ void oracle_all_slots(const int32_t* src_n, const double* src_lo, const double* 
     const int64_t Ns = nx * ny * nz;
     const double T = t - t0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : omp_get_max_threads())
 #endif
     for (int64_t o = 0; o < n_obs; ++o) {
         for (int64_t k = 0; k < nz; ++k) {
