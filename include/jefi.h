@@ -298,7 +298,38 @@ int jefi_eval_fields_noalloc(const jefi_grid* src, const double* obs, int64_t n_
                              const double* rho, const double* J, int64_t n_slices,
                              const jefi_params* p, double t, double* E, double* B, void* stream);
 
-/* Release every device and host resource of the handle (synchronises). */
+/*
+ * Checkpoint and resume of a handle's resident history (paper Sec. 2.2: rho
+ * and J stay on the device between evaluations; a serving process that
+ * restarts keeps them this way instead of pushing the last H slices again).
+ *
+ * The image is opaque bytes owned by the caller: a header (format version,
+ * the source grid, c, dt, t0, H, precision, derivative mode, interpolation
+ * setting, the index of the newest slice) followed by ring slots 0..H-1 of
+ * every cell (FP32 or FP64, 8 channels) and the FP64 state of the
+ * difference rule (the last one or two slices).  Observation points are not
+ * part of it.
+ *
+ * jefi_checkpoint_bytes: size of the image of h.
+ * jefi_checkpoint: writes the image into host memory dst (bytes >= the
+ *   size); synchronous on `stream`.
+ * jefi_restore: loads an image into h, which must have been created with the
+ *   same source grid, c, dt, t0, H, precision, derivative mode and
+ *   interpolation setting (its observation points may differ); the handle
+ *   then holds exactly the history of the checkpointed one and continues
+ *   from its newest slice.  Synchronous on `stream`.  Views of h see it.
+ * Errors: JEFI_EINVAL for a view (views hold no history; checkpoint the
+ * base), a buffer that is too small, or an image that is corrupt or was
+ * taken under other parameters (h is then unchanged).
+ */
+int jefi_checkpoint_bytes(jefi_handle h, size_t* bytes);
+int jefi_checkpoint(jefi_handle h, void* dst, size_t bytes, void* stream);
+int jefi_restore(jefi_handle h, const void* src, size_t bytes, void* stream);
+
+/* Release every device and host resource of the handle.  Waits for the
+ * work enqueued on the handle (on any stream) to finish, not for the whole
+ * device: other handles' work keeps running.  A base with live views
+ * returns JEFI_EINVAL (destroy the views first). */
 int jefi_destroy(jefi_handle h);
 
 const char* jefi_strerror(int code);

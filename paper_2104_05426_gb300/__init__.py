@@ -54,7 +54,7 @@ EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval
            "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info", "jefi_reset_stats",
            "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror",
            "jefi_eval_fields_noalloc", "jefi_eval_batch", "jefi_create_view",
-           "jefi_debug_wait_timeout")
+           "jefi_debug_wait_timeout", "jefi_checkpoint_bytes", "jefi_checkpoint", "jefi_restore")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -138,6 +138,9 @@ def load(build_if_needed: bool = True):
         L.jefi_eval_fields_noalloc.argtypes = [ctypes.POINTER(jefi_grid), P, I64, P, P, I64,
                                                ctypes.POINTER(jefi_params), D, P, P, P]
         L.jefi_eval_fields_noalloc.restype = I
+        L.jefi_checkpoint_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.jefi_checkpoint.argtypes = [P, P, ctypes.c_size_t, P]
+        L.jefi_restore.argtypes = [P, P, ctypes.c_size_t, P]
         L.jefi_strerror.argtypes = [I]
         L.jefi_strerror.restype = ctypes.c_char_p
         for name in ("jefi_create", "jefi_push_sources", "jefi_eval_fields",
@@ -308,6 +311,24 @@ def jefi_eval_fields_multi(h: Handle, times, E, B, stream=None):
     rc = load().jefi_eval_fields_multi(h.ptr, ts.shape[0], ts.ctypes.data, e, b,
                                        1 if on_dev else 0, _stream_ptr(stream))
     _check(rc, "jefi_eval_fields_multi")
+
+
+def jefi_checkpoint(h: Handle, stream=None) -> bytes:
+    """The handle's resident history as an opaque image (see jefi_restore)."""
+    n = ctypes.c_size_t()
+    _check(load().jefi_checkpoint_bytes(h.ptr, ctypes.byref(n)), "jefi_checkpoint_bytes")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(load().jefi_checkpoint(h.ptr, ctypes.cast(buf, ctypes.c_void_p), n.value, _stream_ptr(stream)),
+           "jefi_checkpoint")
+    return buf.raw
+
+
+def jefi_restore(h: Handle, image: bytes, stream=None):
+    """Load a jefi_checkpoint image into a handle created with the same source
+    grid and history parameters."""
+    buf = ctypes.create_string_buffer(bytes(image), len(image))
+    _check(load().jefi_restore(h.ptr, ctypes.cast(buf, ctypes.c_void_p), len(image), _stream_ptr(stream)),
+           "jefi_restore")
 
 
 def jefi_valid_window(h: Handle):

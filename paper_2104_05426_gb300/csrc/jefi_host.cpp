@@ -283,6 +283,8 @@ struct jefi_problem {
     // observation views share a base handle's ring and pushes
     jefi_problem* base = nullptr;
     int32_t n_views = 0;
+    // completion of the latest work enqueued on this handle's memory (any stream)
+    cudaEvent_t last_use = nullptr;
     // statistics
     int64_t launches = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending, ev_free;
@@ -322,10 +324,19 @@ void release_all(jefi_problem* h) {
             cudaFree(a.first);
     }
     h->allocs.clear();
+    if (h->last_use) cudaEventDestroy(h->last_use);
+    h->last_use = nullptr;
     for (auto& e : h->ev_pending) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     for (auto& e : h->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     h->ev_pending.clear();
     h->ev_free.clear();
+}
+
+// Record that work on h's memory was enqueued on stream s (jefi_destroy waits for it).
+int mark_use(jefi_problem* h, cudaStream_t s) {
+    if (!h->last_use) JEFI_CUDA(cudaEventCreateWithFlags(&h->last_use, cudaEventDisableTiming));
+    JEFI_CUDA(cudaEventRecord(h->last_use, s));
+    return JEFI_OK;
 }
 
 int64_t phys_slot(const jefi_problem* h, int64_t k) {
@@ -1056,7 +1067,7 @@ int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const d
     JEFI_CUDA(launch_push(p, s));
     if (n > 0) h->launches++;
     h->n_latest = next;
-    return JEFI_OK;
+    return mark_use(h, s);
 }
 
 static void sync_view(jefi_problem* h) {
@@ -1095,7 +1106,7 @@ static int eval_impl(jefi_handle h, int32_t n_t, const double* t, double* E, dou
             if (st != 0) return st;
         }
     }
-    return JEFI_OK;
+    return mark_use(h, s);
 }
 
 int jefi_eval_fields(jefi_handle h, double t, double* E, double* B, int on_device, void* stream) {
@@ -1260,6 +1271,10 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
                                   reinterpret_cast<const int64_t*>(d + off_rstart), (int)ritems.size(),
                                   rstart.back(), s));
     JEFI_CUDA(cudaEventRecord(arena.done, s));
+    for (int i = 0; i < n; ++i) {
+        const int rc = mark_use(hs[i], s);
+        if (rc != JEFI_OK) return rc;
+    }
     return JEFI_OK;
 }
 
@@ -1406,13 +1421,144 @@ int jefi_reset_stats(jefi_handle h) {
     h->sum_ms = 0;
     h->sum_launches = 0;
     JEFI_CUDA(cudaMemset(h->fallbacks, 0, sizeof(unsigned long long)));
+    return mark_use(h, 0);
+}
+
+// ---------------------------------------------------------------- checkpoint / resume
+namespace {
+
+constexpr char kCkpMagic[8] = {'J', 'E', 'F', 'I', 'C', 'K', 'P', '1'};
+constexpr uint32_t kCkpVersion = 1;
+
+struct CkpHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    int32_t src_n[3];
+    int32_t H;
+    double src_lo[3], src_d[3];
+    double c, dt, t0;
+    int32_t precision, deriv, interp, esz;
+    int64_t n_latest;
+    int64_t n_cells;                 // brick-padded cells
+    int64_t n_src;
+    int64_t ring_bytes;              // slots 0..H-1 of every cell
+    int64_t state_bytes;             // previous slice (and the one before, central differences)
+};
+
+int64_t ckp_ring_bytes(const jefi_problem* h) {
+    return (int64_t)h->n_bricks * kBrickCells * h->H * 8 * (h->fp64 ? 8 : 4);
+}
+
+int64_t ckp_state_bytes(const jefi_problem* h) {
+    return h->n_src * 4 * (int64_t)sizeof(double) * (h->central ? 2 : 1);
+}
+
+CkpHeader ckp_header(const jefi_problem* h) {
+    CkpHeader c{};
+    std::memcpy(c.magic, kCkpMagic, 8);
+    c.version = kCkpVersion;
+    c.header_bytes = sizeof(CkpHeader);
+    for (int a = 0; a < 3; ++a) {
+        c.src_n[a] = h->src.n[a];
+        c.src_lo[a] = h->src.lo[a];
+        c.src_d[a] = h->src.d[a];
+    }
+    c.H = h->H;
+    c.c = h->prm.c;
+    c.dt = h->prm.dt;
+    c.t0 = h->prm.t0;
+    c.precision = h->fp64 ? JEFI_FP64 : JEFI_FP32;   // FP32 and FP32_COMP share the ring format
+    c.deriv = h->prm.deriv;
+    c.interp = h->interp ? 1 : 0;
+    c.esz = h->fp64 ? 8 : 4;
+    c.n_latest = h->n_latest;
+    c.n_cells = (int64_t)h->n_bricks * kBrickCells;
+    c.n_src = h->n_src;
+    c.ring_bytes = ckp_ring_bytes(h);
+    c.state_bytes = ckp_state_bytes(h);
+    return c;
+}
+
+}  // namespace
+
+int jefi_checkpoint_bytes(jefi_handle h, size_t* bytes) {
+    if (!h || !bytes || h->base) return JEFI_EINVAL;
+    *bytes = sizeof(CkpHeader) + (size_t)ckp_ring_bytes(h) + (size_t)ckp_state_bytes(h);
+    return JEFI_OK;
+}
+
+int jefi_checkpoint(jefi_handle h, void* dst, size_t bytes, void* stream) {
+    size_t need = 0;
+    const int rc = jefi_checkpoint_bytes(h, &need);
+    if (rc != JEFI_OK) return rc;
+    if (!dst || bytes < need) return JEFI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const CkpHeader hdr = ckp_header(h);
+    unsigned char* out = static_cast<unsigned char*>(dst);
+    std::memcpy(out, &hdr, sizeof(hdr));
+    unsigned char* ring_out = out + sizeof(hdr);
+    const size_t row = (size_t)8 * hdr.esz;
+    if (hdr.ring_bytes > 0)
+        JEFI_CUDA(cudaMemcpy2DAsync(ring_out, (size_t)h->H * row, h->ring, (size_t)h->Hp * row, (size_t)h->H * row,
+                                    (size_t)hdr.n_cells, cudaMemcpyDeviceToHost, s));
+    unsigned char* st = ring_out + hdr.ring_bytes;
+    const size_t one = (size_t)h->n_src * 4 * sizeof(double);
+    if (one > 0) {
+        JEFI_CUDA(cudaMemcpyAsync(st, h->prev, one, cudaMemcpyDeviceToHost, s));
+        if (h->central) JEFI_CUDA(cudaMemcpyAsync(st + one, h->prev2, one, cudaMemcpyDeviceToHost, s));
+    }
+    JEFI_CUDA(cudaStreamSynchronize(s));
+    return JEFI_OK;
+}
+
+int jefi_restore(jefi_handle h, const void* src, size_t bytes, void* stream) {
+    size_t need = 0;
+    const int rc = jefi_checkpoint_bytes(h, &need);
+    if (rc != JEFI_OK) return rc;
+    if (!src || bytes < need) return JEFI_EINVAL;
+    CkpHeader in;
+    std::memcpy(&in, src, sizeof(in));
+    const CkpHeader want = ckp_header(h);
+    bool same = std::memcmp(in.magic, kCkpMagic, 8) == 0 && in.version == kCkpVersion &&
+                in.header_bytes == sizeof(CkpHeader) && in.H == want.H && in.precision == want.precision &&
+                in.deriv == want.deriv && in.interp == want.interp && in.esz == want.esz &&
+                in.n_cells == want.n_cells && in.n_src == want.n_src && in.ring_bytes == want.ring_bytes &&
+                in.state_bytes == want.state_bytes && in.c == want.c && in.dt == want.dt && in.t0 == want.t0 &&
+                in.n_latest >= -1 && in.n_latest < ((int64_t)1 << 52);
+    for (int a = 0; a < 3; ++a)
+        same = same && in.src_n[a] == want.src_n[a] && in.src_lo[a] == want.src_lo[a] &&
+               in.src_d[a] == want.src_d[a];
+    if (!same) return JEFI_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned char* ring_in = static_cast<const unsigned char*>(src) + sizeof(CkpHeader);
+    const size_t row = (size_t)8 * in.esz;
+    if (in.ring_bytes > 0) {
+        JEFI_CUDA(cudaMemcpy2DAsync(h->ring, (size_t)h->Hp * row, ring_in, (size_t)h->H * row, (size_t)h->H * row,
+                                    (size_t)in.n_cells, cudaMemcpyHostToDevice, s));
+        // this handle's mirror rows: slot H + k repeats slot k, k < min(M, H)
+        const int m = std::min(h->mirror, h->H);
+        if (m > 0)
+            JEFI_CUDA(cudaMemcpy2DAsync(static_cast<unsigned char*>(h->ring) + (size_t)h->H * row, (size_t)h->Hp * row,
+                                        h->ring, (size_t)h->Hp * row, (size_t)m * row, (size_t)in.n_cells,
+                                        cudaMemcpyDeviceToDevice, s));
+    }
+    const unsigned char* st = ring_in + in.ring_bytes;
+    const size_t one = (size_t)h->n_src * 4 * sizeof(double);
+    if (one > 0) {
+        JEFI_CUDA(cudaMemcpyAsync(h->prev, st, one, cudaMemcpyHostToDevice, s));
+        if (h->central) JEFI_CUDA(cudaMemcpyAsync(h->prev2, st + one, one, cudaMemcpyHostToDevice, s));
+    }
+    JEFI_CUDA(cudaStreamSynchronize(s));
+    h->n_latest = in.n_latest;
     return JEFI_OK;
 }
 
 int jefi_destroy(jefi_handle h) {
     if (!h) return JEFI_EINVAL;
     if (h->n_views > 0) return JEFI_EINVAL;              // destroy the views first
-    cudaDeviceSynchronize();
+    // the handle's own work only: other streams and handles keep running
+    if (h->last_use) cudaEventSynchronize(h->last_use);
     if (h->base) h->base->n_views--;
     release_all(h);
     delete h;

@@ -63,26 +63,34 @@ class ServedProblem:
         d = 2.0 * half_width / side
         self.grid = grid((side,) * 3, (-half_width,) * 3, (d,) * 3)
         prm = default_params(dt=dt, history_slots=H, precision="fp32c", flags=JEFI_FLAG_SHARED_RING)
-        self.handle = jefi_create(self.grid, obs_points=np.zeros((0, 3)), params=prm, stream=stream)
+        # PyTorch's caching allocator: views created and destroyed while the
+        # loop runs then cost no cudaMalloc / cudaFree (cudaFree waits for the device)
+        self.handle = jefi_create(self.grid, obs_points=np.zeros((0, 3)), params=prm, stream=stream,
+                                  torch_allocator=True)
         ax = -half_width + (torch.arange(side, dtype=torch.float64, device=self.device) + 0.5) * d
         z, y, x = torch.meshgrid(ax, ax, ax, indexing="ij")
         self.pts = torch.stack([x.reshape(-1), y.reshape(-1), z.reshape(-1)], dim=1)
+        # blob parameters resident on the device: a slice is generated by
+        # device ops alone (a host-to-device copy per slice would block the
+        # host behind the push stream, which waits for the batches in flight)
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.b_x0 = torch.tensor([b.x0 for b in blobs], **f64)
+        self.b_v = torch.tensor([b.v for b in blobs], **f64)
+        self.b_amp = torch.tensor([b.q / ((2.0 * math.pi) ** 1.5 * b.sigma ** 3) for b in blobs], **f64)
+        self.b_inv2s2 = torch.tensor([0.5 / b.sigma ** 2 for b in blobs], **f64)
         self.n_pushed = 0
         self.last_push = None               # event after the latest push
         self.readers: List = []             # events of batches reading the ring
 
     def slice_at(self, t: float):
+        """rho = sum of the blobs' Gaussians at time t, J = sum of rho_blob v_blob."""
         torch = self.torch
-        rho = torch.zeros(self.pts.shape[0], dtype=torch.float64, device=self.device)
-        J = torch.zeros((self.pts.shape[0], 3), dtype=torch.float64, device=self.device)
-        for b in self.blobs:
-            c = torch.tensor([b.x0[a] + b.v[a] * t for a in range(3)], dtype=torch.float64,
-                             device=self.device)
-            r2 = ((self.pts - c) ** 2).sum(dim=1)
-            g = b.q / ((2.0 * math.pi) ** 1.5 * b.sigma ** 3) * torch.exp(-0.5 * r2 / b.sigma ** 2)
-            rho += g
-            J += g[:, None] * torch.tensor(b.v, dtype=torch.float64, device=self.device)[None, :]
-        return rho, J
+        centres = self.b_x0 + self.b_v * t                                # [nb, 3]
+        r2 = ((self.pts[None, :, :] - centres[:, None, :]) ** 2).sum(dim=2)  # [nb, N]
+        g = self.b_amp[:, None] * torch.exp(-r2 * self.b_inv2s2[:, None])
+        rho = g.sum(dim=0)
+        J = torch.einsum("bn,ba->na", g, self.b_v)
+        return rho.contiguous(), J.contiguous()
 
     def push_next(self, stream):
         """Push the next slice on `stream` after every batch still reading the ring."""
@@ -387,20 +395,26 @@ def poisson_requests(n: int, rate: float, n_problems: int, obs_sides=(8, 48), se
 
 def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0), sides=(16, 64),
             H_range=(64, 256), obs_sides=(8, 48), seed: int = 11, tick_s: float = 0.02,
-            n_streams: int = 4, max_batch: int = 32) -> dict:
+            n_streams: int = 4, max_batch: int = 32, memory_budget: Optional[float] = None) -> dict:
     """Latency of Poisson-arriving requests against resident problems.
 
     First the saturated throughput (every request arrives at once), then, for
     each load factor f, a fresh stream of requests arriving at f times that
     rate, with one slice pushed to every problem per tick.  Returns the
-    percentiles per load and the resident memory."""
+    percentiles per load and the resident memory.  The device-memory budget
+    (resident histories, cached views and outputs) defaults to 80 % of the
+    device's memory."""
     import torch
 
+    if memory_budget is None:
+        memory_budget = 0.8 * torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory
     probs = make_problems(n_problems, seed, sides=sides, H_range=H_range)
-    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=n_streams, max_batch=max_batch, tick_s=None)
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=n_streams, max_batch=max_batch, tick_s=None,
+                        memory_budget=memory_budget)
     sat = eng.run(poisson_requests(n_requests, rate=1e9, n_problems=n_problems, obs_sides=obs_sides,
                                    seed=seed + 1))
     out = {"problems": n_problems, "requests_per_load": n_requests, "source_sides": list(sides),
+           "memory_budget_bytes": int(memory_budget),
            "history_slices": list(H_range), "obs_sides": list(obs_sides),
            "resident_ring_bytes": int(eng.resident_bytes),
            "saturated": {"requests_per_s": sat.requests_per_s, "pairs_per_s": sat.pairs_per_s,
@@ -433,10 +447,13 @@ def main(argv=None):
     ap.add_argument("--obs-sides", default="8,48", help="observation grid side range")
     ap.add_argument("--seed", type=int, default=11)
     ap.add_argument("--tick-ms", type=float, default=20.0, help="one slice pushed per problem per tick")
+    ap.add_argument("--budget-gb", type=float, default=None,
+                    help="device memory for histories, views and outputs (default: 80 %% of the device)")
     a = ap.parse_args(argv)
     pair = lambda s: tuple(int(x) for x in s.split(","))
     res = measure(a.problems, a.requests, tuple(float(x) for x in a.loads.split(",")), pair(a.sides),
-                  pair(a.history), pair(a.obs_sides), a.seed, a.tick_ms / 1e3)
+                  pair(a.history), pair(a.obs_sides), a.seed, a.tick_ms / 1e3,
+                  memory_budget=None if a.budget_gb is None else a.budget_gb * 1e9)
     print(json.dumps(res))
 
 
