@@ -278,6 +278,8 @@ struct jefi_problem {
     float* tile_box = nullptr;
     float2* tab2 = nullptr;
     std::vector<float2> h_tab2;
+    float4* tabg = nullptr;          // direct-gather kernel: thresholds and slots per candidate
+    std::vector<float4> h_tabg;
     alignas(64) CUtensorMap tmap;
     int32_t* status = nullptr;
     // observation views share a base handle's ring and pushes
@@ -420,6 +422,35 @@ void build_tables(jefi_problem* h, int ti, double t) {
             t2[e] = make_float2(thi, tlo);
         }
     }
+    if (h->tabg) {
+        // direct-gather kernel: (T_hi, T_lo) of Theta_k' and the physical slots of k', k'-1
+        const int KT = K + 2 * kTabGuard;
+        float4* tg = h->h_tabg.data() + (size_t)ti * KT;
+        auto slot_bits = [&](int64_t k) {
+            const int32_t ps = (int32_t)phys_slot(h, k);
+            float f;
+            std::memcpy(&f, &ps, 4);
+            return f;
+        };
+        for (int e = 0; e < KT; ++e) {
+            const int i = e - kTabGuard;
+            const float z = slot_bits(k0 + i), w = slot_bits(k0 + i - 1);
+            if (i < 0 || i >= K) {
+                tg[e] = make_float4(-INFINITY, INFINITY, z, w);   // never reached; undecided if it were
+                continue;
+            }
+            const double th_k = th[i];
+            float thi, tlo;
+            if (th_k < 0) thi = tlo = -INFINITY;
+            else if (std::isinf(th_k)) thi = tlo = INFINITY;
+            else if (h->exact) thi = tlo = round_down_f32(th_k);
+            else {
+                thi = round_down_f32(th_k - err(th_k));
+                tlo = round_up_f32(th_k + err(th_k));
+            }
+            tg[e] = make_float4(thi, tlo, z, w);
+        }
+    }
     TimeParams tp;
     const double A = T / dt - (double)k0;
     tp.A = (float)A;
@@ -478,6 +509,7 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     p.H = h->H;
     p.status = h->status;
     p.tab2 = h->tab2 ? h->tab2 + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
+    p.tabg = h->tabg ? h->tabg + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
     p.tile_box = h->tile_box;
     for (int a = 0; a < 3; ++a) {
         p.n_src_axis[a] = h->src.n[a];
@@ -513,6 +545,9 @@ int upload_tables(jefi_problem* h, int n_t, cudaStream_t s) {
     if (h->band > 0)
         JEFI_CUDA(cudaMemcpyAsync(h->tab2, h->h_tab2.data(),
                                   sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
+    if (h->tabg)
+        JEFI_CUDA(cudaMemcpyAsync(h->tabg, h->h_tabg.data(),
+                                  sizeof(float4) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
     return JEFI_OK;
 }
 
@@ -873,6 +908,26 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         if (h->n_split < 1) h->n_split = 1;
     }
 
+    // ---------------------------------------------------------------- FP32 candidate bias
+    // g bounds |floor argument in FP32 - FP64 rule| (slots), without the |T/dt|
+    // term that each evaluation adds: floor(A + g - R K) is then n or n+1 and
+    // one threshold decides (both FP32 sum kernels).
+    if (!h->fp64 && h->any_pairs) {
+        const double Kd = 1.0 / (p->c * p->dt);
+        const double u = std::ldexp(1.0, -24);
+        const double eps_rsqrt = std::ldexp(1.0, -22);   // measured max 2^-22.93 over all normals
+        const double eps_S = h->exact ? 0.0
+                                      : h->err_rel + h->err_lin / std::sqrt(h->pad.s_min) + h->err_abs / h->pad.s_min;
+        const double w_max = std::sqrt(h->pad.s_max) * Kd;
+        const double A_max = h->K + 2.0;
+        h->g_bias = 2.0 * (u * (2 * A_max + 2) + w_max * (eps_S / 2 + eps_rsqrt + 4 * u) +
+                           u * (A_max + w_max + 2));
+        if (!(2 * (h->g_bias + 1e-3) < 1.0)) {
+            delete h;
+            return JEFI_EUNSUPPORTED;   // FP32 cannot place the candidate within one slot: use FP64
+        }
+    }
+
     // ---------------------------------------------------------------- staged FP32 kernel
     // The TMA-staged kernel needs every (tile, brick) slot band to fit one of
     // the compiled band heights, and a candidate bias g with 2g < 1.
@@ -905,18 +960,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         int band = 0;
         for (int b : bands)
             if (need <= b) { band = b; break; }
-        // candidate bias: bound on |floor argument in FP32 - FP64 rule| (slots),
-        // without the |T/dt| term that each evaluation adds
-        const double u = std::ldexp(1.0, -24);
-        const double eps_rsqrt = std::ldexp(1.0, -22);   // measured max 2^-22.93 over all normals
-        const double eps_S = h->exact ? 0.0
-                                      : h->err_rel + h->err_lin / std::sqrt(h->pad.s_min) + h->err_abs / h->pad.s_min;
-        const double w_max = std::sqrt(h->pad.s_max) * Kd;
-        const double A_max = h->K + 2.0;
-        h->g_bias = 2.0 * (u * (2 * A_max + 2) + w_max * (eps_S / 2 + eps_rsqrt + 4 * u) +
-                           u * (A_max + w_max + 2));
         if (base && band > base->mirror) band = 0;      // a view fits the base ring's mirror
-        if (band > 0 && 2 * (h->g_bias + 1e-3) < 1.0) {
+        if (band > 0) {
             SumParams probe{};
             probe.K = h->K;
             probe.nbx = h->nbx;
@@ -953,6 +998,11 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->times = (TimeParams*)dev_alloc(h, sizeof(TimeParams) * h->time_chunk);
     h->fallbacks = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
     h->status = (int32_t*)dev_alloc(h, sizeof(int32_t));
+    if (!h->fp64 && h->any_pairs && h->band == 0) {
+        h->tabg = (float4*)dev_alloc(h, sizeof(float4) * h->time_chunk * (h->K + 2 * kTabGuard));
+        if (!h->tabg) h->status = nullptr;
+        h->h_tabg.resize((size_t)h->time_chunk * (h->K + 2 * kTabGuard));
+    }
     if (h->band > 0) {
         h->tile_box = (float*)dev_alloc(h, sizeof(float) * tile_box.size());
         h->tab2 = (float2*)dev_alloc(h, sizeof(float2) * h->time_chunk * (h->K + 2 * kTabGuard));

@@ -83,6 +83,9 @@ struct SumParams {
     int32_t nfull[3];               // whole bricks per axis (bricks past them hold padding cells)
     int32_t H;                      // ring period (physical slot of slice n is n mod H)
     int32_t comp;                   // FP32: compensated (Kahan) per-thread sums
+    // direct-gather kernel: [n_t][K + 2 kTabGuard] {T_hi, T_lo, phys slot of k', of k'-1}
+    // per candidate slot k' (the staged kernel's candidate rule, slots read from global memory)
+    const float4* tabg;
     // second-order retarded time: sources interpolated between slots n and n+1
     int32_t interp;
     float K32_lo;                   // fp32(1/(c dt) - K32)

@@ -33,15 +33,21 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                                                 const int ti) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K;
-    float4* s_tab = reinterpret_cast<float4*>(smem);
+    const int KT = K + 2 * kTabGuard;
+    float4* s_tabg = reinterpret_cast<float4*>(smem);
+    float4* s_tab = s_tabg + KT;
     double* s_th = reinterpret_cast<double*>(s_tab + K);
     float* s_D = reinterpret_cast<float*>(s_th + K + 1);
     const int tid = threadIdx.x;
 
     const float4* g_tab = p.tab32 + (size_t)ti * K;
     const double* g_th = p.theta + (size_t)ti * (K + 1);
+    const float4* g_tabg = p.tabg + (size_t)ti * KT;
+    for (int i = tid; i < KT; i += kTileThreads) s_tabg[i] = g_tabg[i];
     for (int i = tid; i < K; i += kTileThreads) s_tab[i] = g_tab[i];
     for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
+    // s_tabg[bits - kMagicBits + kTabGuard] sits at byte smem + tgbase + 16 bits (offset mod 2^32)
+    const uint32_t tgbase = (uint32_t)(kTabGuard - kMagicBits) * 16u;
 
     // Anchor: the tile's first point.  D[b] = fp32(anchor - centre of the
     // brick's first cell) per axis, so that P = (x_o - anchor) + D is small
@@ -72,6 +78,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
     const float A = tp.A;
     const float K32 = p.K32;
     const float A_lo = tp.A_lo, K32_lo = p.K32_lo;   // interpolation weights only
+    const float Ag = tp.Ag;
     const float d32x = p.d32[0], d32y = p.d32[1], d32z = p.d32[2];
     const int Hp = p.Hp;
     const float4* ring = reinterpret_cast<const float4*>(p.ring);
@@ -138,57 +145,112 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                 pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
             }
         } else {
-            // Far bricks: every squared distance from per-axis squares.
-            float ddx[4], ddy[4], ddz[4], sqx[4], sqy[4], sqz[4];
+            // Far bricks: the staged kernel's slot rule (candidate k' from
+            // A + g, one threshold decides k' or k'-1) with the slot's row
+            // read from global memory; no branch per pair, so the gathers of
+            // a slab can all be in flight together.  The z slabs are a rolled
+            // loop, the 16 cells of a slab are unrolled.
+            float ddx[4], ddy[4], sqx[4], sqy[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 ddx[i] = fmaf(-(float)i, d32x, Px);
                 ddy[i] = fmaf(-(float)i, d32y, Py);
-                ddz[i] = fmaf(-(float)i, d32z, Pz);
                 sqx[i] = __fmul_rn(ddx[i], ddx[i]);
                 sqy[i] = __fmul_rn(ddy[i], ddy[i]);
-                sqz[i] = __fmul_rn(ddz[i], ddz[i]);
             }
-            float sxy[16];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) sxy[j * 4 + i] = __fadd_rn(sqx[i], sqy[j]);
-#pragma unroll
+            uint64_t mask = 0;          // undecided pairs (non-lattice geometry), redone below
+            float2 acc_eyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
+            float acc_ex = 0.f, acc_bz = 0.f;
+#pragma unroll 1
             for (int k = 0; k < 4; ++k) {
+                const float dz = fmaf(-(float)k, d32z, Pz);
+                const float sqz = __fmul_rn(dz, dz);
+                const float4* ck = cbase + (size_t)(k * 16) * Hp * 2;
+                float2 dyz[4], dzx[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    dyz[i] = make_float2(ddy[i], dz);
+                    dzx[i] = make_float2(dz, ddx[i]);
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    const float syz = __fadd_rn(sqy[j], sqz);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const int cl = k * 16 + j * 4 + i;
-                        const float S = __fadd_rn(sxy[j * 4 + i], sqz[k]);
-                        const float ri = rsqrt_ftz(S);
-                        unsigned idx = candidate_index(S, ri, K32, A, K);
-                        float4 e = s_tab[idx];
-                        const bool ok = (S <= e.x) & (S > e.y);
-                        if (__any_sync(kFull, !ok)) {
-                            if (!ok) {
-                                idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1],
-                                                        p.lo[2], p.d[0], p.d[1], p.d[2],
-                                                        kBrick * bx + i, kBrick * by + j,
-                                                        kBrick * bz + k, s_th, K, (int)idx,
-                                                        p.fallbacks);
-                                e = s_tab[idx];
-                            }
+                        const int c16 = j * 4 + i;
+                        const float S = __fadd_rn(sqx[i], syz);
+                        float ri = rsqrt_ftz(S);
+                        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
+                        const float4 e = *reinterpret_cast<const float4*>(smem + (tgbase + bits * 16u));
+                        const bool lower = S > e.y;
+                        if (!(S <= e.x) && !lower) {   // undecided: redo after the brick
+                            mask |= 1ull << (k * 16 + c16);
+                            ri = 0.f;
                         }
+                        const int ps = __float_as_int(lower ? e.w : e.z);
                         if (DEBUG) {
-                            p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells +
-                                          cl] = (int)(tp.k0 + idx);
+                            p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + k * 16 + c16] =
+                                (int)(tp.k0 + (int)(bits - kMagicBits) - (lower ? 1 : 0));
                         }
-                        const float4* q = cbase + (cl * Hp + __float_as_int(e.z)) * 2;
+                        const float4* q = ck + (c16 * Hp + ps) * 2;
                         float4 v0 = __ldg(q), v1 = __ldg(q + 1);
-                        if (INTERP) {
-                            const float4* q1 = cbase + (cl * Hp + __float_as_int(s_tab[idx + 1].z)) * 2;
-                            lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1),
-                                  interp_weight(S, ri, (float)(int)idx, A, A_lo, K32, K32_lo));
+                        if (INTERP) {   // slot n+1: k' when n = k'-1, else k'+1
+                            const float z1 = *reinterpret_cast<const float*>(smem + (tgbase + bits * 16u + 24u));
+                            const float4* q1 = ck + (c16 * Hp + __float_as_int(lower ? e.z : z1)) * 2;
+                            const float nrel = __uint_as_float(bits - (lower ? 1u : 0u)) - kMagic;
+                            lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1), interp_weight(S, ri, nrel, A, A_lo, K32, K32_lo));
                         }
-                        pair_f32(ddx[i], ddy[j], ddz[k], ri, v0, v1, pe, pb);
+                        // Eqs. E-1/B-1, packed, r^-2 factored out (as in the staged kernel)
+                        const float2 ri2 = make_float2(ri, ri);
+                        const float2 r2 = __fmul2_rn(ri2, ri2);
+                        const float2 qvx = __fmul2_rn(__ffma2_rn(make_float2(v0.x, v0.y), ri2,
+                                                                 make_float2(v1.x, v1.y)), r2);
+                        const float2 vyz = __fmul2_rn(__ffma2_rn(make_float2(v0.z, v0.w), ri2,
+                                                                 make_float2(v1.z, v1.w)), r2);
+                        const float qq = qvx.x, vx = qvx.y;
+                        acc_ex = fmaf(ddx[i], qq, acc_ex);
+                        acc_ex = fmaf(-v1.y, ri, acc_ex);
+                        acc_eyz = __ffma2_rn(dyz[j], make_float2(qq, qq), acc_eyz);
+                        acc_eyz = __ffma2_rn(make_float2(-v1.z, -v1.w), ri2, acc_eyz);
+                        acc_bxy = __ffma2_rn(vyz, dzx[i], acc_bxy);
+                        acc_bxy.x = fmaf(-vyz.y, ddy[j], acc_bxy.x);
+                        acc_bxy.y = fmaf(-vx, dz, acc_bxy.y);
+                        acc_bz = fmaf(vx, ddy[j], acc_bz);
+                        acc_bz = fmaf(-vyz.x, ddx[i], acc_bz);
                     }
+                }
+            }
+            pe[0] += acc_ex;
+            pe[1] += acc_eyz.x;
+            pe[2] += acc_eyz.y;
+            pb[0] += acc_bxy.x;
+            pb[1] += acc_bxy.y;
+            pb[2] += acc_bz;
+            if (__any_sync(kFull, mask != 0ull)) {
+                while (mask) {
+                    const int cl = __ffsll((long long)mask) - 1;
+                    mask &= mask - 1;
+                    const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+                    const float dx = fmaf(-(float)i, d32x, Px);
+                    const float dy = fmaf(-(float)j, d32y, Py);
+                    const float dz = fmaf(-(float)k, d32z, Pz);
+                    const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+                    const float ri = rsqrt_ftz(S);
+                    const unsigned cand = candidate_index(S, ri, K32, A, K);
+                    const int idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
+                                                      p.d[1], p.d[2], kBrick * bx + i, kBrick * by + j,
+                                                      kBrick * bz + k, s_th, K, (int)cand, p.fallbacks);
+                    if (DEBUG) {
+                        p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(tp.k0 + idx);
+                    }
+                    const float4* q = cbase + (cl * Hp + __float_as_int(s_tab[idx].z)) * 2;
+                    float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                    if (INTERP) {
+                        const float4* q1 = cbase + (cl * Hp + __float_as_int(s_tab[idx + 1].z)) * 2;
+                        lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1),
+                              interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
+                    }
+                    pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
                 }
             }
         }
@@ -565,6 +627,7 @@ cudaError_t launch_reduce_batch(const ReduceItem* items, const int64_t* out_star
 
 size_t sum_smem_bytes(const SumParams& p) {
     size_t b = (size_t)p.K * sizeof(float4) + (size_t)(p.K + 1) * sizeof(double);
+    if (p.tabg) b += (size_t)(p.K + 2 * kTabGuard) * sizeof(float4);
     return b + (size_t)(p.npx + p.npy + p.npz) * sizeof(double);
 }
 
