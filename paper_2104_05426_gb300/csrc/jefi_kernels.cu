@@ -27,7 +27,48 @@ namespace jefi {
 using namespace dev;
 
 // ============================================================================ FP32
-// Shared memory: tab32[K] float4 | theta[K+1] double | D[nbx+nby+nbz] float
+// Shared memory: tabg[K + 2 guard] float4 | tab32[K] float4 | theta[K+1] double | D[nbx+nby+nbz] float
+
+struct Fix6 {
+    float v[6];   // E', B contributions
+};
+
+// Pairs of a far brick whose slot the FP32 rule left undecided: exact slot
+// in FP64, then the pair as usual.  A call of its own (rare), so that its
+// registers do not weigh on the brick loop.
+template <bool DEBUG, bool INTERP>
+__device__ __noinline__ Fix6 direct_fixup(const SumParams& p, uint64_t mask, int slot, int b, int bx, int by, int bz,
+                                          float Px, float Py, float Pz, const float4* cbase, const float4* s_tab,
+                                          const double* s_th, int64_t k0, float A, float A_lo) {
+    float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
+    const int K = p.K, Hp = p.Hp;
+    const float K32 = p.K32, K32_lo = p.K32_lo;
+    const size_t n_cells = (size_t)p.n_bricks * kBrickCells;
+    while (mask) {
+        const int cl = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+        const float dx = fmaf(-(float)i, p.d32[0], Px);
+        const float dy = fmaf(-(float)j, p.d32[1], Py);
+        const float dz = fmaf(-(float)k, p.d32[2], Pz);
+        const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+        const float ri = rsqrt_ftz(S);
+        const unsigned cand = candidate_index(S, ri, K32, A, K);
+        const int idx = slot_fallback_f32(p.obs_xyz, slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
+                                          kBrick * bx + i, kBrick * by + j, kBrick * bz + k, s_th, K, (int)cand,
+                                          p.fallbacks);
+        if (DEBUG) p.debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
+        const float4* q = cbase + (cl * Hp + __float_as_int(s_tab[idx].z)) * 2;
+        float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+        if (INTERP) {
+            const float4* q1 = cbase + (cl * Hp + __float_as_int(s_tab[idx + 1].z)) * 2;
+            lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1), interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
+        }
+        pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+    }
+    return Fix6{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
+}
+
 template <bool COMP, bool DEBUG, bool INTERP>
 __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int tile, const int split,
                                                 const int ti) {
@@ -227,31 +268,14 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
             pb[1] += acc_bxy.y;
             pb[2] += acc_bz;
             if (__any_sync(kFull, mask != 0ull)) {
-                while (mask) {
-                    const int cl = __ffsll((long long)mask) - 1;
-                    mask &= mask - 1;
-                    const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
-                    const float dx = fmaf(-(float)i, d32x, Px);
-                    const float dy = fmaf(-(float)j, d32y, Py);
-                    const float dz = fmaf(-(float)k, d32z, Pz);
-                    const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-                    const float ri = rsqrt_ftz(S);
-                    const unsigned cand = candidate_index(S, ri, K32, A, K);
-                    const int idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
-                                                      p.d[1], p.d[2], kBrick * bx + i, kBrick * by + j,
-                                                      kBrick * bz + k, s_th, K, (int)cand, p.fallbacks);
-                    if (DEBUG) {
-                        p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(tp.k0 + idx);
-                    }
-                    const float4* q = cbase + (cl * Hp + __float_as_int(s_tab[idx].z)) * 2;
-                    float4 v0 = __ldg(q), v1 = __ldg(q + 1);
-                    if (INTERP) {
-                        const float4* q1 = cbase + (cl * Hp + __float_as_int(s_tab[idx + 1].z)) * 2;
-                        lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1),
-                              interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
-                    }
-                    pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
-                }
+                const Fix6 f = direct_fixup<DEBUG, INTERP>(p, mask, ctx.slot, b, bx, by, bz, Px, Py, Pz, cbase,
+                                                           s_tab, s_th, tp.k0, A, A_lo);
+                pe[0] += f.v[0];
+                pe[1] += f.v[1];
+                pe[2] += f.v[2];
+                pb[0] += f.v[3];
+                pb[1] += f.v[4];
+                pb[2] += f.v[5];
             }
         }
 #pragma unroll
@@ -303,12 +327,18 @@ __device__ __forceinline__ bool next_item(const BatchArgs& a, int* s_item, int* 
     return true;
 }
 
+// One item of the batched direct-gather kernel as a call of its own (the
+// item body keeps the single-problem kernel's register budget).
+template <bool COMP>
+__device__ __noinline__ void direct_batch_item(const SumParams& p, int tile, int split, int ti) {
+    direct_f32_item<COMP, false, false>(p, tile, split, ti);
+}
+
 template <bool COMP>
 __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_batch(const BatchArgs a) {
     __shared__ int s_item;
     int pr, tile, split, ti;
-    while (next_item(a, &s_item, &pr, &tile, &split, &ti))
-        direct_f32_item<COMP, false, false>(a.params[pr], tile, split, ti);
+    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) direct_batch_item<COMP>(a.params[pr], tile, split, ti);
 }
 
 // ============================================================================ FP64
