@@ -1023,8 +1023,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     if (e == cudaSuccess && !base) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
     if (e == cudaSuccess && !base)
         e = cudaMemsetAsync(h->prev, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
-        if (e == cudaSuccess && h->prev2)
-            e = cudaMemsetAsync(h->prev2, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
+    if (e == cudaSuccess && !base && h->prev2)   // a view shares its base's difference state
+        e = cudaMemsetAsync(h->prev2, 0, sizeof(double) * 4 * std::max<int64_t>(1, h->n_src), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fallbacks, 0, sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && h->band > 0)

@@ -235,3 +235,29 @@ def test_interp_refused_by_batched_launch(gpu, c1):
     assert e.value.code == jefi.JEFI_EUNSUPPORTED
     assert bool((E == 7.0).all()) and bool((B == 7.0).all())
     jefi.jefi_destroy(h)
+
+
+def test_view_creation_keeps_the_base_central_difference_state(gpu, c1):
+    """Creating a view in the middle of the pushes must not touch the base's
+    difference state (the view shares it): the base then gives the same
+    fields as a twin that never had a view."""
+    import torch
+
+    p, hist = c1
+    n = hist[0].shape[0]
+    a = create(p, "fp64", flags=INTERP)
+    b = create(p, "fp64", flags=INTERP)
+    push_all(a, hist, upto=n // 2)
+    push_all(b, hist, upto=n // 2)
+    view = jefi.jefi_create_view(a, obs_grid=jefi.grid_from(p.obs_grid))
+    rho, J, _, _ = hist
+    for k in range(n // 2, n):
+        for h in (a, b):
+            jefi.jefi_push_sources(h, torch.from_numpy(rho[k]).cuda(), torch.from_numpy(J[k]).cuda())
+    _, hi = jefi.jefi_valid_window(b)
+    Ea, Ba = jefi.eval_fields(a, [hi - 0.2, hi])
+    Eb, Bb = jefi.eval_fields(b, [hi - 0.2, hi])
+    assert torch.equal(Ea, Eb) and torch.equal(Ba, Bb)
+    jefi.jefi_destroy(view)
+    for h in (a, b):
+        jefi.jefi_destroy(h)
