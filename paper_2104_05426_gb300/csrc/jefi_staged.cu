@@ -98,7 +98,11 @@ struct Layout {
     static constexpr uint32_t kRowBytes = 32;                          // 8 FP32 channels
     static constexpr uint32_t kCellBytes = BAND * kRowBytes;
     static constexpr uint32_t kBufBytes = kBrickCells * kCellBytes;
-    static constexpr uint32_t kCtrl = 2 * kBufBytes;                   // mbarriers, band origins
+    // Bands of 32 and more rows are single-buffered: two CTAs per SM then fit
+    // in shared memory (two double-buffered CTAs would not), and each CTA's
+    // copy of its next brick overlaps the other CTA's arithmetic.
+    static constexpr int kBufs = BAND >= 32 ? 1 : 2;
+    static constexpr uint32_t kCtrl = kBufs * kBufBytes;               // mbarriers, band origins
     static constexpr uint32_t kTab = kCtrl + 64;                        // float2 table
 };
 
@@ -220,7 +224,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
 
     if (tid == 0 && b_begin < b_end) {
         const int rest = b_begin / p.nbx;
-        issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, g_it & 1);
+        issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, L::kBufs == 2 ? (int)(g_it & 1) : 0);
     }
     int64_t aborted_at = -1;
     // brick coordinates of b, advanced incrementally (no division per brick)
@@ -233,8 +237,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     }
     for (int b = b_begin; b < b_end; ++b) {
         const uint32_t it = g_it + (uint32_t)(b - b_begin);
-        const int buf = it & 1;
-        if (tid == 0 && b + 1 < b_end) {
+        // buffer and mbarrier phase of brick b (one phase per copy into a buffer)
+        const int buf = L::kBufs == 2 ? (int)(it & 1) : 0;
+        const uint32_t parity = L::kBufs == 2 ? (it >> 1) & 1 : it & 1;
+        if (L::kBufs == 2 && tid == 0 && b + 1 < b_end) {
             int nx = bx + 1, ny = by, nz = bz;
             if (nx == p.nbx) {
                 nx = 0;
@@ -242,7 +248,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
             }
             issue(nx, ny, nz, b + 1, buf ^ 1);
         }
-        const bool ready = mbar_wait_bounded(mbar_u32[buf], (it >> 1) & 1);
+        const bool ready = mbar_wait_bounded(mbar_u32[buf], parity);
         if (ready) {
             const int band_rel = s_band[buf];
             const float Px = oox + s_D[bx];
@@ -460,6 +466,8 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
             aborted_at = b - b_begin;
             break;
         }
+        // single buffer: the next brick's copy starts now (bx, by, bz already name it)
+        if (L::kBufs == 1 && tid == 0 && b + 1 < b_end) issue(bx, by, bz, b + 1, 0);
     }
     if (aborted_at >= 0) {
         // a copy did not complete in time: report, then wait (bounded) for
@@ -467,8 +475,13 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         if (tid == 0) {
             const uint32_t it = g_it + (uint32_t)aborted_at;
             atomicExch(p.status, kStatusTimeout);
-            mbar_wait_bounded(mbar_u32[it & 1], (it >> 1) & 1);
-            if (b_begin + aborted_at + 1 < b_end) mbar_wait_bounded(mbar_u32[(it + 1) & 1], ((it + 1) >> 1) & 1);
+            if (L::kBufs == 2) {
+                mbar_wait_bounded(mbar_u32[it & 1], (it >> 1) & 1);
+                if (b_begin + aborted_at + 1 < b_end)
+                    mbar_wait_bounded(mbar_u32[(it + 1) & 1], ((it + 1) >> 1) & 1);
+            } else {
+                mbar_wait_bounded(mbar_u32[0], it & 1);   // the next copy was never issued
+            }
         }
         __syncthreads();
     }
@@ -565,7 +578,7 @@ bool staged_band_supported(int band) { return band == 16 || band == 24 || band =
 
 size_t staged_smem_bytes(const SumParams& p, int band) {
     const size_t buf = (size_t)kBrickCells * band * 32;
-    size_t b = 2 * buf + 64;                 // two buffers, mbarriers / band origins / item
+    size_t b = (band >= 32 ? 1 : 2) * buf + 64;   // brick buffers, mbarriers / band origins / item
     b += (size_t)(p.K + 2 * kTabGuard) * sizeof(float2);
     b += (size_t)(p.K + 1) * sizeof(double);
     b += (size_t)(p.nbx + p.nby + p.nbz) * sizeof(float);
