@@ -224,7 +224,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
 
     if (tid == 0 && b_begin < b_end) {
         const int rest = b_begin / p.nbx;
-        issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, L::kBufs == 2 ? (int)(g_it & 1) : 0);
+        if constexpr (L::kBufs == 2)
+            issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, g_it & 1);
+        else
+            issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, 0);
     }
     int64_t aborted_at = -1;
     // brick coordinates of b, advanced incrementally (no division per brick)
@@ -238,17 +241,23 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     for (int b = b_begin; b < b_end; ++b) {
         const uint32_t it = g_it + (uint32_t)(b - b_begin);
         // buffer and mbarrier phase of brick b (one phase per copy into a buffer)
-        const int buf = L::kBufs == 2 ? (int)(it & 1) : 0;
-        const uint32_t parity = L::kBufs == 2 ? (it >> 1) & 1 : it & 1;
-        if (L::kBufs == 2 && tid == 0 && b + 1 < b_end) {
-            int nx = bx + 1, ny = by, nz = bz;
-            if (nx == p.nbx) {
-                nx = 0;
-                if (++ny == p.nby) { ny = 0; ++nz; }
+        int buf;
+        bool ready;
+        if constexpr (L::kBufs == 2) {
+            buf = it & 1;
+            if (tid == 0 && b + 1 < b_end) {
+                int nx = bx + 1, ny = by, nz = bz;
+                if (nx == p.nbx) {
+                    nx = 0;
+                    if (++ny == p.nby) { ny = 0; ++nz; }
+                }
+                issue(nx, ny, nz, b + 1, buf ^ 1);
             }
-            issue(nx, ny, nz, b + 1, buf ^ 1);
+            ready = mbar_wait_bounded(mbar_u32[buf], (it >> 1) & 1);
+        } else {
+            buf = 0;
+            ready = mbar_wait_bounded(mbar_u32[0], it & 1);
         }
-        const bool ready = mbar_wait_bounded(mbar_u32[buf], parity);
         if (ready) {
             const int band_rel = s_band[buf];
             const float Px = oox + s_D[bx];
@@ -466,8 +475,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
             aborted_at = b - b_begin;
             break;
         }
-        // single buffer: the next brick's copy starts now (bx, by, bz already name it)
-        if (L::kBufs == 1 && tid == 0 && b + 1 < b_end) issue(bx, by, bz, b + 1, 0);
+        if constexpr (L::kBufs == 1) {
+            // single buffer: the next brick's copy starts now (bx, by, bz already name it)
+            if (tid == 0 && b + 1 < b_end) issue(bx, by, bz, b + 1, 0);
+        }
     }
     if (aborted_at >= 0) {
         // a copy did not complete in time: report, then wait (bounded) for
@@ -475,7 +486,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         if (tid == 0) {
             const uint32_t it = g_it + (uint32_t)aborted_at;
             atomicExch(p.status, kStatusTimeout);
-            if (L::kBufs == 2) {
+            if constexpr (L::kBufs == 2) {
                 mbar_wait_bounded(mbar_u32[it & 1], (it >> 1) & 1);
                 if (b_begin + aborted_at + 1 < b_end)
                     mbar_wait_bounded(mbar_u32[(it + 1) & 1], ((it + 1) >> 1) & 1);
