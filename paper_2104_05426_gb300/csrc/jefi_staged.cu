@@ -122,6 +122,55 @@ __device__ __forceinline__ void staged_init_barriers() {
     __syncthreads();
 }
 
+struct FixSums {
+    float v[6];   // E', B contributions
+};
+
+// Pairs of a full brick whose slot the FP32 rule left undecided (non-lattice
+// geometry): exact slot in FP64, then the pair from the brick's buffer.  A
+// call of its own (rare), so its registers do not weigh on the brick loop.
+template <int BAND, bool DEBUG, bool INTERP>
+__device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char* bufp, int band_rel, float Px,
+                                             float Py, float Pz, float d32x, float d32y, float d32z, float K32,
+                                             float Ag, float A, float A_lo, float K32_lo, const double* obs_xyz,
+                                             int slot, double lox, double loy, double loz, double dx_, double dy_,
+                                             double dz_, int bx, int by, int bz, const double* s_th, int K,
+                                             unsigned long long* fallbacks, int32_t* status, int32_t* debug_slots,
+                                             size_t n_cells, int b, int64_t k0) {
+    using L = Layout<BAND>;
+    float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
+    while (mask) {
+        const int cl = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+        const float dx = fmaf(-(float)i, d32x, Px);
+        const float dy = fmaf(-(float)j, d32y, Py);
+        const float dz = fmaf(-(float)k, d32z, Pz);
+        const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+        const float ri = rsqrt_ftz(S);
+        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
+        const int idx = slot_fallback_f32(obs_xyz, slot, lox, loy, loz, dx_, dy_, dz_, kBrick * bx + i,
+                                          kBrick * by + j, kBrick * bz + k, s_th, K, (int)(bits - kMagicBits),
+                                          fallbacks);
+        int row = idx - band_rel;
+        if (row < 0 || row >= BAND) {
+            atomicExch(status, kStatusInternal);
+            row = row < 0 ? 0 : BAND - 1;
+        }
+        if (DEBUG) debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
+        const uint32_t off = (uint32_t)cl * L::kCellBytes + (uint32_t)row * L::kRowBytes;
+        float4 v0 = *reinterpret_cast<const float4*>(bufp + off);
+        float4 v1 = *reinterpret_cast<const float4*>(bufp + off + 16u);
+        if (INTERP) {
+            const float4 u0 = *reinterpret_cast<const float4*>(bufp + off + 32u);
+            const float4 u1 = *reinterpret_cast<const float4*>(bufp + off + 48u);
+            lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
+        }
+        pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+    }
+    return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
+}
+
 // One work item: observation tile `tile` x source split `split` at time
 // index `ti` of problem p.  g_it counts the CTA's staged bricks across items
 // (it selects the buffer and the mbarrier phase).  Returns false if a copy
@@ -365,44 +414,16 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                 pb[0] += acc_bxy.x;
                 pb[1] += acc_bxy.y;
                 pb[2] += acc_bz;
-                const uint32_t m_lo = (uint32_t)mask, m_hi = (uint32_t)(mask >> 32);
                 if (!EXACT) {
-                    if (__any_sync(kFull, (m_lo | m_hi) != 0u)) {
-                        uint64_t mask = ((uint64_t)m_hi << 32) | m_lo;
-                        while (mask) {
-                            const int cl = __ffsll((long long)mask) - 1;
-                            mask &= mask - 1;
-                            const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
-                            const float dx = fmaf(-(float)i, d32x, Px);
-                            const float dy = fmaf(-(float)j, d32y, Py);
-                            const float dz = fmaf(-(float)k, d32z, Pz);
-                            const float S = __fadd_rn(__fmul_rn(dx, dx),
-                                                      __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-                            const float ri = rsqrt_ftz(S);
-                            const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-                            const int idx = slot_fallback_f32(
-                                p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
-                                kBrick * bx + i, kBrick * by + j, kBrick * bz + k, s_th, K,
-                                (int)(bits - kMagicBits), p.fallbacks);
-                            int row = idx - band_rel;
-                            if (row < 0 || row >= BAND) {
-                                atomicExch(p.status, kStatusInternal);
-                                row = row < 0 ? 0 : BAND - 1;
-                            }
-                            if (DEBUG) {
-                                p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
-                                    (int)(tp.k0 + idx);
-                            }
-                            const uint32_t off = (uint32_t)buf * L::kBufBytes + (uint32_t)cl * L::kCellBytes +
-                                                 (uint32_t)row * L::kRowBytes;
-                            float4 v0 = *reinterpret_cast<const float4*>(smem + off);
-                            float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
-                            if (INTERP) {
-                                const float4 u0 = *reinterpret_cast<const float4*>(smem + off + 32u);
-                                const float4 u1 = *reinterpret_cast<const float4*>(smem + off + 48u);
-                                lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
-                            }
-                            pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+                    if (__any_sync(kFull, mask != 0ull)) {
+                        FixSums f = staged_fixup<BAND, DEBUG, INTERP>(
+                            mask, smem + (uint32_t)buf * L::kBufBytes, band_rel, Px, Py, Pz, d32x, d32y, d32z,
+                            K32, Ag, A, A_lo, K32_lo, p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1],
+                            p.d[2], bx, by, bz, s_th, K, p.fallbacks, p.status, p.debug_slots, n_cells, b, tp.k0);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            pe[a] += f.v[a];
+                            pb[a] += f.v[3 + a];
                         }
                     }
                 }
