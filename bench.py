@@ -332,6 +332,11 @@ def run_gpu(args):
         jefi.jefi_destroy(hi2)
         if not args.no_serving:
             result["serving"] = serving_leg()
+            from paper_2104_05426_gb300.serving import measure_batch
+
+            result["batch"] = dict(measure_batch(),
+                                   workload="256 independent problems (source sides 8-48, histories "
+                                            "32-128, observation sides 8-32) in one jefi_eval_batch call")
         if not args.no_cpu_baseline:
             result["cpu_baseline"], result["oracle_check"] = cpu_baseline(p, slices[:H], t_first,
                                                                           E_first, B_first)

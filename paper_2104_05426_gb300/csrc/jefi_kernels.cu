@@ -234,12 +234,15 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                                 (int)(tp.k0 + (int)(bits - kMagicBits) - (lower ? 1 : 0));
                         }
                         const float4* q = ck + (c16 * Hp + ps) * 2;
-                        float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+                        float4 v0, v1;
+                        ldg_row8(q, v0, v1);
                         if (INTERP) {   // slot n+1: k' when n = k'-1, else k'+1
                             const float z1 = *reinterpret_cast<const float*>(smem + (tgbase + bits * 16u + 24u));
                             const float4* q1 = ck + (c16 * Hp + __float_as_int(lower ? e.z : z1)) * 2;
                             const float nrel = __uint_as_float(bits - (lower ? 1u : 0u)) - kMagic;
-                            lerp8(v0, v1, __ldg(q1), __ldg(q1 + 1), interp_weight(S, ri, nrel, A, A_lo, K32, K32_lo));
+                            float4 u0, u1;
+                            ldg_row8(q1, u0, u1);
+                            lerp8(v0, v1, u0, u1, interp_weight(S, ri, nrel, A, A_lo, K32, K32_lo));
                         }
                         // Eqs. E-1/B-1, packed, r^-2 factored out (as in the staged kernel)
                         const float2 ri2 = make_float2(ri, ri);

@@ -434,6 +434,54 @@ def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0)
     return out
 
 
+def measure_batch(n_problems: int = 256, sides=(8, 48), H_range=(32, 128), obs_sides=(8, 32), seed: int = 4,
+                  reps: int = 3) -> dict:
+    """Independent problems of uneven sizes in one batched evaluation: source
+    grids of side uniform in `sides`, histories uniform in H_range, one
+    observation grid per problem of side uniform in obs_sides (over a box
+    twice the source box) at one time inside its window; every problem's
+    result comes out of one jefi_eval_batch call (one persistent launch per
+    kernel variant, then one reduction).  Returns the time of the call and
+    the pair rate."""
+    import torch
+
+    probs = make_problems(n_problems, seed, sides=sides, H_range=H_range)
+    rng = np.random.Generator(np.random.PCG64(seed + 100))
+    views, ts, Es, Bs, pairs = [], [], [], [], 0
+    for p in probs:
+        s = int(rng.integers(obs_sides[0], obs_sides[1] + 1))
+        g = grid((s,) * 3, (-2.0,) * 3, (4.0 / s,) * 3)
+        v = jefi_create_view(p.handle, obs_grid=g)
+        lo, hi = jefi_valid_window(v)
+        if not math.isfinite(lo):
+            lo = hi - 4 * p.dt
+        views.append(v)
+        ts.append(lo + (hi - lo) * float(rng.uniform(0.05, 0.95)))
+        Es.append(torch.empty((s ** 3, 3), dtype=torch.float64, device="cuda"))
+        Bs.append(torch.empty_like(Es[-1]))
+        pairs += p.side ** 3 * s ** 3
+    jefi_eval_batch(views, ts, Es, Bs)                 # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        jefi_eval_batch(views, ts, Es, Bs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    bands = [jefi_get_info(v)["staged_band"] for v in views]
+    out = {"problems": n_problems, "source_sides": list(sides), "history_slices": list(H_range),
+           "obs_sides": list(obs_sides), "pairs": pairs, "ms_per_batch": ms, "pairs_per_s": pairs / (ms / 1e3),
+           "staged_problems": sum(1 for b in bands if b > 0),
+           "device_status": max(jefi_get_info(v)["device_status"] for v in views)}
+    for v in views:
+        jefi_destroy(v)
+    for p in probs:
+        jefi_destroy(p.handle)
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
