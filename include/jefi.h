@@ -89,7 +89,9 @@ typedef struct {
     double k_b;               /* B prefactor (mu0/(4 pi); paper: 1/(4 pi))          */
     double dt;                /* slice spacing, > 0                                 */
     double t0;                /* time of slice 0                                    */
-    int32_t history_slots;    /* H: resident slices in the device ring, >= 1        */
+    int32_t history_slots;    /* H: resident slices in the device ring, >= 1 (FP32
+                                 problems on the direct-gather kernel: H + 49 <=
+                                 65536, else jefi_create returns JEFI_EUNSUPPORTED) */
     int32_t precision;        /* jefi_precision                                     */
     int32_t deriv;            /* jefi_deriv_mode                                    */
     int32_t flags;            /* JEFI_FLAG_* bits                                   */

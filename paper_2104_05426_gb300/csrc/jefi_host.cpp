@@ -278,8 +278,10 @@ struct jefi_problem {
     float* tile_box = nullptr;
     float2* tab2 = nullptr;
     std::vector<float2> h_tab2;
-    float4* tabg = nullptr;          // direct-gather kernel: thresholds and slots per candidate
-    std::vector<float4> h_tabg;
+    float2* tabg = nullptr;          // direct-gather kernel: T_lo and packed slots per candidate
+    float* tabh = nullptr;           // direct-gather kernel: T_hi per candidate
+    std::vector<float2> h_tabg;
+    std::vector<float> h_tabh;
     alignas(64) CUtensorMap tmap;
     int32_t* status = nullptr;
     // observation views share a base handle's ring and pushes
@@ -425,18 +427,21 @@ void build_tables(jefi_problem* h, int ti, double t) {
     if (h->tabg) {
         // direct-gather kernel: (T_hi, T_lo) of Theta_k' and the physical slots of k', k'-1
         const int KT = K + 2 * kTabGuard;
-        float4* tg = h->h_tabg.data() + (size_t)ti * KT;
-        auto slot_bits = [&](int64_t k) {
-            const int32_t ps = (int32_t)phys_slot(h, k);
+        float2* tg = h->h_tabg.data() + (size_t)ti * KT;
+        float* th_hi = h->h_tabh.data() + (size_t)ti * KT;
+        auto slot_pair = [&](int64_t k) {   // physical slots of k (low half) and k-1 (high half)
+            const uint32_t pk = (uint32_t)phys_slot(h, k), pm = (uint32_t)phys_slot(h, k - 1);
+            const uint32_t packed = (pk & 0xFFFFu) | (pm << 16);
             float f;
-            std::memcpy(&f, &ps, 4);
+            std::memcpy(&f, &packed, 4);
             return f;
         };
         for (int e = 0; e < KT; ++e) {
             const int i = e - kTabGuard;
-            const float z = slot_bits(k0 + i), w = slot_bits(k0 + i - 1);
+            const float zw = slot_pair(k0 + i);
             if (i < 0 || i >= K) {
-                tg[e] = make_float4(-INFINITY, INFINITY, z, w);   // never reached; undecided if it were
+                tg[e] = make_float2(INFINITY, zw);   // never reached; undecided if it were
+                th_hi[e] = -INFINITY;
                 continue;
             }
             const double th_k = th[i];
@@ -448,7 +453,8 @@ void build_tables(jefi_problem* h, int ti, double t) {
                 thi = round_down_f32(th_k - err(th_k));
                 tlo = round_up_f32(th_k + err(th_k));
             }
-            tg[e] = make_float4(thi, tlo, z, w);
+            tg[e] = make_float2(tlo, zw);
+            th_hi[e] = thi;
         }
     }
     TimeParams tp;
@@ -510,6 +516,8 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     p.status = h->status;
     p.tab2 = h->tab2 ? h->tab2 + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
     p.tabg = h->tabg ? h->tabg + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
+    p.tabh = h->tabh ? h->tabh + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
+    p.exact = h->exact ? 1 : 0;
     p.tile_box = h->tile_box;
     for (int a = 0; a < 3; ++a) {
         p.n_src_axis[a] = h->src.n[a];
@@ -545,9 +553,12 @@ int upload_tables(jefi_problem* h, int n_t, cudaStream_t s) {
     if (h->band > 0)
         JEFI_CUDA(cudaMemcpyAsync(h->tab2, h->h_tab2.data(),
                                   sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
-    if (h->tabg)
+    if (h->tabg) {
         JEFI_CUDA(cudaMemcpyAsync(h->tabg, h->h_tabg.data(),
-                                  sizeof(float4) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
+                                  sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
+        JEFI_CUDA(cudaMemcpyAsync(h->tabh, h->h_tabh.data(),
+                                  sizeof(float) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
+    }
     return JEFI_OK;
 }
 
@@ -978,6 +989,10 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         h->mirror = h->band;
     }
     h->Hp = h->H + h->mirror + kZeroPadSlots;
+    if (!h->fp64 && h->any_pairs && h->band == 0 && h->Hp > 65536) {
+        delete h;   // the direct-gather kernel packs two physical slots in 16 bits each
+        return JEFI_EUNSUPPORTED;
+    }
 
     // ---------------------------------------------------------------- device buffers
     cudaStream_t s = (cudaStream_t)stream;
@@ -999,9 +1014,11 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->fallbacks = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
     h->status = (int32_t*)dev_alloc(h, sizeof(int32_t));
     if (!h->fp64 && h->any_pairs && h->band == 0) {
-        h->tabg = (float4*)dev_alloc(h, sizeof(float4) * h->time_chunk * (h->K + 2 * kTabGuard));
-        if (!h->tabg) h->status = nullptr;
+        h->tabg = (float2*)dev_alloc(h, sizeof(float2) * h->time_chunk * (h->K + 2 * kTabGuard));
+        h->tabh = (float*)dev_alloc(h, sizeof(float) * h->time_chunk * (h->K + 2 * kTabGuard));
+        if (!h->tabg || !h->tabh) h->status = nullptr;
         h->h_tabg.resize((size_t)h->time_chunk * (h->K + 2 * kTabGuard));
+        h->h_tabh.resize((size_t)h->time_chunk * (h->K + 2 * kTabGuard));
     }
     if (h->band > 0) {
         h->tile_box = (float*)dev_alloc(h, sizeof(float) * tile_box.size());

@@ -83,9 +83,12 @@ struct SumParams {
     int32_t nfull[3];               // whole bricks per axis (bricks past them hold padding cells)
     int32_t H;                      // ring period (physical slot of slice n is n mod H)
     int32_t comp;                   // FP32: compensated (Kahan) per-thread sums
-    // direct-gather kernel: [n_t][K + 2 kTabGuard] {T_hi, T_lo, phys slot of k', of k'-1}
-    // per candidate slot k' (the staged kernel's candidate rule, slots read from global memory)
-    const float4* tabg;
+    // direct-gather kernel, per candidate slot k' (the staged kernel's candidate
+    // rule, slots read from global memory): [n_t][K + 2 kTabGuard] {T_lo, physical
+    // slots of k' (low 16 bits) and k'-1 (high 16 bits)}, and T_hi in tabh
+    const float2* tabg;
+    const float* tabh;
+    int32_t exact;                  // lattice geometry: T_hi == T_lo, no pair undecided
     // second-order retarded time: sources interpolated between slots n and n+1
     int32_t interp;
     float K32_lo;                   // fp32(1/(c dt) - K32)

@@ -27,7 +27,8 @@ namespace jefi {
 using namespace dev;
 
 // ============================================================================ FP32
-// Shared memory: tabg[K + 2 guard] float4 | tab32[K] float4 | theta[K+1] double | D[nbx+nby+nbz] float
+// Shared memory: tabg[KT] float2 | tabh[KT] float (padded to 16 B) | tab32[K] float4 | theta[K+1] double |
+// D[nbx+nby+nbz] float, KT = K + 2 guard
 
 struct Fix6 {
     float v[6];   // E', B contributions
@@ -75,20 +76,30 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.K;
     const int KT = K + 2 * kTabGuard;
-    float4* s_tabg = reinterpret_cast<float4*>(smem);
-    float4* s_tab = s_tabg + KT;
+    const uint32_t tabh_off = (uint32_t)KT * 8u;                       // byte offsets in smem
+    const uint32_t tab_off = (tabh_off + (uint32_t)KT * 4u + 15u) & ~15u;
+    float2* s_tabg = reinterpret_cast<float2*>(smem);
+    float* s_tabh = reinterpret_cast<float*>(smem + tabh_off);
+    float4* s_tab = reinterpret_cast<float4*>(smem + tab_off);
     double* s_th = reinterpret_cast<double*>(s_tab + K);
     float* s_D = reinterpret_cast<float*>(s_th + K + 1);
     const int tid = threadIdx.x;
 
     const float4* g_tab = p.tab32 + (size_t)ti * K;
     const double* g_th = p.theta + (size_t)ti * (K + 1);
-    const float4* g_tabg = p.tabg + (size_t)ti * KT;
-    for (int i = tid; i < KT; i += kTileThreads) s_tabg[i] = g_tabg[i];
+    const float2* g_tabg = p.tabg + (size_t)ti * KT;
+    const float* g_tabh = p.tabh + (size_t)ti * KT;
+    for (int i = tid; i < KT; i += kTileThreads) {
+        s_tabg[i] = g_tabg[i];
+        s_tabh[i] = g_tabh[i];
+    }
     for (int i = tid; i < K; i += kTileThreads) s_tab[i] = g_tab[i];
     for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
-    // s_tabg[bits - kMagicBits + kTabGuard] sits at byte smem + tgbase + 16 bits (offset mod 2^32)
-    const uint32_t tgbase = (uint32_t)(kTabGuard - kMagicBits) * 16u;
+    // s_tabg[bits - kMagicBits + kTabGuard] sits at byte smem + tgbase + 8 bits, s_tabh[...] at
+    // smem + thbase + 4 bits (offsets mod 2^32)
+    const uint32_t tgbase = (uint32_t)(kTabGuard - kMagicBits) * 8u;
+    const uint32_t thbase = tabh_off + (uint32_t)(kTabGuard - kMagicBits) * 4u;
+    const bool exact = p.exact != 0;
 
     // Anchor: the tile's first point.  D[b] = fp32(anchor - centre of the
     // brick's first cell) per axis, so that P = (x_o - anchor) + D is small
@@ -222,13 +233,17 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                         const float S = __fadd_rn(sqx[i], syz);
                         float ri = rsqrt_ftz(S);
                         const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-                        const float4 e = *reinterpret_cast<const float4*>(smem + (tgbase + bits * 16u));
-                        const bool lower = S > e.y;
-                        if (!(S <= e.x) && !lower) {   // undecided: redo after the brick
-                            mask |= 1ull << (k * 16 + c16);
-                            ri = 0.f;
+                        const float2 e = *reinterpret_cast<const float2*>(smem + (tgbase + bits * 8u));
+                        const bool lower = S > e.x;
+                        if (!exact) {   // T_hi < S <= T_lo: undecided, redone after the brick
+                            const float th_hi = *reinterpret_cast<const float*>(smem + (thbase + bits * 4u));
+                            if (!(S <= th_hi) && !lower) {
+                                mask |= 1ull << (k * 16 + c16);
+                                ri = 0.f;
+                            }
                         }
-                        const int ps = __float_as_int(lower ? e.w : e.z);
+                        const uint32_t pk = __float_as_uint(e.y);
+                        const int ps = (int)(lower ? (pk >> 16) : (pk & 0xFFFFu));
                         if (DEBUG) {
                             p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + k * 16 + c16] =
                                 (int)(tp.k0 + (int)(bits - kMagicBits) - (lower ? 1 : 0));
@@ -237,8 +252,8 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                         float4 v0, v1;
                         ldg_row8(q, v0, v1);
                         if (INTERP) {   // slot n+1: k' when n = k'-1, else k'+1
-                            const float z1 = *reinterpret_cast<const float*>(smem + (tgbase + bits * 16u + 24u));
-                            const float4* q1 = ck + (c16 * Hp + __float_as_int(lower ? e.z : z1)) * 2;
+                            const uint32_t pk1 = *reinterpret_cast<const uint32_t*>(smem + (tgbase + bits * 8u + 12u));
+                            const float4* q1 = ck + (c16 * Hp + (int)(lower ? (pk & 0xFFFFu) : (pk1 & 0xFFFFu))) * 2;
                             const float nrel = __uint_as_float(bits - (lower ? 1u : 0u)) - kMagic;
                             float4 u0, u1;
                             ldg_row8(q1, u0, u1);
@@ -660,7 +675,7 @@ cudaError_t launch_reduce_batch(const ReduceItem* items, const int64_t* out_star
 
 size_t sum_smem_bytes(const SumParams& p) {
     size_t b = (size_t)p.K * sizeof(float4) + (size_t)(p.K + 1) * sizeof(double);
-    if (p.tabg) b += (size_t)(p.K + 2 * kTabGuard) * sizeof(float4);
+    if (p.tabg) b += ((size_t)(p.K + 2 * kTabGuard) * 12 + 15) & ~(size_t)15;
     return b + (size_t)(p.npx + p.npy + p.npz) * sizeof(double);
 }
 

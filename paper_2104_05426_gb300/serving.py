@@ -482,6 +482,49 @@ def measure_batch(n_problems: int = 256, sides=(8, 48), H_range=(32, 128), obs_s
     return out
 
 
+def measure_single(src_side: int, obs_side: int, H: int, reps: int = 3, seed: int = 9) -> dict:
+    """One resident problem of the serving kind (source grid over [-1,1]^3,
+    observation grid over [-2,2]^3 as a view, dt = R_max/(c (H-8))) and the
+    time of one evaluation in its valid window."""
+    import torch
+
+    rmax = math.sqrt(3.0) * 3.0
+    dt = rmax / (H - 8)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    blobs = [Blob(float(q), float(rng.uniform(0.2, 0.3)), tuple(rng.uniform(-0.2, 0.2, 3)),
+                  tuple(rng.uniform(-0.3, 0.3, 3))) for q in (1.0, -1.0)]
+    p = ServedProblem(src_side, 1.0, H, dt, blobs)
+    s = torch.cuda.current_stream()
+    for _ in range(H + 1):
+        p.push_next(s)
+    g = grid((obs_side,) * 3, (-2.0,) * 3, (4.0 / obs_side,) * 3)
+    v = jefi_create_view(p.handle, obs_grid=g)
+    lo, hi = jefi_valid_window(v)
+    t = 0.5 * (lo + hi) if math.isfinite(lo) else hi - 2 * dt
+    E = torch.empty((obs_side ** 3, 3), dtype=torch.float64, device="cuda")
+    B = torch.empty_like(E)
+    from . import jefi_eval_fields
+
+    jefi_eval_fields(v, t, E, B)                       # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        jefi_eval_fields(v, t, E, B)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    info = jefi_get_info(v)
+    pairs = src_side ** 3 * obs_side ** 3
+    out = {"source_side": src_side, "obs_side": obs_side, "history_slices": H, "dt": dt, "ms": ms,
+           "pairs_per_s": pairs / (ms / 1e3), "staged_band": info["staged_band"], "n_split": info["n_split"],
+           "slot_fallbacks": info["slot_fallbacks"], "device_status": info["device_status"]}
+    jefi_destroy(v)
+    jefi_destroy(p.handle)
+    return out
+
+
 def main(argv=None):
     import argparse
     import json
@@ -497,8 +540,15 @@ def main(argv=None):
     ap.add_argument("--tick-ms", type=float, default=20.0, help="one slice pushed per problem per tick")
     ap.add_argument("--budget-gb", type=float, default=None,
                     help="device memory for histories, views and outputs (default: 80 %% of the device)")
+    ap.add_argument("--single", default=None, metavar="SRC,OBS,H",
+                    help="time one evaluation of one problem (source side, observation side, history)")
+    ap.add_argument("--reps", type=int, default=3, help="evaluations timed with --single")
     a = ap.parse_args(argv)
     pair = lambda s: tuple(int(x) for x in s.split(","))
+    if a.single:
+        src_side, obs_side, H = pair(a.single)
+        print(json.dumps(measure_single(src_side, obs_side, H, a.reps)))
+        return
     res = measure(a.problems, a.requests, tuple(float(x) for x in a.loads.split(",")), pair(a.sides),
                   pair(a.history), pair(a.obs_sides), a.seed, a.tick_ms / 1e3,
                   memory_budget=None if a.budget_gb is None else a.budget_gb * 1e9)
