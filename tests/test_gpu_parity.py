@@ -343,3 +343,24 @@ def test_staged_kernel_matches_direct_gather(gpu, lattice):
         assert info_s["slot_fallbacks"] == 0
     for h in handles.values():
         jefi.jefi_destroy(h)
+
+
+def test_direct_gather_history_limit(gpu):
+    """The direct-gather FP32 kernel packs two physical ring rows in 16 bits
+    each: a handle on it with H + 1 <= 65536 rows is created, one more row is
+    refused with JEFI_EUNSUPPORTED (the FP64 path has no such limit)."""
+    src = Grid.cube(4, -0.5, 0.5)
+    obs = np.array([[3.0, 0.1, 0.2], [-2.5, 1.0, 0.3]])
+    for H, ok in ((65535, True), (65536, False)):
+        prm = jefi.default_params(dt=0.01, history_slots=H, precision="fp32c",
+                                  flags=jefi.JEFI_FLAG_DIRECT_GATHER)
+        if ok:
+            h = jefi.jefi_create(jefi.grid_from(src), obs_points=obs, params=prm)
+            assert jefi.jefi_get_info(h)["staged_band"] == 0
+            jefi.jefi_destroy(h)
+        else:
+            with pytest.raises(jefi.JefiError) as e:
+                jefi.jefi_create(jefi.grid_from(src), obs_points=obs, params=prm)
+            assert e.value.code == jefi.JEFI_EUNSUPPORTED
+    prm = jefi.default_params(dt=0.01, history_slots=65536, precision="fp64")
+    jefi.jefi_destroy(jefi.jefi_create(jefi.grid_from(src), obs_points=obs, params=prm))
