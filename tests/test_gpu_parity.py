@@ -364,3 +364,33 @@ def test_direct_gather_history_limit(gpu):
             assert e.value.code == jefi.JEFI_EUNSUPPORTED
     prm = jefi.default_params(dt=0.01, history_slots=65536, precision="fp64")
     jefi.jefi_destroy(jefi.jefi_create(jefi.grid_from(src), obs_points=obs, params=prm))
+
+
+@pytest.mark.parametrize("src_side,dt,band", [(16, 0.125, 48), (8, 0.2, 32), (12, 0.12, 48), (10, 0.2, 32)])
+def test_wide_band_single_buffer_staged_kernel(gpu, src_side, dt, band):
+    """Coarse observation grids with fine time steps give slot bands of 32 and
+    48 rows, which the staged kernel runs single-buffered (two CTAs per SM):
+    every slot bit-exact with the oracle and the fields within tolerance, on
+    lattice (16^3, 8^3) and non-lattice (12^3, 10^3) source grids."""
+    src = Grid.cube(src_side, -1.0, 1.0)
+    obs = Grid.cube(16, -2.0, 2.0)
+    blob = Blob(1.0, (0.25, 0.3, 0.2), (-0.1, 0.05, 0.0), (0.3, -0.1, 0.2))
+    H = int(math.ceil(6.0 / dt)) + 8
+    p = Problem("wide", src, obs, None, dt, H, H, [], MovingGaussians([blob], noise=0.02, seed=7))
+    hist = history(p)
+    h = create(p, "fp32c")
+    push_all(h, hist)
+    assert jefi.jefi_get_info(h)["staged_band"] == band
+    _, hi = jefi.jefi_valid_window(h)
+    times = [hi - 0.3, hi]
+    ref = oracle_fields(p, hist, times)
+    E, B = gpu_fields(h, times)
+    for i, t in enumerate(times):
+        assert rel_l2(E[i], ref[i][0]) <= FP32C_TOL
+        assert rel_l2(B[i], ref[i][1]) <= FP32C_TOL
+        got = jefi.jefi_debug_slots(h, t)
+        want = oracle.all_slots(p.src.n, p.src.lo, p.src.d, p.obs(), dt=p.dt, t0=p.t0, c=p.c, t=t)
+        scr = want == oracle.SCREENED
+        assert np.array_equal(got[~scr].astype(np.int64), want[~scr])
+    assert jefi.jefi_get_info(h)["device_status"] == 0
+    jefi.jefi_destroy(h)
