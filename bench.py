@@ -282,7 +282,8 @@ def run_gpu(args):
                                      "per step",
                          "precision": "fp32 compensated, fp64 cross-split reduction",
                          "pairs_per_step": pairs_step, "l2": "inputs larger than L2 (FP32 ring "
-                         f"{n_src * (H + 1) * 32 / 1e9:.2f} GB)", "parallelism": f"replicas x{world}"},
+                         f"{n_src * (H + info['staged_band'] + 1) * 32 / 1e9:.2f} GB)",
+                         "parallelism": f"replicas x{world}"},
               "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk}
 
     if rank == 0 and not args.no_extras:
