@@ -279,6 +279,7 @@ void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double 
  *   rho, J     device [n_slices][N_src] and [n_slices][N_src][3] FP64: the
  *              whole history, slice n at time p->t0 + n*p->dt, cells x fastest
  *   p          uses c, k_e, k_b, dt, t0 and screen; other fields are ignored
+ *              (flags included: this entry runs the floor rule of Eq. tr-1)
  *   E, B       device [n_obs][3] FP64 outputs
  * The call is synchronous on `stream` (it returns after E and B are written).
  *
