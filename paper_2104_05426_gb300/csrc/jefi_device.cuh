@@ -51,6 +51,16 @@ static __device__ __noinline__ int slot_fallback_f32(const double* obs_xyz, int 
     return theta_search(th, K, guess, S);
 }
 
+// Exact slot of one pair in FP64 from the point and the source cell centre
+// (each an FP64 value the spec computes: the point as given, the centre by
+// cell_center), stored in shared memory by the caller: the spec's squared
+// distance and the threshold search, with no global load.
+static __device__ __forceinline__ int slot_fp64_stored(const double* xo, double cx, double cy, double cz,
+                                                       const double* th, int K, int guess) {
+    const double S = spec_s64(__dsub_rn(xo[0], cx), __dsub_rn(xo[1], cy), __dsub_rn(xo[2], cz));
+    return theta_search(th, K, guess, S);
+}
+
 static __device__ __forceinline__ unsigned candidate_index(float S, float ri, float K32, float A, int K) {
     const float R = S * ri;
     const float u = fmaf(-R, K32, A);

@@ -978,6 +978,10 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
             probe.nbx = h->nbx;
             probe.nby = h->nby;
             probe.nbz = h->nbz;
+            probe.npx = (int)npad[0];
+            probe.npy = (int)npad[1];
+            probe.npz = (int)npad[2];
+            probe.exact = h->exact ? 1 : 0;
             if (staged_smem_bytes(probe, band) <= 220 * 1024) h->band = band;
         }
     }

@@ -104,7 +104,32 @@ struct Layout {
     static constexpr int kBufs = BAND >= 32 ? 1 : 2;
     static constexpr uint32_t kCtrl = kBufs * kBufBytes;               // mbarriers, band origins
     static constexpr uint32_t kTab = kCtrl + 64;                        // float2 table
+    // control words of the non-lattice fall-back (one item): offset of the
+    // FP64 geometry (the tile's points, then the cell centres of x, y, z),
+    // the cell counts of x and y, and the pairs redone
+    static constexpr uint32_t kGeo = kCtrl + 48;
 };
+
+// Shared-memory offset of the FP64 geometry of one item: after the float2
+// table, the FP64 thresholds and the float brick offsets.
+__host__ __device__ __forceinline__ uint32_t staged_geometry_offset(uint32_t tab, int K, int nb_sum) {
+    const uint32_t d = tab + (uint32_t)(K + 2 * kTabGuard) * 8u + (uint32_t)(K + 1) * 8u;
+    return (d + (uint32_t)nb_sum * 4u + 7u) & ~7u;
+}
+
+// Exact slot of one undecided pair from the FP64 geometry in shared memory
+// (written by the item's preamble); counts the pair.  A call of its own, so
+// the FP64 search does not weigh on the registers of the brick loop.
+template <int BAND>
+__device__ __noinline__ int staged_slot_fp64(int ix, int iy, int iz, const double* s_th, int K, int guess) {
+    using L = Layout<BAND>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t* g = reinterpret_cast<const uint32_t*>(smem + L::kGeo);
+    const double* s_xo = reinterpret_cast<const double*>(smem + g[0]) + 3 * threadIdx.x;
+    const double* s_cc = reinterpret_cast<const double*>(smem + g[0]) + 3 * kTileThreads;
+    atomicAdd(const_cast<uint32_t*>(g + 3), 1u);
+    return slot_fp64_stored(s_xo, s_cc[ix], s_cc[g[1] + iy], s_cc[g[1] + g[2] + iz], s_th, K, guess);
+}
 
 }  // namespace
 
@@ -122,6 +147,32 @@ __device__ __forceinline__ void staged_init_barriers() {
     __syncthreads();
 }
 
+// Non-lattice geometry of one item (before the item's first barrier): the
+// tile's FP64 points and the FP64 cell centres of each axis, for the exact
+// slot of the pairs the FP32 rule leaves undecided; zeroes the item's count.
+template <int BAND>
+__device__ __noinline__ void staged_fill_geometry(const double* txyz, int K, int nb_sum, int npx, int npy, int npz,
+                                                  double lox, double loy, double loz, double dx_, double dy_,
+                                                  double dz_) {
+    using L = Layout<BAND>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const uint32_t geo = staged_geometry_offset(L::kTab, K, nb_sum);
+    double* s_xo = reinterpret_cast<double*>(smem + geo);
+    double* s_cc = s_xo + 3 * kTileThreads;
+    for (int i = tid; i < npx; i += kTileThreads) s_cc[i] = cell_center(lox, dx_, i);
+    for (int i = tid; i < npy; i += kTileThreads) s_cc[npx + i] = cell_center(loy, dy_, i);
+    for (int i = tid; i < npz; i += kTileThreads) s_cc[npx + npy + i] = cell_center(loz, dz_, i);
+    for (int a = 0; a < 3; ++a) s_xo[3 * tid + a] = txyz[3 * tid + a];
+    if (tid == 0) {
+        uint32_t* g = reinterpret_cast<uint32_t*>(smem + L::kGeo);
+        g[0] = geo;
+        g[1] = (uint32_t)npx;
+        g[2] = (uint32_t)npy;
+        g[3] = 0u;
+    }
+}
+
 struct FixSums {
     float v[6];   // E', B contributions
 };
@@ -132,11 +183,9 @@ struct FixSums {
 template <int BAND, bool DEBUG, bool INTERP>
 __device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char* bufp, int band_rel, float Px,
                                              float Py, float Pz, float d32x, float d32y, float d32z, float K32,
-                                             float Ag, float A, float A_lo, float K32_lo, const double* obs_xyz,
-                                             int slot, double lox, double loy, double loz, double dx_, double dy_,
-                                             double dz_, int bx, int by, int bz, const double* s_th, int K,
-                                             unsigned long long* fallbacks, int32_t* status, int32_t* debug_slots,
-                                             size_t n_cells, int b, int64_t k0) {
+                                             float Ag, float A, float A_lo, float K32_lo, int slot, int bx,
+                                             int by, int bz, const double* s_th, int K, int32_t* status,
+                                             int32_t* debug_slots, size_t n_cells, int b, int64_t k0) {
     using L = Layout<BAND>;
     float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
     while (mask) {
@@ -149,9 +198,8 @@ __device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char*
         const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
         const float ri = rsqrt_ftz(S);
         const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-        const int idx = slot_fallback_f32(obs_xyz, slot, lox, loy, loz, dx_, dy_, dz_, kBrick * bx + i,
-                                          kBrick * by + j, kBrick * bz + k, s_th, K, (int)(bits - kMagicBits),
-                                          fallbacks);
+        const int idx = staged_slot_fp64<BAND>(kBrick * bx + i, kBrick * by + j, kBrick * bz + k, s_th, K,
+                                               (int)(bits - kMagicBits));
         int row = idx - band_rel;
         if (row < 0 || row >= BAND) {
             atomicExch(status, kStatusInternal);
@@ -195,6 +243,9 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     const double* g_th = p.theta + (size_t)ti * (K + 1);
     for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
     const double* txyz = p.obs_xyz + (size_t)tile * kTileThreads * 3;
+    if constexpr (!EXACT)
+        staged_fill_geometry<BAND>(txyz, K, p.nbx + p.nby + p.nbz, p.npx, p.npy, p.npz, p.lo[0], p.lo[1], p.lo[2],
+                                   p.d[0], p.d[1], p.d[2]);
     const double cox = txyz[0], coy = txyz[1], coz = txyz[2];
     const int nbxy = p.nbx + p.nby;
     for (int i = tid; i < nbxy + p.nbz; i += kTileThreads) {
@@ -418,8 +469,8 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     if (__any_sync(kFull, mask != 0ull)) {
                         FixSums f = staged_fixup<BAND, DEBUG, INTERP>(
                             mask, smem + (uint32_t)buf * L::kBufBytes, band_rel, Px, Py, Pz, d32x, d32y, d32z,
-                            K32, Ag, A, A_lo, K32_lo, p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1],
-                            p.d[2], bx, by, bz, s_th, K, p.fallbacks, p.status, p.debug_slots, n_cells, b, tp.k0);
+                            K32, Ag, A, A_lo, K32_lo, ctx.slot, bx, by, bz, s_th, K, p.status, p.debug_slots,
+                            n_cells, b, tp.k0);
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             pe[a] += f.v[a];
@@ -449,8 +500,12 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     const bool lower = S > th.y;
                     int idx = (int)tix - kTabGuard - (lower ? 1 : 0);
                     if (use && !(S <= th.x) && !lower) {
-                        idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
-                                                p.d[1], p.d[2], ix, iy, iz, s_th, K, idx, p.fallbacks);
+                        if constexpr (EXACT) {
+                            idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
+                                                    p.d[1], p.d[2], ix, iy, iz, s_th, K, idx, p.fallbacks);
+                        } else {
+                            idx = staged_slot_fp64<BAND>(ix, iy, iz, s_th, K, idx);
+                        }
                     }
                     int row = idx - band_rel;
                     if (!use) {
@@ -518,6 +573,11 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         __syncthreads();
     }
     g_it += (uint32_t)(b_end > b_begin ? b_end - b_begin : 0);
+    if constexpr (!EXACT) {
+        // every thread passed the loop's last barrier: the item's count is complete
+        const uint32_t n = reinterpret_cast<const uint32_t*>(smem + L::kGeo)[3];
+        if (tid == 0 && n) atomicAdd(p.fallbacks, (unsigned long long)n);
+    }
 
     double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
 #pragma unroll
@@ -610,10 +670,14 @@ bool staged_band_supported(int band) { return band == 16 || band == 24 || band =
 
 size_t staged_smem_bytes(const SumParams& p, int band) {
     const size_t buf = (size_t)kBrickCells * band * 32;
-    size_t b = (band >= 32 ? 1 : 2) * buf + 64;   // brick buffers, mbarriers / band origins / item
-    b += (size_t)(p.K + 2 * kTabGuard) * sizeof(float2);
+    const size_t tab = (band >= 32 ? 1 : 2) * buf + 64;   // brick buffers, mbarriers / band origins / item
+    const int nb_sum = p.nbx + p.nby + p.nbz;
+    size_t b = tab + (size_t)(p.K + 2 * kTabGuard) * sizeof(float2);
     b += (size_t)(p.K + 1) * sizeof(double);
-    b += (size_t)(p.nbx + p.nby + p.nbz) * sizeof(float);
+    b += (size_t)nb_sum * sizeof(float);
+    // non-lattice geometry: FP64 points of the tile and cell centres, for the fall-back
+    if (!p.exact)
+        b = staged_geometry_offset((uint32_t)tab, p.K, nb_sum) + (size_t)(3 * kTileThreads + p.npx + p.npy + p.npz) * 8;
     return b;
 }
 
