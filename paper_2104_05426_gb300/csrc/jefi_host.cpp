@@ -982,7 +982,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
             probe.npy = (int)npad[1];
             probe.npz = (int)npad[2];
             probe.exact = h->exact ? 1 : 0;
-            if (staged_smem_bytes(probe, band) <= 220 * 1024) h->band = band;
+            if (staged_smem_bytes(probe, band, false) <= 220 * 1024) h->band = band;
         }
     }
     if (base) {
@@ -1299,7 +1299,7 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
             prm[m] = make_params(h, 1, occ[i], nullptr);
             start[m] = acc;
             acc += h->n_tiles * h->n_split;
-            smem[g] = std::max(smem[g], groups[g].kind == 2 ? staged_smem_bytes(prm[m], groups[g].band)
+            smem[g] = std::max(smem[g], groups[g].kind == 2 ? staged_smem_bytes(prm[m], groups[g].band, true)
                                                              : sum_smem_bytes(prm[m]));
         }
         start[groups[g].members.size()] = acc;

@@ -177,7 +177,7 @@ struct StagedConfig {
 cudaError_t launch_push(const PushParams& p, cudaStream_t s);
 cudaError_t launch_wait_timeout_probe(int32_t* status, uint64_t limit_ns, cudaStream_t s);
 cudaError_t launch_sum_f32_staged(const SumParams& p, const StagedConfig& c, cudaStream_t s);
-size_t staged_smem_bytes(const SumParams& p, int band);
+size_t staged_smem_bytes(const SumParams& p, int band, bool batched);
 bool staged_band_supported(int band);
 cudaError_t launch_sum_f32(const SumParams& p, bool compensated, cudaStream_t s);
 cudaError_t launch_sum_f64(const SumParams& p, cudaStream_t s);

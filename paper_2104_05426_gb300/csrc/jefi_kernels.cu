@@ -355,8 +355,19 @@ __device__ __noinline__ void direct_batch_item(const SumParams& p, int tile, int
 template <bool COMP>
 __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_batch(const BatchArgs a) {
     __shared__ int s_item;
+    __shared__ SumParams s_par;
     int pr, tile, split, ti;
-    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) direct_batch_item<COMP>(a.params[pr], tile, split, ti);
+    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) {
+        // The item's parameters go to shared memory (every thread passed the
+        // queue's barriers, so none still reads the previous item's): read
+        // through a dynamic index into global memory, their loop invariants
+        // would be held in registers and spilled.
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.params[pr]);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_par);
+        for (int w = threadIdx.x; w < (int)(sizeof(SumParams) / 4); w += kTileThreads) dst[w] = src[w];
+        __syncthreads();
+        direct_batch_item<COMP>(s_par, tile, split, ti);
+    }
 }
 
 // ============================================================================ FP64

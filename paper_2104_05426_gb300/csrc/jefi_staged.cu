@@ -180,8 +180,54 @@ struct FixSums {
 // Pairs of a full brick whose slot the FP32 rule left undecided (non-lattice
 // geometry): exact slot in FP64, then the pair from the brick's buffer.  A
 // call of its own (rare), so its registers do not weigh on the brick loop.
+// The batched kernel's form: the point from global memory and a global
+// count (the batched item has no registers to spare for more).
 template <int BAND, bool DEBUG, bool INTERP>
 __device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char* bufp, int band_rel, float Px,
+                                             float Py, float Pz, float d32x, float d32y, float d32z, float K32,
+                                             float Ag, float A, float A_lo, float K32_lo, const double* obs_xyz,
+                                             int slot, double lox, double loy, double loz, double dx_, double dy_,
+                                             double dz_, int bx, int by, int bz, const double* s_th, int K,
+                                             unsigned long long* fallbacks, int32_t* status, int32_t* debug_slots,
+                                             size_t n_cells, int b, int64_t k0) {
+    using L = Layout<BAND>;
+    float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
+    while (mask) {
+        const int cl = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+        const float dx = fmaf(-(float)i, d32x, Px);
+        const float dy = fmaf(-(float)j, d32y, Py);
+        const float dz = fmaf(-(float)k, d32z, Pz);
+        const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+        const float ri = rsqrt_ftz(S);
+        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
+        const int idx = slot_fallback_f32(obs_xyz, slot, lox, loy, loz, dx_, dy_, dz_, kBrick * bx + i,
+                                          kBrick * by + j, kBrick * bz + k, s_th, K, (int)(bits - kMagicBits),
+                                          fallbacks);
+        int row = idx - band_rel;
+        if (row < 0 || row >= BAND) {
+            atomicExch(status, kStatusInternal);
+            row = row < 0 ? 0 : BAND - 1;
+        }
+        if (DEBUG) debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
+        const uint32_t off = (uint32_t)cl * L::kCellBytes + (uint32_t)row * L::kRowBytes;
+        float4 v0 = *reinterpret_cast<const float4*>(bufp + off);
+        float4 v1 = *reinterpret_cast<const float4*>(bufp + off + 16u);
+        if (INTERP) {
+            const float4 u0 = *reinterpret_cast<const float4*>(bufp + off + 32u);
+            const float4 u1 = *reinterpret_cast<const float4*>(bufp + off + 48u);
+            lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
+        }
+        pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+    }
+    return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
+}
+
+// The same, with the FP64 geometry and the count in shared memory (the
+// single-problem kernel).
+template <int BAND, bool DEBUG, bool INTERP>
+__device__ __noinline__ FixSums staged_fixup_geo(uint64_t mask, const unsigned char* bufp, int band_rel, float Px,
                                              float Py, float Pz, float d32x, float d32y, float d32z, float K32,
                                              float Ag, float A, float A_lo, float K32_lo, int slot, int bx,
                                              int by, int bz, const double* s_th, int K, int32_t* status,
@@ -222,8 +268,10 @@ __device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char*
 // One work item: observation tile `tile` x source split `split` at time
 // index `ti` of problem p.  g_it counts the CTA's staged bricks across items
 // (it selects the buffer and the mbarrier phase).  Returns false if a copy
-// did not complete in time (the caller stops).
-template <int BAND, bool EXACT, bool DEBUG, bool INTERP>
+// did not complete in time (the caller stops).  GEO: undecided pairs take
+// their FP64 geometry from shared memory and are counted there (the
+// single-problem kernel); otherwise from global memory (the batched kernel).
+template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool GEO>
 __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const int comp,
                                             const int tile, const int split, const int ti, uint32_t& g_it) {
     using L = Layout<BAND>;
@@ -243,7 +291,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     const double* g_th = p.theta + (size_t)ti * (K + 1);
     for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
     const double* txyz = p.obs_xyz + (size_t)tile * kTileThreads * 3;
-    if constexpr (!EXACT)
+    if constexpr (!EXACT && GEO)
         staged_fill_geometry<BAND>(txyz, K, p.nbx + p.nby + p.nbz, p.npx, p.npy, p.npz, p.lo[0], p.lo[1], p.lo[2],
                                    p.d[0], p.d[1], p.d[2]);
     const double cox = txyz[0], coy = txyz[1], coz = txyz[2];
@@ -467,10 +515,19 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                 pb[2] += acc_bz;
                 if (!EXACT) {
                     if (__any_sync(kFull, mask != 0ull)) {
-                        FixSums f = staged_fixup<BAND, DEBUG, INTERP>(
-                            mask, smem + (uint32_t)buf * L::kBufBytes, band_rel, Px, Py, Pz, d32x, d32y, d32z,
-                            K32, Ag, A, A_lo, K32_lo, ctx.slot, bx, by, bz, s_th, K, p.status, p.debug_slots,
-                            n_cells, b, tp.k0);
+                        FixSums f;
+                        if constexpr (GEO) {
+                            f = staged_fixup_geo<BAND, DEBUG, INTERP>(
+                                mask, smem + (uint32_t)buf * L::kBufBytes, band_rel, Px, Py, Pz, d32x, d32y, d32z,
+                                K32, Ag, A, A_lo, K32_lo, ctx.slot, bx, by, bz, s_th, K, p.status, p.debug_slots,
+                                n_cells, b, tp.k0);
+                        } else {
+                            f = staged_fixup<BAND, DEBUG, INTERP>(
+                                mask, smem + (uint32_t)buf * L::kBufBytes, band_rel, Px, Py, Pz, d32x, d32y, d32z,
+                                K32, Ag, A, A_lo, K32_lo, p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
+                                p.d[1], p.d[2], bx, by, bz, s_th, K, p.fallbacks, p.status, p.debug_slots, n_cells,
+                                b, tp.k0);
+                        }
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
                             pe[a] += f.v[a];
@@ -500,7 +557,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     const bool lower = S > th.y;
                     int idx = (int)tix - kTabGuard - (lower ? 1 : 0);
                     if (use && !(S <= th.x) && !lower) {
-                        if constexpr (EXACT) {
+                        if constexpr (EXACT || !GEO) {
                             idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
                                                     p.d[1], p.d[2], ix, iy, iz, s_th, K, idx, p.fallbacks);
                         } else {
@@ -573,7 +630,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         __syncthreads();
     }
     g_it += (uint32_t)(b_end > b_begin ? b_end - b_begin : 0);
-    if constexpr (!EXACT) {
+    if constexpr (!EXACT && GEO) {
         // every thread passed the loop's last barrier: the item's count is complete
         const uint32_t n = reinterpret_cast<const uint32_t*>(smem + L::kGeo)[3];
         if (tid == 0 && n) atomicAdd(p.fallbacks, (unsigned long long)n);
@@ -593,7 +650,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p) {
     staged_init_barriers<BAND>();
     uint32_t g_it = 0;
-    staged_item<BAND, EXACT, DEBUG, INTERP>(&tmap, p, p.comp, blockIdx.x, blockIdx.y, blockIdx.z, g_it);
+    staged_item<BAND, EXACT, DEBUG, INTERP, true>(&tmap, p, p.comp, blockIdx.x, blockIdx.y, blockIdx.z, g_it);
 }
 
 // One item of the batched kernel as a call of its own: the item body gets
@@ -602,7 +659,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 template <int BAND, bool EXACT>
 __device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int split,
                                                int ti, uint32_t& g_it) {
-    return staged_item<BAND, EXACT, false, false>(map, p, p.comp, tile, split, ti, g_it);
+    return staged_item<BAND, EXACT, false, false, false>(map, p, p.comp, tile, split, ti, g_it);
 }
 
 // Persistent batched kernel: CTAs take (problem, time, split, tile) items
@@ -668,7 +725,7 @@ cudaError_t launch_wait_timeout_probe(int32_t* status, uint64_t limit_ns, cudaSt
 
 bool staged_band_supported(int band) { return band == 16 || band == 24 || band == 32 || band == 48; }
 
-size_t staged_smem_bytes(const SumParams& p, int band) {
+size_t staged_smem_bytes(const SumParams& p, int band, bool batched) {
     const size_t buf = (size_t)kBrickCells * band * 32;
     const size_t tab = (band >= 32 ? 1 : 2) * buf + 64;   // brick buffers, mbarriers / band origins / item
     const int nb_sum = p.nbx + p.nby + p.nbz;
@@ -676,7 +733,7 @@ size_t staged_smem_bytes(const SumParams& p, int band) {
     b += (size_t)(p.K + 1) * sizeof(double);
     b += (size_t)nb_sum * sizeof(float);
     // non-lattice geometry: FP64 points of the tile and cell centres, for the fall-back
-    if (!p.exact)
+    if (!p.exact && !batched)
         b = staged_geometry_offset((uint32_t)tab, p.K, nb_sum) + (size_t)(3 * kTileThreads + p.npx + p.npy + p.npz) * 8;
     return b;
 }
@@ -684,7 +741,7 @@ size_t staged_smem_bytes(const SumParams& p, int band) {
 template <int BAND, bool EXACT, bool DEBUG, bool INTERP = false>
 static cudaError_t launch_variant(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
     const dim3 grid(p.n_tiles, p.n_split, p.n_t);
-    const size_t smem = staged_smem_bytes(p, BAND);
+    const size_t smem = staged_smem_bytes(p, BAND, false);
     auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG, INTERP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
