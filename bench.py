@@ -411,6 +411,89 @@ def cpu_baseline(p, slices, times, E_gpu, B_gpu, stride=512):
     return base, check
 
 
+# Published V100 timings of the paper: Table 2 (410 snapshots, 15^3 x 15^3,
+# total GPU time, constant / sinusoidal sources) and Table 4 (GPU execution
+# per time step at "ntg" = [n^3, n^3], lts = 500).  Context only: another GPU,
+# unstated precision, and Table 4 likely includes per-call overheads.
+PAPER_TABLE2_S = {"E1": 8.696, "E2": 8.111}
+PAPER_TABLE4_S = {20: 1.001, 60: 2.720, 70: 4.858, 100: 32.565, 160: 521.970}
+
+
+def paper_tables(sides=(20, 60, 70, 100, 160), lts=500, snapshots=410):
+    """The paper's own timing workloads through the library (compensated FP32).
+
+    Table 2: E1 (step-on constant) and E2 (sinusoidal) sources at the paper's
+    sizes; per snapshot k = 0..409 one slice is pushed (from device memory)
+    and E, B are evaluated at t = k dt, fields left on the device.  The ring
+    holds 448 slices, more than E2's longest delay (416), so every snapshot
+    sees its whole history.  Table 4: coincident n^3 grids over [-3,3]^3 with
+    dt = d_m / lts (d_m the largest centre distance), lts + 8 resident slices
+    of constant sources, one evaluation at the newest time (after one
+    untimed)."""
+    import torch
+
+    import paper_2104_05426_gb300 as jefi
+    from workloads import Grid, e1_constant, e2_sinusoidal
+
+    dev = torch.device("cuda", 0)
+    out = {"table2": {}, "table4": {}}
+    for name, prob in (("E1", e1_constant()), ("E2", e2_sinusoidal())):
+        H = 448
+        prm = jefi.default_params(c=prob.c, k_e=prob.k_e, k_b=prob.k_b, dt=prob.dt, t0=prob.t0,
+                                  history_slots=H, precision="fp32c")
+        h = jefi.jefi_create(jefi.grid_from(prob.src), obs_grid=jefi.grid_from(prob.obs_grid), params=prm,
+                             torch_allocator=True)
+        sl = [prob.source.sample(prob.src, prob.t0 + k * prob.dt, k) for k in range(snapshots)]
+        rho = torch.from_numpy(np.stack([r for r, _ in sl])).to(dev)
+        J = torch.from_numpy(np.stack([j for _, j in sl])).to(dev)
+        E = torch.empty((snapshots, prob.n_obs, 3), dtype=torch.float64, device=dev)
+        B = torch.empty_like(E)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for k in range(snapshots):
+            jefi.jefi_push_sources(h, rho[k], J[k])
+            jefi.jefi_eval_fields(h, prob.t0 + k * prob.dt, E[k], B[k])
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        pairs = prob.src.size * prob.n_obs * snapshots
+        out["table2"][name] = {"snapshots": snapshots, "total_s": ms / 1e3, "pairs_per_s": pairs / (ms / 1e3),
+                               "paper_v100_total_s": PAPER_TABLE2_S[name],
+                               "device_status": jefi.jefi_get_info(h)["device_status"]}
+        jefi.jefi_destroy(h)
+    for n in sides:
+        g = Grid.cube(n, -3.0, 3.0)
+        d_m = math.sqrt(3.0) * (6.0 - g.d[0])
+        dt = d_m / lts
+        H = lts + 8
+        prm = jefi.default_params(dt=dt, history_slots=H, precision="fp32c")
+        h = jefi.jefi_create(jefi.grid_from(g), obs_grid=jefi.grid_from(g), params=prm, torch_allocator=True)
+        rho = torch.ones(g.size, dtype=torch.float64, device=dev)
+        J = torch.ones((g.size, 3), dtype=torch.float64, device=dev)
+        for _ in range(H):
+            jefi.jefi_push_sources(h, rho, J)
+        t = (H - 1) * dt
+        E = torch.empty((g.size, 3), dtype=torch.float64, device=dev)
+        B = torch.empty_like(E)
+        jefi.jefi_eval_fields(h, t, E, B)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        jefi.jefi_eval_fields(h, t, E, B)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        info = jefi.jefi_get_info(h)
+        out["table4"][str(n)] = {"lts": lts, "step_s": ms / 1e3, "pairs_per_s": g.size * g.size / (ms / 1e3),
+                                 "staged_band": info["staged_band"], "paper_v100_step_s": PAPER_TABLE4_S.get(n),
+                                 "device_status": info["device_status"]}
+        jefi.jefi_destroy(h)
+        del rho, J, E, B
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
     world, rank, _ = dist_env()
@@ -465,13 +548,17 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and oracle legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--paper-tables", action="store_true",
+                    help="only time the paper's own workloads (Tables 2 and 4) and print them")
     ap.add_argument("--side", type=int, default=64,
                     help="grid side of the heavy-ion workload (64 = the benchmark; smaller "
                          "sides only for profiler captures)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.paper_tables:
+        print(json.dumps(paper_tables()))
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -82,3 +82,49 @@ def test_batch_rejects_bad_arguments(gpu, batch_problems):
         jefi.jefi_eval_batch([h] * 9, [probs[0].times[0]] * 9, [E] * 9, [B] * 9)
     assert e.value.code == jefi.JEFI_EUNSUPPORTED
     jefi.jefi_destroy(h)
+
+
+@pytest.mark.parametrize("direct", [False, True])
+def test_fallback_count_single_equals_batched(gpu, direct):
+    """Non-lattice geometry with many undecided pairs: the single-problem
+    kernel counts its FP64 fall-backs per item in shared memory, the batched
+    kernel per pair in global memory.  Both decide the same pairs, so the
+    counts agree, and the fields are bit-identical.
+
+    Source and observation centres differ by odd multiples of 1/60 on each
+    axis, dt = sqrt(3)/20 and t is a whole number of steps: every pair on a
+    body diagonal at a distance of a multiple of 3 * sqrt(3)/60 then sits on
+    a slot boundary of Eq. tr-1, which FP32 cannot decide."""
+    import torch
+
+    from workloads import Blob, Grid, MovingGaussians, Problem
+
+    src = Grid.box((12, 12, 12), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))
+    obs = Grid.box((20, 20, 20), (-2.0, -2.0, -2.0), (2.0, 2.0, 2.0))
+    dt = float(np.sqrt(3.0)) / 20.0
+    blob = Blob(1.0, (0.3, 0.25, 0.3), (-0.1, 0.05, 0.0), (0.2, 0.1, -0.05))
+    prob = Problem("fb", src, obs, None, dt, 64, 64, [], MovingGaussians([blob], noise=0.02, seed=6))
+    hist = history(prob)
+    flags = jefi.JEFI_FLAG_DIRECT_GATHER if direct else 0
+    h1, h2 = create(prob, "fp32c", flags=flags), create(prob, "fp32c", flags=flags)
+    for h in (h1, h2):
+        push_all(h, hist)
+    assert (jefi.jefi_get_info(h1)["staged_band"] == 0) == direct
+    lo, hi = jefi.jefi_valid_window(h1)
+    t = prob.t0 + np.floor((hi - prob.t0) / dt) * dt
+    assert lo <= t <= hi
+    E1, B1 = _alloc(h1)
+    jefi.jefi_eval_fields(h1, t, E1, B1)
+    E2, B2 = _alloc(h2)
+    jefi.jefi_eval_batch([h2], [t], [E2], [B2])
+    torch.cuda.synchronize()
+    n1 = jefi.jefi_get_info(h1)["slot_fallbacks"]
+    n2 = jefi.jefi_get_info(h2)["slot_fallbacks"]
+    assert n1 > 0 and n1 == n2
+    assert torch.equal(E1, E2) and torch.equal(B1, B2)
+    rho, J, _, _ = hist
+    Er, Br = oracle.fields(src.n, src.lo, src.d, prob.obs(), rho, J, dt=dt, t0=prob.t0, t=t)
+    assert rel_l2(E1.cpu().numpy(), Er) <= 1e-5 and rel_l2(B1.cpu().numpy(), Br) <= 1e-5
+    for h in (h1, h2):
+        assert jefi.jefi_get_info(h)["device_status"] == 0
+        jefi.jefi_destroy(h)
