@@ -329,6 +329,35 @@ int jefi_checkpoint_bytes(jefi_handle h, size_t* bytes);
 int jefi_checkpoint(jefi_handle h, void* dst, size_t bytes, void* stream);
 int jefi_restore(jefi_handle h, const void* src, size_t bytes, void* stream);
 
+/*
+ * Choice of the FP32 sum kernel of a handle after creation.  At creation a
+ * geometry rule picks the TMA-staged kernel whenever every (tile, brick)
+ * slot band fits 48 rows, else the direct gather.  On wide bands either can
+ * be the faster (Eqs. E-1, B-1, tr-1 are computed the same way by both:
+ * identical slots, fields equal to FP32 rounding, not bit for bit).
+ *
+ * mode JEFI_KERNEL_MEASURE: time one evaluation at t with each kernel (after
+ *   one untimed evaluation each, so four in all) and keep the faster; t must
+ *   be in the valid window.  The call synchronises `stream`.
+ * mode JEFI_KERNEL_DIRECT: switch to the direct gather (t unused).
+ * mode JEFI_KERNEL_STAGED: switch back to the staged kernel of creation (t
+ *   unused).
+ * staged_band (may be NULL) receives the band of the kernel in use, 0 for
+ *   the direct gather (the value jefi_get_info reports as staged_band).
+ * Errors: JEFI_EINVAL for a bad mode or an FP64 handle; for
+ *   JEFI_KERNEL_MEASURE a t outside the window gives JEFI_ENOTYET /
+ *   JEFI_EEVICTED as in jefi_eval_fields.  JEFI_EUNSUPPORTED when the kernel
+ *   a switch asks for cannot run this handle (no staged band at creation;
+ *   for the direct gather a ring of more than 65536 rows or tables beyond
+ *   its shared memory): the choice is then unchanged.  Where there is no
+ *   alternative, JEFI_KERNEL_MEASURE keeps the kernel in use and returns
+ *   JEFI_OK.  Later evaluations, single or batched, use the chosen kernel.
+ */
+#define JEFI_KERNEL_MEASURE 0
+#define JEFI_KERNEL_DIRECT 1
+#define JEFI_KERNEL_STAGED 2
+int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_band, void* stream);
+
 /* Release every device and host resource of the handle.  Waits for the
  * work enqueued on the handle (on any stream) to finish, not for the whole
  * device: other handles' work keeps running.  A base with live views

@@ -46,6 +46,9 @@ JEFI_FLAG_STATS = 1
 JEFI_FLAG_DIRECT_GATHER = 2
 JEFI_FLAG_SHARED_RING = 4
 JEFI_FLAG_INTERP = 8
+JEFI_KERNEL_MEASURE = 0
+JEFI_KERNEL_DIRECT = 1
+JEFI_KERNEL_STAGED = 2
 
 PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 
@@ -54,7 +57,8 @@ EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval
            "jefi_eval_fields_multi", "jefi_valid_window", "jefi_get_info", "jefi_reset_stats",
            "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror",
            "jefi_eval_fields_noalloc", "jefi_eval_batch", "jefi_create_view",
-           "jefi_debug_wait_timeout", "jefi_checkpoint_bytes", "jefi_checkpoint", "jefi_restore")
+           "jefi_debug_wait_timeout", "jefi_checkpoint_bytes", "jefi_checkpoint", "jefi_restore",
+           "jefi_select_kernel")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -141,6 +145,8 @@ def load(build_if_needed: bool = True):
         L.jefi_checkpoint_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         L.jefi_checkpoint.argtypes = [P, P, ctypes.c_size_t, P]
         L.jefi_restore.argtypes = [P, P, ctypes.c_size_t, P]
+        L.jefi_select_kernel.argtypes = [P, I32, D, ctypes.POINTER(I32), P]
+        L.jefi_select_kernel.restype = I
         L.jefi_strerror.argtypes = [I]
         L.jefi_strerror.restype = ctypes.c_char_p
         for name in ("jefi_create", "jefi_push_sources", "jefi_eval_fields",
@@ -329,6 +335,16 @@ def jefi_restore(h: Handle, image: bytes, stream=None):
     buf = ctypes.create_string_buffer(bytes(image), len(image))
     _check(load().jefi_restore(h.ptr, ctypes.cast(buf, ctypes.c_void_p), len(image), _stream_ptr(stream)),
            "jefi_restore")
+
+
+def jefi_select_kernel(h: Handle, mode: int, t: float = 0.0, stream=None) -> int:
+    """Choose the FP32 sum kernel of h (JEFI_KERNEL_MEASURE times both at t
+    and keeps the faster; _DIRECT / _STAGED switch).  Returns the staged band
+    in use, 0 for the direct gather."""
+    band = ctypes.c_int32()
+    rc = load().jefi_select_kernel(h.ptr, int(mode), float(t), ctypes.byref(band), _stream_ptr(stream))
+    _check(rc, "jefi_select_kernel")
+    return band.value
 
 
 def jefi_valid_window(h: Handle):

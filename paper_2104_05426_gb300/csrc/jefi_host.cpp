@@ -272,6 +272,7 @@ struct jefi_problem {
     std::vector<TimeParams> h_times;
     // staged FP32 kernel (0 = direct-gather kernel)
     int32_t band = 0;
+    int32_t band0 = 0;               // the staged band chosen at creation (0: none)
     int32_t mirror = 0;              // M: mirrored ring slots
     bool exact = false;              // lattice geometry: S32 == S64
     double g_bias = 0;               // bound on the FP32 candidate error (slots)
@@ -334,6 +335,20 @@ void release_all(jefi_problem* h) {
     for (auto& e : h->ev_free) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     h->ev_pending.clear();
     h->ev_free.clear();
+}
+
+// Device and host tables of the direct-gather kernel; false if out of memory.
+bool alloc_direct_tables(jefi_problem* h) {
+    if (h->tabg) return true;
+    const size_t n = (size_t)h->time_chunk * (h->K + 2 * kTabGuard);
+    float2* g = (float2*)dev_alloc(h, sizeof(float2) * n);
+    float* t = g ? (float*)dev_alloc(h, sizeof(float) * n) : nullptr;
+    if (!g || !t) return false;
+    h->tabg = g;
+    h->tabh = t;
+    h->h_tabg.resize(n);
+    h->h_tabh.resize(n);
+    return true;
 }
 
 // Record that work on h's memory was enqueued on stream s (jefi_destroy waits for it).
@@ -424,7 +439,7 @@ void build_tables(jefi_problem* h, int ti, double t) {
             t2[e] = make_float2(thi, tlo);
         }
     }
-    if (h->tabg) {
+    if (h->tabg && h->band == 0) {
         // direct-gather kernel: (T_hi, T_lo) of Theta_k' and the physical slots of k', k'-1
         const int KT = K + 2 * kTabGuard;
         float2* tg = h->h_tabg.data() + (size_t)ti * KT;
@@ -553,7 +568,7 @@ int upload_tables(jefi_problem* h, int n_t, cudaStream_t s) {
     if (h->band > 0)
         JEFI_CUDA(cudaMemcpyAsync(h->tab2, h->h_tab2.data(),
                                   sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
-    if (h->tabg) {
+    if (h->tabg && h->band == 0) {
         JEFI_CUDA(cudaMemcpyAsync(h->tabg, h->h_tabg.data(),
                                   sizeof(float2) * (K + 2 * kTabGuard) * n_t, cudaMemcpyHostToDevice, s));
         JEFI_CUDA(cudaMemcpyAsync(h->tabh, h->h_tabh.data(),
@@ -993,6 +1008,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         h->mirror = h->band;
     }
     h->Hp = h->H + h->mirror + kZeroPadSlots;
+    h->band0 = h->band;
     if (!h->fp64 && h->any_pairs && h->band == 0 && h->Hp > 65536) {
         delete h;   // the direct-gather kernel packs two physical slots in 16 bits each
         return JEFI_EUNSUPPORTED;
@@ -1017,13 +1033,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->times = (TimeParams*)dev_alloc(h, sizeof(TimeParams) * h->time_chunk);
     h->fallbacks = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
     h->status = (int32_t*)dev_alloc(h, sizeof(int32_t));
-    if (!h->fp64 && h->any_pairs && h->band == 0) {
-        h->tabg = (float2*)dev_alloc(h, sizeof(float2) * h->time_chunk * (h->K + 2 * kTabGuard));
-        h->tabh = (float*)dev_alloc(h, sizeof(float) * h->time_chunk * (h->K + 2 * kTabGuard));
-        if (!h->tabg || !h->tabh) h->status = nullptr;
-        h->h_tabg.resize((size_t)h->time_chunk * (h->K + 2 * kTabGuard));
-        h->h_tabh.resize((size_t)h->time_chunk * (h->K + 2 * kTabGuard));
-    }
+    if (!h->fp64 && h->any_pairs && h->band == 0 && !alloc_direct_tables(h)) h->status = nullptr;
     if (h->band > 0) {
         h->tile_box = (float*)dev_alloc(h, sizeof(float) * tile_box.size());
         h->tab2 = (float2*)dev_alloc(h, sizeof(float2) * h->time_chunk * (h->K + 2 * kTabGuard));
@@ -1400,6 +1410,77 @@ int jefi_debug_wait_timeout(double limit_s, void* stream) {
     cudaFree(d);
     if (e != cudaSuccess) return JEFI_ECUDA;
     return st;
+}
+
+namespace {
+
+// Can the direct-gather kernel run handle h?
+bool direct_possible(jefi_problem* h) {
+    if (h->Hp > 65536) return false;   // two physical slots packed in 16 bits each
+    if (!alloc_direct_tables(h)) return false;
+    return sum_smem_bytes(make_params(h, 1, 0, nullptr)) <= 200 * 1024;
+}
+
+// Device time of one evaluation of h at t into the handle's staging buffer,
+// after one untimed evaluation, in ms.  Returns JEFI_OK or an error code.
+int time_eval(jefi_problem* h, double t, cudaStream_t s, float* ms) {
+    const size_t per_t = (size_t)h->n_obs * 3;
+    double* E = h->out_stage;
+    double* B = h->out_stage + h->time_chunk * per_t;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int rc = JEFI_OK;
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) rc = JEFI_ECUDA;
+    if (rc == JEFI_OK) rc = launch_chunk(h, 1, &t, E, B, s, nullptr);
+    if (rc == JEFI_OK && cudaEventRecord(ev[0], s) != cudaSuccess) rc = JEFI_ECUDA;
+    if (rc == JEFI_OK) rc = launch_chunk(h, 1, &t, E, B, s, nullptr);
+    if (rc == JEFI_OK && (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                          cudaEventElapsedTime(ms, ev[0], ev[1]) != cudaSuccess))
+        rc = JEFI_ECUDA;
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc == JEFI_ECUDA) cudaGetLastError();
+    return rc;
+}
+
+}  // namespace
+
+int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_band, void* stream) {
+    if (!h || h->fp64 || mode < JEFI_KERNEL_MEASURE || mode > JEFI_KERNEL_STAGED) return JEFI_EINVAL;
+    sync_view(h);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = JEFI_OK;
+    if (mode == JEFI_KERNEL_STAGED) {
+        if (h->band0 == 0) rc = JEFI_EUNSUPPORTED;
+        else h->band = h->band0;
+    } else if (mode == JEFI_KERNEL_DIRECT) {
+        if (h->band != 0 && h->any_pairs) {
+            if (direct_possible(h)) h->band = 0;
+            else rc = JEFI_EUNSUPPORTED;
+        }
+    } else {
+        rc = check_time(h, t);
+        if (rc == JEFI_OK && h->band0 != 0 && h->any_pairs && h->n_obs > 0 && direct_possible(h)) {
+            const int32_t keep = h->band;
+            float ms_staged = 0.f, ms_direct = 0.f;
+            h->band = h->band0;
+            rc = time_eval(h, t, s, &ms_staged);
+            if (rc == JEFI_OK) {
+                h->band = 0;
+                rc = time_eval(h, t, s, &ms_direct);
+            }
+            h->band = rc != JEFI_OK ? keep : (ms_direct < ms_staged ? 0 : h->band0);
+            if (rc == JEFI_OK) {
+                int32_t st = 0;
+                JEFI_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, s));
+                JEFI_CUDA(cudaStreamSynchronize(s));
+                if (st != 0) rc = st;
+            }
+            const int mu = mark_use(h, s);
+            if (rc == JEFI_OK) rc = mu;
+        }
+    }
+    if (staged_band) *staged_band = h->band;
+    return rc;
 }
 
 int jefi_valid_window(jefi_handle h, double* t_lo, double* t_hi) {

@@ -345,6 +345,72 @@ def test_staged_kernel_matches_direct_gather(gpu, lattice):
         jefi.jefi_destroy(h)
 
 
+def test_select_kernel_switches_and_measures(gpu):
+    """jefi_select_kernel on a staged handle: switched to the direct gather it
+    gives the slots and fields of a handle created on the direct gather, bit
+    for bit; switched back, its own again; measuring keeps one of the two,
+    and a batched evaluation follows the choice.  Handles without a staged
+    band at creation and FP64 handles refuse."""
+    import torch
+
+    src = Grid((16, 16, 16), (-0.731, -0.683, -0.802), (0.0931, 0.0877, 0.1013))
+    obs = Grid((16, 16, 8), (1.113, -0.917, -0.419), (0.1207, 0.1133, 0.1049))
+    blob = Blob(1.0, (0.25, 0.2, 0.3), (-0.2, 0.05, 0.0), (0.2, 0.1, -0.05))
+    prob = Problem("sel", src, obs, None, 0.0517, 120, 120, [], MovingGaussians([blob], noise=0.02, seed=3))
+    hist = history(prob)
+    hs = create(prob, "fp32c")
+    hd = create(prob, "fp32c", flags=jefi.JEFI_FLAG_DIRECT_GATHER)
+    for h in (hs, hd):
+        push_all(h, hist)
+    band0 = jefi.jefi_get_info(hs)["staged_band"]
+    assert band0 > 0 and jefi.jefi_get_info(hd)["staged_band"] == 0
+    lo, hi = jefi.jefi_valid_window(hs)
+    times = [hi - 0.4, hi - 0.02]
+    f_staged = gpu_fields(hs, times)
+    f_direct = gpu_fields(hd, times)
+    slots_d = [jefi.jefi_debug_slots(hd, t) for t in times]
+
+    assert jefi.jefi_select_kernel(hs, jefi.JEFI_KERNEL_DIRECT) == 0
+    assert jefi.jefi_get_info(hs)["staged_band"] == 0
+    for a, b in zip(gpu_fields(hs, times), f_direct):
+        assert np.array_equal(a, b)
+    for t, sd in zip(times, slots_d):
+        assert np.array_equal(jefi.jefi_debug_slots(hs, t), sd)
+
+    assert jefi.jefi_select_kernel(hs, jefi.JEFI_KERNEL_STAGED) == band0
+    for a, b in zip(gpu_fields(hs, times), f_staged):
+        assert np.array_equal(a, b)
+
+    band = jefi.jefi_select_kernel(hs, jefi.JEFI_KERNEL_MEASURE, times[0])
+    assert band in (0, band0) and jefi.jefi_get_info(hs)["staged_band"] == band
+    mine = gpu_fields(hs, times)
+    for a, b in zip(mine, f_direct if band == 0 else f_staged):
+        assert np.array_equal(a, b)
+    E = torch.empty((prob.n_obs, 3), dtype=torch.float64, device="cuda")
+    B = torch.empty_like(E)
+    jefi.jefi_eval_batch([hs], [times[1]], [E], [B])
+    torch.cuda.synchronize()
+    assert np.array_equal(E.cpu().numpy(), mine[0][1]) and np.array_equal(B.cpu().numpy(), mine[1][1])
+    ref = oracle_fields(prob, hist, times)
+    for i in range(len(times)):
+        assert rel_l2(mine[0][i], ref[i][0]) <= FP32C_TOL and rel_l2(mine[1][i], ref[i][1]) <= FP32C_TOL
+
+    with pytest.raises(jefi.JefiError) as e:
+        jefi.jefi_select_kernel(hd, jefi.JEFI_KERNEL_STAGED)
+    assert e.value.code == jefi.JEFI_EUNSUPPORTED
+    assert jefi.jefi_select_kernel(hd, jefi.JEFI_KERNEL_MEASURE, times[0]) == 0
+    with pytest.raises(jefi.JefiError) as e:
+        jefi.jefi_select_kernel(hs, jefi.JEFI_KERNEL_MEASURE, hi + 10.0)
+    assert e.value.code != 0
+    h64 = create(prob, "fp64")
+    with pytest.raises(jefi.JefiError) as e:
+        jefi.jefi_select_kernel(h64, jefi.JEFI_KERNEL_DIRECT)
+    assert e.value.code == jefi.JEFI_EINVAL
+    for h in (hs, hd, h64):
+        assert jefi.jefi_get_info(h)["device_status"] == 0
+        jefi.jefi_destroy(h)
+
+
 def test_direct_gather_history_limit(gpu):
     """The direct-gather FP32 kernel packs two physical ring rows in 16 bits
     each: a handle on it with H + 1 <= 65536 rows is created, one more row is
