@@ -337,7 +337,9 @@ def run_gpu(args):
 
             result["batch"] = dict(measure_batch(),
                                    workload="256 independent problems (source sides 8-48, histories "
-                                            "32-128, observation sides 8-32) in one jefi_eval_batch call")
+                                            "32-128, observation sides 8-32) in one jefi_eval_batch call; "
+                                            "graph: the same batch as a batch plan (one CUDA-graph launch); "
+                                            "tuned: after the plan's autotuner (kernels, source splits)")
         if not args.no_cpu_baseline:
             result["cpu_baseline"], result["oracle_check"] = cpu_baseline(p, slices[:H], t_first,
                                                                           E_first, B_first)

@@ -358,10 +358,78 @@ int jefi_restore(jefi_handle h, const void* src, size_t bytes, void* stream);
 #define JEFI_KERNEL_STAGED 2
 int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_band, void* stream);
 
+/*
+ * Batch plans: a fixed set of problems evaluated again and again, each call
+ * at new times, as one CUDA graph (Eqs. E-1, B-1, tr-1 for every problem,
+ * exactly as jefi_eval_batch computes them).
+ *
+ * jefi_batch_plan_create records, once, everything jefi_eval_batch issues
+ * for hs[n] with outputs E[i], B[i] (device [N_obs_i][3] FP64, fixed for the
+ * plan's life): one host-to-device copy of the batch's metadata and slot
+ * tables, one persistent launch per kernel variant and the reduction.  It
+ * captures that sequence into two CUDA graphs (the metadata of call k is
+ * written on the host while call k-1 may still run on the device) and
+ * allocates the plan's own device and pinned host buffers.  A handle may
+ * appear up to 8 times (a view up to 2 times), as in jefi_eval_batch; FP64,
+ * FP32 and compensated FP32 handles mix freely; handles with
+ * JEFI_FLAG_INTERP give JEFI_EUNSUPPORTED.
+ *
+ * jefi_batch_plan_launch evaluates problem i at t[i] (host array [n]):
+ * checks every time against its handle's window (JEFI_ENOTYET /
+ * JEFI_EEVICTED, nothing enqueued), builds the exact slot tables on the
+ * host and replays the graph with one cudaGraphLaunch on `stream`.
+ * Asynchronous; every result is bit-identical to jefi_eval_batch (and to
+ * jefi_eval_fields) on the same handles and times.  If a handle's kernel or
+ * source-split count changed since the graphs were recorded
+ * (jefi_select_kernel, a tuner), the call first waits for the plan's
+ * earlier launches and records the graphs again.  Launches of one plan must
+ * be issued on one stream (or serialised by the caller); a handle must not
+ * be in two plans or batches in flight at once (they share its scratch).
+ *
+ * jefi_batch_plan_tune is the autotuner of the batched launch.  It times the
+ * plan, on the device, at times t[n] (which it evaluates, overwriting the
+ * outputs) in each of these configurations and keeps the fastest:
+ *   - kernel choice per problem: the handles' current choice, and the one
+ *     jefi_select_kernel(JEFI_KERNEL_MEASURE) makes for each FP32 handle
+ *     that has both kernels (staged band vs direct gather);
+ *   - source splits per observation tile (the work-item shape): every
+ *     handle's creation-time split count divided by 1, 2, 4 or 8 (a batch
+ *     fills the GPU with many problems, so fewer and larger items can win).
+ * The choice stays with the handles: later single, batched and planned
+ * evaluations use it.  Fields then differ from the untuned ones at the
+ * rounding level of the precision (the split sums change), still within
+ * the accuracy contract.  `report` (may be NULL) receives what was tried
+ * and kept.  The call synchronises `stream`.
+ *
+ * jefi_batch_plan_destroy waits for the plan's launches and frees it.
+ * Destroy every plan before the handles it holds: jefi_destroy of a handle
+ * in a live plan returns JEFI_EINVAL.
+ */
+typedef struct jefi_batch_plan_s* jefi_batch_plan;
+
+typedef struct {
+    int32_t candidates;       /* configurations timed                                */
+    int32_t split_divisor;    /* kept: creation-time split counts divided by this
+                                 (1, 2, 4, 8), or 0 if the splits the handles had
+                                 at the call were kept                             */
+    int32_t measured_kernels; /* kept: 1 = per-problem measured kernel choice,
+                                 0 = the handles' choice at the call               */
+    int32_t staged_problems;  /* batch entries on the staged kernel after tuning      */
+    double ms_initial;        /* device time of one launch as the handles were       */
+    double ms_tuned;          /* device time of one launch as kept                   */
+} jefi_tune_report;
+
+int jefi_batch_plan_create(const jefi_handle* hs, double* const* E, double* const* B, int32_t n,
+                           jefi_batch_plan* out);
+int jefi_batch_plan_launch(jefi_batch_plan plan, const double* t, void* stream);
+int jefi_batch_plan_tune(jefi_batch_plan plan, const double* t, void* stream, jefi_tune_report* report);
+int jefi_batch_plan_destroy(jefi_batch_plan plan);
+
 /* Release every device and host resource of the handle.  Waits for the
  * work enqueued on the handle (on any stream) to finish, not for the whole
  * device: other handles' work keeps running.  A base with live views
- * returns JEFI_EINVAL (destroy the views first). */
+ * returns JEFI_EINVAL (destroy the views first), and so does a handle that
+ * a live batch plan holds. */
 int jefi_destroy(jefi_handle h);
 
 const char* jefi_strerror(int code);

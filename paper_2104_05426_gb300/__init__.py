@@ -58,7 +58,8 @@ EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval
            "jefi_debug_slots", "jefi_host_pair_slots", "jefi_destroy", "jefi_strerror",
            "jefi_eval_fields_noalloc", "jefi_eval_batch", "jefi_create_view",
            "jefi_debug_wait_timeout", "jefi_checkpoint_bytes", "jefi_checkpoint", "jefi_restore",
-           "jefi_select_kernel")
+           "jefi_select_kernel", "jefi_batch_plan_create", "jefi_batch_plan_launch",
+           "jefi_batch_plan_tune", "jefi_batch_plan_destroy")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -93,6 +94,15 @@ class jefi_info(ctypes.Structure):
                 ("sum_launches", ctypes.c_int64), ("sum_ms_total", ctypes.c_double),
                 ("n_split", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("device_status", ctypes.c_int32), ("staged_band", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class jefi_tune_report(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int32), ("split_divisor", ctypes.c_int32),
+                ("measured_kernels", ctypes.c_int32), ("staged_problems", ctypes.c_int32),
+                ("ms_initial", ctypes.c_double), ("ms_tuned", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -147,6 +157,13 @@ def load(build_if_needed: bool = True):
         L.jefi_restore.argtypes = [P, P, ctypes.c_size_t, P]
         L.jefi_select_kernel.argtypes = [P, I32, D, ctypes.POINTER(I32), P]
         L.jefi_select_kernel.restype = I
+        L.jefi_batch_plan_create.argtypes = [P, P, P, I32, ctypes.POINTER(P)]
+        L.jefi_batch_plan_launch.argtypes = [P, P, P]
+        L.jefi_batch_plan_tune.argtypes = [P, P, P, ctypes.POINTER(jefi_tune_report)]
+        L.jefi_batch_plan_destroy.argtypes = [P]
+        for name in ("jefi_batch_plan_create", "jefi_batch_plan_launch", "jefi_batch_plan_tune",
+                     "jefi_batch_plan_destroy"):
+            getattr(L, name).restype = I
         L.jefi_strerror.argtypes = [I]
         L.jefi_strerror.restype = ctypes.c_char_p
         for name in ("jefi_create", "jefi_push_sources", "jefi_eval_fields",
@@ -444,6 +461,67 @@ def jefi_eval_batch(handles, times, E_list, B_list, stream=None):
     bp = (ctypes.c_void_p * n)(*bs)
     rc = load().jefi_eval_batch(hs, ts, ep, bp, n, _stream_ptr(stream))
     _check(rc, "jefi_eval_batch")
+
+
+class BatchPlan:
+    """Owns a jefi_batch_plan and keeps its handles and output tensors alive."""
+
+    def __init__(self, ptr, handles, keep):
+        self.ptr = ptr
+        self.handles = handles
+        self._keep = keep
+
+
+def _times(plan: BatchPlan, times):
+    n = len(plan.handles)
+    if len(times) != n:
+        raise ValueError("one time per batch entry")
+    return (ctypes.c_double * max(n, 1))(*[float(x) for x in times])
+
+
+def jefi_batch_plan_create(handles, E_list, B_list) -> BatchPlan:
+    """Record the batched evaluation of handles[i] into E_list[i], B_list[i]
+    (CUDA float64 tensors [N_obs_i, 3], fixed for the plan's life) as CUDA
+    graphs (see include/jefi.h)."""
+    n = len(handles)
+    if not (len(E_list) == len(B_list) == n):
+        raise ValueError("handles and outputs must have the same length")
+    es, bs = [], []
+    for E, B in zip(E_list, B_list):
+        e, on_e, _ = _buf(E)
+        b, on_b, _ = _buf(B)
+        if not (on_e and on_b):
+            raise ValueError("a batch plan writes device (CUDA) tensors only")
+        es.append(e)
+        bs.append(b)
+    hs = (ctypes.c_void_p * max(n, 1))(*[h.ptr.value for h in handles])
+    ep = (ctypes.c_void_p * max(n, 1))(*es)
+    bp = (ctypes.c_void_p * max(n, 1))(*bs)
+    out = ctypes.c_void_p()
+    rc = load().jefi_batch_plan_create(hs, ep, bp, n, ctypes.byref(out))
+    _check(rc, "jefi_batch_plan_create")
+    return BatchPlan(out, list(handles), (list(E_list), list(B_list)))
+
+
+def jefi_batch_plan_launch(plan: BatchPlan, times, stream=None):
+    """Evaluate entry i at times[i]: one graph launch, asynchronous on `stream`."""
+    rc = load().jefi_batch_plan_launch(plan.ptr, _times(plan, times), _stream_ptr(stream))
+    _check(rc, "jefi_batch_plan_launch")
+
+
+def jefi_batch_plan_tune(plan: BatchPlan, times, stream=None) -> dict:
+    """Autotune the plan's kernels and source splits at `times`; returns the report."""
+    rep = jefi_tune_report()
+    rc = load().jefi_batch_plan_tune(plan.ptr, _times(plan, times), _stream_ptr(stream), ctypes.byref(rep))
+    _check(rc, "jefi_batch_plan_tune")
+    return rep.as_dict()
+
+
+def jefi_batch_plan_destroy(plan: BatchPlan):
+    if plan.ptr is not None and plan.ptr.value:
+        rc = load().jefi_batch_plan_destroy(plan.ptr)
+        _check(rc, "jefi_batch_plan_destroy")
+        plan.ptr = None
 
 
 def jefi_create_view(base: Handle, obs_grid: Optional[jefi_grid] = None, obs_points=None, stream=None):

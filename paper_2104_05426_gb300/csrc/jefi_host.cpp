@@ -237,6 +237,7 @@ struct jefi_problem {
     double screen[3] = {0, 0, 0};
     int64_t n_latest = -1;
     int32_t n_split = 1, bricks_per_split = 0;
+    int32_t n_split_max = 1;         // splits the partials buffer was sized for (creation)
     int32_t K = 0;                 // candidate-table length per time
     // exact squared-distance extremes over unscreened pairs
     Extremes real, pad;
@@ -288,6 +289,7 @@ struct jefi_problem {
     // observation views share a base handle's ring and pushes
     jefi_problem* base = nullptr;
     int32_t n_views = 0;
+    int32_t n_plans = 0;             // live batch plans holding this handle
     // completion of the latest work enqueued on this handle's memory (any stream)
     cudaEvent_t last_use = nullptr;
     // statistics
@@ -932,6 +934,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         if (h->bricks_per_split < 1) h->bricks_per_split = 1;
         h->n_split = (int32_t)((h->n_bricks + h->bricks_per_split - 1) / h->bricks_per_split);
         if (h->n_split < 1) h->n_split = 1;
+        h->n_split_max = h->n_split;
     }
 
     // ---------------------------------------------------------------- FP32 candidate bias
@@ -1706,9 +1709,543 @@ int jefi_restore(jefi_handle h, const void* src, size_t bytes, void* stream) {
     return JEFI_OK;
 }
 
+// ---------------------------------------------------------------- batch plans
+// A fixed batch recorded as CUDA graphs.  The plan's buffer holds what
+// jefi_eval_batch puts in its arena (kernel parameters, work-item starts,
+// queue counters, reduction items) plus every entry's slot tables, so one
+// host-to-device copy per launch refreshes all of it; the kernel parameters
+// point at the plan's copy of the tables instead of the handles' own.
+}  // extern "C"
+
+struct jefi_batch_plan_s {
+    std::vector<jefi_problem*> hs;
+    std::vector<double*> E, B;
+    std::vector<int> occ;                     // scratch slot of entry i in its handle
+    std::vector<int32_t> cap_band, cap_split, cap_bps;   // handle configuration the graphs were recorded with
+    struct Tables {                           // byte offsets in the buffer; 0 = absent
+        size_t tab32 = 0, theta = 0, times = 0, tab2 = 0, tabg = 0, tabh = 0;
+    };
+    std::vector<Tables> tabs;                 // per entry; tab32 == 0: nothing to copy
+    size_t bytes = 0;
+    void* dev = nullptr;
+    unsigned char* pinned[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    bool pending[2] = {false, false};
+    int next = 0;
+    int n_sm = 0;
+    bool built = false;
+};
+
+namespace {
+
+// Wait for every launch of the plan still in flight (they read its pinned buffers).
+int plan_wait(jefi_batch_plan_s* p) {
+    for (int j = 0; j < 2; ++j)
+        if (p->pending[j]) {
+            JEFI_CUDA(cudaEventSynchronize(p->done[j]));
+            p->pending[j] = false;
+        }
+    return JEFI_OK;
+}
+
+void plan_release_graphs(jefi_batch_plan_s* p) {
+    for (int j = 0; j < 2; ++j) {
+        if (p->exec[j]) cudaGraphExecDestroy(p->exec[j]);
+        p->exec[j] = nullptr;
+        if (p->pinned[j]) cudaFreeHost(p->pinned[j]);
+        p->pinned[j] = nullptr;
+    }
+    if (p->dev) cudaFree(p->dev);
+    p->dev = nullptr;
+    p->bytes = 0;
+    p->built = false;
+}
+
+bool plan_stale(const jefi_batch_plan_s* p) {
+    if (!p->built) return true;
+    for (size_t i = 0; i < p->hs.size(); ++i)
+        if (p->hs[i]->band != p->cap_band[i] || p->hs[i]->n_split != p->cap_split[i] ||
+            p->hs[i]->bricks_per_split != p->cap_bps[i])
+            return true;
+    return false;
+}
+
+// Record the plan's graphs for the handles' current kernels and splits.
+// Earlier launches must have finished (plan_wait).
+int plan_build(jefi_batch_plan_s* p) {
+    plan_release_graphs(p);
+    const int n = (int)p->hs.size();
+    // Kernel variants as in jefi_eval_batch: one persistent launch per group.
+    struct Group {
+        int kind;           // 0 FP64, 1 FP32 direct, 2 FP32 staged
+        int comp, band;
+        bool exact;
+        std::vector<int> members;
+    };
+    std::vector<Group> groups;
+    std::vector<ReduceItem> ritems;
+    std::vector<int64_t> rstart(1, 0);
+    std::vector<int> zero_entries;
+    p->tabs.assign(n, jefi_batch_plan_s::Tables{});
+    p->cap_band.resize(n);
+    p->cap_split.resize(n);
+    p->cap_bps.resize(n);
+    for (int i = 0; i < n; ++i) {
+        jefi_problem* h = p->hs[i];
+        p->cap_band[i] = h->band;
+        p->cap_split[i] = h->n_split;
+        p->cap_bps[i] = h->bricks_per_split;
+        if (h->n_obs == 0) continue;
+        if (!h->any_pairs) {
+            zero_entries.push_back(i);
+            continue;
+        }
+        Group key{h->fp64 ? 0 : (h->band > 0 ? 2 : 1), h->prm.precision == JEFI_FP32_COMP ? 1 : 0, h->band,
+                  h->exact, {}};
+        if (key.kind != 1) key.comp = 0;
+        if (key.kind != 2) { key.band = 0; key.exact = false; }
+        Group* g = nullptr;
+        for (auto& x : groups)
+            if (x.kind == key.kind && x.comp == key.comp && x.band == key.band && x.exact == key.exact &&
+                (x.kind != 2 || (int)x.members.size() < kMaxBatchMaps))
+                g = &x;
+        if (!g) {
+            groups.push_back(key);
+            g = &groups.back();
+        }
+        g->members.push_back(i);
+        ReduceItem r{};
+        r.inv_perm = h->d_inv_perm;
+        r.partials = h->partials + (size_t)p->occ[i] * h->n_split * 6 * h->n_slots;
+        r.n_obs = (int32_t)h->n_obs;
+        r.n_slots = h->n_slots;
+        r.n_split = h->n_split;
+        r.e_scale = h->prm.k_e * (h->src.d[0] * h->src.d[1] * h->src.d[2]) / h->prm.c;
+        r.b_scale = h->prm.k_b * (h->src.d[0] * h->src.d[1] * h->src.d[2]);
+        r.E = p->E[i];
+        r.B = p->B[i];
+        ritems.push_back(r);
+        rstart.push_back(rstart.back() + h->n_obs);
+    }
+
+    // Layout: per group [params | item_start | counter], then [reduce items |
+    // starts], then every entry's tables; all 256-byte aligned.
+    std::vector<size_t> off_params(groups.size()), off_start(groups.size()), off_counter(groups.size());
+    size_t bytes = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        off_params[g] = bytes;
+        bytes = align256(bytes + sizeof(SumParams) * groups[g].members.size());
+        off_start[g] = bytes;
+        bytes = align256(bytes + sizeof(int32_t) * (groups[g].members.size() + 1));
+        off_counter[g] = bytes;
+        bytes = align256(bytes + sizeof(unsigned int));
+    }
+    const size_t off_ritems = bytes;
+    bytes = align256(bytes + sizeof(ReduceItem) * ritems.size());
+    const size_t off_rstart = bytes;
+    bytes = align256(bytes + sizeof(int64_t) * rstart.size());
+    for (const auto& grp : groups)
+        for (int i : grp.members) {
+            const jefi_problem* h = p->hs[i];
+            const size_t KT = (size_t)h->K + 2 * kTabGuard;
+            auto& tb = p->tabs[i];
+            tb.tab32 = bytes;
+            bytes = align256(bytes + sizeof(float4) * h->K);
+            tb.theta = bytes;
+            bytes = align256(bytes + sizeof(double) * (h->K + 1));
+            tb.times = bytes;
+            bytes = align256(bytes + sizeof(TimeParams));
+            if (h->band > 0) {
+                tb.tab2 = bytes;
+                bytes = align256(bytes + sizeof(float2) * KT);
+            } else if (h->tabg) {
+                tb.tabg = bytes;
+                bytes = align256(bytes + sizeof(float2) * KT);
+                tb.tabh = bytes;
+                bytes = align256(bytes + sizeof(float) * KT);
+            }
+        }
+    if (groups.empty() && zero_entries.empty()) {   // nothing on the device
+        p->built = true;
+        return JEFI_OK;
+    }
+    bytes = std::max<size_t>(bytes, 256);
+    if (cudaMalloc(&p->dev, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p->dev = nullptr;
+        return JEFI_ENOMEM;
+    }
+    p->bytes = bytes;
+    for (int j = 0; j < 2; ++j) {
+        if (cudaHostAlloc((void**)&p->pinned[j], bytes, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            p->pinned[j] = nullptr;
+            plan_release_graphs(p);
+            return JEFI_ENOMEM;
+        }
+        std::memset(p->pinned[j], 0, bytes);    // queue counters start at zero on every launch
+    }
+
+    // Constant part: kernel parameters (tables redirected into the buffer),
+    // item starts, reduction items.
+    unsigned char* d = static_cast<unsigned char*>(p->dev);
+    unsigned char* host = p->pinned[0];
+    std::vector<int> n_items(groups.size());
+    std::vector<size_t> smem(groups.size(), 0);
+    for (size_t g = 0; g < groups.size(); ++g) {
+        SumParams* prm = reinterpret_cast<SumParams*>(host + off_params[g]);
+        int32_t* start = reinterpret_cast<int32_t*>(host + off_start[g]);
+        int32_t acc = 0;
+        for (size_t m = 0; m < groups[g].members.size(); ++m) {
+            const int i = groups[g].members[m];
+            const jefi_problem* h = p->hs[i];
+            const auto& tb = p->tabs[i];
+            SumParams q = make_params(h, 1, p->occ[i], nullptr);
+            q.tab32 = reinterpret_cast<const float4*>(d + tb.tab32);
+            q.theta = reinterpret_cast<const double*>(d + tb.theta);
+            q.times = reinterpret_cast<const TimeParams*>(d + tb.times);
+            q.tab2 = tb.tab2 ? reinterpret_cast<const float2*>(d + tb.tab2) : nullptr;
+            q.tabg = tb.tabg ? reinterpret_cast<const float2*>(d + tb.tabg) : nullptr;
+            q.tabh = tb.tabh ? reinterpret_cast<const float*>(d + tb.tabh) : nullptr;
+            prm[m] = q;
+            start[m] = acc;
+            acc += h->n_tiles * h->n_split;
+            smem[g] = std::max(smem[g], groups[g].kind == 2 ? staged_smem_bytes(q, groups[g].band, true)
+                                                             : sum_smem_bytes(q));
+        }
+        start[groups[g].members.size()] = acc;
+        n_items[g] = acc;
+        if (smem[g] > 220 * 1024) {
+            plan_release_graphs(p);
+            return JEFI_EUNSUPPORTED;
+        }
+    }
+    if (!ritems.empty()) std::memcpy(host + off_ritems, ritems.data(), sizeof(ReduceItem) * ritems.size());
+    std::memcpy(host + off_rstart, rstart.data(), sizeof(int64_t) * rstart.size());
+    std::memcpy(p->pinned[1], p->pinned[0], bytes);
+
+    // Record: [zero fields] -> copy -> one persistent launch per group -> reduction.
+    cudaStream_t cs = nullptr;
+    JEFI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = JEFI_OK;
+    for (int j = 0; j < 2 && rc == JEFI_OK; ++j) {
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            rc = JEFI_ECUDA;
+            break;
+        }
+        cudaError_t e = cudaSuccess;
+        for (int i : zero_entries) {
+            const size_t fb = sizeof(double) * 3 * p->hs[i]->n_obs;
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->E[i], 0, fb, cs);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->B[i], 0, fb, cs);
+        }
+        if (e == cudaSuccess && !groups.empty())
+            e = cudaMemcpyAsync(d, p->pinned[j], bytes, cudaMemcpyHostToDevice, cs);
+        for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+            const int per_sm = groups[g].kind == 0 ? 1 : (smem[g] > 110 * 1024 ? 1 : 2);
+            const int grid = std::max(1, std::min(n_items[g], per_sm * p->n_sm));
+            if (groups[g].kind == 2) {
+                StagedBatchArgs a;
+                std::memset(&a, 0, sizeof(a));
+                a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
+                a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
+                a.n = (int32_t)groups[g].members.size();
+                a.n_items = n_items[g];
+                a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
+                for (size_t m = 0; m < groups[g].members.size(); ++m) a.maps[m] = p->hs[groups[g].members[m]]->tmap;
+                e = launch_sum_f32_staged_batch(a, groups[g].band, groups[g].exact, smem[g], grid, cs);
+            } else {
+                BatchArgs a;
+                a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
+                a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
+                a.n = (int32_t)groups[g].members.size();
+                a.n_items = n_items[g];
+                a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
+                e = groups[g].kind == 0 ? launch_sum_f64_batch(a, smem[g], grid, cs)
+                                        : launch_sum_f32_batch(a, groups[g].comp != 0, smem[g], grid, cs);
+            }
+        }
+        if (e == cudaSuccess && !groups.empty())
+            e = launch_reduce_batch(reinterpret_cast<const ReduceItem*>(d + off_ritems),
+                                    reinterpret_cast<const int64_t*>(d + off_rstart), (int)ritems.size(),
+                                    rstart.back(), cs);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = ee;
+        if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&p->exec[j], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || !p->exec[j]) {
+            cudaGetLastError();
+            rc = JEFI_ECUDA;
+        }
+    }
+    cudaStreamDestroy(cs);
+    if (rc != JEFI_OK) {
+        plan_release_graphs(p);
+        return rc;
+    }
+    p->built = true;
+    return JEFI_OK;
+}
+
+// Every entry's time must be in its window; graphs recorded for the
+// handles' current configuration.
+int plan_check(jefi_batch_plan_s* p, const double* t) {
+    for (size_t i = 0; i < p->hs.size(); ++i) {
+        sync_view(p->hs[i]);
+        const int rc = check_time(p->hs[i], t[i]);
+        if (rc != JEFI_OK) return rc;
+    }
+    if (plan_stale(p)) {
+        int rc = plan_wait(p);
+        if (rc == JEFI_OK) rc = plan_build(p);
+        if (rc != JEFI_OK) return rc;
+    }
+    return JEFI_OK;
+}
+
+// Slot tables of every entry at its time into pinned copy j (after the
+// launch that last read that copy has finished).
+int plan_prepare(jefi_batch_plan_s* p, int j, const double* t) {
+    if (p->pending[j]) {
+        JEFI_CUDA(cudaEventSynchronize(p->done[j]));
+        p->pending[j] = false;
+    }
+    if (!p->pinned[j]) return JEFI_OK;
+    unsigned char* host = p->pinned[j];
+    for (size_t i = 0; i < p->hs.size(); ++i) {
+        const auto& tb = p->tabs[i];
+        if (!tb.tab32) continue;
+        jefi_problem* h = p->hs[i];
+        const int o = p->occ[i];
+        const size_t K = (size_t)h->K, KT = K + 2 * kTabGuard;
+        build_tables(h, o, t[i]);
+        std::memcpy(host + tb.tab32, h->h_tab.data() + o * K, sizeof(float4) * K);
+        std::memcpy(host + tb.theta, h->h_theta.data() + o * (K + 1), sizeof(double) * (K + 1));
+        std::memcpy(host + tb.times, &h->h_times[o], sizeof(TimeParams));
+        if (tb.tab2) std::memcpy(host + tb.tab2, h->h_tab2.data() + o * KT, sizeof(float2) * KT);
+        if (tb.tabg) {
+            std::memcpy(host + tb.tabg, h->h_tabg.data() + o * KT, sizeof(float2) * KT);
+            std::memcpy(host + tb.tabh, h->h_tabh.data() + o * KT, sizeof(float) * KT);
+        }
+    }
+    return JEFI_OK;
+}
+
+int plan_submit(jefi_batch_plan_s* p, int j, cudaStream_t s) {
+    if (p->exec[j]) {
+        JEFI_CUDA(cudaGraphLaunch(p->exec[j], s));
+        JEFI_CUDA(cudaEventRecord(p->done[j], s));
+        p->pending[j] = true;
+    }
+    for (jefi_problem* h : p->hs) {
+        const int rc = mark_use(h, s);
+        if (rc != JEFI_OK) return rc;
+    }
+    return JEFI_OK;
+}
+
+// Split the source bricks of h into about `want` parts (at most the count
+// its partial sums were sized for at creation).
+void set_splits(jefi_problem* h, int64_t want) {
+    want = std::max<int64_t>(1, std::min<int64_t>(want, h->n_split_max));
+    const int64_t nb = std::max<int32_t>(h->n_bricks, 1);
+    h->bricks_per_split = (int32_t)std::max<int64_t>(1, (nb + want - 1) / want);
+    h->n_split = (int32_t)std::max<int64_t>(1, (nb + h->bricks_per_split - 1) / h->bricks_per_split);
+}
+
+// Device time of one launch of the plan at t, after one untimed launch, in ms.
+int plan_time(jefi_batch_plan_s* p, const double* t, cudaStream_t s, double* ms) {
+    int rc = plan_wait(p);
+    if (rc == JEFI_OK && plan_stale(p)) rc = plan_build(p);
+    if (rc != JEFI_OK) return rc;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess) rc = JEFI_ECUDA;
+    if (rc == JEFI_OK) rc = plan_prepare(p, 0, t);
+    if (rc == JEFI_OK) rc = plan_submit(p, 0, s);
+    if (rc == JEFI_OK) rc = plan_prepare(p, 1, t);
+    if (rc == JEFI_OK && cudaEventRecord(ev[0], s) != cudaSuccess) rc = JEFI_ECUDA;
+    if (rc == JEFI_OK) rc = plan_submit(p, 1, s);
+    float f = 0.f;
+    if (rc == JEFI_OK && (cudaEventRecord(ev[1], s) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                          cudaEventElapsedTime(&f, ev[0], ev[1]) != cudaSuccess))
+        rc = JEFI_ECUDA;
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (rc == JEFI_ECUDA) cudaGetLastError();
+    p->next = 0;
+    *ms = f;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int jefi_batch_plan_create(const jefi_handle* hs, double* const* E, double* const* B, int32_t n,
+                           jefi_batch_plan* out) {
+    if (!out || n < 0 || (n > 0 && (!hs || !E || !B))) return JEFI_EINVAL;
+    *out = nullptr;
+    std::map<jefi_problem*, int> count;
+    std::vector<int> occ(n);
+    for (int i = 0; i < n; ++i) {
+        jefi_problem* h = hs[i];
+        if (!h) return JEFI_EINVAL;
+        if (h->interp) return JEFI_EUNSUPPORTED;   // batched kernels run the floor rule only
+        if (h->n_obs > 0 && (!E[i] || !B[i])) return JEFI_EINVAL;
+        occ[i] = count[h]++;
+        if (occ[i] >= h->time_chunk) return JEFI_EUNSUPPORTED;   // scratch slots per handle
+    }
+    jefi_batch_plan_s* p = new (std::nothrow) jefi_batch_plan_s();
+    if (!p) return JEFI_ENOMEM;
+    p->hs.assign(hs, hs + n);
+    p->E.assign(E, E + n);
+    p->B.assign(B, B + n);
+    p->occ = occ;
+    int dev = 0;
+    int rc = JEFI_OK;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->done[1], cudaEventDisableTiming) != cudaSuccess)
+        rc = JEFI_ECUDA;
+    for (int i = 0; i < n && rc == JEFI_OK; ++i) sync_view(p->hs[i]);
+    if (rc == JEFI_OK) rc = plan_build(p);
+    if (rc != JEFI_OK) {
+        cudaGetLastError();
+        plan_release_graphs(p);
+        for (cudaEvent_t e : p->done)
+            if (e) cudaEventDestroy(e);
+        delete p;
+        return rc;
+    }
+    for (auto& kv : count) kv.first->n_plans++;
+    *out = p;
+    return JEFI_OK;
+}
+
+int jefi_batch_plan_launch(jefi_batch_plan p, const double* t, void* stream) {
+    if (!p || (!t && !p->hs.empty())) return JEFI_EINVAL;
+    if (p->hs.empty()) return JEFI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = plan_check(p, t);
+    const int j = p->next;
+    if (rc == JEFI_OK) rc = plan_prepare(p, j, t);
+    if (rc == JEFI_OK) rc = plan_submit(p, j, s);
+    if (rc == JEFI_OK) p->next ^= 1;
+    return rc;
+}
+
+int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_tune_report* report) {
+    if (!p || (!t && !p->hs.empty())) return JEFI_EINVAL;
+    jefi_tune_report rep{};
+    rep.split_divisor = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = plan_check(p, t);
+    if (rc != JEFI_OK) return rc;
+    // distinct handles with pairs, in order of first appearance, and one time each
+    std::vector<jefi_problem*> uniq;
+    std::vector<double> t_of;
+    for (size_t i = 0; i < p->hs.size(); ++i) {
+        jefi_problem* h = p->hs[i];
+        if (!h->any_pairs || h->n_obs == 0 || std::find(uniq.begin(), uniq.end(), h) != uniq.end()) continue;
+        uniq.push_back(h);
+        t_of.push_back(t[i]);
+    }
+    const size_t u = uniq.size();
+    std::vector<int32_t> band_in(u), split_in(u), bps_in(u), band_meas(u);
+    for (size_t k = 0; k < u; ++k) {
+        band_in[k] = uniq[k]->band;
+        split_in[k] = uniq[k]->n_split;
+        bps_in[k] = uniq[k]->bricks_per_split;
+    }
+    auto restore = [&]() {
+        for (size_t k = 0; k < u; ++k) {
+            uniq[k]->band = band_in[k];
+            uniq[k]->n_split = split_in[k];
+            uniq[k]->bricks_per_split = bps_in[k];
+        }
+    };
+    double ms = 0;
+    rc = plan_time(p, t, s, &ms);
+    if (rc != JEFI_OK) return rc;
+    rep.candidates = 1;
+    rep.ms_initial = ms;
+    double best_ms = ms;
+    int best_pol = 0, best_div = 0;   // best_div 0: splits as they were
+
+    // Kernel choice measured per FP32 handle that has both kernels.
+    bool differs = false;
+    for (size_t k = 0; k < u && rc == JEFI_OK; ++k) {
+        jefi_problem* h = uniq[k];
+        band_meas[k] = h->band;
+        if (h->fp64 || h->band0 == 0) continue;
+        int32_t b = h->band;
+        rc = jefi_select_kernel(h, JEFI_KERNEL_MEASURE, t_of[k], &b, stream);
+        band_meas[k] = b;
+        h->band = band_in[k];
+        differs = differs || b != band_in[k];
+    }
+    const int divs[4] = {1, 2, 4, 8};
+    for (int pol = 0; pol < 2 && rc == JEFI_OK; ++pol) {
+        if (pol == 1 && !differs) break;
+        std::vector<std::vector<int32_t>> seen;
+        if (pol == 0) seen.push_back(split_in);
+        for (int dv : divs) {
+            for (size_t k = 0; k < u; ++k) {
+                uniq[k]->band = pol ? band_meas[k] : band_in[k];
+                set_splits(uniq[k], (uniq[k]->n_split_max + dv - 1) / dv);
+            }
+            std::vector<int32_t> cur(u);
+            for (size_t k = 0; k < u; ++k) cur[k] = uniq[k]->n_split;
+            if (std::find(seen.begin(), seen.end(), cur) != seen.end()) continue;
+            seen.push_back(cur);
+            rc = plan_time(p, t, s, &ms);
+            if (rc != JEFI_OK) break;
+            rep.candidates++;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_pol = pol;
+                best_div = dv;
+            }
+        }
+    }
+    restore();
+    if (rc != JEFI_OK) return rc;
+    for (size_t k = 0; k < u; ++k) {
+        if (best_pol == 1) uniq[k]->band = band_meas[k];
+        if (best_div > 0) set_splits(uniq[k], (uniq[k]->n_split_max + best_div - 1) / best_div);
+    }
+    rc = plan_wait(p);
+    if (rc == JEFI_OK && plan_stale(p)) rc = plan_build(p);
+    if (rc != JEFI_OK) return rc;
+    rep.split_divisor = best_div > 0 ? best_div : 0;
+    rep.measured_kernels = best_pol;
+    rep.ms_tuned = best_ms;
+    for (jefi_problem* h : p->hs)
+        if (!h->fp64 && h->band > 0 && h->any_pairs && h->n_obs > 0) rep.staged_problems++;
+    if (report) *report = rep;
+    return JEFI_OK;
+}
+
+int jefi_batch_plan_destroy(jefi_batch_plan p) {
+    if (!p) return JEFI_EINVAL;
+    plan_wait(p);
+    plan_release_graphs(p);
+    for (cudaEvent_t e : p->done)
+        if (e) cudaEventDestroy(e);
+    std::map<jefi_problem*, int> seen;
+    for (jefi_problem* h : p->hs)
+        if (seen[h]++ == 0) h->n_plans--;
+    delete p;
+    return JEFI_OK;
+}
+
 int jefi_destroy(jefi_handle h) {
     if (!h) return JEFI_EINVAL;
     if (h->n_views > 0) return JEFI_EINVAL;              // destroy the views first
+    if (h->n_plans > 0) return JEFI_EINVAL;              // destroy the batch plans first
     // the handle's own work only: other streams and handles keep running
     if (h->last_use) cudaEventSynchronize(h->last_use);
     if (h->base) h->base->n_views--;

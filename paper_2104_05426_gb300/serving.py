@@ -32,7 +32,8 @@ from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
-from . import (JEFI_FLAG_SHARED_RING, JefiError, default_params, grid, jefi_create,
+from . import (JEFI_FLAG_SHARED_RING, JefiError, default_params, grid, jefi_batch_plan_create,
+               jefi_batch_plan_destroy, jefi_batch_plan_launch, jefi_batch_plan_tune, jefi_create,
                jefi_create_view, jefi_destroy, jefi_eval_batch, jefi_get_info, jefi_push_sources,
                jefi_valid_window)
 
@@ -442,7 +443,8 @@ def measure_batch(n_problems: int = 256, sides=(8, 48), H_range=(32, 128), obs_s
     twice the source box) at one time inside its window; every problem's
     result comes out of one jefi_eval_batch call (one persistent launch per
     kernel variant, then one reduction).  Returns the time of the call and
-    the pair rate."""
+    the pair rate; then the same batch as a batch plan (one CUDA-graph
+    launch per call), before and after the plan's autotuner."""
     import torch
 
     probs = make_problems(n_problems, seed, sides=sides, H_range=H_range)
@@ -473,8 +475,34 @@ def measure_batch(n_problems: int = 256, sides=(8, 48), H_range=(32, 128), obs_s
     bands = [jefi_get_info(v)["staged_band"] for v in views]
     out = {"problems": n_problems, "source_sides": list(sides), "history_slices": list(H_range),
            "obs_sides": list(obs_sides), "pairs": pairs, "ms_per_batch": ms, "pairs_per_s": pairs / (ms / 1e3),
-           "staged_problems": sum(1 for b in bands if b > 0),
-           "device_status": max(jefi_get_info(v)["device_status"] for v in views)}
+           "staged_problems": sum(1 for b in bands if b > 0)}
+
+    def time_plan(plan):
+        jefi_batch_plan_launch(plan, ts)              # warm-up
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            jefi_batch_plan_launch(plan, ts)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    plan = None
+    try:
+        plan = jefi_batch_plan_create(views, Es, Bs)
+        ms_graph = time_plan(plan)
+        out["graph"] = {"ms_per_batch": ms_graph, "pairs_per_s": pairs / (ms_graph / 1e3)}
+        rep = jefi_batch_plan_tune(plan, ts)
+        ms_tuned = time_plan(plan)
+        bands = [jefi_get_info(v)["staged_band"] for v in views]
+        out["tuned"] = {"ms_per_batch": ms_tuned, "pairs_per_s": pairs / (ms_tuned / 1e3),
+                        "staged_problems": sum(1 for b in bands if b > 0), "tuner": rep}
+    except JefiError as e:
+        out["plan_error"] = str(e)
+    finally:
+        if plan is not None:
+            jefi_batch_plan_destroy(plan)
+    out["device_status"] = max(jefi_get_info(v)["device_status"] for v in views)
     for v in views:
         jefi_destroy(v)
     for p in probs:
