@@ -369,7 +369,10 @@ int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_ba
  * tables, one persistent launch per kernel variant and the reduction.  It
  * captures that sequence into two CUDA graphs (the metadata of call k is
  * written on the host while call k-1 may still run on the device) and
- * allocates the plan's own device and pinned host buffers.  A handle may
+ * allocates the plan's own device and pinned host buffers.  In the graphs
+ * the launches of different kernel variants are parallel branches between
+ * the copy and the reduction (their work items are independent), so one
+ * variant's first items can run beside another's last ones.  A handle may
  * appear up to 8 times (a view up to 2 times), as in jefi_eval_batch; FP64,
  * FP32 and compensated FP32 handles mix freely; handles with
  * JEFI_FLAG_INTERP give JEFI_EUNSUPPORTED.
@@ -389,6 +392,8 @@ int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_ba
  * jefi_batch_plan_tune is the autotuner of the batched launch.  It times the
  * plan, on the device, at times t[n] (which it evaluates, overwriting the
  * outputs) in each of these configurations and keeps the fastest:
+ *   - the kernel variants' launches as parallel graph branches or one after
+ *     another (decided first, then kept for the candidates below);
  *   - kernel choice per problem: the handles' current choice, and the one
  *     jefi_select_kernel(JEFI_KERNEL_MEASURE) makes for each FP32 handle
  *     that has both kernels (staged band vs direct gather);
@@ -415,6 +420,8 @@ typedef struct {
     int32_t measured_kernels; /* kept: 1 = per-problem measured kernel choice,
                                  0 = the handles' choice at the call               */
     int32_t staged_problems;  /* batch entries on the staged kernel after tuning      */
+    int32_t concurrent_groups;/* kept: 1 = kernel variants as parallel graph
+                                 branches, 0 = one after another                   */
     double ms_initial;        /* device time of one launch as the handles were       */
     double ms_tuned;          /* device time of one launch as kept                   */
 } jefi_tune_report;

@@ -102,6 +102,7 @@ class jefi_info(ctypes.Structure):
 class jefi_tune_report(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int32), ("split_divisor", ctypes.c_int32),
                 ("measured_kernels", ctypes.c_int32), ("staged_problems", ctypes.c_int32),
+                ("concurrent_groups", ctypes.c_int32),
                 ("ms_initial", ctypes.c_double), ("ms_tuned", ctypes.c_double)]
 
     def as_dict(self):

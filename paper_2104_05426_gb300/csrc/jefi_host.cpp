@@ -1735,6 +1735,7 @@ struct jefi_batch_plan_s {
     int next = 0;
     int n_sm = 0;
     bool built = false;
+    bool concurrent = true;                   // kernel variants as parallel graph branches
 };
 
 namespace {
@@ -1926,9 +1927,19 @@ int plan_build(jefi_batch_plan_s* p) {
     std::memcpy(p->pinned[1], p->pinned[0], bytes);
 
     // Record: [zero fields] -> copy -> one persistent launch per group -> reduction.
+    // Concurrent: the groups' launches are parallel branches between the copy
+    // and the reduction (their items are independent), so the device can
+    // start one variant's items while another's last items finish.
+    const bool fork = p->concurrent && groups.size() > 1;
     cudaStream_t cs = nullptr;
-    JEFI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> side(fork ? groups.size() : 0, nullptr);
+    std::vector<cudaEvent_t> evs(fork ? groups.size() + 1 : 0, nullptr);
     int rc = JEFI_OK;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = JEFI_ECUDA;
+    for (auto& x : side)
+        if (rc == JEFI_OK && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) rc = JEFI_ECUDA;
+    for (auto& x : evs)
+        if (rc == JEFI_OK && cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) rc = JEFI_ECUDA;
     for (int j = 0; j < 2 && rc == JEFI_OK; ++j) {
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
             rc = JEFI_ECUDA;
@@ -1942,7 +1953,11 @@ int plan_build(jefi_batch_plan_s* p) {
         }
         if (e == cudaSuccess && !groups.empty())
             e = cudaMemcpyAsync(d, p->pinned[j], bytes, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess && fork) e = cudaEventRecord(evs[groups.size()], cs);
         for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+            const cudaStream_t gs = fork ? side[g] : cs;
+            if (fork) e = cudaStreamWaitEvent(gs, evs[groups.size()], 0);
+            if (e != cudaSuccess) break;
             const int per_sm = groups[g].kind == 0 ? 1 : (smem[g] > 110 * 1024 ? 1 : 2);
             const int grid = std::max(1, std::min(n_items[g], per_sm * p->n_sm));
             if (groups[g].kind == 2) {
@@ -1954,7 +1969,7 @@ int plan_build(jefi_batch_plan_s* p) {
                 a.n_items = n_items[g];
                 a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
                 for (size_t m = 0; m < groups[g].members.size(); ++m) a.maps[m] = p->hs[groups[g].members[m]]->tmap;
-                e = launch_sum_f32_staged_batch(a, groups[g].band, groups[g].exact, smem[g], grid, cs);
+                e = launch_sum_f32_staged_batch(a, groups[g].band, groups[g].exact, smem[g], grid, gs);
             } else {
                 BatchArgs a;
                 a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
@@ -1962,9 +1977,11 @@ int plan_build(jefi_batch_plan_s* p) {
                 a.n = (int32_t)groups[g].members.size();
                 a.n_items = n_items[g];
                 a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
-                e = groups[g].kind == 0 ? launch_sum_f64_batch(a, smem[g], grid, cs)
-                                        : launch_sum_f32_batch(a, groups[g].comp != 0, smem[g], grid, cs);
+                e = groups[g].kind == 0 ? launch_sum_f64_batch(a, smem[g], grid, gs)
+                                        : launch_sum_f32_batch(a, groups[g].comp != 0, smem[g], grid, gs);
             }
+            if (e == cudaSuccess && fork) e = cudaEventRecord(evs[g], gs);
+            if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(cs, evs[g], 0);
         }
         if (e == cudaSuccess && !groups.empty())
             e = launch_reduce_batch(reinterpret_cast<const ReduceItem*>(d + off_ritems),
@@ -1980,7 +1997,11 @@ int plan_build(jefi_batch_plan_s* p) {
             rc = JEFI_ECUDA;
         }
     }
-    cudaStreamDestroy(cs);
+    if (cs) cudaStreamDestroy(cs);
+    for (auto x : side)
+        if (x) cudaStreamDestroy(x);
+    for (auto x : evs)
+        if (x) cudaEventDestroy(x);
     if (rc != JEFI_OK) {
         plan_release_graphs(p);
         return rc;
@@ -2175,6 +2196,24 @@ int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_
     double best_ms = ms;
     int best_pol = 0, best_div = 0;   // best_div 0: splits as they were
 
+    // Kernel variants in parallel graph branches or one after another: kept
+    // for the remaining candidates.
+    p->concurrent = !p->concurrent;
+    p->built = false;
+    rc = plan_time(p, t, s, &ms);
+    if (rc != JEFI_OK) {
+        p->concurrent = !p->concurrent;
+        p->built = false;
+        return rc;
+    }
+    rep.candidates++;
+    if (ms < best_ms) {
+        best_ms = ms;
+    } else {
+        p->concurrent = !p->concurrent;
+        p->built = false;
+    }
+
     // Kernel choice measured per FP32 handle that has both kernels.
     bool differs = false;
     for (size_t k = 0; k < u && rc == JEFI_OK; ++k) {
@@ -2222,6 +2261,7 @@ int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_
     if (rc != JEFI_OK) return rc;
     rep.split_divisor = best_div > 0 ? best_div : 0;
     rep.measured_kernels = best_pol;
+    rep.concurrent_groups = p->concurrent ? 1 : 0;
     rep.ms_tuned = best_ms;
     for (jefi_problem* h : p->hs)
         if (!h->fp64 && h->band > 0 && h->any_pairs && h->n_obs > 0) rep.staged_problems++;
