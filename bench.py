@@ -331,6 +331,7 @@ def run_gpu(args):
                                   "note": "JEFI_FLAG_INTERP: sources interpolated at the retarded "
                                           "time, central differences; same 8-time launch"}
         jefi.jefi_destroy(hi2)
+        result["dipole"] = dipole_leg(dev)
         if not args.no_serving:
             result["serving"] = serving_leg()
             from paper_2104_05426_gb300.serving import measure_batch
@@ -348,6 +349,63 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def dipole_leg(dev, reps=5):
+    """The oscillating-dipole workload (32^3 sources over [-0.5,0.5]^3, 4096
+    points on shells R = 5, 10, 20, 40, 256-slice history, backward
+    differences): 4 evaluation times per launch, compensated FP32 and FP64.
+    Reports pairs/s from the library's kernel events, the FP32 pipe fraction
+    of the compensated path (same canonical count as the benchmark) and its
+    rel-L2 against the FP64 GPU path per shell (the FP64 path matches the
+    oracle to 1e-12 in the test suite)."""
+    import torch
+
+    import paper_2104_05426_gb300 as jefi
+    from workloads import c3_dipole
+
+    p = c3_dipole()
+    rho, J, _, _ = p.source.history(p.src, p.n_push, p.dt, p.t0)
+    slices = [(torch.from_numpy(np.ascontiguousarray(rho[n])).to(dev),
+               torch.from_numpy(np.ascontiguousarray(J[n])).to(dev)) for n in range(p.n_push)]
+    n_obs, n_src, n_t = len(p.obs_points), p.src.size, len(p.times)
+    pairs = n_obs * n_src * n_t
+    out, fields = {}, {}
+    for prec in ("fp32c", "fp64"):
+        prm = jefi.default_params(c=p.c, k_e=p.k_e, k_b=p.k_b, dt=p.dt, t0=p.t0, history_slots=p.H,
+                                  precision=prec, flags=jefi.JEFI_FLAG_STATS)
+        h = jefi.jefi_create(jefi.grid_from(p.src), obs_points=p.obs_points, params=prm,
+                             torch_allocator=True)
+        for r_n, j_n in slices:
+            jefi.jefi_push_sources(h, r_n, j_n)
+        E = torch.empty((n_t, n_obs, 3), dtype=torch.float64, device=dev)
+        B = torch.empty_like(E)
+        jefi.jefi_eval_fields_multi(h, p.times, E, B)          # warm-up
+        jefi.jefi_reset_stats(h)
+        for _ in range(reps if prec == "fp32c" else 1):
+            jefi.jefi_eval_fields_multi(h, p.times, E, B)
+        info = jefi.jefi_get_info(h)
+        ms = info["sum_ms_total"] / max(info["sum_launches"], 1)
+        out[prec] = {"value": pairs / (ms / 1e3), "unit": UNIT, "kernel_ms": ms,
+                     "kernel": (f"staged band {info['staged_band']}" if info["staged_band"] and prec != "fp64"
+                                else ("sum_f64_kernel" if prec == "fp64" else "sum_f32_kernel (direct gather)")),
+                     "device_status": info["device_status"]}
+        fields[prec] = (E, B)
+        jefi.jefi_destroy(h)
+    peak = N_SM * FP32_LANES_PER_SM * 2070e6
+    out["fp32c"]["fp32_pipe_frac"] = out["fp32c"]["value"] * SUM_FP32_INSTR_PER_PAIR / peak
+    out["fp32c_speedup_kernel"] = out["fp32c"]["value"] / out["fp64"]["value"]
+    radii = np.linalg.norm(p.obs_points, axis=1)
+    errs = {}
+    for R in (5.0, 10.0, 20.0, 40.0):
+        m = torch.from_numpy(np.abs(radii - R) < 1e-6 * R).to(dev)
+        errs[str(R)] = max(float(torch.linalg.norm(fields["fp32c"][k][:, m] - fields["fp64"][k][:, m]) /
+                                 torch.linalg.norm(fields["fp64"][k][:, m])) for k in (0, 1))
+    out["rel_l2_fp32c_vs_fp64_by_shell"] = errs
+    out["workload"] = ("oscillating dipole: 32^3 sources over [-0.5,0.5]^3, 4096 points on shells "
+                       "R = 5, 10, 20, 40, H = 256, 4 times per launch, backward differences")
+    out["pairs_per_launch"] = pairs
+    return out
 
 
 def serving_leg(n_problems=16, n_requests=600, seed=11, tick_s=0.02):
