@@ -403,12 +403,11 @@ def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0)
     each load factor f, a fresh stream of requests arriving at f times that
     rate, with one slice pushed to every problem per tick.  Returns the
     percentiles per load and the resident memory.  The device-memory budget
-    (resident histories, cached views and outputs) defaults to 80 % of the
-    device's memory."""
+    (resident histories, cached views and outputs) defaults to 64 GB."""
     import torch
 
     if memory_budget is None:
-        memory_budget = 0.8 * torch.cuda.get_device_properties(torch.cuda.current_device()).total_memory
+        memory_budget = 64e9
     probs = make_problems(n_problems, seed, sides=sides, H_range=H_range)
     eng = ServingEngine(probs, obs_half_width=2.0, n_streams=n_streams, max_batch=max_batch, tick_s=None,
                         memory_budget=memory_budget)
@@ -567,7 +566,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=11)
     ap.add_argument("--tick-ms", type=float, default=20.0, help="one slice pushed per problem per tick")
     ap.add_argument("--budget-gb", type=float, default=None,
-                    help="device memory for histories, views and outputs (default: 80 %% of the device)")
+                    help="device memory for histories, views and outputs (default: 64 GB)")
     ap.add_argument("--single", default=None, metavar="SRC,OBS,H",
                     help="time one evaluation of one problem (source side, observation side, history)")
     ap.add_argument("--reps", type=int, default=3, help="evaluations timed with --single")
