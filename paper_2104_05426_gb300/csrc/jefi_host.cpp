@@ -684,6 +684,157 @@ int arena_reserve(BatchArena& a, size_t bytes) {
     return JEFI_OK;
 }
 
+// ---------------------------------------------------------------- batch layout
+// Shared by jefi_eval_batch and batch plans: the problems of a batch grouped
+// by kernel variant (one persistent launch per group), their reduction
+// items, and the byte layout of the launch metadata.
+struct BatchGroup {
+    int kind;           // 0 FP64, 1 FP32 direct, 2 FP32 staged
+    int comp, band;
+    bool exact;
+    std::vector<int> members;
+};
+
+struct BatchLayout {
+    std::vector<BatchGroup> groups;
+    std::vector<ReduceItem> ritems;
+    std::vector<int64_t> rstart;
+    std::vector<int> zero_entries;      // entries with points but no pairs: zero fields
+    // per group [params | item_start | counter], then [reduce items | starts]
+    std::vector<size_t> off_params, off_start, off_counter;
+    size_t off_ritems = 0, off_rstart = 0, bytes = 0;
+    // filled by batch_fill
+    std::vector<int> n_items;
+    std::vector<size_t> smem;
+};
+
+// Group entries i (handle hs[i], scratch slot occ[i], outputs E[i], B[i]) and
+// lay out the metadata from byte 0, 256-byte aligned.
+void batch_layout(jefi_problem* const* hs, const int* occ, double* const* E, double* const* B, int n,
+                  BatchLayout* L) {
+    L->groups.clear();
+    L->ritems.clear();
+    L->rstart.assign(1, 0);
+    L->zero_entries.clear();
+    for (int i = 0; i < n; ++i) {
+        jefi_problem* h = hs[i];
+        if (h->n_obs == 0) continue;
+        if (!h->any_pairs) {
+            L->zero_entries.push_back(i);
+            continue;
+        }
+        BatchGroup key{h->fp64 ? 0 : (h->band > 0 ? 2 : 1), h->prm.precision == JEFI_FP32_COMP ? 1 : 0, h->band,
+                       h->exact, {}};
+        if (key.kind != 1) key.comp = 0;
+        if (key.kind != 2) { key.band = 0; key.exact = false; }
+        BatchGroup* g = nullptr;
+        for (auto& x : L->groups)
+            if (x.kind == key.kind && x.comp == key.comp && x.band == key.band && x.exact == key.exact &&
+                (x.kind != 2 || (int)x.members.size() < kMaxBatchMaps))
+                g = &x;
+        if (!g) {
+            L->groups.push_back(key);
+            g = &L->groups.back();
+        }
+        g->members.push_back(i);
+        ReduceItem r{};
+        r.inv_perm = h->d_inv_perm;
+        r.partials = h->partials + (size_t)occ[i] * h->n_split * 6 * h->n_slots;
+        r.n_obs = (int32_t)h->n_obs;
+        r.n_slots = h->n_slots;
+        r.n_split = h->n_split;
+        r.e_scale = h->prm.k_e * (h->src.d[0] * h->src.d[1] * h->src.d[2]) / h->prm.c;
+        r.b_scale = h->prm.k_b * (h->src.d[0] * h->src.d[1] * h->src.d[2]);
+        r.E = E[i];
+        r.B = B[i];
+        L->ritems.push_back(r);
+        L->rstart.push_back(L->rstart.back() + h->n_obs);
+    }
+    const size_t ng = L->groups.size();
+    L->off_params.resize(ng);
+    L->off_start.resize(ng);
+    L->off_counter.resize(ng);
+    size_t bytes = 0;
+    for (size_t g = 0; g < ng; ++g) {
+        L->off_params[g] = bytes;
+        bytes = align256(bytes + sizeof(SumParams) * L->groups[g].members.size());
+        L->off_start[g] = bytes;
+        bytes = align256(bytes + sizeof(int32_t) * (L->groups[g].members.size() + 1));
+        L->off_counter[g] = bytes;
+        bytes = align256(bytes + sizeof(unsigned int));
+    }
+    L->off_ritems = bytes;
+    bytes = align256(bytes + sizeof(ReduceItem) * L->ritems.size());
+    L->off_rstart = bytes;
+    bytes = align256(bytes + sizeof(int64_t) * L->rstart.size());
+    L->bytes = bytes;
+}
+
+// Write the metadata into the host image `host` (zeroed by the caller, so
+// the queue counters start at zero): kernel parameters of every member
+// (params(i) gives entry i's), work-item starts, reduction items; record
+// per group its item count and shared memory.  JEFI_EUNSUPPORTED if a
+// group needs more shared memory than a block may have.
+template <class Params>
+int batch_fill(BatchLayout* L, unsigned char* host, Params&& params) {
+    const size_t ng = L->groups.size();
+    L->n_items.assign(ng, 0);
+    L->smem.assign(ng, 0);
+    for (size_t g = 0; g < ng; ++g) {
+        const BatchGroup& G = L->groups[g];
+        SumParams* prm = reinterpret_cast<SumParams*>(host + L->off_params[g]);
+        int32_t* start = reinterpret_cast<int32_t*>(host + L->off_start[g]);
+        int32_t acc = 0;
+        for (size_t m = 0; m < G.members.size(); ++m) {
+            prm[m] = params(G.members[m]);
+            start[m] = acc;
+            acc += prm[m].n_tiles * prm[m].n_split;
+            L->smem[g] = std::max(L->smem[g], G.kind == 2 ? staged_smem_bytes(prm[m], G.band, true)
+                                                            : sum_smem_bytes(prm[m]));
+        }
+        start[G.members.size()] = acc;
+        L->n_items[g] = acc;
+        if (L->smem[g] > 220 * 1024) return JEFI_EUNSUPPORTED;
+    }
+    if (!L->ritems.empty())
+        std::memcpy(host + L->off_ritems, L->ritems.data(), sizeof(ReduceItem) * L->ritems.size());
+    std::memcpy(host + L->off_rstart, L->rstart.data(), sizeof(int64_t) * L->rstart.size());
+    return JEFI_OK;
+}
+
+// Persistent launch of group g on stream s, reading the metadata at device address d.
+cudaError_t batch_launch_group(const BatchLayout& L, size_t g, jefi_problem* const* hs, unsigned char* d,
+                               int n_sm, cudaStream_t s) {
+    const BatchGroup& G = L.groups[g];
+    const int per_sm = G.kind == 0 ? 1 : (L.smem[g] > 110 * 1024 ? 1 : 2);
+    const int grid = std::max(1, std::min(L.n_items[g], per_sm * n_sm));
+    if (G.kind == 2) {
+        StagedBatchArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.params = reinterpret_cast<const SumParams*>(d + L.off_params[g]);
+        a.item_start = reinterpret_cast<const int32_t*>(d + L.off_start[g]);
+        a.n = (int32_t)G.members.size();
+        a.n_items = L.n_items[g];
+        a.counter = reinterpret_cast<unsigned int*>(d + L.off_counter[g]);
+        for (size_t m = 0; m < G.members.size(); ++m) a.maps[m] = hs[G.members[m]]->tmap;
+        return launch_sum_f32_staged_batch(a, G.band, G.exact, L.smem[g], grid, s);
+    }
+    BatchArgs a;
+    a.params = reinterpret_cast<const SumParams*>(d + L.off_params[g]);
+    a.item_start = reinterpret_cast<const int32_t*>(d + L.off_start[g]);
+    a.n = (int32_t)G.members.size();
+    a.n_items = L.n_items[g];
+    a.counter = reinterpret_cast<unsigned int*>(d + L.off_counter[g]);
+    return G.kind == 0 ? launch_sum_f64_batch(a, L.smem[g], grid, s)
+                       : launch_sum_f32_batch(a, G.comp != 0, L.smem[g], grid, s);
+}
+
+cudaError_t batch_launch_reduce(const BatchLayout& L, unsigned char* d, cudaStream_t s) {
+    return launch_reduce_batch(reinterpret_cast<const ReduceItem*>(d + L.off_ritems),
+                               reinterpret_cast<const int64_t*>(d + L.off_rstart), (int)L.ritems.size(),
+                               L.rstart.back(), s);
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -1228,132 +1379,34 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
             if (rc != JEFI_OK) return rc;
         }
 
-    // Group the problems by kernel variant: one persistent launch per group.
-    struct Group {
-        int kind;           // 0 FP64, 1 FP32 direct, 2 FP32 staged
-        int comp, band;
-        bool exact;
-        std::vector<int> members;
-    };
-    std::vector<Group> groups;
-    std::vector<ReduceItem> ritems;
-    std::vector<int64_t> rstart(1, 0);
-    for (int i = 0; i < n; ++i) {
-        jefi_problem* h = hs[i];
-        if (h->n_obs == 0) continue;
-        if (!h->any_pairs) {
-            JEFI_CUDA(cudaMemsetAsync(E[i], 0, sizeof(double) * 3 * h->n_obs, s));
-            JEFI_CUDA(cudaMemsetAsync(B[i], 0, sizeof(double) * 3 * h->n_obs, s));
-            continue;
-        }
-        Group key{h->fp64 ? 0 : (h->band > 0 ? 2 : 1), h->prm.precision == JEFI_FP32_COMP ? 1 : 0, h->band,
-                  h->exact, {}};
-        if (key.kind != 1) key.comp = 0;
-        if (key.kind != 2) { key.band = 0; key.exact = false; }
-        Group* g = nullptr;
-        for (auto& x : groups)
-            if (x.kind == key.kind && x.comp == key.comp && x.band == key.band && x.exact == key.exact &&
-                (x.kind != 2 || (int)x.members.size() < kMaxBatchMaps))
-                g = &x;
-        if (!g) {
-            groups.push_back(key);
-            g = &groups.back();
-        }
-        g->members.push_back(i);
-        ReduceItem r{};
-        r.inv_perm = h->d_inv_perm;
-        r.partials = h->partials + (size_t)occ[i] * h->n_split * 6 * h->n_slots;
-        r.n_obs = (int32_t)h->n_obs;
-        r.n_slots = h->n_slots;
-        r.n_split = h->n_split;
-        r.e_scale = h->prm.k_e * (h->src.d[0] * h->src.d[1] * h->src.d[2]) / h->prm.c;
-        r.b_scale = h->prm.k_b * (h->src.d[0] * h->src.d[1] * h->src.d[2]);
-        r.E = E[i];
-        r.B = B[i];
-        ritems.push_back(r);
-        rstart.push_back(rstart.back() + h->n_obs);
+    // One persistent launch per kernel variant, then one reduction.
+    BatchLayout L;
+    batch_layout(hs, occ.data(), E, B, n, &L);
+    for (int i : L.zero_entries) {
+        JEFI_CUDA(cudaMemsetAsync(E[i], 0, sizeof(double) * 3 * hs[i]->n_obs, s));
+        JEFI_CUDA(cudaMemsetAsync(B[i], 0, sizeof(double) * 3 * hs[i]->n_obs, s));
     }
-    if (groups.empty()) return JEFI_OK;
-
-    // Arena layout: per group [params | item_start | counter], then [reduce items | starts].
-    std::vector<size_t> off_params(groups.size()), off_start(groups.size()), off_counter(groups.size());
-    size_t bytes = 0;
-    for (size_t g = 0; g < groups.size(); ++g) {
-        off_params[g] = bytes;
-        bytes = align256(bytes + sizeof(SumParams) * groups[g].members.size());
-        off_start[g] = bytes;
-        bytes = align256(bytes + sizeof(int32_t) * (groups[g].members.size() + 1));
-        off_counter[g] = bytes;
-        bytes = align256(bytes + sizeof(unsigned int));
-    }
-    const size_t off_ritems = bytes;
-    bytes = align256(bytes + sizeof(ReduceItem) * ritems.size());
-    const size_t off_rstart = bytes;
-    bytes = align256(bytes + sizeof(int64_t) * rstart.size());
+    if (L.groups.empty()) return JEFI_OK;
 
     int dev = 0;
     JEFI_CUDA(cudaGetDevice(&dev));
     BatchArena& arena = arena_for(dev, s);
     std::lock_guard<std::mutex> guard(arena.lock);
     {
-        const int rc = arena_reserve(arena, bytes);
+        const int rc = arena_reserve(arena, L.bytes);
         if (rc != JEFI_OK) return rc;
     }
-    std::vector<unsigned char> host(bytes, 0);
-    std::vector<int> n_items(groups.size());
-    std::vector<size_t> smem(groups.size(), 0);
-    for (size_t g = 0; g < groups.size(); ++g) {
-        SumParams* prm = reinterpret_cast<SumParams*>(host.data() + off_params[g]);
-        int32_t* start = reinterpret_cast<int32_t*>(host.data() + off_start[g]);
-        int32_t acc = 0;
-        for (size_t m = 0; m < groups[g].members.size(); ++m) {
-            const int i = groups[g].members[m];
-            jefi_problem* h = hs[i];
-            prm[m] = make_params(h, 1, occ[i], nullptr);
-            start[m] = acc;
-            acc += h->n_tiles * h->n_split;
-            smem[g] = std::max(smem[g], groups[g].kind == 2 ? staged_smem_bytes(prm[m], groups[g].band, true)
-                                                             : sum_smem_bytes(prm[m]));
-        }
-        start[groups[g].members.size()] = acc;
-        n_items[g] = acc;
-        if (smem[g] > 220 * 1024) return JEFI_EUNSUPPORTED;
+    std::vector<unsigned char> host(L.bytes, 0);
+    {
+        const int rc = batch_fill(&L, host.data(), [&](int i) { return make_params(hs[i], 1, occ[i], nullptr); });
+        if (rc != JEFI_OK) return rc;
     }
-    std::memcpy(host.data() + off_ritems, ritems.data(), sizeof(ReduceItem) * ritems.size());
-    std::memcpy(host.data() + off_rstart, rstart.data(), sizeof(int64_t) * rstart.size());
-
     unsigned char* d = static_cast<unsigned char*>(arena.dev);
     JEFI_CUDA(cudaStreamWaitEvent(s, arena.done, 0));
-    JEFI_CUDA(cudaMemcpyAsync(d, host.data(), bytes, cudaMemcpyHostToDevice, s));
-    for (size_t g = 0; g < groups.size(); ++g) {
-        const int per_sm = groups[g].kind == 0 ? 1 : (smem[g] > 110 * 1024 ? 1 : 2);
-        const int grid = std::max(1, std::min(n_items[g], per_sm * arena.n_sm));
-        cudaError_t e;
-        if (groups[g].kind == 2) {
-            StagedBatchArgs a;
-            std::memset(&a, 0, sizeof(a));
-            a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
-            a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
-            a.n = (int32_t)groups[g].members.size();
-            a.n_items = n_items[g];
-            a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
-            for (size_t m = 0; m < groups[g].members.size(); ++m) a.maps[m] = hs[groups[g].members[m]]->tmap;
-            e = launch_sum_f32_staged_batch(a, groups[g].band, groups[g].exact, smem[g], grid, s);
-        } else {
-            BatchArgs a;
-            a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
-            a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
-            a.n = (int32_t)groups[g].members.size();
-            a.n_items = n_items[g];
-            a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
-            e = groups[g].kind == 0 ? launch_sum_f64_batch(a, smem[g], grid, s)
-                                    : launch_sum_f32_batch(a, groups[g].comp != 0, smem[g], grid, s);
-        }
-        if (e != cudaSuccess) return JEFI_ECUDA;
-    }
-    JEFI_CUDA(launch_reduce_batch(reinterpret_cast<const ReduceItem*>(d + off_ritems),
-                                  reinterpret_cast<const int64_t*>(d + off_rstart), (int)ritems.size(),
-                                  rstart.back(), s));
+    JEFI_CUDA(cudaMemcpyAsync(d, host.data(), L.bytes, cudaMemcpyHostToDevice, s));
+    for (size_t g = 0; g < L.groups.size(); ++g)
+        if (batch_launch_group(L, g, hs, d, arena.n_sm, s) != cudaSuccess) return JEFI_ECUDA;
+    JEFI_CUDA(batch_launch_reduce(L, d, s));
     JEFI_CUDA(cudaEventRecord(arena.done, s));
     for (int i = 0; i < n; ++i) {
         const int rc = mark_use(hs[i], s);
@@ -1777,76 +1830,20 @@ bool plan_stale(const jefi_batch_plan_s* p) {
 int plan_build(jefi_batch_plan_s* p) {
     plan_release_graphs(p);
     const int n = (int)p->hs.size();
-    // Kernel variants as in jefi_eval_batch: one persistent launch per group.
-    struct Group {
-        int kind;           // 0 FP64, 1 FP32 direct, 2 FP32 staged
-        int comp, band;
-        bool exact;
-        std::vector<int> members;
-    };
-    std::vector<Group> groups;
-    std::vector<ReduceItem> ritems;
-    std::vector<int64_t> rstart(1, 0);
-    std::vector<int> zero_entries;
+    BatchLayout L;
+    batch_layout(p->hs.data(), p->occ.data(), p->E.data(), p->B.data(), n, &L);
     p->tabs.assign(n, jefi_batch_plan_s::Tables{});
     p->cap_band.resize(n);
     p->cap_split.resize(n);
     p->cap_bps.resize(n);
     for (int i = 0; i < n; ++i) {
-        jefi_problem* h = p->hs[i];
-        p->cap_band[i] = h->band;
-        p->cap_split[i] = h->n_split;
-        p->cap_bps[i] = h->bricks_per_split;
-        if (h->n_obs == 0) continue;
-        if (!h->any_pairs) {
-            zero_entries.push_back(i);
-            continue;
-        }
-        Group key{h->fp64 ? 0 : (h->band > 0 ? 2 : 1), h->prm.precision == JEFI_FP32_COMP ? 1 : 0, h->band,
-                  h->exact, {}};
-        if (key.kind != 1) key.comp = 0;
-        if (key.kind != 2) { key.band = 0; key.exact = false; }
-        Group* g = nullptr;
-        for (auto& x : groups)
-            if (x.kind == key.kind && x.comp == key.comp && x.band == key.band && x.exact == key.exact &&
-                (x.kind != 2 || (int)x.members.size() < kMaxBatchMaps))
-                g = &x;
-        if (!g) {
-            groups.push_back(key);
-            g = &groups.back();
-        }
-        g->members.push_back(i);
-        ReduceItem r{};
-        r.inv_perm = h->d_inv_perm;
-        r.partials = h->partials + (size_t)p->occ[i] * h->n_split * 6 * h->n_slots;
-        r.n_obs = (int32_t)h->n_obs;
-        r.n_slots = h->n_slots;
-        r.n_split = h->n_split;
-        r.e_scale = h->prm.k_e * (h->src.d[0] * h->src.d[1] * h->src.d[2]) / h->prm.c;
-        r.b_scale = h->prm.k_b * (h->src.d[0] * h->src.d[1] * h->src.d[2]);
-        r.E = p->E[i];
-        r.B = p->B[i];
-        ritems.push_back(r);
-        rstart.push_back(rstart.back() + h->n_obs);
+        p->cap_band[i] = p->hs[i]->band;
+        p->cap_split[i] = p->hs[i]->n_split;
+        p->cap_bps[i] = p->hs[i]->bricks_per_split;
     }
-
-    // Layout: per group [params | item_start | counter], then [reduce items |
-    // starts], then every entry's tables; all 256-byte aligned.
-    std::vector<size_t> off_params(groups.size()), off_start(groups.size()), off_counter(groups.size());
-    size_t bytes = 0;
-    for (size_t g = 0; g < groups.size(); ++g) {
-        off_params[g] = bytes;
-        bytes = align256(bytes + sizeof(SumParams) * groups[g].members.size());
-        off_start[g] = bytes;
-        bytes = align256(bytes + sizeof(int32_t) * (groups[g].members.size() + 1));
-        off_counter[g] = bytes;
-        bytes = align256(bytes + sizeof(unsigned int));
-    }
-    const size_t off_ritems = bytes;
-    bytes = align256(bytes + sizeof(ReduceItem) * ritems.size());
-    const size_t off_rstart = bytes;
-    bytes = align256(bytes + sizeof(int64_t) * rstart.size());
-    for (const auto& grp : groups)
+    // Every entry's slot tables follow the launch metadata.
+    size_t bytes = L.bytes;
+    for (const auto& grp : L.groups)
         for (int i : grp.members) {
             const jefi_problem* h = p->hs[i];
             const size_t KT = (size_t)h->K + 2 * kTabGuard;
@@ -1867,7 +1864,7 @@ int plan_build(jefi_batch_plan_s* p) {
                 bytes = align256(bytes + sizeof(float) * KT);
             }
         }
-    if (groups.empty() && zero_entries.empty()) {   // nothing on the device
+    if (L.groups.empty() && L.zero_entries.empty()) {   // nothing on the device
         p->built = true;
         return JEFI_OK;
     }
@@ -1888,52 +1885,35 @@ int plan_build(jefi_batch_plan_s* p) {
         std::memset(p->pinned[j], 0, bytes);    // queue counters start at zero on every launch
     }
 
-    // Constant part: kernel parameters (tables redirected into the buffer),
-    // item starts, reduction items.
+    // Launch metadata, with every entry's kernel parameters pointing at the
+    // plan's copy of its tables.
     unsigned char* d = static_cast<unsigned char*>(p->dev);
-    unsigned char* host = p->pinned[0];
-    std::vector<int> n_items(groups.size());
-    std::vector<size_t> smem(groups.size(), 0);
-    for (size_t g = 0; g < groups.size(); ++g) {
-        SumParams* prm = reinterpret_cast<SumParams*>(host + off_params[g]);
-        int32_t* start = reinterpret_cast<int32_t*>(host + off_start[g]);
-        int32_t acc = 0;
-        for (size_t m = 0; m < groups[g].members.size(); ++m) {
-            const int i = groups[g].members[m];
-            const jefi_problem* h = p->hs[i];
-            const auto& tb = p->tabs[i];
-            SumParams q = make_params(h, 1, p->occ[i], nullptr);
-            q.tab32 = reinterpret_cast<const float4*>(d + tb.tab32);
-            q.theta = reinterpret_cast<const double*>(d + tb.theta);
-            q.times = reinterpret_cast<const TimeParams*>(d + tb.times);
-            q.tab2 = tb.tab2 ? reinterpret_cast<const float2*>(d + tb.tab2) : nullptr;
-            q.tabg = tb.tabg ? reinterpret_cast<const float2*>(d + tb.tabg) : nullptr;
-            q.tabh = tb.tabh ? reinterpret_cast<const float*>(d + tb.tabh) : nullptr;
-            prm[m] = q;
-            start[m] = acc;
-            acc += h->n_tiles * h->n_split;
-            smem[g] = std::max(smem[g], groups[g].kind == 2 ? staged_smem_bytes(q, groups[g].band, true)
-                                                             : sum_smem_bytes(q));
-        }
-        start[groups[g].members.size()] = acc;
-        n_items[g] = acc;
-        if (smem[g] > 220 * 1024) {
-            plan_release_graphs(p);
-            return JEFI_EUNSUPPORTED;
-        }
+    const int frc = batch_fill(&L, p->pinned[0], [&](int i) {
+        const auto& tb = p->tabs[i];
+        SumParams q = make_params(p->hs[i], 1, p->occ[i], nullptr);
+        q.tab32 = reinterpret_cast<const float4*>(d + tb.tab32);
+        q.theta = reinterpret_cast<const double*>(d + tb.theta);
+        q.times = reinterpret_cast<const TimeParams*>(d + tb.times);
+        q.tab2 = tb.tab2 ? reinterpret_cast<const float2*>(d + tb.tab2) : nullptr;
+        q.tabg = tb.tabg ? reinterpret_cast<const float2*>(d + tb.tabg) : nullptr;
+        q.tabh = tb.tabh ? reinterpret_cast<const float*>(d + tb.tabh) : nullptr;
+        return q;
+    });
+    if (frc != JEFI_OK) {
+        plan_release_graphs(p);
+        return frc;
     }
-    if (!ritems.empty()) std::memcpy(host + off_ritems, ritems.data(), sizeof(ReduceItem) * ritems.size());
-    std::memcpy(host + off_rstart, rstart.data(), sizeof(int64_t) * rstart.size());
     std::memcpy(p->pinned[1], p->pinned[0], bytes);
 
     // Record: [zero fields] -> copy -> one persistent launch per group -> reduction.
     // Concurrent: the groups' launches are parallel branches between the copy
     // and the reduction (their items are independent), so the device can
     // start one variant's items while another's last items finish.
-    const bool fork = p->concurrent && groups.size() > 1;
+    const size_t ng = L.groups.size();
+    const bool fork = p->concurrent && ng > 1;
     cudaStream_t cs = nullptr;
-    std::vector<cudaStream_t> side(fork ? groups.size() : 0, nullptr);
-    std::vector<cudaEvent_t> evs(fork ? groups.size() + 1 : 0, nullptr);
+    std::vector<cudaStream_t> side(fork ? ng : 0, nullptr);
+    std::vector<cudaEvent_t> evs(fork ? ng + 1 : 0, nullptr);
     int rc = JEFI_OK;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = JEFI_ECUDA;
     for (auto& x : side)
@@ -1946,47 +1926,21 @@ int plan_build(jefi_batch_plan_s* p) {
             break;
         }
         cudaError_t e = cudaSuccess;
-        for (int i : zero_entries) {
+        for (int i : L.zero_entries) {
             const size_t fb = sizeof(double) * 3 * p->hs[i]->n_obs;
             if (e == cudaSuccess) e = cudaMemsetAsync(p->E[i], 0, fb, cs);
             if (e == cudaSuccess) e = cudaMemsetAsync(p->B[i], 0, fb, cs);
         }
-        if (e == cudaSuccess && !groups.empty())
-            e = cudaMemcpyAsync(d, p->pinned[j], bytes, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess && fork) e = cudaEventRecord(evs[groups.size()], cs);
-        for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g) {
+        if (e == cudaSuccess && ng > 0) e = cudaMemcpyAsync(d, p->pinned[j], bytes, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess && fork) e = cudaEventRecord(evs[ng], cs);
+        for (size_t g = 0; g < ng && e == cudaSuccess; ++g) {
             const cudaStream_t gs = fork ? side[g] : cs;
-            if (fork) e = cudaStreamWaitEvent(gs, evs[groups.size()], 0);
-            if (e != cudaSuccess) break;
-            const int per_sm = groups[g].kind == 0 ? 1 : (smem[g] > 110 * 1024 ? 1 : 2);
-            const int grid = std::max(1, std::min(n_items[g], per_sm * p->n_sm));
-            if (groups[g].kind == 2) {
-                StagedBatchArgs a;
-                std::memset(&a, 0, sizeof(a));
-                a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
-                a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
-                a.n = (int32_t)groups[g].members.size();
-                a.n_items = n_items[g];
-                a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
-                for (size_t m = 0; m < groups[g].members.size(); ++m) a.maps[m] = p->hs[groups[g].members[m]]->tmap;
-                e = launch_sum_f32_staged_batch(a, groups[g].band, groups[g].exact, smem[g], grid, gs);
-            } else {
-                BatchArgs a;
-                a.params = reinterpret_cast<const SumParams*>(d + off_params[g]);
-                a.item_start = reinterpret_cast<const int32_t*>(d + off_start[g]);
-                a.n = (int32_t)groups[g].members.size();
-                a.n_items = n_items[g];
-                a.counter = reinterpret_cast<unsigned int*>(d + off_counter[g]);
-                e = groups[g].kind == 0 ? launch_sum_f64_batch(a, smem[g], grid, gs)
-                                        : launch_sum_f32_batch(a, groups[g].comp != 0, smem[g], grid, gs);
-            }
+            if (fork) e = cudaStreamWaitEvent(gs, evs[ng], 0);
+            if (e == cudaSuccess) e = batch_launch_group(L, g, p->hs.data(), d, p->n_sm, gs);
             if (e == cudaSuccess && fork) e = cudaEventRecord(evs[g], gs);
             if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(cs, evs[g], 0);
         }
-        if (e == cudaSuccess && !groups.empty())
-            e = launch_reduce_batch(reinterpret_cast<const ReduceItem*>(d + off_ritems),
-                                    reinterpret_cast<const int64_t*>(d + off_rstart), (int)ritems.size(),
-                                    rstart.back(), cs);
+        if (e == cudaSuccess && ng > 0) e = batch_launch_reduce(L, d, cs);
         cudaGraph_t graph = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = ee;
