@@ -10,7 +10,8 @@ B at 8 times spread over the valid window (one launch).  Pairs per step =
 flush is needed between steps.
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle instead (the reference arm of this build), on a bounded sample.
+oracle instead, on a bounded sample (the paper is the only artifact: there is
+no reference code to run).
 Multi-GPU runs (torchrun) are independent replicas: the path needs no
 exchange, so each rank runs the full workload on its own GPU ("weak").
 """
@@ -34,7 +35,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pair-interactions/s, compensated FP32 vs plain FP64 at 1e-5 err; serving p50/p99"
 UNIT = "pairs/s"
-SUM_FP32_INSTR_PER_PAIR = 31       # canonical FP32 pipe instructions per pair
+# Canonical FP32 pipe instructions per pair: D (3 FADD), S (1 FMUL + 2 FFMA), R (1 FMUL),
+# slot (1 FFMA + 1 floor), r^-2 and r^-3 (2 FMUL), the scalar E term (1 FMUL + 1 FFMA),
+# E (6 FFMA), V (3 FMUL + 3 FFMA), B (6 FFMA): 3 FADD + 8 FMUL + 19 FFMA + 1 floor = 31.
+SUM_FP32_INSTR_PER_PAIR = 31
 N_SM = 152
 FP32_LANES_PER_SM = 128
 

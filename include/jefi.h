@@ -54,7 +54,7 @@ typedef enum {
     JEFI_ECUDA = 5,        /* a CUDA runtime call failed                          */
     JEFI_ETIMEOUT = 6,     /* a bounded device wait expired                       */
     JEFI_EINTERNAL = 7,    /* internal consistency check failed                   */
-    JEFI_EUNSUPPORTED = 8  /* valid request outside what this build supports      */
+    JEFI_EUNSUPPORTED = 8  /* valid request outside what this library supports    */
 } jefi_status;
 
 typedef struct jefi_problem* jefi_handle;

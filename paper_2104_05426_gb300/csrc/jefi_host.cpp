@@ -864,7 +864,7 @@ const char* jefi_strerror(int code) {
         case JEFI_ECUDA: return "CUDA runtime error";
         case JEFI_ETIMEOUT: return "bounded device wait expired";
         case JEFI_EINTERNAL: return "internal consistency check failed";
-        case JEFI_EUNSUPPORTED: return "request outside what this build supports";
+        case JEFI_EUNSUPPORTED: return "request outside what this library supports";
         default: return "unknown jefi status";
     }
 }

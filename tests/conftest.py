@@ -15,7 +15,7 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def gpu():
-    """The CUDA library, built and loaded; skips nothing on a GPU machine."""
+    """The CUDA library, built and loaded; skips nothing on a machine with a GPU."""
     import torch
 
     if not torch.cuda.is_available():
