@@ -86,3 +86,42 @@ def test_handle_creation_without_gpu_fails_cleanly():
         jefi.jefi_create(g, obs_points=np.zeros((5, 3)) + 3.0,
                          params=jefi.default_params(dt=0.1, history_slots=8), stream=0)
     assert e.value.code in (jefi.JEFI_ENOMEM, jefi.JEFI_ECUDA)
+
+
+def test_batch_plan_entry_points_reject_bad_arguments():
+    """Argument checks of the batch-plan calls happen before any CUDA call."""
+    import ctypes
+
+    L = jefi.load()
+    out = ctypes.c_void_p()
+    assert L.jefi_batch_plan_create(None, None, None, -1, ctypes.byref(out)) == jefi.JEFI_EINVAL
+    assert L.jefi_batch_plan_create(None, None, None, 1, ctypes.byref(out)) == jefi.JEFI_EINVAL
+    assert L.jefi_batch_plan_create(None, None, None, 0, None) == jefi.JEFI_EINVAL
+    assert L.jefi_batch_plan_launch(None, None, None) == jefi.JEFI_EINVAL
+    assert L.jefi_batch_plan_tune(None, None, None, None) == jefi.JEFI_EINVAL
+    assert L.jefi_batch_plan_destroy(None) == jefi.JEFI_EINVAL
+    with pytest.raises(ValueError):                   # one output pair per handle
+        jefi.jefi_batch_plan_create([object()], [], [])
+    with pytest.raises(ValueError):                   # outputs must be device tensors
+        jefi.jefi_batch_plan_create([object()], [np.zeros((1, 3))], [np.zeros((1, 3))])
+
+
+def test_no_cpu_fallback_without_a_device():
+    """Without a CUDA device every compute entry fails with an error code:
+    there is no CPU path behind the C ABI."""
+    import ctypes
+
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    L = jefi.load()
+    g = jefi.grid((4, 4, 4), (0.0,) * 3, (0.25,) * 3)
+    obs = jefi.grid((4, 4, 4), (2.0,) * 3, (0.25,) * 3)
+    with pytest.raises(jefi.JefiError) as e:
+        jefi.jefi_create(g, obs_grid=obs, params=jefi.default_params(dt=0.1, history_slots=8))
+    assert e.value.code in (jefi.JEFI_ENOMEM, jefi.JEFI_ECUDA)
+    assert jefi.jefi_debug_wait_timeout(0.01) == jefi.JEFI_ECUDA
+    out = ctypes.c_void_p()
+    assert L.jefi_batch_plan_create(None, None, None, 0, ctypes.byref(out)) == jefi.JEFI_ECUDA
+    assert not out.value
