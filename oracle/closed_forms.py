@@ -17,6 +17,10 @@ of moving charges below assume the Maxwell-consistent choice k_b = k_e / c^2.
 * ``hertz_dipole``   oscillating point dipole p(t) z-hat with near,
                      intermediate and far terms, times the Gaussian form
                      factor exp(-(omega sigma / c)^2 / 2) of a smeared dipole
+* ``uniform_box``    static field of a uniformly charged rectangular box
+                     (the saturated state of the paper's step-on sources,
+                     Sec. 3.1), in closed form
+* ``xoy_deviation``  the paper's error norm in the XOY plane (Eq. norms)
 """
 from __future__ import annotations
 
@@ -126,6 +130,52 @@ def hertz_dipole(p0, omega, obs, t, c=1.0, k_e=1.0, k_b=None, sigma=0.0, phase=0
     B = np.cross(vec(pd), n) / r[:, None] ** 2 + np.cross(vec(pdd), n) / (c * r[:, None])
     F = math.exp(-0.5 * (omega * sigma / c) ** 2)
     return k_e * F * E, k_b * F * B
+
+
+def _rect_inv_r(u, va, vb, wa, wb):
+    """Integral of 1/sqrt(u^2 + v^2 + w^2) over v in [va, vb], w in [wa, wb],
+    from the antiderivative G = v ln(w + r) + w ln(v + r) - u atan(v w / (u r))
+    (d^2 G / dv dw = 1/r; the u term vanishes with u)."""
+    def G(v, w):
+        r = np.sqrt(u * u + v * v + w * w)
+        safe_u = np.where(u == 0.0, 1.0, u)
+        at = np.where(u == 0.0, 0.0, u * np.arctan(v * w / (safe_u * r)))
+        return v * np.log(w + r) + w * np.log(v + r) - at
+
+    return G(vb, wb) - G(va, wb) - G(vb, wa) + G(va, wa)
+
+
+def uniform_box(obs, lo, hi, rho=1.0, k_e=1.0):
+    """E of charge density rho filling the box [lo, hi] (static Coulomb field,
+    the rho/R^3 term of Eq. E integrated over the box).
+
+    Along axis a the kernel (x_a - x'_a)/R^3 integrates in closed form to
+    1/R(x_a - hi_a) - 1/R(x_a - lo_a); the remaining integral of 1/R over the
+    box's face rectangle is _rect_inv_r.  Valid off the box's edge lines
+    (every point strictly inside or outside works; cell centres qualify).
+    A uniform current J in the same box gives B = (k_b / (k_e rho)) J x E."""
+    P = _as_pts(obs)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    E = np.empty_like(P)
+    for a in range(3):
+        b, c = (a + 1) % 3, (a + 2) % 3
+        va, vb = P[:, b] - hi[b], P[:, b] - lo[b]
+        wa, wb = P[:, c] - hi[c], P[:, c] - lo[c]
+        E[:, a] = _rect_inv_r(P[:, a] - hi[a], va, vb, wa, wb) - _rect_inv_r(P[:, a] - lo[a], va, vb, wa, wb)
+    return k_e * rho * E
+
+
+def xoy_deviation(A, A_ref):
+    """The paper's comparison in the XOY plane (Eq. norms): per point
+    |A_ref - A| = sqrt(dA_x^2 + dA_y^2) and |A_ref| = sqrt(A_x^2 + A_y^2), z
+    components left out.  Returns (max deviation, max |A_ref|) over the
+    points given; their ratio is the relative deviation the paper quotes."""
+    A = np.asarray(A, dtype=np.float64).reshape(-1, 3)
+    R = np.asarray(A_ref, dtype=np.float64).reshape(-1, 3)
+    dev = np.hypot(R[:, 0] - A[:, 0], R[:, 1] - A[:, 1])
+    nrm = np.hypot(R[:, 0], R[:, 1])
+    return float(dev.max()), float(nrm.max())
 
 
 def rel_l2(a, b):

@@ -281,6 +281,58 @@ def test_step_sources_saturate_after_longest_path():
     assert not np.array_equal(Ec, Eb)
 
 
+def test_uniform_box_closed_form_against_quadrature():
+    """The closed-form field of a uniformly charged box (used below) against
+    an independent triple quadrature of the Coulomb kernel, its monopole limit
+    far away, and its zero at the centre of a cube."""
+    from scipy import integrate
+
+    lo, hi = np.array([-1.0, -0.5, -2.0]), np.array([1.5, 0.7, 0.3])
+    for p in (np.array([3.0, 1.0, 2.0]), np.array([-2.0, 2.5, -3.0]), np.array([0.4, 1.5, -0.7])):
+        E = cf.uniform_box([p], lo, hi)[0]
+        for a in range(3):
+            f = lambda z, y, x: (p[a] - (x, y, z)[a]) / ((p[0] - x) ** 2 + (p[1] - y) ** 2 + (p[2] - z) ** 2) ** 1.5
+            ref = integrate.tplquad(f, lo[0], hi[0], lo[1], hi[1], lo[2], hi[2], epsabs=1e-11, epsrel=1e-11)[0]
+            assert abs(E[a] - ref) <= 1e-8 * np.linalg.norm(E), (p, a)
+    far = np.array([[300.0, 400.0, 1200.0]])
+    mono = cf.coulomb(np.prod(hi - lo), (lo + hi) / 2, far)
+    assert cf.rel_l2(cf.uniform_box(far, lo, hi), mono) < 2e-5       # quadrupole ~ (size / r)^2
+    assert np.abs(cf.uniform_box([[0.0, 0.0, 0.0]], [-3.0] * 3, [3.0] * 3)).max() < 1e-12
+
+
+def _e1_saturated(n, dt, t=12.0):
+    g = Grid.cube(n, -3.0, 3.0)
+    rho, J, _, _ = StepConstant().history(g, int(t / dt) + 2, dt)
+    pts = g.points()
+    E, B = oracle.fields(g.n, g.lo, g.d, pts, rho, J, dt=dt, t=t)
+    return pts, E, B, cf.uniform_box(pts, [-3.0] * 3, [3.0] * 3)
+
+
+def test_e1_saturated_fields_against_continuous_uniform_cube():
+    """Paper Sec. 3.1 compares its step-on sources (rho = 1, J = (1,1,1) in
+    15^3 cells over [-3,3]^3, half-cell screening) with a numerical integral
+    of the continuous equations and reports the deviation in the XOY plane
+    (Eq. norms): within ~3 %.  Once saturated (every retarded slot >= 1) the
+    continuous fields are those of a uniformly charged cube, E in closed form
+    and B = J x E (k_e = k_b = 1): the discrete sum must approach them as the
+    cells shrink (midpoint rule; the screened self cell contributes nothing
+    to the continuous field at a cell centre, by symmetry)."""
+    pts, E, B, Et = _e1_saturated(15, 0.05)
+    Bt = np.cross(np.ones(3), Et)
+    plane = np.abs(pts[:, 2]) < 1e-12                       # z = 0: the middle layer of cells
+    assert plane.sum() == 15 * 15
+    for A, At in ((E, Et), (B, Bt)):
+        dev, nrm = cf.xoy_deviation(A[plane], At[plane])
+        assert dev / nrm < 5e-3                             # measured 0.21 %
+        assert cf.rel_l2(A, At) < 2e-3                      # all points, 3D: measured 0.11 %
+    # convergence with the cell size: the error falls ~2.9x from 10^3 to 20^3 cells
+    errs = []
+    for n in (10, 20):
+        _, E_n, _, Et_n = _e1_saturated(n, 0.25)
+        errs.append(cf.rel_l2(E_n, Et_n))
+    assert errs[0] / errs[1] > 2.5, errs
+
+
 def test_mirror_symmetry_of_charge_moving_along_x():
     """C1 geometry (grids symmetric in y and z), charge moving along x:
     J || x gives B_x == 0 exactly; E_y, B_z are odd and E_x even under
