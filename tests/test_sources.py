@@ -1,0 +1,58 @@
+"""Self-tests of the seeded source generators (CPU): charge continuity.
+
+Every source model feeding the oracle and the GPU path must satisfy
+d rho/dt + div J = 0, as the paper notes for its sinusoidal sources
+(Sec. 3.2); the moving Gaussians carry J = v rho and the dipole has
+rho = -dP_z/dz, J = dP/dt.  Central differences on a fine grid give a
+residual that is second order in the spacing and small against d rho/dt;
+the dipole's supplied time derivatives must match differences in time."""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import Blob, Dipole, Grid, MovingGaussians, Sinusoidal
+
+
+def _residual(model, n, lo, hi, t, ht=1e-5):
+    """Relative continuity residual on the interior cells, ||drho/dt + div J|| / ||drho/dt||."""
+    g = Grid.cube(n, lo, hi)
+    d = g.d[0]
+    rho_p = model.sample(g, t + ht)[0]
+    rho_m = model.sample(g, t - ht)[0]
+    drho = ((rho_p - rho_m) / (2.0 * ht)).reshape(n, n, n)          # [z][y][x]
+    J = model.sample(g, t)[1].reshape(n, n, n, 3)
+    div = ((J[1:-1, 1:-1, 2:, 0] - J[1:-1, 1:-1, :-2, 0]) +
+           (J[1:-1, 2:, 1:-1, 1] - J[1:-1, :-2, 1:-1, 1]) +
+           (J[2:, 1:-1, 1:-1, 2] - J[:-2, 1:-1, 1:-1, 2])) / (2.0 * d)
+    dr = drho[1:-1, 1:-1, 1:-1]
+    return float(np.linalg.norm(dr + div) / np.linalg.norm(dr))
+
+
+MODELS = {
+    "sinusoidal (paper Sec. 3.2)": (Sinusoidal(), -3.0, 3.0, 2.3),
+    "moving Gaussians": (MovingGaussians([Blob(1.0, (0.3, 0.25, 0.35), (0.1, -0.05, 0.0), (0.4, -0.2, 0.3)),
+                                          Blob(-0.5, (0.2, 0.2, 0.2), (-0.2, 0.1, 0.1), (0.0, 0.5, -0.1))]),
+                         -1.5, 1.5, 0.3),
+    "dipole": (Dipole(1.0, 2.0 * math.pi / 8.0, 0.1), -0.5, 0.5, 1.1),
+}
+
+
+@pytest.mark.parametrize("name", list(MODELS))
+def test_sources_satisfy_continuity(name):
+    model, lo, hi, t = MODELS[name]
+    r1 = _residual(model, 40, lo, hi, t)
+    r2 = _residual(model, 80, lo, hi, t)
+    assert r2 < 2e-2, (r1, r2)
+    assert r1 / r2 > 3.0, (r1, r2)        # second order in the spacing: the residual is the difference error
+
+
+def test_dipole_supplied_derivatives_match_time_differences():
+    model = Dipole(1.0, 2.0 * math.pi / 8.0, 0.1)
+    g = Grid.cube(16, -0.5, 0.5)
+    t, h = 1.7, 1e-5
+    rho, J, drho, dJ = model.sample(g, t)
+    rp, Jp, _, _ = model.sample(g, t + h)
+    rm, Jm, _, _ = model.sample(g, t - h)
+    assert np.allclose(drho, (rp - rm) / (2 * h), rtol=1e-6, atol=1e-9 * np.abs(drho).max())
+    assert np.allclose(dJ, (Jp - Jm) / (2 * h), rtol=1e-6, atol=1e-9 * np.abs(dJ).max())
