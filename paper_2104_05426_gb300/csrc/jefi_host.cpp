@@ -8,6 +8,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cfloat>
@@ -300,6 +301,15 @@ struct jefi_problem {
 };
 
 namespace {
+
+// A named NVTX range around one C-ABI call (profiler timelines, ncu --nvtx
+// filters); a no-op unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 #define JEFI_CUDA(x)                                     \
     do {                                                 \
@@ -1237,11 +1247,13 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
 
 int jefi_create(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
                 int64_t n_obs, const jefi_params* p, void* stream, jefi_handle* out) {
+    NvtxRange nvtx_range("jefi_create");
     return create_impl(src, obs_grid, obs_points, n_obs, p, stream, nullptr, out);
 }
 
 int jefi_create_view(jefi_handle base, const jefi_grid* obs_grid, const double* obs_points,
                      int64_t n_obs, void* stream, jefi_handle* out) {
+    NvtxRange nvtx_range("jefi_create_view");
     if (!base || !out) return JEFI_EINVAL;
     if (base->base) return JEFI_EINVAL;                  // views of views are not supported
     return create_impl(&base->src, obs_grid, obs_points, n_obs, &base->prm, stream, base, out);
@@ -1249,6 +1261,7 @@ int jefi_create_view(jefi_handle base, const jefi_grid* obs_grid, const double* 
 
 int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const double* drho,
                       const double* dJ, int on_device, void* stream) {
+    NvtxRange nvtx_range("jefi_push_sources");
     if (!h || h->base) return JEFI_EINVAL;               // views read the base's history
     const bool supplied = h->prm.deriv == JEFI_DERIV_SUPPLIED;
     if (h->n_src > 0 && (!rho || !J)) return JEFI_EINVAL;
@@ -1311,6 +1324,7 @@ static void sync_view(jefi_problem* h) {
 
 static int eval_impl(jefi_handle h, int32_t n_t, const double* t, double* E, double* B,
                      int on_device, void* stream) {
+    NvtxRange nvtx_range("jefi_eval_fields");
     if (!h || n_t < 0 || (n_t > 0 && !t)) return JEFI_EINVAL;
     sync_view(h);
     if (n_t == 0 || h->n_obs == 0) return JEFI_OK;
@@ -1355,6 +1369,7 @@ int jefi_eval_fields_multi(jefi_handle h, int32_t n_t, const double* t, double* 
 
 int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, double* const* B, int32_t n,
                     void* stream) {
+    NvtxRange nvtx_range("jefi_eval_batch");
     if (n < 0 || (n > 0 && (!hs || !t || !E || !B))) return JEFI_EINVAL;
     if (n == 0) return JEFI_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1501,6 +1516,7 @@ int time_eval(jefi_problem* h, double t, cudaStream_t s, float* ms) {
 }  // namespace
 
 int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_band, void* stream) {
+    NvtxRange nvtx_range("jefi_select_kernel");
     if (!h || h->fp64 || mode < JEFI_KERNEL_MEASURE || mode > JEFI_KERNEL_STAGED) return JEFI_EINVAL;
     sync_view(h);
     cudaStream_t s = (cudaStream_t)stream;
@@ -2060,6 +2076,7 @@ extern "C" {
 
 int jefi_batch_plan_create(const jefi_handle* hs, double* const* E, double* const* B, int32_t n,
                            jefi_batch_plan* out) {
+    NvtxRange nvtx_range("jefi_batch_plan_create");
     if (!out || n < 0 || (n > 0 && (!hs || !E || !B))) return JEFI_EINVAL;
     *out = nullptr;
     std::map<jefi_problem*, int> count;
@@ -2101,6 +2118,7 @@ int jefi_batch_plan_create(const jefi_handle* hs, double* const* E, double* cons
 }
 
 int jefi_batch_plan_launch(jefi_batch_plan p, const double* t, void* stream) {
+    NvtxRange nvtx_range("jefi_batch_plan_launch");
     if (!p || (!t && !p->hs.empty())) return JEFI_EINVAL;
     if (p->hs.empty()) return JEFI_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -2113,6 +2131,7 @@ int jefi_batch_plan_launch(jefi_batch_plan p, const double* t, void* stream) {
 }
 
 int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_tune_report* report) {
+    NvtxRange nvtx_range("jefi_batch_plan_tune");
     if (!p || (!t && !p->hs.empty())) return JEFI_EINVAL;
     jefi_tune_report rep{};
     rep.split_divisor = 1;
