@@ -21,6 +21,9 @@ of moving charges below assume the Maxwell-consistent choice k_b = k_e / c^2.
                      (the saturated state of the paper's step-on sources,
                      Sec. 3.1), in closed form
 * ``xoy_deviation``  the paper's error norm in the XOY plane (Eq. norms)
+* ``step_box``       E and B of uniform rho and J switched on at t = 0 in a
+                     box (the paper's Sec. 3.1 sources) at any time, from
+                     the sphere-box moments of the switch-on front
 * ``jefimenko_quadrature``  the continuous Eqs. E and B over a box for
                      analytic sources, by tensor Gauss-Legendre quadrature
                      (spectrally accurate while the integrand is smooth)
@@ -179,6 +182,104 @@ def xoy_deviation(A, A_ref):
     dev = np.hypot(R[:, 0] - A[:, 0], R[:, 1] - A[:, 1])
     nrm = np.hypot(R[:, 0], R[:, 1])
     return float(dev.max()), float(nrm.max())
+
+
+def _arcs_in_rectangle(rho, ax, bx, ay, by):
+    """Angles phi in [-pi, pi] (as intervals) where the circle point
+    (rho cos phi, rho sin phi) lies in [ax, bx] x [ay, by]."""
+    cuts = [-math.pi, math.pi]
+    for cv in (ax, bx):
+        if abs(cv) <= rho:
+            a = math.acos(max(-1.0, min(1.0, cv / rho)))
+            cuts += [a, -a]
+    for cv in (ay, by):
+        if abs(cv) <= rho:
+            a = math.asin(max(-1.0, min(1.0, cv / rho)))
+            cuts += [a, (math.pi - a) if a >= 0 else (-math.pi - a)]
+    cuts = sorted(set(cuts))
+    out = []
+    for p0, p1 in zip(cuts[:-1], cuts[1:]):
+        m = 0.5 * (p0 + p1)
+        x, y = rho * math.cos(m), rho * math.sin(m)
+        if p1 > p0 and ax <= x <= bx and ay <= y <= by:
+            out.append((p0, p1))
+    return out
+
+
+def sphere_box_moments(r, R, lo, hi, n_gl=16):
+    """For the sphere of radius R about r: the solid angle C of directions n
+    with r - R n inside the box [lo, hi], and the vector A = integral of n
+    over those directions.  On the unit sphere dOmega = du dphi with
+    u = n_z; each z-slice is a circle whose part inside the box's (x, y)
+    rectangle is a union of arcs in closed form, and the u integral runs
+    piecewise (Gauss-Legendre) between the u where the arcs change."""
+    r = np.asarray(r, dtype=np.float64)
+    a = (r - np.asarray(hi, dtype=np.float64)) / R
+    b = (r - np.asarray(lo, dtype=np.float64)) / R
+    u0, u1 = max(a[2], -1.0), min(b[2], 1.0)
+    if u0 >= u1:
+        return 0.0, np.zeros(3)
+    cuts = {u0, u1}
+    for cv in (a[0], b[0], a[1], b[1]):
+        if abs(cv) < 1.0:
+            cuts |= {math.sqrt(1.0 - cv * cv), -math.sqrt(1.0 - cv * cv)}
+    for cx in (a[0], b[0]):
+        for cy in (a[1], b[1]):
+            q = cx * cx + cy * cy
+            if q < 1.0:
+                cuts |= {math.sqrt(1.0 - q), -math.sqrt(1.0 - q)}
+    cuts = sorted(x for x in cuts if u0 <= x <= u1)
+    x, w = np.polynomial.legendre.leggauss(n_gl)
+    C, A = 0.0, np.zeros(3)
+    for p, q in zip(cuts[:-1], cuts[1:]):
+        for xi, wi in zip(x, w):
+            u = 0.5 * (p + q) + 0.5 * (q - p) * xi
+            ww = 0.5 * (q - p) * wi
+            rho = math.sqrt(max(0.0, 1.0 - u * u))
+            for p0, p1 in _arcs_in_rectangle(rho, a[0], b[0], a[1], b[1]):
+                C += ww * (p1 - p0)
+                A += ww * np.array([rho * (math.sin(p1) - math.sin(p0)),
+                                    rho * (math.cos(p0) - math.cos(p1)), u * (p1 - p0)])
+    return C, A
+
+
+def step_box(r, t, lo, hi, J0, n_gl=16, k_e=1.0, k_b=1.0):
+    """E and B at point r and time t (c = 1) of rho = 1 and J = J0 switched on
+    at t = 0 inside the box [lo, hi] (the paper's Sec. 3.1 sources).
+
+    With n the unit vector from source to observer and R the distance, the
+    terms of Eqs. E and B become, for step sources (d/dt = delta(t_r)),
+      E = Int_0^t A(R) dR + t A(t) - J0 t C(t)
+      B = J0 x ( Int_0^t A(R) dR + t A(t) )
+    where C(R), A(R) are the sphere-box moments above: the Coulomb and
+    Biot-Savart terms gather the ball R < t already switched on, the
+    derivative terms the switch-on front R = t.  The R integral runs
+    piecewise between the distances at which the sphere meets a face, an
+    edge or a corner of the box."""
+    r = np.asarray(r, dtype=np.float64)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    J0 = np.asarray(J0, dtype=np.float64)
+    cuts = {0.0, float(t)}
+    for a in range(3):
+        cuts |= {abs(r[a] - lo[a]), abs(r[a] - hi[a])}
+        b, c = (a + 1) % 3, (a + 2) % 3
+        for fb in (lo[b], hi[b]):
+            for fc in (lo[c], hi[c]):
+                cuts.add(math.hypot(r[b] - fb, r[c] - fc))
+    for fx in (lo[0], hi[0]):
+        for fy in (lo[1], hi[1]):
+            for fz in (lo[2], hi[2]):
+                cuts.add(math.sqrt((r[0] - fx) ** 2 + (r[1] - fy) ** 2 + (r[2] - fz) ** 2))
+    cuts = sorted(x for x in cuts if 0.0 <= x <= t)
+    x, w = np.polynomial.legendre.leggauss(n_gl)
+    ball = np.zeros(3)
+    for p, q in zip(cuts[:-1], cuts[1:]):
+        for xi, wi in zip(x, w):
+            R = 0.5 * (p + q) + 0.5 * (q - p) * xi
+            ball += 0.5 * (q - p) * wi * sphere_box_moments(r, R, lo, hi, n_gl)[1]
+    Ct, At = sphere_box_moments(r, t, lo, hi, n_gl) if t > 0 else (0.0, np.zeros(3))
+    return k_e * (ball + t * At - J0 * t * Ct), k_b * np.cross(J0, ball + t * At)
 
 
 def jefimenko_quadrature(obs, t, lo, hi, sources, n_gl=32, c=1.0, k_e=1.0, k_b=1.0):
