@@ -24,6 +24,10 @@ of moving charges below assume the Maxwell-consistent choice k_b = k_e / c^2.
 * ``step_box``       E and B of uniform rho and J switched on at t = 0 in a
                      box (the paper's Sec. 3.1 sources) at any time, from
                      the sphere-box moments of the switch-on front
+* ``jefimenko_ball``  the same for sources that switch on continuously at
+                     t = 0: the integral over the part of the box inside
+                     the ball R < c t, in spherical coordinates about each
+                     observation point (accurate while the front crosses)
 * ``jefimenko_quadrature``  the continuous Eqs. E and B over a box for
                      analytic sources, by tensor Gauss-Legendre quadrature
                      (spectrally accurate while the integrand is smooth)
@@ -280,6 +284,85 @@ def step_box(r, t, lo, hi, J0, n_gl=16, k_e=1.0, k_b=1.0):
             ball += 0.5 * (q - p) * wi * sphere_box_moments(r, R, lo, hi, n_gl)[1]
     Ct, At = sphere_box_moments(r, t, lo, hi, n_gl) if t > 0 else (0.0, np.zeros(3))
     return k_e * (ball + t * At - J0 * t * Ct), k_b * np.cross(J0, ball + t * At)
+
+
+def _box_cuts(r, lo, hi):
+    """Distances from r at which a sphere about r meets a face plane, an edge
+    line or a corner of the box [lo, hi]."""
+    cuts = set()
+    for a in range(3):
+        cuts |= {abs(r[a] - lo[a]), abs(r[a] - hi[a])}
+        b, c = (a + 1) % 3, (a + 2) % 3
+        for fb in (lo[b], hi[b]):
+            for fc in (lo[c], hi[c]):
+                cuts.add(math.hypot(r[b] - fb, r[c] - fc))
+    for fx in (lo[0], hi[0]):
+        for fy in (lo[1], hi[1]):
+            for fz in (lo[2], hi[2]):
+                cuts.add(math.sqrt((r[0] - fx) ** 2 + (r[1] - fy) ** 2 + (r[2] - fz) ** 2))
+    return cuts
+
+
+def jefimenko_ball(obs, t, lo, hi, sources, n_gl=16, c=1.0, k_e=1.0, k_b=1.0):
+    """E and B of the continuous Eqs. E and B (as ``jefimenko_quadrature``)
+    for sources that are zero before t = 0 and continuous in time there
+    (their derivatives may jump): only the part of the box inside the ball
+    R < c t contributes.  In spherical coordinates about each observation
+    point, r' = r - R n with dV' = R^2 dR dOmega and dOmega = du dphi
+    (u = n_z), the integrands become
+      E: n rho + n drho R / c - dJ R / c^2,   B: (J + dJ R / c) x n
+    and every layer is smooth: R runs piecewise between the distances at
+    which the sphere meets a face, an edge or a corner of the box (and c t),
+    u between the values where the slice's arcs inside the box change, phi
+    over those arcs, each piece by Gauss-Legendre."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    x, w = np.polynomial.legendre.leggauss(int(n_gl))
+    obs = _as_pts(obs)
+    E = np.zeros_like(obs)
+    B = np.zeros_like(obs)
+    for k, r in enumerate(obs):
+        cuts = sorted(v for v in _box_cuts(r, lo, hi) | {0.0, c * t} if 0.0 <= v <= c * t)
+        for p, q in zip(cuts[:-1], cuts[1:]):
+            for xi, wi in zip(x, w):
+                R = 0.5 * (p + q) + 0.5 * (q - p) * xi
+                wR = 0.5 * (q - p) * wi
+                a = (r - hi) / R
+                b = (r - lo) / R
+                u0, u1 = max(a[2], -1.0), min(b[2], 1.0)
+                if u0 >= u1:
+                    continue
+                uc = {u0, u1}
+                for cv in (a[0], b[0], a[1], b[1]):
+                    if abs(cv) < 1.0:
+                        uc |= {math.sqrt(1.0 - cv * cv), -math.sqrt(1.0 - cv * cv)}
+                for cx in (a[0], b[0]):
+                    for cy in (a[1], b[1]):
+                        qq = cx * cx + cy * cy
+                        if qq < 1.0:
+                            uc |= {math.sqrt(1.0 - qq), -math.sqrt(1.0 - qq)}
+                uc = sorted(v for v in uc if u0 <= v <= u1)
+                dirs, wts = [], []
+                for up, uq in zip(uc[:-1], uc[1:]):
+                    for xj, wj in zip(x, w):
+                        u = 0.5 * (up + uq) + 0.5 * (uq - up) * xj
+                        wu = 0.5 * (uq - up) * wj
+                        rho_u = math.sqrt(max(0.0, 1.0 - u * u))
+                        for p0, p1 in _arcs_in_rectangle(rho_u, a[0], b[0], a[1], b[1]):
+                            phi = 0.5 * (p0 + p1) + 0.5 * (p1 - p0) * x
+                            dirs.append(np.stack([rho_u * np.cos(phi), rho_u * np.sin(phi),
+                                                  np.full_like(phi, u)], axis=1))
+                            wts.append(wR * wu * 0.5 * (p1 - p0) * w)
+                if not dirs:
+                    continue
+                n = np.concatenate(dirs)
+                ww = np.concatenate(wts)
+                rho, drho, J, dJ = sources(r - R * n, np.full(len(n), t - R / c))
+                e = n * (rho + drho * R / c)[:, None] - dJ * (R / (c * c))
+                bb = np.cross(J + dJ * (R / c), n)
+                E[k] += ww @ e
+                B[k] += ww @ bb
+    return k_e * E, k_b * B
 
 
 def jefimenko_quadrature(obs, t, lo, hi, sources, n_gl=32, c=1.0, k_e=1.0, k_b=1.0):
