@@ -476,6 +476,29 @@ def measure_batch(n_problems: int = 256, sides=(8, 48), H_range=(32, 128), obs_s
            "obs_sides": list(obs_sides), "pairs": pairs, "ms_per_batch": ms, "pairs_per_s": pairs / (ms / 1e3),
            "staged_problems": sum(1 for b in bands if b > 0)}
 
+    # Each kernel variant's problems as a batch of their own: where the
+    # batch's time goes (the staged band of each view, 0 = direct gather).
+    by_kernel = {}
+    try:
+        groups = {}
+        for i, b in enumerate(bands):
+            groups.setdefault(int(b), []).append(i)
+        for b, idx in sorted(groups.items()):
+            sub = ([views[i] for i in idx], [ts[i] for i in idx], [Es[i] for i in idx], [Bs[i] for i in idx])
+            jefi_eval_batch(*sub)                     # warm-up
+            torch.cuda.synchronize()
+            e0.record()
+            jefi_eval_batch(*sub)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_b = e0.elapsed_time(e1)
+            pairs_b = sum(probs[i].side ** 3 * Es[i].shape[0] for i in idx)
+            by_kernel[str(b)] = {"problems": len(idx), "pairs": pairs_b, "ms": ms_b,
+                                 "pairs_per_s": pairs_b / (ms_b / 1e3)}
+        out["by_kernel"] = by_kernel
+    except Exception as e:      # a diagnostic: never lose the batch measurement to it
+        out["by_kernel_error"] = f"{type(e).__name__}: {e}"
+
     def time_plan(plan):
         jefi_batch_plan_launch(plan, ts)              # warm-up
         torch.cuda.synchronize()
