@@ -348,6 +348,10 @@ def run_gpu(args):
         if not args.no_cpu_baseline:
             result["cpu_baseline"], result["oracle_check"] = cpu_baseline(p, slices[:H], t_first,
                                                                           E_first, B_first)
+            try:
+                result["oracle_check"]["configs"] = config_errors(dev)
+            except Exception as e:      # a diagnostic: never lose the benchmark line to it
+                result["oracle_check"]["configs_error"] = f"{type(e).__name__}: {e}"
     jefi.jefi_destroy(h)
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -473,6 +477,52 @@ def cpu_baseline(p, slices, times, E_gpu, B_gpu, stride=512):
                                   f"1 time = {len(sub1) * p.src.size:.3e} pairs, {dt1:.1f} s, 1 thread"}
     check = {"max_rel_l2_fp32c_vs_oracle": errs, "points": int(len(sub)), "times": len(times)}
     return base, check
+
+
+def config_errors(dev):
+    """Part of the oracle leg: rel-L2 of every GPU precision against the FP64
+    oracle, worst over the evaluation times, on the moving-charge workload
+    (16^3 sources x 16^3 points, 4 times) and the dipole workload (32^3
+    sources x 4096 points on shells, 4 times; worst shell)."""
+    import torch
+
+    import oracle
+    import paper_2104_05426_gb300 as jefi
+    from workloads import c1_lienard_wiechert, c3_dipole
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    out = {}
+    for name, p in (("moving charge 16^3 x 16^3", c1_lienard_wiechert()),
+                     ("dipole 32^3 x 4096 points", c3_dipole())):
+        rho, J, _, _ = p.source.history(p.src, p.n_push, p.dt, p.t0)
+        obs = p.obs()
+        ref = [oracle.fields(p.src.n, p.src.lo, p.src.d, obs, rho, J, c=p.c, k_e=p.k_e, k_b=p.k_b,
+                             dt=p.dt, t0=p.t0, t=t) for t in p.times]
+        if p.obs_grid is None:
+            r = np.linalg.norm(obs, axis=1)
+            parts = [np.abs(r - R) < 1e-6 * R for R in np.unique(np.round(r, 6))]
+        else:
+            parts = [np.ones(len(obs), dtype=bool)]
+        res = {}
+        for prec in ("fp64", "fp32c", "fp32"):
+            prm = jefi.default_params(c=p.c, k_e=p.k_e, k_b=p.k_b, dt=p.dt, t0=p.t0, history_slots=p.H,
+                                      precision=prec)
+            src = jefi.grid_from(p.src)
+            h = (jefi.jefi_create(src, obs_grid=jefi.grid_from(p.obs_grid), params=prm)
+                 if p.obs_grid is not None else jefi.jefi_create(src, obs_points=obs, params=prm))
+            for n in range(p.n_push):
+                jefi.jefi_push_sources(h, torch.from_numpy(np.ascontiguousarray(rho[n])).to(dev),
+                                       torch.from_numpy(np.ascontiguousarray(J[n])).to(dev))
+            E, B = jefi.eval_fields(h, list(p.times))
+            E, B = E.cpu().numpy(), B.cpu().numpy()
+            res[prec] = {f: max(rel(A[i][m], ref[i][k][m]) for i in range(len(p.times)) for m in parts)
+                         for k, (f, A) in enumerate((("E", E), ("B", B)))}
+            res[prec]["device_status"] = jefi.jefi_get_info(h)["device_status"]
+            jefi.jefi_destroy(h)
+        out[name] = res
+    return out
 
 
 # Published V100 timings of the paper: Table 2 (410 snapshots, 15^3 x 15^3,
