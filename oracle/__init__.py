@@ -20,7 +20,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jefi_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "libjefi_oracle.so")
+# JEFI_ORACLE_LIB: load a prebuilt oracle library instead (the mutation test
+# plants mistakes in a copy of jefi_oracle.c and runs the pins against it).
+_LIB_OVERRIDE = os.environ.get("JEFI_ORACLE_LIB")
+_LIB_PATH = _LIB_OVERRIDE or os.path.join(_HERE, "libjefi_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -33,6 +36,8 @@ ENOTYET = 3
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library in-tree and return its path."""
+    if _LIB_OVERRIDE:
+        return _LIB_PATH
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
