@@ -2,8 +2,9 @@
 
 Each case plants one mistake in a copy of oracle/jefi_oracle.c -- a dropped
 term, a wrong sign, a transposed operand, an off-by-one slot, a missing
-factor -- builds it, and runs the pins of test_oracle_pins.py against that
-library (JEFI_ORACLE_LIB).  Every mutant must fail at least one pin.  The
+factor, swapped interpolation weights -- builds it, and runs the pins of
+test_oracle_pins.py (floor rule) or test_oracle_interp_pins.py (second-order
+variant) against that library (JEFI_ORACLE_LIB).  Every mutant must fail at least one pin.  The
 pins stop at the first failure, so a caught mutant costs little."""
 import os
 import subprocess
@@ -53,24 +54,57 @@ MUTANTS = [
 ]
 
 
-def _run_pins(text, tmp):
+def _run_pins(text, tmp, pins="test_oracle_pins.py"):
     src = os.path.join(tmp, "oracle_copy.c")
     lib = os.path.join(tmp, "liboracle_copy.so")
     with open(src, "w") as f:
         f.write(text)
     subprocess.run(["gcc", *oracle.CFLAGS, "-o", lib, src, "-lm"], check=True)
     env = dict(os.environ, JEFI_ORACLE_LIB=lib)
-    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+    return subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins),
                            "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"],
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
 
 
-def test_unmutated_copy_passes():
+@pytest.mark.parametrize("pins", ["test_oracle_pins.py", "test_oracle_interp_pins.py"])
+def test_unmutated_copy_passes(pins):
     """Control: the pins pass on a copy built the same way, so a failure
     below comes from the planted mistake."""
     with tempfile.TemporaryDirectory() as tmp:
-        r = _run_pins(open(SRC).read(), tmp)
+        r = _run_pins(open(SRC).read(), tmp, pins)
     assert r.returncode == 0, r.stdout[-2000:]
+
+
+# (name, text in the second-order sum, planted replacement): pinned by
+# test_oracle_interp_pins.py
+INTERP_MUTANTS = [
+    ("interpolation weights swapped",
+     "const double r_n = (1.0 - w) * r2[0] + w * r2[1];", "const double r_n = w * r2[0] + (1.0 - w) * r2[1];"),
+    ("one-sided instead of central difference",
+     "hist_at(rho, Ns, m + 1, cell, -1) - hist_at(rho, Ns, m - 1, cell, -1)",
+     "hist_at(rho, Ns, m, cell, -1) - hist_at(rho, Ns, m - 1, cell, -1)"),
+    ("drho/dt not interpolated",
+     "const double dr = (1.0 - w) * dr2[0] + w * dr2[1];", "const double dr = dr2[0];"),
+    ("dJ/dt not interpolated",
+     "dj[a] = (1.0 - w) * dj2[0][a] + w * dj2[1][a];", "dj[a] = dj2[0][a];"),
+    ("no interpolation weight (the floor rule)",
+     "const double w = u - fl;", "const double w = 0.0;"),
+    ("derivative before the first slice not zero",
+     "if (m < 0) {", "if (m < -1) {"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", INTERP_MUTANTS, ids=[m[0] for m in INTERP_MUTANTS])
+def test_interp_pins_catch_planted_mistake(name, old, new):
+    text = open(SRC).read()
+    start = text.index("int oracle_fields_interp(")
+    end = text.index("\n}\n", start)
+    part = text[start:end]
+    assert part.count(old) == 1, f"mutation site not unique: {old}"
+    mutated = text[:start] + part.replace(old, new) + text[end:]
+    with tempfile.TemporaryDirectory() as tmp:
+        r = _run_pins(mutated, tmp, "test_oracle_interp_pins.py")
+    assert r.returncode == 1, f"no pin caught: {name}\n{r.stdout[-2000:]}"
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
