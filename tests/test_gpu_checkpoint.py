@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import paper_2104_05426_gb300 as jefi
-from jefi_cases import create, history, push_all
+from jefi_cases import create, history
 from workloads import Blob, Grid, MovingGaussians, Problem
 
 pytestmark = pytest.mark.gpu

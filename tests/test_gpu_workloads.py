@@ -4,12 +4,10 @@ sources (Sec. 3.1 step-on constant, Sec. 3.2 sinusoidal) at the paper's
 sizes.  FP64 within 1e-12 of the oracle; the FP32 errors are recorded per
 shell and bounded."""
 import json
-import math
 
 import numpy as np
 import pytest
 
-import oracle
 import paper_2104_05426_gb300 as jefi
 from jefi_cases import create, gpu_fields, history, oracle_fields, push_all, rel_l2
 from workloads import c3_dipole, e1_constant, e2_sinusoidal
