@@ -125,3 +125,46 @@ def test_no_cpu_fallback_without_a_device():
     out = ctypes.c_void_p()
     assert L.jefi_batch_plan_create(None, None, None, 0, ctypes.byref(out)) == jefi.JEFI_ECUDA
     assert not out.value
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "jefi.h"
+
+/* every entry point, by address: the header must declare them all for C */
+typedef void (*entry_fn)(void);
+static const entry_fn entries[] = {
+    (entry_fn)jefi_default_params, (entry_fn)jefi_create, (entry_fn)jefi_create_view, (entry_fn)jefi_push_sources,
+    (entry_fn)jefi_eval_fields, (entry_fn)jefi_eval_fields_multi, (entry_fn)jefi_eval_batch,
+    (entry_fn)jefi_valid_window, (entry_fn)jefi_get_info, (entry_fn)jefi_reset_stats, (entry_fn)jefi_debug_slots,
+    (entry_fn)jefi_debug_wait_timeout, (entry_fn)jefi_host_pair_slots, (entry_fn)jefi_eval_fields_noalloc,
+    (entry_fn)jefi_checkpoint_bytes, (entry_fn)jefi_checkpoint, (entry_fn)jefi_restore, (entry_fn)jefi_select_kernel,
+    (entry_fn)jefi_batch_plan_create, (entry_fn)jefi_batch_plan_launch, (entry_fn)jefi_batch_plan_tune,
+    (entry_fn)jefi_batch_plan_destroy, (entry_fn)jefi_destroy, (entry_fn)jefi_strerror};
+
+int main(void) {
+    jefi_params p;
+    jefi_default_params(&p);
+    double xo[3] = {3.0, 4.0, 0.0}, xs[3] = {0.0, 0.0, 0.0};
+    int64_t slot = -1;
+    jefi_host_pair_slots(1, xo, xs, 10.0, 0.0, 1.0, 0.5, &slot);   /* floor((10 - 5)/0.5) = 10 */
+    printf("%d %d %s %lld %d\n", (int)(sizeof(entries) / sizeof(entries[0])), p.history_slots,
+           jefi_strerror(JEFI_OK), (long long)slot, jefi_destroy(NULL));
+    return 0;
+}
+"""
+
+
+def test_header_is_c99_and_the_library_links_from_c(tmp_path):
+    """include/jefi.h compiles as C99 with warnings as errors, a C program
+    links libjefi.so and calls the entry points that need no device."""
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    lib_dir = os.path.dirname(jefi._build.build())
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", lib_dir, "-l:libjefi.so", "-Wl,-rpath," + lib_dir],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out == ["24", "64", "ok", "10", str(jefi.JEFI_EINVAL)]
