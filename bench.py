@@ -39,8 +39,36 @@ UNIT = "pairs/s"
 # slot (1 FFMA + 1 floor), r^-2 and r^-3 (2 FMUL), the scalar E term (1 FMUL + 1 FFMA),
 # E (6 FFMA), V (3 FMUL + 3 FFMA), B (6 FFMA): 3 FADD + 8 FMUL + 19 FFMA + 1 floor = 31.
 SUM_FP32_INSTR_PER_PAIR = 31
-N_SM = 152
+# The same algorithm in FP64 (the plain FP64 path): the 31 operations above as
+# DADD/DMUL/DFMA; the FP64 reciprocal square root's Newton steps and the
+# threshold compares are not counted as useful work.
+SUM_FP64_INSTR_PER_PAIR = 31
 FP32_LANES_PER_SM = 128
+# FP64 FMA results per SM per clock on GB300: 2.  An FMA throughput probe
+# (1216 CTAs x 256 threads x 8 independent DFMA chains) measured 1.994 DFMA
+# per SM per clock at 2070 MHz (FFMA: 124.7 of 128); the part's nominal
+# 1.25 TFLOP/s FP64 is the same figure (152 x 2 x 2 FLOP x 2.07 GHz).
+FP64_LANES_PER_SM = 2
+DEFAULT_SM_MAX_MHZ = 2070.0
+
+
+def device_sm_count(dev) -> int:
+    """Streaming multiprocessors of the device (the roofline's unit count)."""
+    import torch
+
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def sm_max_mhz(clk) -> float:
+    """Maximum SM clock: from the nvidia-smi samples, else the part's 2070 MHz."""
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"])
+    return DEFAULT_SM_MAX_MHZ
+
+
+def pipe_peak(n_sm: int, lanes: int, mhz: float) -> float:
+    """Instructions per second of one arithmetic pipe over the whole GPU."""
+    return n_sm * lanes * mhz * 1e6
 
 
 # ---------------------------------------------------------------------------- distributed
@@ -190,7 +218,7 @@ def run_gpu(args):
         return jefi.jefi_create(jefi.grid_from(p.src), obs_grid=jefi.grid_from(p.obs_grid),
                                 params=prm, torch_allocator=True)
 
-    h = make("fp32c", jefi.JEFI_FLAG_STATS)
+    h = make(args.precision, jefi.JEFI_FLAG_STATS)
     for n in range(H):
         jefi.jefi_push_sources(h, *dev_slices[n])
     n_obs = p.n_obs
@@ -252,16 +280,23 @@ def run_gpu(args):
     # dominant kernel: the sum kernel, timed by the library's events on this stream
     sum_ms = info["sum_ms_total"] / max(info["sum_launches"], 1)
     pairs_launch = pairs_step
-    achieved = pairs_launch * SUM_FP32_INSTR_PER_PAIR / (sum_ms / 1e3) / 1e12
-    peak = N_SM * FP32_LANES_PER_SM * 2070e6 / 1e12
+    n_sm = device_sm_count(dev)
+    mhz = sm_max_mhz(clk)
+    if args.precision == "fp64":
+        instr, lanes, unit, kname = SUM_FP64_INSTR_PER_PAIR, FP64_LANES_PER_SM, "FP64 Tinstr/s", "sum_f64_kernel"
+    else:
+        instr, lanes, unit = SUM_FP32_INSTR_PER_PAIR, FP32_LANES_PER_SM, "FP32 Tinstr/s"
+        kname = (f"sum_f32_staged_kernel<band={info['staged_band']}>" if info["staged_band"]
+                 else "sum_f32_kernel (direct gather)")
+    achieved = pairs_launch * instr / (sum_ms / 1e3) / 1e12
+    peak = pipe_peak(n_sm, lanes, mhz) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "FP32 Tinstr/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic(),
-                "kernel": (f"sum_f32_staged_kernel<band={info['staged_band']}>" if info["staged_band"]
-                           else "sum_f32_kernel (direct gather)"),
-                "device_status": info["device_status"],
+                "unit": unit, "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic() if args.precision == "fp32c" and args.side == 64 else None,
+                "kernel": kname, "device_status": info["device_status"],
                 "kernel_ms": round(sum_ms, 3), "fallback_pairs": info["slot_fallbacks"],
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz (max SM clock)"}
+                "peak_basis": f"{n_sm} SMs (device query) x {lanes} {unit.split()[0]} lanes x "
+                              f"{mhz:.0f} MHz (max SM clock); {instr} instructions per pair"}
 
     # end to end through the C ABI with pinned host buffers
     pinned = [(torch.from_numpy(r).pin_memory(), torch.from_numpy(j).pin_memory())
@@ -280,11 +315,13 @@ def run_gpu(args):
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-              "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
               "config": {"workload": f"heavy-ion {args.side}^3 src x {args.side}^3 obs over [-5,5]^3, "
                                      "2 Gaussian charges +-0.995c + 1% noise, H=128, 8 eval times "
                                      "per step",
-                         "precision": "fp32 compensated, fp64 cross-split reduction",
+                         "precision": {"fp32c": "fp32 compensated, fp64 cross-split reduction",
+                                       "fp32": "fp32, fp64 cross-split reduction",
+                                       "fp64": "fp64"}[args.precision],
                          "pairs_per_step": pairs_step, "l2": "inputs larger than L2 (FP32 ring "
                          f"{n_src * (H + info['staged_band'] + 1) * 32 / 1e9:.2f} GB)",
                          "parallelism": f"replicas x{world}"},
@@ -400,7 +437,7 @@ def dipole_leg(dev, reps=5):
                      "device_status": info["device_status"]}
         fields[prec] = (E, B)
         jefi.jefi_destroy(h)
-    peak = N_SM * FP32_LANES_PER_SM * 2070e6
+    peak = pipe_peak(device_sm_count(dev), FP32_LANES_PER_SM, DEFAULT_SM_MAX_MHZ)
     out["fp32c"]["fp32_pipe_frac"] = out["fp32c"]["value"] * SUM_FP32_INSTR_PER_PAIR / peak
     out["fp32c_speedup_kernel"] = out["fp32c"]["value"] / out["fp64"]["value"]
     radii = np.linalg.norm(p.obs_points, axis=1)
@@ -664,6 +701,9 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--paper-tables", action="store_true",
                     help="only time the paper's own workloads (Tables 2 and 4) and print them")
+    ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp32", "fp64"],
+                    help="precision of the timed path (fp32c = the benchmark; the others for "
+                         "profiler captures and comparisons)")
     ap.add_argument("--side", type=int, default=64,
                     help="grid side of the heavy-ion workload (64 = the benchmark; smaller "
                          "sides only for profiler captures)")

@@ -285,11 +285,14 @@ void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double 
  *
  * Working memory is one file-scope device array of JEFI_NOALLOC_SCRATCH_BYTES
  * per GPU that loads the library, held until the process exits.  The first
- * call on a device, with that device current, finds the array's address
- * (cudaGetSymbolAddress, which also loads the module): make that first call
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents; calls that overlap on the GPU race on it, so callers
- * on several streams or threads must serialise them.
+ * call on a device, with that device current, does the set-up: it finds the
+ * array's address (cudaGetSymbolAddress, which also loads the module) and the
+ * device's SM count; make that first call before any stream capture begins.
+ * All calls share the array and it keeps the last call's contents (the call
+ * clears its status word itself); calls that overlap on the GPU race on it,
+ * so callers on several streams or threads must serialise them.  The library
+ * cannot check the sizes of the caller's device buffers: they must hold the
+ * element counts above.
  *
  * Limits: ceil(n_obs/256)*256 <= (JEFI_NOALLOC_SCRATCH_BYTES - 256)/48 (that
  * is n_obs <= 698880), and 4*(ceil(nx/4)+ceil(ny/4)+ceil(nz/4)) <= 6144;

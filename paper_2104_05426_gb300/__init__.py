@@ -429,13 +429,30 @@ def jefi_eval_fields_noalloc(src: jefi_grid, obs, rho, J, params: jefi_params, t
     For callers that cannot allocate device memory at this point (see
     include/jefi.h): every buffer is the caller's own -- obs [N_obs, 3],
     rho [n_slices, N_src], J [n_slices, N_src, 3], E and B [N_obs, 3], all
-    contiguous float64 CUDA tensors.  Synchronous on `stream`.
+    contiguous float64 CUDA tensors, N_src = src.n[0] * src.n[1] * src.n[2].
+    The library cannot see the size of a device buffer, so the shapes are
+    checked here, before anything reaches the GPU (ValueError otherwise).
+    Returns after E and B are written on `stream`.
     """
+    n_src = int(src.n[0]) * int(src.n[1]) * int(src.n[2])
+
+    def shape(x):
+        return tuple(int(d) for d in x.shape) if hasattr(x, "shape") else None
+
+    if shape(obs) is None or len(shape(obs)) != 2 or shape(obs)[1] != 3:
+        raise ValueError(f"obs must have shape (n_obs, 3), got {shape(obs)}")
+    n_obs = shape(obs)[0]
+    if shape(rho) is None or len(shape(rho)) != 2 or shape(rho)[1] != n_src:
+        raise ValueError(f"rho must have shape (n_slices, {n_src}), got {shape(rho)}")
+    n_slices = shape(rho)[0]
+    if shape(J) != (n_slices, n_src, 3):
+        raise ValueError(f"J must have shape {(n_slices, n_src, 3)}, got {shape(J)}")
+    for name, x in (("E", E), ("B", B)):
+        if shape(x) != (n_obs, 3):
+            raise ValueError(f"{name} must have shape {(n_obs, 3)}, got {shape(x)}")
     bufs = [_buf(x) for x in (obs, rho, J, E, B)]
     if not all(b[1] for b in bufs):
         raise ValueError("jefi_eval_fields_noalloc takes device (CUDA) tensors only")
-    n_obs = int(obs.shape[0]) if obs.dim() == 2 else int(obs.numel() // 3)
-    n_slices = int(rho.shape[0])
     rc = load().jefi_eval_fields_noalloc(ctypes.byref(src), bufs[0][0], n_obs, bufs[1][0], bufs[2][0],
                                          n_slices, ctypes.byref(params), float(t), bufs[3][0],
                                          bufs[4][0], _stream_ptr(stream))

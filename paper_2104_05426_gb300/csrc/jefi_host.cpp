@@ -363,6 +363,19 @@ bool alloc_direct_tables(jefi_problem* h) {
     return true;
 }
 
+// SM count of the current device (the work split targets whole waves of
+// CTAs).  Without a device the query fails and 1 is returned: such a
+// creation fails at its first device call anyway.
+int current_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n < 1) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n;
+}
+
 // Record that work on h's memory was enqueued on stream s (jefi_destroy waits for it).
 int mark_use(jefi_problem* h, cudaStream_t s) {
     if (!h->last_use) JEFI_CUDA(cudaEventCreateWithFlags(&h->last_use, cudaEventDisableTiming));
@@ -1088,7 +1101,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         h->K = 1;
     }
     {
-        const int64_t target = 2 * 152 * 2;  // two waves of two CTAs per SM
+        const int64_t target = 2 * 2 * (int64_t)current_sm_count();  // two waves of two CTAs per SM
         int64_t ns = std::max<int64_t>(1, (target + h->n_tiles - 1) / std::max<int32_t>(h->n_tiles, 1));
         ns = std::min<int64_t>(ns, std::max<int32_t>(h->n_bricks, 1));
         h->bricks_per_split = (int32_t)((h->n_bricks + ns - 1) / ns);

@@ -11,7 +11,9 @@
 //
 // Set-up: the first call on a device (with that device current) looks up the
 // array's device address with cudaGetSymbolAddress, which also loads this
-// module on the device.  Make that first call before any stream capture.
+// module on the device, and the device's SM count; make that first call
+// before any stream capture begins.  Each call returns after its kernels have
+// finished on the caller's stream (it reads the status word back).
 // Every call shares the array and it keeps the last call's contents; the call
 // clears what must start at zero.  Calls that overlap on the GPU (different
 // streams or host threads) race on the array and must be serialised by the
@@ -160,21 +162,27 @@ __global__ void noalloc_reduce(const double* partials, int64_t n_obs, int n_slot
 
 std::mutex g_setup_lock;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set-up on first use).
-int scratch_on_current_device(unsigned char** out) {
+// Device address of the scratch array on the current device and the
+// device's SM count (set-up on first use).
+int scratch_on_current_device(unsigned char** out, int* n_sm) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return JEFI_ECUDA;
     std::lock_guard<std::mutex> guard(g_setup_lock);
     if (!g_scratch_ptr[dev]) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+        int sms = 0;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
             cudaGetLastError();
             return JEFI_ECUDA;
         }
+        g_sm_count[dev] = sms;
         g_scratch_ptr[dev] = static_cast<unsigned char*>(ptr);
     }
     *out = g_scratch_ptr[dev];
+    *n_sm = g_sm_count[dev];
     return JEFI_OK;
 }
 
@@ -220,7 +228,12 @@ extern "C" int jefi_eval_fields_noalloc(const jefi_grid* src, const double* obs,
     // Capacity: the partial sums [n_split][6][n_slots] FP64 must fit the array.
     const int64_t cap = (int64_t)(JEFI_NOALLOC_SCRATCH_BYTES - kHeaderBytes) / (int64_t)(6 * sizeof(double));
     if (n_slots > cap) return JEFI_EUNSUPPORTED;       // more points than the array can hold
-    int64_t n_split = std::max<int64_t>(1, (2 * 152 + n_tiles - 1) / n_tiles);
+    unsigned char* scratch = nullptr;
+    int n_sm = 0;
+    int rc = scratch_on_current_device(&scratch, &n_sm);
+    if (rc != JEFI_OK) return rc;
+    // two CTAs per SM over tiles x source splits
+    int64_t n_split = std::max<int64_t>(1, (2 * (int64_t)n_sm + n_tiles - 1) / n_tiles);
     n_split = std::min<int64_t>(n_split, std::min<int64_t>(n_bricks, cap / n_slots));
     p.bricks_per_split = (int32_t)((n_bricks + n_split - 1) / n_split);
     p.n_split = (int32_t)((n_bricks + p.bricks_per_split - 1) / p.bricks_per_split);
@@ -240,9 +253,6 @@ extern "C" int jefi_eval_fields_noalloc(const jefi_grid* src, const double* obs,
     p.rho = rho;
     p.J = J;
 
-    unsigned char* scratch = nullptr;
-    int rc = scratch_on_current_device(&scratch);
-    if (rc != JEFI_OK) return rc;
     p.status = reinterpret_cast<int32_t*>(scratch);
     p.partials = reinterpret_cast<double*>(scratch + kHeaderBytes);
 

@@ -168,3 +168,30 @@ def test_header_is_c99_and_the_library_links_from_c(tmp_path):
                    check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     assert out == ["24", "64", "ok", "10", str(jefi.JEFI_EINVAL)]
+
+
+def test_noalloc_wrapper_checks_shapes_before_any_launch():
+    """The allocation-free entry cannot see the sizes of device buffers, so the
+    binding checks every shape against the grid before anything is launched
+    (host arrays here: the shape error comes before the device check)."""
+    g = jefi.grid((3, 4, 5), (0.0,) * 3, (0.1,) * 3)        # N_src = 60
+    prm = jefi.default_params(dt=0.1)
+    obs, rho, J = np.zeros((7, 3)), np.zeros((4, 60)), np.zeros((4, 60, 3))
+    E, B = np.zeros((7, 3)), np.zeros((7, 3))
+    bad = [
+        dict(obs=np.zeros((7, 2))),
+        dict(obs=np.zeros(21)),
+        dict(rho=np.zeros((4, 59))),
+        dict(rho=np.zeros(240)),
+        dict(J=np.zeros((4, 60, 2))),
+        dict(J=np.zeros((3, 60, 3))),
+        dict(E=np.zeros((6, 3))),
+        dict(B=np.zeros((7, 3, 1))),
+    ]
+    for change in bad:
+        args = dict(obs=obs, rho=rho, J=J, E=E, B=B)
+        args.update(change)
+        with pytest.raises(ValueError, match="shape"):
+            jefi.jefi_eval_fields_noalloc(g, args["obs"], args["rho"], args["J"], prm, 1.0, args["E"], args["B"])
+    with pytest.raises(ValueError, match="device"):     # right shapes, host buffers
+        jefi.jefi_eval_fields_noalloc(g, obs, rho, J, prm, 1.0, E, B)

@@ -85,3 +85,61 @@ def test_noalloc_rejects_more_points_than_its_array_holds(gpu):
         jefi.jefi_eval_fields_noalloc(jefi.grid_from(src), obs, rho, J,
                                       jefi.default_params(dt=0.1), 4.0, E, B)
     assert e.value.code == jefi.JEFI_EUNSUPPORTED
+
+
+def test_noalloc_matches_the_oracle(gpu):
+    """Once against the FP64 CPU oracle directly (not only through jefi_eval_fields)."""
+    import torch
+
+    import oracle
+
+    rng = np.random.Generator(np.random.PCG64(5))
+    src = Grid((6, 5, 7), (-0.4, -0.3, -0.5), (0.13, 0.12, 0.14))
+    obs = rng.uniform(-1.5, 1.5, (300, 3))
+    case = _case(src, obs, [Blob(0.8, (0.2, 0.25, 0.2), (0.0, 0.1, -0.1), (0.2, -0.1, 0.0))],
+                 dt=0.06, n_slices=70, t=3.5, seed=3)
+    E, B = _noalloc(case)
+    rho, J = case["rho"].cpu().numpy(), case["J"].cpu().numpy()
+    Er, Br = oracle.fields(src.n, src.lo, src.d, obs, rho, J, dt=0.06, t=3.5)
+    assert _rel(E, torch.from_numpy(Er)) <= TOL
+    assert _rel(B, torch.from_numpy(Br)) <= TOL
+
+
+def test_noalloc_reports_a_missing_slice_then_recovers(gpu):
+    """A time whose pairs need slices past the given history returns
+    JEFI_ENOTYET (the kernel sets the status word); the next call with a
+    valid time returns OK, so the status word was cleared between calls."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(8))
+    src = Grid.cube(8, -0.5, 0.5)
+    obs = rng.uniform(-1.0, 1.0, (256, 3))
+    case = _case(src, obs, [Blob(1.0, (0.2, 0.2, 0.2), (0.0, 0.0, 0.0), (0.1, 0.1, 0.0))],
+                 dt=0.05, n_slices=40, t=1.8, seed=4)
+    E = torch.empty_like(case["E_ref"])
+    B = torch.empty_like(case["B_ref"])
+    g = jefi.grid_from(case["src"])
+    # slices 0..39 cover t <= 1.95; at t = 2.5 every pair closer than R = 0.5
+    # needs slice 40 or later, which was not given
+    with pytest.raises(jefi.JefiError) as e:
+        jefi.jefi_eval_fields_noalloc(g, case["obs"], case["rho"], case["J"], case["prm"], 2.5, E, B)
+    assert e.value.code == jefi.JEFI_ENOTYET
+    E2, B2 = _noalloc(case)                 # t = 1.8: every slice present
+    assert _rel(E2, case["E_ref"]) <= TOL
+    assert _rel(B2, case["B_ref"]) <= TOL
+
+
+def test_noalloc_rejects_grids_past_its_axis_limit(gpu):
+    """More than 6144 padded source cells over the three axes (the kernel's
+    shared-memory table of cell centres) is refused before any launch."""
+    import torch
+
+    src = Grid((6200, 1, 1), (0.0, 0.0, 0.0), (0.01, 0.1, 0.1))    # 4 * (1550 + 1 + 1) = 6208 padded
+    obs = torch.full((4, 3), 100.0, dtype=torch.float64, device="cuda")
+    rho = torch.zeros((2, src.size), dtype=torch.float64, device="cuda")
+    J = torch.zeros((2, src.size, 3), dtype=torch.float64, device="cuda")
+    E = torch.empty((4, 3), dtype=torch.float64, device="cuda")
+    B = torch.empty_like(E)
+    with pytest.raises(jefi.JefiError) as e:
+        jefi.jefi_eval_fields_noalloc(jefi.grid_from(src), obs, rho, J, jefi.default_params(dt=0.1), 1.0, E, B)
+    assert e.value.code == jefi.JEFI_EUNSUPPORTED
