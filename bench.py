@@ -168,7 +168,7 @@ def eval_times(lo, hi, k=8):
 def kernel_source_hash():
     """Hash of the sources of the dominant kernel (the staged FP32 sum)."""
     h = hashlib.sha256()
-    for f in ("jefi_staged.cu", "jefi_device.cuh"):
+    for f in ("jefi_staged.cuh", "jefi_staged.cu", "jefi_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2104_05426_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -346,10 +346,42 @@ def run_gpu(args):
                "B": float(torch.linalg.norm(B[0] - B64[0]) / torch.linalg.norm(B64[0]))}
         fp32c_kernel_pairs_s = pairs_launch / (sum_ms / 1e3)
         fp64_pairs_s = n_obs * n_src / (ms64 / 1e3)
+        fp64_peak = pipe_peak(n_sm, FP64_LANES_PER_SM, mhz)
+        fp64_ach = fp64_pairs_s * SUM_FP64_INSTR_PER_PAIR
         result["fp64_plain"] = {"value": fp64_pairs_s, "unit": UNIT, "kernel_ms": ms64,
                                 "fp32c_speedup_kernel": fp32c_kernel_pairs_s / fp64_pairs_s,
-                                "rel_l2_fp32c_vs_fp64_all_points": err}
+                                "rel_l2_fp32c_vs_fp64_all_points": err,
+                                "roofline": {"bound": "alu", "achieved": round(fp64_ach / 1e12, 4),
+                                             "peak": round(fp64_peak / 1e12, 4), "unit": "FP64 Tinstr/s",
+                                             "frac": round(fp64_ach / fp64_peak, 4),
+                                             "peak_basis": f"{n_sm} SMs x {FP64_LANES_PER_SM} FP64 lanes (DFMA "
+                                                           f"probe: 1.994 per SM per clock) x {mhz:.0f} MHz; "
+                                                           f"{SUM_FP64_INSTR_PER_PAIR} instructions per pair"}}
+        # plain FP32 (no compensation) on the same 8-time launch: what the
+        # compensation costs, and what it buys against the FP64 path
+        h32 = make("fp32", jefi.JEFI_FLAG_STATS, first_slice=next_slice - H)
+        for n in range(next_slice - H, next_slice):
+            jefi.jefi_push_sources(h32, *dev_slices[n])
+        ts_now = times_now(next_slice - 1)
+        jefi.jefi_eval_fields_multi(h32, ts_now, E, B)         # warm-up
+        jefi.jefi_reset_stats(h32)
+        for _ in range(3):
+            jefi.jefi_eval_fields_multi(h32, ts_now, E, B)
+        i32 = jefi.jefi_get_info(h32)
+        ms32 = i32["sum_ms_total"] / max(i32["sum_launches"], 1)
+        jefi.jefi_eval_fields_multi(h32, [tmid], E[:1], B[:1])
+        torch.cuda.synchronize()
+        err32 = {"E": float(torch.linalg.norm(E[0] - E64[0]) / torch.linalg.norm(E64[0])),
+                 "B": float(torch.linalg.norm(B[0] - B64[0]) / torch.linalg.norm(B64[0]))}
+        result["fp32_plain"] = {"value": pairs_launch / (ms32 / 1e3), "unit": UNIT, "kernel_ms": ms32,
+                                "compensation_cost": sum_ms / ms32 - 1.0,
+                                "rel_l2_fp32_vs_fp64_all_points": err32,
+                                "rel_l2_fp32c_vs_fp64_all_points": err,
+                                "note": "same 8-time launch without the Kahan step per brick"}
+        jefi.jefi_destroy(h32)
         jefi.jefi_destroy(h64)
+        result["so_decomposition"] = so_leg(p, dev_slices, next_slice, H, times_now(next_slice - 1)[n_t // 2],
+                                            E64[0], B64[0])
         # second-order retarded time (opt-in) on the same workload, 8 times per
         # launch: central differences read two slices past the slot, so the
         # handle holds two more slices and the times sit two slices back
@@ -374,7 +406,7 @@ def run_gpu(args):
         jefi.jefi_destroy(hi2)
         result["dipole"] = dipole_leg(dev)
         if not args.no_serving:
-            result["serving"] = serving_leg()
+            result["serving"], served = serving_leg()
             from paper_2104_05426_gb300.serving import measure_batch
 
             result["batch"] = dict(measure_batch(),
@@ -385,6 +417,11 @@ def run_gpu(args):
         if not args.no_cpu_baseline:
             result["cpu_baseline"], result["oracle_check"] = cpu_baseline(p, slices[:H], t_first,
                                                                           E_first, B_first)
+            if not args.no_serving:
+                try:
+                    result["serving"]["oracle_check"] = served_oracle_check(served, point_stride=31)
+                except Exception as e:      # a diagnostic: never lose the benchmark line to it
+                    result["serving"]["oracle_check_error"] = f"{type(e).__name__}: {e}"
             try:
                 result["oracle_check"]["configs"] = config_errors(dev)
             except Exception as e:      # a diagnostic: never lose the benchmark line to it
@@ -394,6 +431,46 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def so_leg(p, dev_slices, next_slice, H, t, E64, B64, parts=(2, 1, 1), reps=3):
+    """The paper's S-O decomposition (Sec. 2.2, Fig. 2) of the heavy-ion
+    workload on this one GPU: the source grid in `parts` brick-aligned boxes,
+    one handle per (box, all observation points) pair fed from the whole
+    grid's slices, the fields summed in box order by jefi_sum_fields.  Its
+    evaluation time against the whole problem's, and its FP64 fields against
+    the whole FP64 handle's."""
+    import torch
+
+    import paper_2104_05426_gb300 as jefi
+    from paper_2104_05426_gb300.decomp import SODecomposition
+
+    g = jefi.grid_from(p.src)
+    prm = dict(c=p.c, k_e=p.k_e, k_b=p.k_b, dt=p.dt, t0=p.t0 + (next_slice - H) * p.dt, history_slots=H)
+    out = {"parts": list(parts), "workload": "heavy-ion source grid in brick-aligned boxes, all observers"}
+    for prec in ("fp32c", "fp64"):
+        so = SODecomposition(g, p.obs_grid.points(), dict(prm, precision=prec, flags=jefi.JEFI_FLAG_STATS),
+                             src_parts=parts, torch_allocator=True)
+        for n in range(next_slice - H, next_slice):
+            so.push(*dev_slices[n])
+        n_rep = reps if prec == "fp32c" else 1           # FP64: one evaluation (its accuracy only)
+        if prec == "fp32c":
+            so.fields(t)                                 # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n_rep):
+            E, B = so.fields(t)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n_rep
+        out[prec] = {"ms_per_eval": ms, "pairs_per_s": p.n_obs * p.src.size / (ms / 1e3),
+                     "rel_l2_vs_whole_fp64": {
+                         "E": float(torch.linalg.norm(E - E64) / torch.linalg.norm(E64)),
+                         "B": float(torch.linalg.norm(B - B64) / torch.linalg.norm(B64))}}
+        so.close()
+    return out
 
 
 def dipole_leg(dev, reps=5):
@@ -453,12 +530,14 @@ def dipole_leg(dev, reps=5):
     return out
 
 
-def serving_leg(n_problems=16, n_requests=600, seed=11, tick_s=0.02):
+def serving_leg(n_problems=16, n_requests=600, seed=11, tick_s=0.02, n_samples=6):
     """Continuous batching of Poisson-arriving requests against resident
     problems (source sides 16-48, histories 64-128 slices, observation sides
     8-48, one slice pushed to every problem per tick): saturated throughput
-    first (all requests at once), then p50/p99 latency at 0.8x that rate."""
-    from paper_2104_05426_gb300.serving import ServingEngine, make_problems, poisson_requests
+    first (all requests at once), then p50/p99 latency at 0.8x that rate.
+    Returns the figures and a seeded sample of served requests (kept for the
+    oracle check)."""
+    from paper_2104_05426_gb300.serving import ServingEngine, make_problems, poisson_requests, served_sample
 
     probs = make_problems(n_problems, seed, sides=(16, 48), H_range=(64, 128))
     sides = [8, 16, 24, 32, 40, 48]
@@ -467,18 +546,52 @@ def serving_leg(n_problems=16, n_requests=600, seed=11, tick_s=0.02):
                                    side_choices=sides))
     rate = 0.8 * sat.requests_per_s
     eng.tick_s = tick_s
-    st = eng.run(poisson_requests(n_requests, rate=rate, n_problems=n_problems, seed=seed + 2,
-                                  side_choices=sides))
+    reqs = poisson_requests(n_requests, rate=rate, n_problems=n_problems, seed=seed + 2, side_choices=sides)
+    eng.keep_ids = {int(k) for k in np.random.Generator(np.random.PCG64(seed + 3)).choice(
+        n_requests, n_samples, replace=False)}
+    st = eng.run(reqs)
+    samples = [served_sample(eng, r) for r in reqs if r.rid in eng.keep_ids and not r.error]
     eng.close()
     return {"p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
             "offered_requests_per_s": rate, "requests_per_s": st.requests_per_s,
             "pairs_per_s": st.pairs_per_s, "saturated_requests_per_s": sat.requests_per_s,
             "saturated_pairs_per_s": sat.pairs_per_s, "completed": st.completed,
-            "rejected": st.rejected, "mean_batch": st.mean_batch, "max_batch": st.max_batch,
+            "rejected": st.rejected, "evicted": st.evicted, "failed": st.failed,
+            "mean_batch": st.mean_batch, "max_batch": st.max_batch,
             "peak_device_bytes": st.peak_bytes,
             "workload": f"{n_problems} resident problems, {n_requests} Poisson requests at 0.8x "
                         f"saturation, obs sides {sides}, slice push every {tick_s * 1e3:.0f} ms, "
-                        "compensated FP32"}
+                        "compensated FP32"}, samples
+
+
+def served_oracle_check(samples, point_stride=1):
+    """Served requests recomputed by the FP64 CPU oracle from the same source
+    model (slice n at n dt), on every point_stride-th observation point:
+    rel-L2 per field, worst over the sample."""
+    import oracle
+    from workloads import Grid, MovingGaussians
+
+    worst = {"E": 0.0, "B": 0.0}
+    pairs = 0
+    t_start = time.perf_counter()
+    for sm in samples:
+        src = Grid.cube(sm["src_side"], -sm["src_half_width"], sm["src_half_width"])
+        obs_all = Grid.cube(sm["obs_side"], -sm["obs_half_width"], sm["obs_half_width"]).points()
+        idx = np.arange(0, len(obs_all), point_stride)
+        dt, t = sm["dt"], sm["t"]
+        model = MovingGaussians(sm["blobs"])
+        rmax = math.sqrt(3.0) * (sm["src_half_width"] + sm["obs_half_width"])
+        n_lo = max(0, int(math.floor((t - rmax) / dt)) - 2)
+        n_hi = min(sm["n_pushed"] - 1, int(math.ceil(t / dt)) + 1)
+        hist = [model.sample(src, n * dt) for n in range(n_lo, n_hi + 1)]
+        rho = np.stack([h[0] for h in hist])
+        J = np.stack([h[1] for h in hist])
+        Er, Br = oracle.fields(src.n, src.lo, src.d, obs_all[idx], rho, J, dt=dt, t0=n_lo * dt, t=t)
+        for k, got, ref in (("E", sm["E"][idx], Er), ("B", sm["B"][idx], Br)):
+            worst[k] = max(worst[k], float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        pairs += len(idx) * src.size
+    return {"requests": len(samples), "point_stride": point_stride, "pairs": pairs,
+            "rel_l2_worst": worst, "seconds": time.perf_counter() - t_start}
 
 
 def cpu_baseline(p, slices, times, E_gpu, B_gpu, stride=512):
@@ -699,6 +812,11 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and oracle legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-c5", action="store_true",
+                    help="only run the serving configuration (64 problems, --serving-requests per load "
+                         "level at 0.5/0.8/1.0x saturation, 64 GB budget) with an oracle check of a "
+                         "sample of served requests, and print it")
+    ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--paper-tables", action="store_true",
                     help="only time the paper's own workloads (Tables 2 and 4) and print them")
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp32", "fp64"],
@@ -712,6 +830,12 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.paper_tables:
         print(json.dumps(paper_tables()))
+    elif args.serving_c5:
+        from paper_2104_05426_gb300.serving import measure
+
+        res, samples = measure(n_requests=args.serving_requests, n_samples=8)
+        res["oracle_check"] = served_oracle_check(samples, point_stride=31)
+        print(json.dumps(res))
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -90,8 +90,10 @@ typedef struct {
     double dt;                /* slice spacing, > 0                                 */
     double t0;                /* time of slice 0                                    */
     int32_t history_slots;    /* H: resident slices in the device ring, >= 1 (FP32
-                                 problems on the direct-gather kernel: H + 49 <=
-                                 65536, else jefi_create returns JEFI_EUNSUPPORTED) */
+                                 problems on the direct-gather kernel: the ring's
+                                 rows, P + mirror + 4 with P = H rounded up to a
+                                 multiple of 4, at most 65536, else jefi_create
+                                 returns JEFI_EUNSUPPORTED)                       */
     int32_t precision;        /* jefi_precision                                     */
     int32_t deriv;            /* jefi_deriv_mode                                    */
     int32_t flags;            /* JEFI_FLAG_* bits                                   */
@@ -99,7 +101,31 @@ typedef struct {
     jefi_alloc_fn alloc;
     jefi_free_fn free;
     void* alloc_ctx;
+    /* First cell of the source grid in its lattice: cell i of axis a is
+     * centred at lo[a] + (src_origin[a] + i + 0.5) d[a].  0 for a grid of
+     * its own; a source sub-box of a larger grid (an S-O pair, paper Sec. 2.2,
+     * Fig. 2; see jefi_so_partition) keeps the large grid's lo and d and
+     * names its first cell here, so its cell centres are bit-identical to the
+     * large grid's. */
+    int32_t src_origin[3];
+    /* Observation grids only: the shape of the 256-point tiles one CTA
+     * evaluates, JEFI_TILE_8x8x4 ... JEFI_TILE_4x4x16, or JEFI_TILE_AUTO (0):
+     * for FP32 problems the shape whose widest tile spans the narrowest range
+     * of pair distances (the slot band the staged kernel copies), else
+     * 8x8x4.  Point lists are tiled in Morton order (or by distance from the
+     * sources when that narrows the bands clearly). */
+    int32_t tile_shape;
 } jefi_params;
+
+#define JEFI_TILE_AUTO 0
+#define JEFI_TILE_8x8x4 1
+#define JEFI_TILE_16x4x4 2
+#define JEFI_TILE_4x8x8 3
+#define JEFI_TILE_8x4x8 4
+#define JEFI_TILE_4x16x4 5
+#define JEFI_TILE_16x8x2 6
+#define JEFI_TILE_8x16x2 7
+#define JEFI_TILE_4x4x16 8
 
 #define JEFI_FLAG_STATS 1u    /* time the sum kernel with CUDA events on the call's stream */
 #define JEFI_FLAG_DIRECT_GATHER 2u  /* FP32: never use the TMA-staged kernel (for comparisons) */
@@ -114,10 +140,9 @@ typedef struct {
  * written when slice k+1 is pushed).  Slices before the first are zero,
  * values and derivatives alike.  An evaluation needs slices up to n+1
  * (supplied) or n+2 (central) to be pushed: the valid window ends one or two
- * slices earlier than with the floor rule.  Every single-handle path
- * (FP64, FP32 staged and direct gather) supports it; jefi_eval_batch returns
- * JEFI_EUNSUPPORTED for such handles; a view inherits the setting of its
- * base. */
+ * slices earlier than with the floor rule.  Every path supports it (FP64,
+ * FP32 staged and direct gather, single, batched and planned evaluations; a
+ * batch may mix both rules); a view inherits the setting of its base. */
 #define JEFI_FLAG_INTERP 8u
 
 /* Fills p with: c = 1, k_e = k_b = 1, dt = 1, t0 = 0, H = 64, FP32_COMP,
@@ -231,6 +256,8 @@ typedef struct {
     int32_t device_status;    /* first error a kernel reported (0 = none), sticky  */
     int32_t staged_band;      /* FP32 sum kernel: history rows staged per cell by
                                  TMA, or 0 for the direct-gather kernel            */
+    int32_t tile_shape;       /* observation grids: the JEFI_TILE_* shape of the
+                                 256-point tiles; 0 for point lists               */
 } jefi_info;
 
 /* Fills *out (waits for the handle's outstanding work).  Kernel-side errors
@@ -264,6 +291,49 @@ int jefi_debug_wait_timeout(double limit_s, void* stream);
  */
 void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double t, double t0,
                           double c, double dt, int64_t* out);
+
+/*
+ * Push one slice given as a region of larger arrays: rho, J (and drho, dJ
+ * when supplied) cover full_n[0] x full_n[1] x full_n[2] cells, x fastest,
+ * and the handle's cell (i, j, k) is their cell offset + (i, j, k).  The
+ * source side of an S-O pair (paper Sec. 2.2, Fig. 2) pushes its sub-box
+ * straight from the whole grid's slice this way.  offset + the handle's grid
+ * extents must lie within full_n (JEFI_EINVAL otherwise).  Otherwise as
+ * jefi_push_sources; host arrays (on_device = 0) are gathered on the host
+ * and the call returns once they have been copied.
+ */
+int jefi_push_sources_region(jefi_handle h, const double* rho, const double* J, const double* drho,
+                             const double* dJ, const int32_t full_n[3], const int32_t offset[3], int on_device,
+                             void* stream);
+
+/*
+ * Source/observation (S-O) decomposition (paper Sec. 2.2, Fig. 2: the source
+ * and observation regions are cut into rectangular sub-boxes and every pair
+ * of a source box and an observation box is evaluated on its own, e.g. one
+ * pair per GPU; the fields of the pairs that share an observation box add).
+ *
+ * jefi_so_partition cuts the source grid into parts[0] x parts[1] x parts[2]
+ * boxes along whole 4-cell bricks (box k = (kz parts[1] + ky) parts[0] + kx,
+ * x fastest; a box may be empty when there are fewer bricks than parts).
+ * Box k is sub[k] with origin[3k .. 3k+2]: sub[k] keeps src's lo and d and
+ * its first cell is src cell origin[3k + a] -- create its handle with
+ * jefi_params.src_origin = that origin so its cell centres are bit-identical
+ * to src's, and push its slices with jefi_push_sources_region.  sub holds
+ * parts[0] parts[1] parts[2] grids and origin three times as many int32.
+ * Host-only; JEFI_EINVAL for parts outside [1, 4096].
+ */
+int jefi_so_partition(const jefi_grid* src, const int32_t parts[3], jefi_grid* sub, int32_t* origin);
+
+/*
+ * E = E_parts[0] + E_parts[1] + ... and the same for B, summed in FP64 in
+ * that order, element by element over n_obs points ([n_obs][3] device
+ * arrays, caller-owned): the fields of S-O pairs that share their
+ * observation points, summed in source-box order whatever the number of
+ * ranks that produced them (deterministic).  1 <= n_parts <= 64; enqueued
+ * on `stream`.
+ */
+int jefi_sum_fields(int32_t n_parts, const double* const* E_parts, const double* const* B_parts, int64_t n_obs,
+                    double* E, double* B, void* stream);
 
 /*
  * One-shot FP64 evaluation that allocates no device memory.  The paper has
@@ -339,9 +409,11 @@ int jefi_restore(jefi_handle h, const void* src, size_t bytes, void* stream);
  * be the faster (Eqs. E-1, B-1, tr-1 are computed the same way by both:
  * identical slots, fields equal to FP32 rounding, not bit for bit).
  *
- * mode JEFI_KERNEL_MEASURE: time one evaluation at t with each kernel (after
- *   one untimed evaluation each, so four in all) and keep the faster; t must
- *   be in the valid window.  The call synchronises `stream`.
+ * mode JEFI_KERNEL_MEASURE: time one evaluation at t with each candidate --
+ *   the staged band of creation, the next wider compiled band when the
+ *   ring's mirror holds it (other stages, other shared-memory layout) and
+ *   the direct gather -- after one untimed evaluation each, and keep the
+ *   fastest; t must be in the valid window.  The call synchronises `stream`.
  * mode JEFI_KERNEL_DIRECT: switch to the direct gather (t unused).
  * mode JEFI_KERNEL_STAGED: switch back to the staged kernel of creation (t
  *   unused).
@@ -377,8 +449,8 @@ int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_ba
  * the copy and the reduction (their work items are independent), so one
  * variant's first items can run beside another's last ones.  A handle may
  * appear up to 8 times (a view up to 2 times), as in jefi_eval_batch; FP64,
- * FP32 and compensated FP32 handles mix freely; handles with
- * JEFI_FLAG_INTERP give JEFI_EUNSUPPORTED.
+ * FP32 and compensated FP32 handles mix freely, with and without
+ * JEFI_FLAG_INTERP.
  *
  * jefi_batch_plan_launch evaluates problem i at t[i] (host array [n]):
  * checks every time against its handle's window (JEFI_ENOTYET /
@@ -399,15 +471,28 @@ int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_ba
  *     another (decided first, then kept for the candidates below);
  *   - kernel choice per problem: the handles' current choice, and the one
  *     jefi_select_kernel(JEFI_KERNEL_MEASURE) makes for each FP32 handle
- *     that has both kernels (staged band vs direct gather);
+ *     that has alternatives (staged band of creation, the next wider
+ *     compiled band, direct gather);
  *   - source splits per observation tile (the work-item shape): every
  *     handle's creation-time split count divided by 1, 2, 4 or 8 (a batch
  *     fills the GPU with many problems, so fewer and larger items can win).
+ * (The observation tile shape is the third work-item dimension; it is
+ * chosen when a handle is created, see jefi_params.tile_shape.)
  * The choice stays with the handles: later single, batched and planned
  * evaluations use it.  Fields then differ from the untuned ones at the
  * rounding level of the precision (the split sums change), still within
  * the accuracy contract.  `report` (may be NULL) receives what was tried
  * and kept.  The call synchronises `stream`.
+ *
+ * Tune cache: when the environment variable JEFI_TUNE_CACHE names a file,
+ * the tuner first looks there for the plan's key (a hash of every entry's
+ * geometry -- source grid and origin, observation points, history, dt, c,
+ * precision, derivative rule, creation bands and splits -- and the
+ * device's SM count).  On a hit it applies the stored choice (branches,
+ * per-problem kernel, split divisor), times it once and returns with
+ * from_cache = 1; otherwise it tunes and appends one line with the choice.
+ * The file is plain text, one line per plan; an unreadable or malformed
+ * file counts as a miss.
  *
  * jefi_batch_plan_destroy waits for the plan's launches and frees it.
  * Destroy every plan before the handles it holds: jefi_destroy of a handle
@@ -427,6 +512,8 @@ typedef struct {
                                  branches, 0 = one after another                   */
     double ms_initial;        /* device time of one launch as the handles were       */
     double ms_tuned;          /* device time of one launch as kept                   */
+    int32_t from_cache;       /* 1: the choice came from the JEFI_TUNE_CACHE file    */
+    int32_t widened_bands;    /* batch entries kept on the wider staged band         */
 } jefi_tune_report;
 
 int jefi_batch_plan_create(const jefi_handle* hs, double* const* E, double* const* B, int32_t n,

@@ -50,6 +50,10 @@ JEFI_KERNEL_MEASURE = 0
 JEFI_KERNEL_DIRECT = 1
 JEFI_KERNEL_STAGED = 2
 
+# Observation-grid tile shapes (points per tile along x, y, z); 0 = chosen at creation
+TILE_SHAPES = {0: None, 1: (8, 8, 4), 2: (16, 4, 4), 3: (4, 8, 8), 4: (8, 4, 8), 5: (4, 16, 4),
+               6: (16, 8, 2), 7: (8, 16, 2), 8: (4, 4, 16)}
+
 PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 
 # Every symbol include/jefi.h declares (checked by the CPU test suite).
@@ -59,7 +63,8 @@ EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval
            "jefi_eval_fields_noalloc", "jefi_eval_batch", "jefi_create_view",
            "jefi_debug_wait_timeout", "jefi_checkpoint_bytes", "jefi_checkpoint", "jefi_restore",
            "jefi_select_kernel", "jefi_batch_plan_create", "jefi_batch_plan_launch",
-           "jefi_batch_plan_tune", "jefi_batch_plan_destroy")
+           "jefi_batch_plan_tune", "jefi_batch_plan_destroy", "jefi_push_sources_region",
+           "jefi_so_partition", "jefi_sum_fields")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -84,7 +89,8 @@ class jefi_params(ctypes.Structure):
                 ("history_slots", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("deriv", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("screen", ctypes.c_double * 3),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("src_origin", ctypes.c_int32 * 3), ("tile_shape", ctypes.c_int32)]
 
 
 class jefi_info(ctypes.Structure):
@@ -93,7 +99,8 @@ class jefi_info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("slot_fallbacks", ctypes.c_int64),
                 ("sum_launches", ctypes.c_int64), ("sum_ms_total", ctypes.c_double),
                 ("n_split", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("device_status", ctypes.c_int32), ("staged_band", ctypes.c_int32)]
+                ("device_status", ctypes.c_int32), ("staged_band", ctypes.c_int32),
+                ("tile_shape", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -103,7 +110,8 @@ class jefi_tune_report(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int32), ("split_divisor", ctypes.c_int32),
                 ("measured_kernels", ctypes.c_int32), ("staged_problems", ctypes.c_int32),
                 ("concurrent_groups", ctypes.c_int32),
-                ("ms_initial", ctypes.c_double), ("ms_tuned", ctypes.c_double)]
+                ("ms_initial", ctypes.c_double), ("ms_tuned", ctypes.c_double),
+                ("from_cache", ctypes.c_int32), ("widened_bands", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -165,6 +173,13 @@ def load(build_if_needed: bool = True):
         for name in ("jefi_batch_plan_create", "jefi_batch_plan_launch", "jefi_batch_plan_tune",
                      "jefi_batch_plan_destroy"):
             getattr(L, name).restype = I
+        L.jefi_push_sources_region.argtypes = [P, P, P, P, P, ctypes.POINTER(I32), ctypes.POINTER(I32), I, P]
+        L.jefi_push_sources_region.restype = I
+        L.jefi_so_partition.argtypes = [ctypes.POINTER(jefi_grid), ctypes.POINTER(I32), ctypes.POINTER(jefi_grid),
+                                        ctypes.POINTER(I32)]
+        L.jefi_so_partition.restype = I
+        L.jefi_sum_fields.argtypes = [I32, P, P, I64, P, P, P]
+        L.jefi_sum_fields.restype = I
         L.jefi_strerror.argtypes = [I]
         L.jefi_strerror.restype = ctypes.c_char_p
         for name in ("jefi_create", "jefi_push_sources", "jefi_eval_fields",
@@ -211,6 +226,10 @@ def default_params(**kw) -> jefi_params:
         if k == "screen":
             for a in range(3):
                 p.screen[a] = float(v[a])
+            continue
+        if k == "src_origin":
+            for a in range(3):
+                p.src_origin[a] = int(v[a])
             continue
         setattr(p, k, v)
     return p
@@ -315,6 +334,66 @@ def jefi_push_sources(h: Handle, rho, J, drho_dt=None, dJ_dt=None, stream=None):
         raise ValueError("rho and J must both be host or both device buffers")
     rc = load().jefi_push_sources(h.ptr, r, j, dr, dj, 1 if on_dev else 0, _stream_ptr(stream))
     _check(rc, "jefi_push_sources")
+
+
+def jefi_push_sources_region(h: Handle, rho, J, full_n, offset, drho_dt=None, dJ_dt=None, stream=None):
+    """Push one slice whose arrays cover the grid full_n (x fastest); the
+    handle's cell (i, j, k) is their cell offset + (i, j, k)."""
+    r, on_dev, k1 = _buf(rho)
+    j, on_dev_j, k2 = _buf(J)
+    dr, _, k3 = _buf(drho_dt)
+    dj, _, k4 = _buf(dJ_dt)
+    if on_dev_j is not None and on_dev is not None and on_dev != on_dev_j:
+        raise ValueError("rho and J must both be host or both device buffers")
+    n_full = int(full_n[0]) * int(full_n[1]) * int(full_n[2])
+    for name, x, per in (("rho", rho, 1), ("J", J, 3), ("drho_dt", drho_dt, 1), ("dJ_dt", dJ_dt, 3)):
+        if x is not None and int(np.prod(x.shape)) != per * n_full:
+            raise ValueError(f"{name} must hold {per} x {n_full} values for the grid {tuple(full_n)}")
+    fn = (ctypes.c_int32 * 3)(*[int(v) for v in full_n])
+    off = (ctypes.c_int32 * 3)(*[int(v) for v in offset])
+    rc = load().jefi_push_sources_region(h.ptr, r, j, dr, dj, fn, off, 1 if on_dev else 0, _stream_ptr(stream))
+    _check(rc, "jefi_push_sources_region")
+
+
+def jefi_so_partition(src: jefi_grid, parts):
+    """The source grid cut into parts[0] x parts[1] x parts[2] brick-aligned
+    boxes (x fastest): a list of (sub-grid, origin) -- create each box's
+    handle with default_params(..., src_origin=origin)."""
+    n = int(parts[0]) * int(parts[1]) * int(parts[2])
+    if n < 1:
+        raise ValueError("parts must be positive")
+    sub = (jefi_grid * n)()
+    org = (ctypes.c_int32 * (3 * n))()
+    p = (ctypes.c_int32 * 3)(*[int(v) for v in parts])
+    _check(load().jefi_so_partition(ctypes.byref(src), p, sub, org), "jefi_so_partition")
+    return [(sub[k], (org[3 * k], org[3 * k + 1], org[3 * k + 2])) for k in range(n)]
+
+
+def jefi_sum_fields(E_parts, B_parts, E, B, stream=None):
+    """E = E_parts[0] + E_parts[1] + ... (FP64, in list order), the same for
+    B; all CUDA float64 tensors of one shape [n_obs, 3]."""
+    n = len(E_parts)
+    if n != len(B_parts) or n < 1:
+        raise ValueError("E_parts and B_parts must be non-empty lists of the same length")
+    shape = tuple(E.shape)
+    ptrs_e, ptrs_b = [], []
+    for x in list(E_parts) + list(B_parts) + [E, B]:
+        if tuple(x.shape) != shape:
+            raise ValueError(f"every field array must have the shape {shape}")
+    for x_list, ptrs in ((E_parts, ptrs_e), (B_parts, ptrs_b)):
+        for x in x_list:
+            p, on_dev, _ = _buf(x)
+            if not on_dev:
+                raise ValueError("jefi_sum_fields takes device (CUDA) tensors only")
+            ptrs.append(p)
+    e, on_e, _ = _buf(E)
+    bb, on_b, _ = _buf(B)
+    if not (on_e and on_b):
+        raise ValueError("jefi_sum_fields takes device (CUDA) tensors only")
+    pe = (ctypes.c_void_p * n)(*ptrs_e)
+    pb = (ctypes.c_void_p * n)(*ptrs_b)
+    n_obs = int(np.prod(shape)) // 3
+    _check(load().jefi_sum_fields(n, pe, pb, n_obs, e, bb, _stream_ptr(stream)), "jefi_sum_fields")
 
 
 def jefi_eval_fields(h: Handle, t: float, E, B, stream=None):

@@ -26,9 +26,10 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
              "-I" + INCLUDE, "-I" + CSRC, "-I" + os.path.join(CUDA_HOME, "include")]
 
-CU_SOURCES = ["jefi_kernels.cu", "jefi_staged.cu", "jefi_noalloc.cu"]
+CU_SOURCES = ["jefi_kernels.cu", "jefi_staged.cu", "jefi_staged_b32_48.cu", "jefi_staged_b64_96.cu",
+              "jefi_noalloc.cu"]
 CXX_SOURCES = ["jefi_host.cpp"]
-HEADERS = ["jefi_internal.h", "jefi_device.cuh"]
+HEADERS = ["jefi_internal.h", "jefi_device.cuh", "jefi_staged.cuh"]
 _lock = threading.Lock()
 
 

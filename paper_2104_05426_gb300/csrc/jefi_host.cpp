@@ -15,6 +15,8 @@
 #include <climits>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -108,9 +110,9 @@ struct AxisInfo {
 
 // Per-axis extremes of one observation coordinate against source centres
 // j in [0, nlim) (monotone: D(j) = xo - x_j is non-increasing in j).
-AxisInfo axis_info(double xo, double lo, double d, int64_t nlim, int64_t npad, double delta) {
+AxisInfo axis_info(double xo, double lo, double d, int64_t org, int64_t nlim, int64_t npad, double delta) {
     AxisInfo r;
-    auto D = [&](int64_t j) { return xo - center(lo, d, j); };
+    auto D = [&](int64_t j) { return xo - center(lo, d, org + j); };
     // screening range over the padded index space [0, npad)
     int64_t a = 0, b = npad;  // first j with D(j) <= delta
     while (a < b) {
@@ -173,6 +175,18 @@ void fold(Extremes& e, const AxisInfo (&ax)[3]) {
 }
 
 // Morton key of a point quantised to 21 bits per axis inside [lo, hi].
+constexpr uint64_t kFnvBasis = 1469598103934665603ull;
+
+// FNV-1a hash of n bytes, continuing from h.
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
 uint64_t morton(const double* p, const double* lo, const double* hi) {
     uint64_t key = 0;
     uint32_t q[3];
@@ -193,7 +207,7 @@ bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]
 // source spacing are integer multiples of one power of two q, small enough that
 // the FP32 kernel's squared-distance chain (anchor offsets, brick offsets,
 // differences, squares and their sums) is exact: then S32 == S64 for every pair.
-bool exact_lattice(const std::vector<double>& obs_xyz, const jefi_grid& src, const int64_t* npad) {
+bool exact_lattice(const std::vector<double>& obs_xyz, const jefi_grid& src, const int32_t* org, const int64_t* npad) {
     std::vector<double> vals(obs_xyz);
     double lo[3], hi[3], olo[3] = {INFINITY, INFINITY, INFINITY}, ohi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (size_t i = 0; i < obs_xyz.size(); ++i) {
@@ -202,9 +216,9 @@ bool exact_lattice(const std::vector<double>& obs_xyz, const jefi_grid& src, con
     }
     for (int a = 0; a < 3; ++a) {
         vals.push_back(src.d[a]);
-        for (int64_t j = 0; j < npad[a]; ++j) vals.push_back(center(src.lo[a], src.d[a], j));
-        lo[a] = center(src.lo[a], src.d[a], 0);
-        hi[a] = center(src.lo[a], src.d[a], npad[a] - 1);
+        for (int64_t j = 0; j < npad[a]; ++j) vals.push_back(center(src.lo[a], src.d[a], org[a] + j));
+        lo[a] = center(src.lo[a], src.d[a], org[a]);
+        hi[a] = center(src.lo[a], src.d[a], org[a] + npad[a] - 1);
     }
     int e = -40;
     for (; e <= 60; ++e) {
@@ -227,6 +241,82 @@ bool exact_lattice(const std::vector<double>& obs_xyz, const jefi_grid& src, con
 }  // namespace
 
 // ============================================================================ handle
+namespace {
+
+// Centre O of the source grid, the farthest (brick-padded) cell centre from
+// it, and the diagonal of one brick's cell centres: the source-side terms of
+// the staged kernel's band bounds.
+void source_shell(const jefi_grid& src, const int32_t* org, const int64_t* npad, double* O, double* r_src,
+                  double* db) {
+    double r2 = 0, d2 = 0;
+    for (int a = 0; a < 3; ++a) {
+        O[a] = src.lo[a] + (org[a] + 0.5 * src.n[a]) * src.d[a];
+        const double far = std::max(std::fabs(center(src.lo[a], src.d[a], org[a]) - O[a]),
+                                    std::fabs(center(src.lo[a], src.d[a], org[a] + npad[a] - 1) - O[a]));
+        r2 += far * far;
+        d2 += 9.0 * src.d[a] * src.d[a];
+    }
+    *r_src = std::sqrt(r2);
+    *db = std::sqrt(d2);
+}
+
+// Widest pair-distance range over the tiles of `order` (256 entries per
+// tile, -1 = padding): per tile the tighter of the box bound (the tile box's
+// diagonal plus a brick's) and the shell bound (the range of the tile's
+// distances from O plus twice the farthest source cell from O).
+double tiles_extent(const std::vector<int64_t>& order, const double* pts, const double* O, double r_src, double db) {
+    double ext_max = 0;
+    for (size_t t0 = 0; t0 < order.size(); t0 += kTileThreads) {
+        double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        double rho_lo = INFINITY, rho_hi = 0;
+        for (size_t s = t0; s < t0 + kTileThreads && s < order.size(); ++s) {
+            if (order[s] < 0) continue;
+            const double* x = pts + 3 * order[s];
+            double r2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = std::min(mn[a], x[a]);
+                mx[a] = std::max(mx[a], x[a]);
+                r2 += (x[a] - O[a]) * (x[a] - O[a]);
+            }
+            rho_lo = std::min(rho_lo, std::sqrt(r2));
+            rho_hi = std::max(rho_hi, std::sqrt(r2));
+        }
+        if (!(rho_hi >= rho_lo)) continue;
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) d2 += (mx[a] - mn[a]) * (mx[a] - mn[a]);
+        ext_max = std::max(ext_max, std::min(std::sqrt(d2) + db, (rho_hi - rho_lo) + 2 * r_src));
+    }
+    return ext_max;
+}
+
+// Tile shapes of observation grids (points per tile along x, y, z; each a
+// whole number of 4x4x2-point warps, 256 points): index 1..8, 0 = chosen at
+// creation.  A tile's warps are laid out x fastest, then y, then z.
+constexpr int kTileShapes[9][3] = {{0, 0, 0}, {8, 8, 4}, {16, 4, 4}, {4, 8, 8}, {8, 4, 8},
+                                   {4, 16, 4}, {16, 8, 2}, {8, 16, 2}, {4, 4, 16}};
+constexpr int kNumTileShapes = 8;
+
+// Observation order of a gx x gy x gz grid in tiles of shape s: tile slot ->
+// point index (x fastest), -1 for padding.
+void grid_tile_order(int64_t gx, int64_t gy, int64_t gz, int s, std::vector<int64_t>& order) {
+    const int sx = kTileShapes[s][0], sy = kTileShapes[s][1], sz = kTileShapes[s][2];
+    const int wx = sx / 4, wy = sy / 4;
+    const int64_t tx = (gx + sx - 1) / sx, ty = (gy + sy - 1) / sy, tz = (gz + sz - 1) / sz;
+    order.assign((size_t)(tx * ty * tz) * kTileThreads, -1);
+    for (int64_t tile = 0; tile < tx * ty * tz; ++tile) {
+        const int64_t bx = tile % tx, by = (tile / tx) % ty, bz = tile / (tx * ty);
+        for (int tid = 0; tid < kTileThreads; ++tid) {
+            const int w = tid >> 5, l = tid & 31;
+            const int64_t i = sx * bx + 4 * (w % wx) + (l & 3);
+            const int64_t j = sy * by + 4 * ((w / wx) % wy) + ((l >> 2) & 3);
+            const int64_t k = sz * bz + 2 * (w / (wx * wy)) + (l >> 4);
+            if (i < gx && j < gy && k < gz) order[tile * kTileThreads + tid] = (k * gy + j) * gx + i;
+        }
+    }
+}
+
+}  // namespace
+
 struct jefi_problem {
     jefi_params prm{};
     jefi_grid src{};
@@ -235,6 +325,10 @@ struct jefi_problem {
     int64_t n_src = 0, n_obs = 0;
     int32_t n_slots = 0, n_tiles = 0;
     int32_t H = 0, Hp = 0;
+    int32_t P = 0;                   // ring period: H rounded up to a multiple of 4
+    int32_t org[3] = {0, 0, 0};      // first source cell in the source lattice (jefi_params.src_origin)
+    int32_t tile_shape = 0;          // observation-grid tile shape (kTileShapes index; 0: point list)
+    uint64_t obs_sig = 0;            // hash of the observation points in tile order (tune cache key)
     double screen[3] = {0, 0, 0};
     int64_t n_latest = -1;
     int32_t n_split = 1, bricks_per_split = 0;
@@ -275,6 +369,8 @@ struct jefi_problem {
     // staged FP32 kernel (0 = direct-gather kernel)
     int32_t band = 0;
     int32_t band0 = 0;               // the staged band chosen at creation (0: none)
+    int32_t band_alt = 0;            // the next wider compiled band the ring's mirror allows (0: none)
+    int32_t tmap_band = 0;           // the band the tensor map was encoded for
     int32_t mirror = 0;              // M: mirrored ring slots
     bool exact = false;              // lattice geometry: S32 == S64
     double g_bias = 0;               // bound on the FP32 candidate error (slots)
@@ -384,8 +480,8 @@ int mark_use(jefi_problem* h, cudaStream_t s) {
 }
 
 int64_t phys_slot(const jefi_problem* h, int64_t k) {
-    if (k < 0 || k > h->n_latest || k < h->n_latest - h->H + 1) return h->H + h->mirror;  // zero slot
-    return k % h->H;
+    if (k < 0 || k > h->n_latest || k < h->n_latest - h->H + 1) return h->P + h->mirror;  // zero slot
+    return k % h->P;
 }
 
 // Slices past a pair's slot n that an evaluation reads: 0 (floor rule),
@@ -514,23 +610,59 @@ void build_tables(jefi_problem* h, int ti, double t) {
     h->h_times[ti] = tp;
 }
 
-// TMA descriptor over the FP32 ring [cells][Hp][8]: box = 8 channels x band
-// slots x one brick of 64 cells.
+// TMA descriptor over the FP32 ring.  Narrow bands: the ring as [cells][Hp][8]
+// floats, box = 8 channels x band slots x the stage's cells, dense rows.
+// Swizzled bands: the ring as [cells][Hp/4][32] floats (128-byte lines of 4
+// slots), box = one line x band/4 lines x the stage's cells, 128-byte
+// swizzle.  Before any launch the box is checked against the stage buffer it
+// lands in: the bytes it writes must equal the buffer's size (the kernel
+// waits for exactly that many) and a swizzled box's inner extent must be the
+// full 128-byte swizzle span (a narrower one would not land densely).
+// JEFI_EINTERNAL otherwise.
 int make_tensor_map(jefi_problem* h) {
+    const bool swz = staged_swizzled(h->band);
+    const cuuint32_t box_inner = swz ? 32 : 8;                      // floats
+    const cuuint32_t box_rows = swz ? (cuuint32_t)h->band / 4 : (cuuint32_t)h->band;
+    const cuuint32_t box_cells = (cuuint32_t)staged_stage_cells(h->band);
+    const size_t landed = (size_t)box_inner * sizeof(float) * box_rows * box_cells;
+    if (landed != staged_buffer_bytes(h->band) || (swz && box_inner * sizeof(float) != 128) ||
+        (swz && (h->band % 4 != 0 || h->Hp % 4 != 0 || h->P % 4 != 0 || h->mirror % 4 != 0)) || box_rows > 256 ||
+        box_cells > 256)
+        return JEFI_EINTERNAL;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
             cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess)
         return JEFI_ECUDA;
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    const cuuint64_t dims[3] = {8, (cuuint64_t)h->Hp, (cuuint64_t)h->n_bricks * kBrickCells};
-    const cuuint64_t strides[2] = {8 * sizeof(float), (cuuint64_t)h->Hp * 8 * sizeof(float)};
-    const cuuint32_t box[3] = {8, (cuuint32_t)h->band, kBrickCells};
+    const cuuint64_t rows = swz ? (cuuint64_t)h->Hp / 4 : (cuuint64_t)h->Hp;
+    const cuuint64_t dims[3] = {box_inner, rows, (cuuint64_t)h->n_bricks * kBrickCells};
+    const cuuint64_t strides[2] = {box_inner * sizeof(float), (cuuint64_t)h->Hp * 8 * sizeof(float)};
+    const cuuint32_t box[3] = {box_inner, box_rows, box_cells};
     const cuuint32_t elem[3] = {1, 1, 1};
-    const CUresult r = encode(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ring, dims, strides, box,
-                              elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const CUresult r = encode(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ring, dims, strides, box, elem,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? JEFI_OK : JEFI_ECUDA;
+    if (r != CUDA_SUCCESS) return JEFI_ECUDA;
+    h->tmap_band = h->band;
+    return JEFI_OK;
+}
+
+// Switch h's FP32 sum kernel: 0 = the direct gather, else a staged band
+// (the creation band or the wider alternative), re-encoding the tensor map
+// for a band it was not encoded for.
+int set_band(jefi_problem* h, int32_t b) {
+    const int32_t old = h->band;
+    h->band = b;
+    if (b > 0 && b != h->tmap_band) {
+        const int rc = make_tensor_map(h);
+        if (rc != JEFI_OK) {
+            h->band = old;
+            return rc;
+        }
+    }
+    return JEFI_OK;
 }
 
 // Kernel parameters of handle h for n_t evaluation times whose tables sit in
@@ -539,6 +671,7 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     const int K = h->K;
     SumParams p{};
     p.nbx = h->nbx; p.nby = h->nby; p.nbz = h->nbz; p.n_bricks = h->n_bricks;
+    for (int a = 0; a < 3; ++a) p.org[a] = h->org[a];
     p.npx = h->npx; p.npy = h->npy; p.npz = h->npz;
     for (int a = 0; a < 3; ++a) {
         p.lo[a] = h->src.lo[a];
@@ -551,8 +684,8 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     p.obs_scr = h->obs_scr;
     p.ring = h->ring;
     p.Hp = h->Hp;
-    p.zero_slot = h->H + h->mirror;
-    p.H = h->H;
+    p.zero_slot = h->P + h->mirror;
+    p.H = h->P;
     p.status = h->status;
     p.tab2 = h->tab2 ? h->tab2 + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
     p.tabg = h->tabg ? h->tabg + (size_t)slot0 * (K + 2 * kTabGuard) : nullptr;
@@ -915,7 +1048,9 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         return JEFI_EINVAL;
     for (int a = 0; a < 3; ++a) {
         if (src->n[a] < 0 || !(src->d[a] > 0) || !std::isfinite(src->d[a]) ||
-            !std::isfinite(src->lo[a]) || !std::isfinite(p->screen[a]))
+            !std::isfinite(src->lo[a]) || !std::isfinite(p->screen[a]) || p->src_origin[a] < 0 ||
+            p->tile_shape < 0 || p->tile_shape > kNumTileShapes ||
+            (int64_t)p->src_origin[a] + src->n[a] + 4 > ((int64_t)1 << 30))
             return JEFI_EINVAL;
     }
     int64_t n_obs = 0;
@@ -931,7 +1066,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         for (int64_t i = 0; i < n_obs; ++i)
             if (!finite3(obs_points + 3 * i)) return JEFI_EINVAL;
     }
-    if (n_obs > (int64_t)1 << 28) return JEFI_EUNSUPPORTED;
+    if (n_obs > (int64_t)1 << 28 || p->history_slots > (1 << 28)) return JEFI_EUNSUPPORTED;
 
     jefi_problem* h = new (std::nothrow) jefi_problem();
     if (!h) return JEFI_ENOMEM;
@@ -943,6 +1078,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->interp = (p->flags & JEFI_FLAG_INTERP) != 0;
     h->central = h->interp && p->deriv == JEFI_DERIV_BACKWARD;
     h->H = p->history_slots;
+    for (int a = 0; a < 3; ++a) h->org[a] = p->src_origin[a];
+    h->P = (h->H + 3) / 4 * 4;
     for (int a = 0; a < 3; ++a) h->screen[a] = p->screen[a] < 0 ? src->d[a] / 2 : p->screen[a];
     h->n_src = (int64_t)src->n[0] * src->n[1] * src->n[2];
     h->n_obs = n_obs;
@@ -954,7 +1091,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->npz = 4 * h->nbz;
     const int64_t n_bricks = (int64_t)h->nbx * h->nby * h->nbz;
     const int64_t n_cells = n_bricks * kBrickCells;
-    if (n_bricks > INT32_MAX / 2 || (double)n_cells * (h->H + 64.0) > 4e11) {
+    if (n_bricks > INT32_MAX / 2 || (double)n_cells * (h->P + kStagedMaxBand + 4.0) > 4e11) {
         delete h;
         return JEFI_EUNSUPPORTED;
     }
@@ -972,19 +1109,28 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
             pts[3 * o + 2] = center(obs_grid->lo[2], obs_grid->d[2], k);
         }
         if (n_obs > 0) {
-            const int tx = (gx + 7) / 8, ty = (gy + 7) / 8, tz = (gz + 3) / 4;
-            order.assign((size_t)tx * ty * tz * kTileThreads, -1);
-            for (int64_t tile = 0; tile < (int64_t)tx * ty * tz; ++tile) {
-                const int64_t bx = tile % tx, by = (tile / tx) % ty, bz = tile / ((int64_t)tx * ty);
-                for (int tid = 0; tid < kTileThreads; ++tid) {
-                    const int w = tid >> 5, l = tid & 31;
-                    const int64_t i = 8 * bx + 4 * (w & 1) + (l & 3);
-                    const int64_t j = 8 * by + 4 * ((w >> 1) & 1) + ((l >> 2) & 3);
-                    const int64_t k = 4 * bz + 2 * (w >> 2) + (l >> 4);
-                    if (i < gx && j < gy && k < gz)
-                        order[tile * kTileThreads + tid] = (k * gy + j) * gx + i;
+            int shape = p->tile_shape > 0 ? p->tile_shape : 1;
+            if (p->tile_shape == 0 && !h->fp64 && h->n_src > 0) {
+                // the shape whose widest tile spans the narrowest pair-distance
+                // range (the staged kernel's band); the first shape on ties.
+                // FP32 handles choose alike whichever kernel they start on, so
+                // a handle switched between kernels equals one created on the
+                // other (same tiles, same sums)
+                const int64_t np3[3] = {h->npx, h->npy, h->npz};
+                double O[3], r_src, db;
+                source_shell(*src, h->org, np3, O, &r_src, &db);
+                double best = INFINITY;
+                for (int s = 1; s <= kNumTileShapes; ++s) {
+                    grid_tile_order(gx, gy, gz, s, order);
+                    const double e = tiles_extent(order, pts.data(), O, r_src, db);
+                    if (e < best * (1 - 1e-9)) {
+                        best = e;
+                        shape = s;
+                    }
                 }
             }
+            h->tile_shape = shape;
+            grid_tile_order(gx, gy, gz, shape, order);
         }
     } else {
         std::memcpy(pts.data(), obs_points, sizeof(double) * 3 * (size_t)n_obs);
@@ -1001,6 +1147,34 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
             const int64_t n_tiles = (n_obs + kTileThreads - 1) / kTileThreads;
             order.assign((size_t)n_tiles * kTileThreads, -1);
             for (int64_t o = 0; o < n_obs; ++o) order[o] = keys[o].second;
+            if (!h->fp64 && h->n_src > 0) {
+                // Points far from the sources (shells, distant detectors) have
+                // narrow slot bands when a tile holds points at similar
+                // distances from the source grid, whatever its box: take the
+                // radial order (Morton order among equal distances) when it
+                // narrows the widest tile's distance range clearly.
+                const int64_t np3[3] = {h->npx, h->npy, h->npz};
+                double O[3], r_src, db;
+                source_shell(*src, h->org, np3, O, &r_src, &db);
+                std::vector<std::pair<double, uint64_t>> rk((size_t)n_obs);
+                for (int64_t o = 0; o < n_obs; ++o) {
+                    double r2 = 0;
+                    for (int a = 0; a < 3; ++a) r2 += (pts[3 * o + a] - O[a]) * (pts[3 * o + a] - O[a]);
+                    rk[o] = {std::sqrt(r2), (uint64_t)o};
+                }
+                std::vector<int64_t> by_r((size_t)n_obs);
+                for (int64_t o = 0; o < n_obs; ++o) by_r[o] = o;
+                std::vector<uint64_t> mkey((size_t)n_obs);
+                for (int64_t o = 0; o < n_obs; ++o) mkey[o] = morton(&pts[3 * o], lo, hi);
+                std::sort(by_r.begin(), by_r.end(), [&](int64_t a, int64_t b) {
+                    return rk[a].first != rk[b].first ? rk[a].first < rk[b].first : mkey[a] < mkey[b];
+                });
+                std::vector<int64_t> radial((size_t)n_tiles * kTileThreads, -1);
+                for (int64_t o = 0; o < n_obs; ++o) radial[o] = by_r[o];
+                const double e_m = tiles_extent(order, pts.data(), O, r_src, db);
+                const double e_r = tiles_extent(radial, pts.data(), O, r_src, db);
+                if (e_r < 0.75 * e_m) order.swap(radial);
+            }
         }
     }
     h->n_slots = (int32_t)order.size();
@@ -1013,7 +1187,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     const int64_t npad_axis[3] = {h->npx, h->npy, h->npz};
     for (int a = 0; a < 3; ++a) {
         Xmax = std::max(Xmax, std::fabs(src->lo[a]));
-        Xmax = std::max(Xmax, std::fabs(center(src->lo[a], src->d[a], npad_axis[a])));
+        Xmax = std::max(Xmax, std::fabs(center(src->lo[a], src->d[a], h->org[a] + npad_axis[a])));
     }
     for (int64_t tile = 0; tile < h->n_tiles; ++tile) {
         // padding slots repeat the last real point of their tile (or the first)
@@ -1038,6 +1212,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         }
     }
 
+    h->obs_sig = fnv1a(kFnvBasis, slot_xyz.data(), sizeof(double) * slot_xyz.size());
+
     // ---------------------------------------------------------------- screening and extremes
     const int64_t nlim[3] = {src->n[0], src->n[1], src->n[2]};
     const int64_t npad[3] = {h->npx, h->npy, h->npz};
@@ -1054,8 +1230,8 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
                     pad_ax[a] = it->second.first;
                     real_ax[a] = it->second.second;
                 } else {
-                    pad_ax[a] = axis_info(x, src->lo[a], src->d[a], npad[a], npad[a], h->screen[a]);
-                    real_ax[a] = axis_info(x, src->lo[a], src->d[a], nlim[a], npad[a], h->screen[a]);
+                    pad_ax[a] = axis_info(x, src->lo[a], src->d[a], h->org[a], npad[a], npad[a], h->screen[a]);
+                    real_ax[a] = axis_info(x, src->lo[a], src->d[a], h->org[a], nlim[a], npad[a], h->screen[a]);
                     if (obs_grid) memo[a][x] = {pad_ax[a], real_ax[a]};
                 }
                 scr[(2 * a) * h->n_slots + s] = pad_ax[a].rlo;
@@ -1072,7 +1248,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     }
 
     // ---------------------------------------------------------------- FP32 error model
-    h->exact = exact_lattice(slot_xyz, *src, npad);
+    h->exact = exact_lattice(slot_xyz, *src, h->org, npad);
     if (h->exact) {
         h->err_rel = h->err_lin = h->err_abs = 0.0;   // S32 == S64 exactly
     } else {
@@ -1132,37 +1308,54 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     }
 
     // ---------------------------------------------------------------- staged FP32 kernel
-    // The TMA-staged kernel needs every (tile, brick) slot band to fit one of
-    // the compiled band heights, and a candidate bias g with 2g < 1.
-    std::vector<float> tile_box((size_t)h->n_tiles * 6);
+    // The TMA-staged kernel needs every (tile, stage) slot band to fit one of
+    // the compiled band heights, and a candidate bias g with 2g < 1.  Per
+    // tile the kernel bounds the pair distances two ways and keeps the
+    // tighter: the tile's box against the stage's box, and the shell
+    // [rho_lo, rho_hi] of the tile's distances from O (the source grid's
+    // centre) widened by the farthest source cell from O.  The host takes
+    // the widest band over tiles of the same bounds (plus one spare slot).
+    std::vector<float> tile_box((size_t)h->n_tiles * kTileBoxFloats);
     if (!h->fp64 && h->any_pairs && !(p->flags & JEFI_FLAG_DIRECT_GATHER)) {
-        double diag_max = 0;
+        double O[3], r_src, db;
+        source_shell(*src, h->org, npad, O, &r_src, &db);
+        double ext_max = 0;
         for (int64_t tile = 0; tile < h->n_tiles; ++tile) {
             double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+            double rho_lo = INFINITY, rho_hi = 0;
             const double* anchor = &slot_xyz[3 * tile * kTileThreads];
             for (int tid = 0; tid < kTileThreads; ++tid) {
                 const double* x = &slot_xyz[3 * (tile * kTileThreads + tid)];
+                double r2 = 0;
                 for (int a = 0; a < 3; ++a) {
                     mn[a] = std::min(mn[a], x[a] - anchor[a]);
                     mx[a] = std::max(mx[a], x[a] - anchor[a]);
+                    r2 += (x[a] - O[a]) * (x[a] - O[a]);
                 }
+                rho_lo = std::min(rho_lo, std::sqrt(r2));
+                rho_hi = std::max(rho_hi, std::sqrt(r2));
             }
             double d2 = 0;
+            float* tb = &tile_box[tile * kTileBoxFloats];
             for (int a = 0; a < 3; ++a) {
-                tile_box[tile * 6 + a] = round_down_f32(mn[a]);
-                tile_box[tile * 6 + 3 + a] = round_up_f32(mx[a]);
+                tb[a] = round_down_f32(mn[a]);
+                tb[3 + a] = round_up_f32(mx[a]);
+                tb[6 + a] = (float)(O[a] - anchor[a]);
                 d2 += (mx[a] - mn[a]) * (mx[a] - mn[a]);
             }
-            diag_max = std::max(diag_max, std::sqrt(d2));
+            tb[9] = round_down_f32(rho_lo * (1 - 1e-12));
+            tb[10] = round_up_f32(rho_hi * (1 + 1e-12));
+            tb[11] = 0.f;
+            // widest distance range of any pair of this tile: box bound or shell bound
+            const double ext_box = std::sqrt(d2) + db;
+            const double ext_shell = (rho_hi - rho_lo) + 2 * r_src;
+            ext_max = std::max(ext_max, std::min(ext_box, ext_shell));
         }
-        double db2 = 0;
-        for (int a = 0; a < 3; ++a) db2 += 9.0 * src->d[a] * src->d[a];
         const double Kd = 1.0 / (p->c * p->dt);
-        const double need = std::ceil((diag_max + std::sqrt(db2)) * Kd * (1 + 1e-4) + 1e-3) + 7;
-        const int bands[4] = {16, 24, 32, 48};
+        const double need = std::ceil(ext_max * Kd * (1 + 1e-4) + 1e-3) + 7;
         int band = 0;
-        for (int b : bands)
-            if (need <= b) { band = b; break; }
+        for (int b : kStagedBands)   // swizzled bands start on a 4-slot line: 3 more slots
+            if (need + (staged_swizzled(b) ? 3 : 0) <= b) { band = b; break; }
         if (base && band > base->mirror) band = 0;      // a view fits the base ring's mirror
         if (band > 0) {
             SumParams probe{};
@@ -1175,16 +1368,24 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
             probe.npz = (int)npad[2];
             probe.exact = h->exact ? 1 : 0;
             if (staged_smem_bytes(probe, band, false) <= 220 * 1024) h->band = band;
+            // the next compiled height: a wider band with other stages (cells,
+            // swizzle) that the tuner may time against this one
+            for (int b : kStagedBands)
+                if (h->band > 0 && b > h->band && !(base && b > base->mirror) &&
+                    staged_smem_bytes(probe, b, false) <= 220 * 1024) {
+                    h->band_alt = b;
+                    break;
+                }
         }
     }
     if (base) {
         h->mirror = base->mirror;
     } else if (!h->fp64 && (p->flags & JEFI_FLAG_SHARED_RING)) {
-        h->mirror = 48;                                  // room for the widest staged band of any view
+        h->mirror = kStagedMaxBand;                      // room for the widest staged band of any view
     } else {
-        h->mirror = h->band;
+        h->mirror = std::max(h->band, h->band_alt);
     }
-    h->Hp = h->H + h->mirror + kZeroPadSlots;
+    h->Hp = h->P + h->mirror + kZeroPadSlots;
     h->band0 = h->band;
     if (!h->fp64 && h->any_pairs && h->band == 0 && h->Hp > 65536) {
         delete h;   // the direct-gather kernel packs two physical slots in 16 bits each
@@ -1237,7 +1438,11 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int32_t), s);
     if (e == cudaSuccess && h->band > 0)
         e = cudaMemcpyAsync(h->tile_box, tile_box.data(), sizeof(float) * tile_box.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && h->band > 0 && make_tensor_map(h) != JEFI_OK) e = cudaErrorInvalidValue;
+    int tmap_rc = JEFI_OK;
+    if (e == cudaSuccess && h->band > 0) {
+        tmap_rc = make_tensor_map(h);
+        if (tmap_rc != JEFI_OK) e = cudaErrorInvalidValue;
+    }
     if (e == cudaSuccess && !slot_xyz.empty())
         e = cudaMemcpyAsync(h->obs_xyz, slot_xyz.data(), sizeof(double) * slot_xyz.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !scr.empty())
@@ -1246,9 +1451,11 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         e = cudaMemcpyAsync(h->d_inv_perm, h->inv_perm.data(), sizeof(int32_t) * h->inv_perm.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);   // copies already enqueued finish before the memory is released
+        cudaGetLastError();
         release_all(h);
         delete h;
-        return JEFI_ECUDA;
+        return tmap_rc != JEFI_OK ? tmap_rc : JEFI_ECUDA;
     }
     if (base) {
         base->n_views++;
@@ -1272,28 +1479,64 @@ int jefi_create_view(jefi_handle base, const jefi_grid* obs_grid, const double* 
     return create_impl(&base->src, obs_grid, obs_points, n_obs, &base->prm, stream, base, out);
 }
 
-int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const double* drho,
-                      const double* dJ, int on_device, void* stream) {
-    NvtxRange nvtx_range("jefi_push_sources");
+// Push one slice whose arrays cover full_n cells (x fastest); the handle's
+// cell (i, j, k) is their cell offset + (i, j, k).
+static int push_impl(jefi_handle h, const double* rho, const double* J, const double* drho, const double* dJ,
+                     const int32_t* full_n, const int32_t* offset, int on_device, void* stream) {
     if (!h || h->base) return JEFI_EINVAL;               // views read the base's history
     const bool supplied = h->prm.deriv == JEFI_DERIV_SUPPLIED;
     if (h->n_src > 0 && (!rho || !J)) return JEFI_EINVAL;
     if (supplied != (drho != nullptr) || supplied != (dJ != nullptr)) return JEFI_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (offset[a] < 0 || full_n[a] < 0 || (int64_t)offset[a] + h->src.n[a] > full_n[a]) return JEFI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = h->n_src;
+    const bool region = full_n[0] != h->src.n[0] || full_n[1] != h->src.n[1] || full_n[2] != h->src.n[2];
     const double *r = rho, *j = J, *dr = drho, *dj = dJ;
+    int32_t fnx = full_n[0], fny = full_n[1], ox = offset[0], oy = offset[1], oz = offset[2];
     if (!on_device && n > 0) {
+        // host slices: the handle's cells (gathered from a region first) go
+        // to the staging buffer, then the push reads them as a whole grid
+        std::vector<double> gather;
+        const double *hr = rho, *hj = J, *hdr = drho, *hdj = dJ;
+        if (region) {
+            const int nx = h->src.n[0], ny = h->src.n[1], nz = h->src.n[2];
+            gather.resize((size_t)n * (supplied ? 8 : 4));
+            double* gr = gather.data();
+            double* gj = gr + n;
+            for (int k = 0; k < nz; ++k)
+                for (int jj = 0; jj < ny; ++jj)
+                    for (int i = 0; i < nx; ++i) {
+                        const int64_t g = ((int64_t)k * ny + jj) * nx + i;
+                        const int64_t f = ((int64_t)(oz + k) * fny + (oy + jj)) * fnx + (ox + i);
+                        gr[g] = rho[f];
+                        for (int a = 0; a < 3; ++a) gj[3 * g + a] = J[3 * f + a];
+                        if (supplied) {
+                            gr[4 * n + g] = drho[f];
+                            for (int a = 0; a < 3; ++a) gr[5 * n + 3 * g + a] = dJ[3 * f + a];
+                        }
+                    }
+            hr = gr;
+            hj = gj;
+            hdr = supplied ? gr + 4 * n : nullptr;
+            hdj = supplied ? gr + 5 * n : nullptr;
+            fnx = nx;
+            fny = ny;
+            ox = oy = oz = 0;
+        }
         double* st = h->stage_in;
-        JEFI_CUDA(cudaMemcpyAsync(st, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-        JEFI_CUDA(cudaMemcpyAsync(st + n, J, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+        JEFI_CUDA(cudaMemcpyAsync(st, hr, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        JEFI_CUDA(cudaMemcpyAsync(st + n, hj, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
         r = st;
         j = st + n;
         if (supplied) {
-            JEFI_CUDA(cudaMemcpyAsync(st + 4 * n, drho, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-            JEFI_CUDA(cudaMemcpyAsync(st + 5 * n, dJ, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+            JEFI_CUDA(cudaMemcpyAsync(st + 4 * n, hdr, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            JEFI_CUDA(cudaMemcpyAsync(st + 5 * n, hdj, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
             dr = st + 4 * n;
             dj = st + 5 * n;
         }
+        // the gathered copy must outlive the (pageable) copies above
+        if (region) JEFI_CUDA(cudaStreamSynchronize(s));
     }
     const int64_t next = h->n_latest + 1;
     PushParams p{};
@@ -1303,9 +1546,14 @@ int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const d
     p.nbx = h->nbx;
     p.nby = h->nby;
     p.n_src = n;
+    p.fnx = fnx;
+    p.fny = fny;
+    p.ox = ox;
+    p.oy = oy;
+    p.oz = oz;
     p.Hp = h->Hp;
-    p.slot = (int32_t)(next % h->H);
-    p.mirror_slot = p.slot < h->mirror ? p.slot + h->H : -1;
+    p.slot = (int32_t)(next % h->P);
+    p.mirror_slot = p.slot < h->mirror ? p.slot + h->P : -1;
     p.supplied = supplied;
     p.fp64 = h->fp64;
     p.c = h->prm.c;
@@ -1322,13 +1570,29 @@ int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const d
     p.prev_slot = -1;
     p.prev_mirror_slot = -1;
     if (h->central && next >= 1) {
-        p.prev_slot = (int32_t)((next - 1) % h->H);
-        p.prev_mirror_slot = p.prev_slot < h->mirror ? p.prev_slot + h->H : -1;
+        p.prev_slot = (int32_t)((next - 1) % h->P);
+        p.prev_mirror_slot = p.prev_slot < h->mirror ? p.prev_slot + h->P : -1;
     }
     JEFI_CUDA(launch_push(p, s));
     if (n > 0) h->launches++;
     h->n_latest = next;
     return mark_use(h, s);
+}
+
+int jefi_push_sources(jefi_handle h, const double* rho, const double* J, const double* drho,
+                      const double* dJ, int on_device, void* stream) {
+    NvtxRange nvtx_range("jefi_push_sources");
+    if (!h) return JEFI_EINVAL;
+    const int32_t zero[3] = {0, 0, 0};
+    return push_impl(h, rho, J, drho, dJ, h->src.n, zero, on_device, stream);
+}
+
+int jefi_push_sources_region(jefi_handle h, const double* rho, const double* J, const double* drho,
+                             const double* dJ, const int32_t* full_n, const int32_t* offset, int on_device,
+                             void* stream) {
+    NvtxRange nvtx_range("jefi_push_sources_region");
+    if (!h || !full_n || !offset) return JEFI_EINVAL;
+    return push_impl(h, rho, J, drho, dJ, full_n, offset, on_device, stream);
 }
 
 static void sync_view(jefi_problem* h) {
@@ -1391,7 +1655,6 @@ int jefi_eval_batch(const jefi_handle* hs, const double* t, double* const* E, do
     for (int i = 0; i < n; ++i) {
         jefi_problem* h = hs[i];
         if (!h) return JEFI_EINVAL;
-        if (h->interp) return JEFI_EUNSUPPORTED;   // batched kernels run the floor rule only
         sync_view(h);
         if (h->n_obs > 0 && (!E[i] || !B[i])) return JEFI_EINVAL;
         const int rc = check_time(h, t[i]);
@@ -1536,7 +1799,7 @@ int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_ba
     int rc = JEFI_OK;
     if (mode == JEFI_KERNEL_STAGED) {
         if (h->band0 == 0) rc = JEFI_EUNSUPPORTED;
-        else h->band = h->band0;
+        else rc = set_band(h, h->band0);
     } else if (mode == JEFI_KERNEL_DIRECT) {
         if (h->band != 0 && h->any_pairs) {
             if (direct_possible(h)) h->band = 0;
@@ -1544,17 +1807,28 @@ int jefi_select_kernel(jefi_handle h, int32_t mode, double t, int32_t* staged_ba
         }
     } else {
         rc = check_time(h, t);
-        if (rc == JEFI_OK && h->band0 != 0 && h->any_pairs && h->n_obs > 0 && direct_possible(h)) {
+        if (rc == JEFI_OK && h->band0 != 0 && h->any_pairs && h->n_obs > 0) {
+            // candidates: the creation band, the wider compiled band, the direct gather
+            int32_t cand[3];
+            int nc = 0;
+            cand[nc++] = h->band0;
+            if (h->band_alt > 0) cand[nc++] = h->band_alt;
+            if (direct_possible(h)) cand[nc++] = 0;
             const int32_t keep = h->band;
-            float ms_staged = 0.f, ms_direct = 0.f;
-            h->band = h->band0;
-            rc = time_eval(h, t, s, &ms_staged);
-            if (rc == JEFI_OK) {
-                h->band = 0;
-                rc = time_eval(h, t, s, &ms_direct);
+            int32_t best = keep;
+            float best_ms = INFINITY;
+            for (int c = 0; c < nc && nc > 1 && rc == JEFI_OK; ++c) {
+                float ms = 0.f;
+                rc = set_band(h, cand[c]);
+                if (rc == JEFI_OK) rc = time_eval(h, t, s, &ms);
+                if (rc == JEFI_OK && ms < best_ms) {
+                    best_ms = ms;
+                    best = cand[c];
+                }
             }
-            h->band = rc != JEFI_OK ? keep : (ms_direct < ms_staged ? 0 : h->band0);
-            if (rc == JEFI_OK) {
+            const int rb = set_band(h, rc != JEFI_OK ? keep : best);
+            if (rc == JEFI_OK) rc = rb;
+            if (rc == JEFI_OK && nc > 1) {
                 int32_t st = 0;
                 JEFI_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost, s));
                 JEFI_CUDA(cudaStreamSynchronize(s));
@@ -1647,6 +1921,7 @@ int jefi_get_info(jefi_handle h, jefi_info* out) {
     JEFI_CUDA(cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
     out->device_status = st;
     out->staged_band = h->band;
+    out->tile_shape = h->tile_shape;
     return JEFI_OK;
 }
 
@@ -1665,7 +1940,7 @@ int jefi_reset_stats(jefi_handle h) {
 namespace {
 
 constexpr char kCkpMagic[8] = {'J', 'E', 'F', 'I', 'C', 'K', 'P', '1'};
-constexpr uint32_t kCkpVersion = 1;
+constexpr uint32_t kCkpVersion = 2;    // 2: the ring image holds the P = 4 ceil(H/4) slots of the period
 
 struct CkpHeader {
     char magic[8];
@@ -1673,18 +1948,20 @@ struct CkpHeader {
     uint32_t header_bytes;
     int32_t src_n[3];
     int32_t H;
+    int32_t src_origin[3];
+    int32_t pad0;
     double src_lo[3], src_d[3];
     double c, dt, t0;
     int32_t precision, deriv, interp, esz;
     int64_t n_latest;
     int64_t n_cells;                 // brick-padded cells
     int64_t n_src;
-    int64_t ring_bytes;              // slots 0..H-1 of every cell
+    int64_t ring_bytes;              // slots 0..P-1 of every cell (P: the ring's period)
     int64_t state_bytes;             // previous slice (and the one before, central differences)
 };
 
 int64_t ckp_ring_bytes(const jefi_problem* h) {
-    return (int64_t)h->n_bricks * kBrickCells * h->H * 8 * (h->fp64 ? 8 : 4);
+    return (int64_t)h->n_bricks * kBrickCells * h->P * 8 * (h->fp64 ? 8 : 4);
 }
 
 int64_t ckp_state_bytes(const jefi_problem* h) {
@@ -1698,6 +1975,7 @@ CkpHeader ckp_header(const jefi_problem* h) {
     c.header_bytes = sizeof(CkpHeader);
     for (int a = 0; a < 3; ++a) {
         c.src_n[a] = h->src.n[a];
+        c.src_origin[a] = h->org[a];
         c.src_lo[a] = h->src.lo[a];
         c.src_d[a] = h->src.d[a];
     }
@@ -1737,7 +2015,7 @@ int jefi_checkpoint(jefi_handle h, void* dst, size_t bytes, void* stream) {
     unsigned char* ring_out = out + sizeof(hdr);
     const size_t row = (size_t)8 * hdr.esz;
     if (hdr.ring_bytes > 0)
-        JEFI_CUDA(cudaMemcpy2DAsync(ring_out, (size_t)h->H * row, h->ring, (size_t)h->Hp * row, (size_t)h->H * row,
+        JEFI_CUDA(cudaMemcpy2DAsync(ring_out, (size_t)h->P * row, h->ring, (size_t)h->Hp * row, (size_t)h->P * row,
                                     (size_t)hdr.n_cells, cudaMemcpyDeviceToHost, s));
     unsigned char* st = ring_out + hdr.ring_bytes;
     const size_t one = (size_t)h->n_src * 4 * sizeof(double);
@@ -1765,18 +2043,18 @@ int jefi_restore(jefi_handle h, const void* src, size_t bytes, void* stream) {
                 in.n_latest >= -1 && in.n_latest < ((int64_t)1 << 52);
     for (int a = 0; a < 3; ++a)
         same = same && in.src_n[a] == want.src_n[a] && in.src_lo[a] == want.src_lo[a] &&
-               in.src_d[a] == want.src_d[a];
+               in.src_d[a] == want.src_d[a] && in.src_origin[a] == want.src_origin[a];
     if (!same) return JEFI_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned char* ring_in = static_cast<const unsigned char*>(src) + sizeof(CkpHeader);
     const size_t row = (size_t)8 * in.esz;
     if (in.ring_bytes > 0) {
-        JEFI_CUDA(cudaMemcpy2DAsync(h->ring, (size_t)h->Hp * row, ring_in, (size_t)h->H * row, (size_t)h->H * row,
+        JEFI_CUDA(cudaMemcpy2DAsync(h->ring, (size_t)h->Hp * row, ring_in, (size_t)h->P * row, (size_t)h->P * row,
                                     (size_t)in.n_cells, cudaMemcpyHostToDevice, s));
-        // this handle's mirror rows: slot H + k repeats slot k, k < min(M, H)
-        const int m = std::min(h->mirror, h->H);
+        // this handle's mirror rows: slot P + k repeats slot k, k < min(M, P)
+        const int m = std::min(h->mirror, h->P);
         if (m > 0)
-            JEFI_CUDA(cudaMemcpy2DAsync(static_cast<unsigned char*>(h->ring) + (size_t)h->H * row, (size_t)h->Hp * row,
+            JEFI_CUDA(cudaMemcpy2DAsync(static_cast<unsigned char*>(h->ring) + (size_t)h->P * row, (size_t)h->Hp * row,
                                         h->ring, (size_t)h->Hp * row, (size_t)m * row, (size_t)in.n_cells,
                                         cudaMemcpyDeviceToDevice, s));
     }
@@ -2097,7 +2375,6 @@ int jefi_batch_plan_create(const jefi_handle* hs, double* const* E, double* cons
     for (int i = 0; i < n; ++i) {
         jefi_problem* h = hs[i];
         if (!h) return JEFI_EINVAL;
-        if (h->interp) return JEFI_EUNSUPPORTED;   // batched kernels run the floor rule only
         if (h->n_obs > 0 && (!E[i] || !B[i])) return JEFI_EINVAL;
         occ[i] = count[h]++;
         if (occ[i] >= h->time_chunk) return JEFI_EUNSUPPORTED;   // scratch slots per handle
@@ -2143,6 +2420,77 @@ int jefi_batch_plan_launch(jefi_batch_plan p, const double* t, void* stream) {
     return rc;
 }
 
+// ---------------------------------------------------------------- tune cache
+// What decides a handle's kernels' work, hashed: the tune cache's key part.
+static uint64_t handle_signature(const jefi_problem* h) {
+    uint64_t s = kFnvBasis;
+    s = fnv1a(s, &h->src, sizeof(h->src));
+    s = fnv1a(s, h->org, sizeof(h->org));
+    s = fnv1a(s, &h->obs_sig, sizeof(h->obs_sig));
+    const int32_t ints[11] = {h->H, h->prm.precision, h->prm.deriv, (int32_t)(h->prm.flags & ~JEFI_FLAG_STATS),
+                              h->interp ? 1 : 0, h->band0, h->band_alt, h->n_split_max, h->tile_shape,
+                              h->base ? 1 : 0, h->mirror};
+    s = fnv1a(s, ints, sizeof(ints));
+    const double dbl[3] = {h->prm.dt, h->prm.c, h->prm.t0};
+    return fnv1a(s, dbl, sizeof(dbl));
+}
+
+static uint64_t plan_signature(const jefi_batch_plan_s* p, int n_sm) {
+    uint64_t s = fnv1a(kFnvBasis, &n_sm, sizeof(n_sm));
+    for (const jefi_problem* h : p->hs) {
+        const uint64_t hs = handle_signature(h);
+        s = fnv1a(s, &hs, sizeof(hs));
+    }
+    return s;
+}
+
+struct TuneChoice {
+    int concurrent = 1, divisor = 0;
+    std::vector<int32_t> bands;     // per distinct handle, in order of first appearance
+};
+
+// The last line of the cache file with this key; false on a miss (or no file).
+static bool tune_cache_find(const char* path, uint64_t key, size_t u, TuneChoice* out) {
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[65536];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        unsigned long long k = 0;
+        int conc = 0, div = 0, n = 0, pos = 0;
+        if (std::sscanf(line, "jefi-tune-1 %llx %d %d %d%n", &k, &conc, &div, &n, &pos) != 4 || k != key ||
+            n != (int)u)
+            continue;
+        TuneChoice c;
+        c.concurrent = conc;
+        c.divisor = div;
+        const char* q = line + pos;
+        bool ok = true;
+        for (int i = 0; i < n && ok; ++i) {
+            int b = 0, used = 0;
+            ok = std::sscanf(q, "%d%n", &b, &used) == 1;
+            q += used;
+            c.bands.push_back(b);
+        }
+        if (ok) {
+            *out = c;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static void tune_cache_store(const char* path, uint64_t key, const TuneChoice& c) {
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "jefi-tune-1 %016llx %d %d %d", (unsigned long long)key, c.concurrent, c.divisor,
+                 (int)c.bands.size());
+    for (int32_t b : c.bands) std::fprintf(f, " %d", b);
+    std::fprintf(f, "\n");
+    std::fclose(f);
+}
+
 int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_tune_report* report) {
     NvtxRange nvtx_range("jefi_batch_plan_tune");
     if (!p || (!t && !p->hs.empty())) return JEFI_EINVAL;
@@ -2169,12 +2517,54 @@ int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_
     }
     auto restore = [&]() {
         for (size_t k = 0; k < u; ++k) {
-            uniq[k]->band = band_in[k];
+            set_band(uniq[k], band_in[k]);
             uniq[k]->n_split = split_in[k];
             uniq[k]->bricks_per_split = bps_in[k];
         }
     };
     double ms = 0;
+    // a choice stored for this plan's geometry: applied and timed once
+    const char* cache_path = std::getenv("JEFI_TUNE_CACHE");
+    const uint64_t cache_key = plan_signature(p, p->n_sm);
+    TuneChoice hit;
+    if (cache_path && cache_path[0] && tune_cache_find(cache_path, cache_key, u, &hit)) {
+        bool ok = true;
+        for (size_t k = 0; k < u && ok; ++k) {
+            const int32_t b = hit.bands[k];
+            jefi_problem* h = uniq[k];
+            ok = b == h->band || (!h->fp64 && ((b > 0 && (b == h->band0 || b == h->band_alt)) ||
+                                                (b == 0 && h->band0 > 0 && direct_possible(h))));
+        }
+        ok = ok && (hit.divisor == 0 || hit.divisor == 1 || hit.divisor == 2 || hit.divisor == 4 || hit.divisor == 8);
+        if (ok) {
+            p->concurrent = hit.concurrent != 0;
+            p->built = false;
+            for (size_t k = 0; k < u && rc == JEFI_OK; ++k) {
+                rc = set_band(uniq[k], hit.bands[k]);
+                if (hit.divisor > 0) set_splits(uniq[k], (uniq[k]->n_split_max + hit.divisor - 1) / hit.divisor);
+            }
+            if (rc == JEFI_OK) rc = plan_wait(p);
+            if (rc == JEFI_OK && plan_stale(p)) rc = plan_build(p);
+            if (rc == JEFI_OK) rc = plan_time(p, t, s, &ms);
+            if (rc != JEFI_OK) {
+                restore();
+                return rc;
+            }
+            rep.candidates = 1;
+            rep.ms_initial = rep.ms_tuned = ms;
+            rep.split_divisor = hit.divisor;
+            rep.concurrent_groups = p->concurrent ? 1 : 0;
+            rep.from_cache = 1;
+            for (size_t k = 0; k < u; ++k) {
+                if (uniq[k]->band != band_in[k]) rep.measured_kernels = 1;
+                if (uniq[k]->band > 0 && uniq[k]->band == uniq[k]->band_alt) rep.widened_bands++;
+            }
+            for (jefi_problem* h : p->hs)
+                if (!h->fp64 && h->band > 0 && h->any_pairs && h->n_obs > 0) rep.staged_problems++;
+            if (report) *report = rep;
+            return JEFI_OK;
+        }
+    }
     rc = plan_time(p, t, s, &ms);
     if (rc != JEFI_OK) return rc;
     rep.candidates = 1;
@@ -2209,7 +2599,7 @@ int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_
         int32_t b = h->band;
         rc = jefi_select_kernel(h, JEFI_KERNEL_MEASURE, t_of[k], &b, stream);
         band_meas[k] = b;
-        h->band = band_in[k];
+        set_band(h, band_in[k]);
         differs = differs || b != band_in[k];
     }
     const int divs[4] = {1, 2, 4, 8};
@@ -2219,7 +2609,7 @@ int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_
         if (pol == 0) seen.push_back(split_in);
         for (int dv : divs) {
             for (size_t k = 0; k < u; ++k) {
-                uniq[k]->band = pol ? band_meas[k] : band_in[k];
+                set_band(uniq[k], pol ? band_meas[k] : band_in[k]);
                 set_splits(uniq[k], (uniq[k]->n_split_max + dv - 1) / dv);
             }
             std::vector<int32_t> cur(u);
@@ -2239,7 +2629,7 @@ int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_
     restore();
     if (rc != JEFI_OK) return rc;
     for (size_t k = 0; k < u; ++k) {
-        if (best_pol == 1) uniq[k]->band = band_meas[k];
+        if (best_pol == 1) set_band(uniq[k], band_meas[k]);
         if (best_div > 0) set_splits(uniq[k], (uniq[k]->n_split_max + best_div - 1) / best_div);
     }
     rc = plan_wait(p);
@@ -2250,7 +2640,17 @@ int jefi_batch_plan_tune(jefi_batch_plan p, const double* t, void* stream, jefi_
     rep.concurrent_groups = p->concurrent ? 1 : 0;
     rep.ms_tuned = best_ms;
     for (jefi_problem* h : p->hs)
-        if (!h->fp64 && h->band > 0 && h->any_pairs && h->n_obs > 0) rep.staged_problems++;
+        if (!h->fp64 && h->band > 0 && h->any_pairs && h->n_obs > 0) {
+            rep.staged_problems++;
+            if (h->band == h->band_alt) rep.widened_bands++;
+        }
+    if (cache_path && cache_path[0]) {
+        TuneChoice c;
+        c.concurrent = p->concurrent ? 1 : 0;
+        c.divisor = rep.split_divisor;
+        for (size_t k = 0; k < u; ++k) c.bands.push_back(uniq[k]->band);
+        tune_cache_store(cache_path, cache_key, c);
+    }
     if (report) *report = rep;
     return JEFI_OK;
 }
@@ -2265,6 +2665,57 @@ int jefi_batch_plan_destroy(jefi_batch_plan p) {
     for (jefi_problem* h : p->hs)
         if (seen[h]++ == 0) h->n_plans--;
     delete p;
+    return JEFI_OK;
+}
+
+// ---------------------------------------------------------------- S-O decomposition
+int jefi_so_partition(const jefi_grid* src, const int32_t* parts, jefi_grid* sub, int32_t* origin) {
+    if (!src || !parts || !sub || !origin) return JEFI_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (parts[a] < 1 || parts[a] > 4096 || src->n[a] < 0) return JEFI_EINVAL;
+    // per axis: part k holds bricks [k nb / p, (k + 1) nb / p) of the nb = ceil(n / 4)
+    // bricks, i.e. cells [4 b0, min(4 b1, n))
+    std::vector<int32_t> first[3], count[3];
+    for (int a = 0; a < 3; ++a) {
+        const int64_t nb = (src->n[a] + 3) / 4, p = parts[a];
+        for (int64_t k = 0; k < p; ++k) {
+            const int64_t b0 = k * nb / p, b1 = (k + 1) * nb / p;
+            const int64_t c0 = std::min<int64_t>(4 * b0, src->n[a]), c1 = std::min<int64_t>(4 * b1, src->n[a]);
+            first[a].push_back((int32_t)c0);
+            count[a].push_back((int32_t)(c1 - c0));
+        }
+    }
+    int64_t k = 0;
+    for (int kz = 0; kz < parts[2]; ++kz)
+        for (int ky = 0; ky < parts[1]; ++ky)
+            for (int kx = 0; kx < parts[0]; ++kx, ++k) {
+                const int idx[3] = {kx, ky, kz};
+                for (int a = 0; a < 3; ++a) {
+                    sub[k].n[a] = count[a][idx[a]];
+                    sub[k].lo[a] = src->lo[a];
+                    sub[k].d[a] = src->d[a];
+                    origin[3 * k + a] = first[a][idx[a]];
+                }
+            }
+    return JEFI_OK;
+}
+
+int jefi_sum_fields(int32_t n_parts, const double* const* E_parts, const double* const* B_parts, int64_t n_obs,
+                    double* E, double* B, void* stream) {
+    NvtxRange nvtx_range("jefi_sum_fields");
+    if (n_parts < 1 || n_parts > kMaxSumParts || !E_parts || !B_parts || n_obs < 0 || (n_obs > 0 && (!E || !B)))
+        return JEFI_EINVAL;
+    SumPartsParams p{};
+    p.n_parts = n_parts;
+    p.n = n_obs * 3;
+    for (int k = 0; k < n_parts; ++k) {
+        if (n_obs > 0 && (!E_parts[k] || !B_parts[k])) return JEFI_EINVAL;
+        p.E_parts[k] = E_parts[k];
+        p.B_parts[k] = B_parts[k];
+    }
+    p.E = E;
+    p.B = B;
+    JEFI_CUDA(launch_sum_parts(p, (cudaStream_t)stream));
     return JEFI_OK;
 }
 

@@ -2,14 +2,18 @@
 //
 // Device data layout (all owned by one problem handle):
 //
-//   ring      [cell][Hp][8]  FP32 or FP64, Hp = H + M + 1.  Cells are in brick
+//   ring      [cell][Hp][8]  FP32 or FP64, Hp = P + M + 4.  Cells are in brick
 //             order: brick b = (bz*nby + by)*nbx + bx covers the 4x4x4 source
 //             cells (4bx+i, 4by+j, 4bz+k); cell = b*64 + (k*16 + j*4 + i).
 //             Grid extents are padded up to whole bricks with cells whose
-//             channels stay zero.  Slice n lives in slot n mod H; slots
-//             [H, H+M) mirror slots [0, M) so that any M consecutive slots are
-//             one contiguous TMA box; slot H+M is a permanent zero slot
-//             (sources before slice 0).  M = 0 unless the staged kernel is used.
+//             channels stay zero.  The ring's period P is the history length
+//             H rounded up to a multiple of 4: slice n lives in slot n mod P
+//             (slots of slices older than the last H are never read); slots
+//             [P, P+M) mirror slots [0, M) so that any M consecutive slots are
+//             one contiguous TMA box; slots P+M .. P+M+3 are permanently zero
+//             (slot P+M stands for sources before slice 0).  M = 0 unless the
+//             staged kernel is used, and a multiple of 4, so the ring is also
+//             a whole number of 128-byte lines of 4 slots per cell.
 //             Channels: c*rho, Jx, Jy, Jz, drho/dt, dJx/dt/c, dJy/dt/c, dJz/dt/c.
 //             With these, per pair
 //               E' += D (ch0/R^3 + ch4/R^2) - ch5..7/R   ->  E = (k_e dV / c) E'
@@ -33,7 +37,26 @@ namespace jefi {
 constexpr int kTileThreads = 256;   // observation points per tile (one per thread)
 constexpr int kBrick = 4;           // source brick edge (cells)
 constexpr int kBrickCells = 64;
-constexpr int kZeroPadSlots = 1;    // the zero slot after the H ring slots
+constexpr int kZeroPadSlots = 4;    // the zero line after the P + M ring slots
+
+#ifdef __CUDACC__
+#define JEFI_HD __host__ __device__
+#else
+#define JEFI_HD
+#endif
+
+// Staged FP32 kernel: compiled band heights (slots per staged cell), the
+// cells per stage of each, and whether its rows are copied as 128-byte
+// swizzled lines (bands of 32 slots and more, whose rows spread over many
+// shared-memory banks).  Stage buffers start on a 1024-byte boundary; the
+// dynamic shared memory gets kStagedAlignPad extra bytes for that.
+constexpr int kStagedBands[6] = {16, 24, 32, 48, 64, 96};
+constexpr int kStagedMaxBand = 96;
+constexpr int kStagedAlignPad = 1024;
+JEFI_HD constexpr bool staged_swizzled(int band) { return band >= 32; }
+JEFI_HD constexpr int staged_stage_cells(int band) { return band <= 24 ? 64 : (band <= 48 ? 32 : 16); }
+constexpr int kTileBoxFloats = 12;  // per tile: box lo xyz, hi xyz, O xyz, rho_lo, rho_hi, 0
+constexpr int kStagedCtrlBytes = 128;   // control block after the stage buffers
 
 struct TimeParams {
     float A;            // fp32(T/dt - k0): candidate index ~ floor(A - R/(c dt))
@@ -50,7 +73,9 @@ struct SumParams {
     // source geometry
     int32_t nbx, nby, nbz, n_bricks;
     int32_t npx, npy, npz;          // padded grid extents (4 * nb)
-    double lo[3], d[3];             // source grid, FP64
+    double lo[3], d[3];             // source lattice, FP64
+    int32_t org[3];                 // first cell of the source grid in its lattice: cell i of
+                                    // axis a is centred at lo[a] + (org[a] + i + 0.5) d[a]
     float d32[3];
     // observation tiles
     int32_t n_slots;                // padded observation count
@@ -59,8 +84,8 @@ struct SumParams {
     const int32_t* obs_scr;
     // history ring
     const void* ring;
-    int32_t Hp;                     // slots per cell including the zero slot
-    int32_t zero_slot;              // == H + M
+    int32_t Hp;                     // slots per cell including the mirror and the zero line
+    int32_t zero_slot;              // == P + M
     // per-time tables
     const float4* tab32;
     const double* theta;
@@ -78,10 +103,12 @@ struct SumParams {
     int32_t* status;                // device error word (0 = ok, else a jefi_status)
     // staged kernel only
     const float2* tab2;             // [n_t][K + 2 kTabGuard] {T_hi, T_lo} per candidate slot
-    const float* tile_box;          // [n_tiles][6] min xyz, max xyz of (x_o - anchor), fp32 outward
+    const float* tile_box;          // [n_tiles][kTileBoxFloats]: min xyz, max xyz of (x_o - anchor) and
+                                    // O - anchor (O the source grid's centre), fp32; the range
+                                    // [rho_lo, rho_hi] of |x_o - O| over the tile, fp32 outward
     int32_t n_src_axis[3];          // real source cells per axis
     int32_t nfull[3];               // whole bricks per axis (bricks past them hold padding cells)
-    int32_t H;                      // ring period (physical slot of slice n is n mod H)
+    int32_t H;                      // ring period P (physical slot of slice n is n mod P)
     int32_t comp;                   // FP32: compensated (Kahan) per-thread sums
     // direct-gather kernel, per candidate slot k' (the staged kernel's candidate
     // rule, slots read from global memory): [n_t][K + 2 kTabGuard] {T_lo, physical
@@ -109,6 +136,10 @@ struct PushParams {
     int32_t nx, ny, nz;
     int32_t nbx, nby;
     int64_t n_src;
+    // the slice arrays cover a larger grid of fnx x fny x ... cells; this
+    // handle's cell (i, j, k) is their cell (ox + i, oy + j, oz + k)
+    int32_t fnx, fny;
+    int32_t ox, oy, oz;
     int32_t Hp;
     int32_t slot;                   // physical slot to write
     int32_t supplied;
@@ -174,11 +205,37 @@ struct StagedConfig {
     const void* tensor_map;         // CUtensorMap over the FP32 ring
 };
 
+// Rank-ordered FP64 sum of the fields of several S-O pairs over the same points.
+constexpr int kMaxSumParts = 64;
+struct SumPartsParams {
+    int32_t n_parts;
+    int64_t n;                      // doubles per field array (3 per point)
+    const double* E_parts[kMaxSumParts];
+    const double* B_parts[kMaxSumParts];
+    double* E;
+    double* B;
+};
+cudaError_t launch_sum_parts(const SumPartsParams& p, cudaStream_t s);
+
 cudaError_t launch_push(const PushParams& p, cudaStream_t s);
 cudaError_t launch_wait_timeout_probe(int32_t* status, uint64_t limit_ns, cudaStream_t s);
 cudaError_t launch_sum_f32_staged(const SumParams& p, const StagedConfig& c, cudaStream_t s);
 size_t staged_smem_bytes(const SumParams& p, int band, bool batched);
+size_t staged_buffer_bytes(int band);   // one stage buffer: cells per stage x band x 32 bytes
 bool staged_band_supported(int band);
+#ifdef CUDA_VERSION
+#define JEFI_DECLARE_STAGED_BAND(BAND)                                                                  \
+    cudaError_t staged_launch_##BAND(const SumParams& p, const StagedConfig& c, cudaStream_t s);          \
+    cudaError_t staged_launch_batch_##BAND(const StagedBatchArgs& a, bool exact, size_t smem, int grid,  \
+                                           cudaStream_t s);
+JEFI_DECLARE_STAGED_BAND(16)
+JEFI_DECLARE_STAGED_BAND(24)
+JEFI_DECLARE_STAGED_BAND(32)
+JEFI_DECLARE_STAGED_BAND(48)
+JEFI_DECLARE_STAGED_BAND(64)
+JEFI_DECLARE_STAGED_BAND(96)
+#undef JEFI_DECLARE_STAGED_BAND
+#endif
 cudaError_t launch_sum_f32(const SumParams& p, bool compensated, cudaStream_t s);
 cudaError_t launch_sum_f64(const SumParams& p, cudaStream_t s);
 cudaError_t launch_reduce(const ReduceParams& p, cudaStream_t s);

@@ -56,8 +56,8 @@ __device__ __noinline__ Fix6 direct_fixup(const SumParams& p, uint64_t mask, int
         const float ri = rsqrt_ftz(S);
         const unsigned cand = candidate_index(S, ri, K32, A, K);
         const int idx = slot_fallback_f32(p.obs_xyz, slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
-                                          kBrick * bx + i, kBrick * by + j, kBrick * bz + k, s_th, K, (int)cand,
-                                          p.fallbacks);
+                                          p.org[0] + kBrick * bx + i, p.org[1] + kBrick * by + j,
+                                          p.org[2] + kBrick * bz + k, s_th, K, (int)cand, p.fallbacks);
         if (DEBUG) p.debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
         const float4* q = cbase + (cl * Hp + __float_as_int(s_tab[idx].z)) * 2;
         float4 v0 = __ldg(q), v1 = __ldg(q + 1);
@@ -111,7 +111,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
         int a = i < p.nbx ? 0 : (i < nbxy ? 1 : 2);
         int b = a == 0 ? i : (a == 1 ? i - p.nbx : i - nbxy);
         double co = a == 0 ? cox : (a == 1 ? coy : coz);
-        s_D[i] = __double2float_rn(__dsub_rn(co, cell_center(p.lo[a], p.d[a], kBrick * b)));
+        s_D[i] = __double2float_rn(__dsub_rn(co, cell_center(p.lo[a], p.d[a], p.org[a] + kBrick * b)));
     }
     __syncthreads();
 
@@ -175,8 +175,8 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                 if (__any_sync(kFull, !ok)) {
                     if (!ok) {
                         idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2],
-                                                p.d[0], p.d[1], p.d[2], ix, iy, iz, s_th, K,
-                                                (int)idx, p.fallbacks);
+                                                p.d[0], p.d[1], p.d[2], p.org[0] + ix, p.org[1] + iy,
+                                                p.org[2] + iz, s_th, K, (int)idx, p.fallbacks);
                         e = s_tab[idx];
                     }
                 }
@@ -347,9 +347,9 @@ __device__ __forceinline__ bool next_item(const BatchArgs& a, int* s_item, int* 
 
 // One item of the batched direct-gather kernel as a call of its own (the
 // item body keeps the single-problem kernel's register budget).
-template <bool COMP>
+template <bool COMP, bool INTERP>
 __device__ __noinline__ void direct_batch_item(const SumParams& p, int tile, int split, int ti) {
-    direct_f32_item<COMP, false, false>(p, tile, split, ti);
+    direct_f32_item<COMP, false, INTERP>(p, tile, split, ti);
 }
 
 template <bool COMP>
@@ -366,7 +366,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_batch(const BatchArgs
         uint32_t* dst = reinterpret_cast<uint32_t*>(&s_par);
         for (int w = threadIdx.x; w < (int)(sizeof(SumParams) / 4); w += kTileThreads) dst[w] = src[w];
         __syncthreads();
-        direct_batch_item<COMP>(s_par, tile, split, ti);
+        if (s_par.interp)     // the retarded-time rule is a property of the problem (uniform per item)
+            direct_batch_item<COMP, true>(s_par, tile, split, ti);
+        else
+            direct_batch_item<COMP, false>(s_par, tile, split, ti);
     }
 }
 
@@ -417,9 +420,9 @@ __device__ __forceinline__ void f64_item(const SumParams& p, const int tile, con
     const double* g_th = p.theta + (size_t)ti * (K + 1);
     for (int i = tid; i < K; i += kTileThreads) s_tab[i] = g_tab[i];
     for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
-    for (int i = tid; i < p.npx; i += kTileThreads) s_xs[i] = cell_center(p.lo[0], p.d[0], i);
-    for (int i = tid; i < p.npy; i += kTileThreads) s_ys[i] = cell_center(p.lo[1], p.d[1], i);
-    for (int i = tid; i < p.npz; i += kTileThreads) s_zs[i] = cell_center(p.lo[2], p.d[2], i);
+    for (int i = tid; i < p.npx; i += kTileThreads) s_xs[i] = cell_center(p.lo[0], p.d[0], p.org[0] + i);
+    for (int i = tid; i < p.npy; i += kTileThreads) s_ys[i] = cell_center(p.lo[1], p.d[1], p.org[1] + i);
+    for (int i = tid; i < p.npz; i += kTileThreads) s_zs[i] = cell_center(p.lo[2], p.d[2], p.org[2] + i);
     __syncthreads();
 
     ThreadCtx ctx;
@@ -525,7 +528,12 @@ __global__ void __launch_bounds__(kTileThreads, 1) sum_f64_kernel(const SumParam
 __global__ void __launch_bounds__(kTileThreads, 1) sum_f64_batch(const BatchArgs a) {
     __shared__ int s_item;
     int pr, tile, split, ti;
-    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) f64_item<false, false>(a.params[pr], tile, split, ti);
+    while (next_item(a, &s_item, &pr, &tile, &split, &ti)) {
+        if (a.params[pr].interp)
+            f64_item<false, true>(a.params[pr], tile, split, ti);
+        else
+            f64_item<false, false>(a.params[pr], tile, split, ti);
+    }
 }
 
 // ============================================================================ push
@@ -538,9 +546,11 @@ __global__ void push_kernel(const PushParams p) {
     const int iz = (int)(r / p.ny);
     const int64_t brick = ((int64_t)(iz >> 2) * p.nby + (iy >> 2)) * p.nbx + (ix >> 2);
     const int64_t cell = brick * kBrickCells + ((iz & 3) * 16 + (iy & 3) * 4 + (ix & 3));
+    // the same cell in the caller's slice arrays (a region of a larger grid, or the grid itself)
+    const int64_t gs = ((int64_t)(p.oz + iz) * p.fny + (p.oy + iy)) * p.fnx + (p.ox + ix);
 
-    const double rho = p.rho[g];
-    const double j0 = p.J[3 * g + 0], j1 = p.J[3 * g + 1], j2 = p.J[3 * g + 2];
+    const double rho = p.rho[gs];
+    const double j0 = p.J[3 * gs + 0], j1 = p.J[3 * gs + 1], j2 = p.J[3 * gs + 2];
     if (p.central && p.prev_slot >= 0) {
         // slice n-1 now has both neighbours: its derivative channels become
         // the central difference (f[n] - f[n-2]) / (2 dt), f[-1] = 0
@@ -576,10 +586,10 @@ __global__ void push_kernel(const PushParams p) {
     }
     double dr, dj0, dj1, dj2;
     if (p.supplied) {
-        dr = p.drho[g];
-        dj0 = p.dJ[3 * g + 0];
-        dj1 = p.dJ[3 * g + 1];
-        dj2 = p.dJ[3 * g + 2];
+        dr = p.drho[gs];
+        dj0 = p.dJ[3 * gs + 0];
+        dj1 = p.dJ[3 * gs + 1];
+        dj2 = p.dJ[3 * gs + 2];
     } else {
         // backward difference (f[n] - f[n-1]) / dt, Eq. E-1
         double* pv = p.prev + 4 * g;
@@ -661,7 +671,29 @@ __global__ void reduce_batch_kernel(const ReduceItem* items, const int64_t* out_
     }
 }
 
+// ============================================================================ S-O sums
+// E = sum over parts k = 0, 1, ... of E_parts[k], in that order (FP64): the
+// fields of S-O pairs that share their observation points (paper Sec. 2.2,
+// Fig. 2), summed in the same order whatever the number of ranks.
+__global__ void sum_parts_kernel(const SumPartsParams p) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    double e = 0.0, b = 0.0;
+    for (int k = 0; k < p.n_parts; ++k) {
+        e += p.E_parts[k][i];
+        b += p.B_parts[k][i];
+    }
+    p.E[i] = e;
+    p.B[i] = b;
+}
+
 // ============================================================================ launchers
+cudaError_t launch_sum_parts(const SumPartsParams& p, cudaStream_t s) {
+    if (p.n == 0) return cudaSuccess;
+    sum_parts_kernel<<<(unsigned)((p.n + 255) / 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum_f32_batch(const BatchArgs& a, bool compensated, size_t smem, int grid, cudaStream_t s) {
     void (*k)(BatchArgs) = compensated ? sum_f32_batch<true> : sum_f32_batch<false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,709 +1,16 @@
-// jefi_staged.cu -- FP32 retarded direct sum (Eqs. E-1, B-1, tr-1) with the
-// history band of every source brick staged in shared memory by TMA.
-//
-// One CTA = one tile of 256 observation points x a contiguous range of source
-// bricks.  For each brick one thread computes, from the tile's and the brick's
-// bounding boxes, the band of slots [lo, lo + BAND) that any pair of the two
-// can retard into, and one cp.async.bulk.tensor copies the 64 cells x BAND
-// slots x 8 channels of the ring into a shared-memory buffer (two buffers,
-// the next brick's copy overlaps the current brick's arithmetic; completion
-// through an mbarrier, waits bounded in time).
-//
-// Slot selection per pair, exact with respect to the FP64 rule of Eq. tr-1:
-//   k' = floor(A + g - R32/(c dt)), g bounding the FP32 error of the
-//   candidate, so that k' is n or n+1; one threshold entry (T_hi, T_lo) of
-//   Theta_k' (largest S64 whose slot is >= k') decides: S32 > T_lo -> n = k'-1,
-//   S32 <= T_hi -> n = k'.  On exact-lattice geometry S32 == S64 and
-//   T_hi == T_lo == Theta_k' rounded down, so every pair is decided without a
-//   branch.  Otherwise the rare pairs between T_hi and T_lo contribute nothing
-//   in the unrolled loop and are redone after the brick with their slot
-//   recomputed in FP64.
-#include <cuda.h>
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "jefi_device.cuh"
-#include "jefi_internal.h"
+// jefi_staged.cu -- the TMA-staged FP32 sum: launches of the narrow band
+// heights (16 and 24 slots, whole-brick stages, dense rows), the dispatch
+// over every compiled height, and the bounded-wait diagnostic.  The kernels
+// themselves are the templates of jefi_staged.cuh; the wide heights are
+// compiled in jefi_staged_b32_48.cu and jefi_staged_b64_96.cu.
+#include "jefi_staged.cuh"
 
 namespace jefi {
-using namespace dev;
 
-namespace {
+JEFI_STAGED_BAND_LAUNCHERS(16)
+JEFI_STAGED_BAND_LAUNCHERS(24)
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // a bounded wait gives up after 2 s
-constexpr int kStatusTimeout = 6;                    // JEFI_ETIMEOUT
-constexpr int kStatusInternal = 7;                   // JEFI_EINTERNAL
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase with the given parity; false if it has not completed
-// after limit_ns.
-__device__ __noinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
-    if (mbar_try_wait(a, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 1; it != 0; ++it) {
-        if (mbar_try_wait(a, parity)) return true;
-        if ((it & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
-    }
-    return false;
-}
-
-// ~0u if a > b, else 0 (false for NaN operands)
-__device__ __forceinline__ uint32_t gt_mask(float a, float b) {
-    uint32_t r;
-    asm("set.gt.u32.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
-    return r;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, uint32_t mbar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
-        : "memory");
-}
-
-template <int BAND>
-struct Layout {
-    static constexpr uint32_t kRowBytes = 32;                          // 8 FP32 channels
-    static constexpr uint32_t kCellBytes = BAND * kRowBytes;
-    static constexpr uint32_t kBufBytes = kBrickCells * kCellBytes;
-    // Bands of 32 and more rows are single-buffered: two CTAs per SM then fit
-    // in shared memory (two double-buffered CTAs would not), and each CTA's
-    // copy of its next brick overlaps the other CTA's arithmetic.
-    static constexpr int kBufs = BAND >= 32 ? 1 : 2;
-    static constexpr uint32_t kCtrl = kBufs * kBufBytes;               // mbarriers, band origins
-    static constexpr uint32_t kTab = kCtrl + 64;                        // float2 table
-    // control words of the non-lattice fall-back (one item): offset of the
-    // FP64 geometry (the tile's points, then the cell centres of x, y, z),
-    // the cell counts of x and y, and the pairs redone
-    static constexpr uint32_t kGeo = kCtrl + 48;
-};
-
-// Shared-memory offset of the FP64 geometry of one item: after the float2
-// table, the FP64 thresholds and the float brick offsets.
-__host__ __device__ __forceinline__ uint32_t staged_geometry_offset(uint32_t tab, int K, int nb_sum) {
-    const uint32_t d = tab + (uint32_t)(K + 2 * kTabGuard) * 8u + (uint32_t)(K + 1) * 8u;
-    return (d + (uint32_t)nb_sum * 4u + 7u) & ~7u;
-}
-
-// Exact slot of one undecided pair from the FP64 geometry in shared memory
-// (written by the item's preamble); counts the pair.  A call of its own, so
-// the FP64 search does not weigh on the registers of the brick loop.
-template <int BAND>
-__device__ __noinline__ int staged_slot_fp64(int ix, int iy, int iz, const double* s_th, int K, int guess) {
-    using L = Layout<BAND>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t* g = reinterpret_cast<const uint32_t*>(smem + L::kGeo);
-    const double* s_xo = reinterpret_cast<const double*>(smem + g[0]) + 3 * threadIdx.x;
-    const double* s_cc = reinterpret_cast<const double*>(smem + g[0]) + 3 * kTileThreads;
-    atomicAdd(const_cast<uint32_t*>(g + 3), 1u);
-    return slot_fp64_stored(s_xo, s_cc[ix], s_cc[g[1] + iy], s_cc[g[1] + g[2] + iz], s_th, K, guess);
-}
-
-}  // namespace
-
-// Both staged kernels initialise the two mbarriers once per CTA.
-template <int BAND>
-__device__ __forceinline__ void staged_init_barriers() {
-    using L = Layout<BAND>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    if (threadIdx.x == 0) {
-        uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + L::kCtrl);
-        mbar_init(smem_u32(&s_mbar[0]), 1);
-        mbar_init(smem_u32(&s_mbar[1]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-}
-
-// Non-lattice geometry of one item (before the item's first barrier): the
-// tile's FP64 points and the FP64 cell centres of each axis, for the exact
-// slot of the pairs the FP32 rule leaves undecided; zeroes the item's count.
-template <int BAND>
-__device__ __noinline__ void staged_fill_geometry(const double* txyz, int K, int nb_sum, int npx, int npy, int npz,
-                                                  double lox, double loy, double loz, double dx_, double dy_,
-                                                  double dz_) {
-    using L = Layout<BAND>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int tid = threadIdx.x;
-    const uint32_t geo = staged_geometry_offset(L::kTab, K, nb_sum);
-    double* s_xo = reinterpret_cast<double*>(smem + geo);
-    double* s_cc = s_xo + 3 * kTileThreads;
-    for (int i = tid; i < npx; i += kTileThreads) s_cc[i] = cell_center(lox, dx_, i);
-    for (int i = tid; i < npy; i += kTileThreads) s_cc[npx + i] = cell_center(loy, dy_, i);
-    for (int i = tid; i < npz; i += kTileThreads) s_cc[npx + npy + i] = cell_center(loz, dz_, i);
-    for (int a = 0; a < 3; ++a) s_xo[3 * tid + a] = txyz[3 * tid + a];
-    if (tid == 0) {
-        uint32_t* g = reinterpret_cast<uint32_t*>(smem + L::kGeo);
-        g[0] = geo;
-        g[1] = (uint32_t)npx;
-        g[2] = (uint32_t)npy;
-        g[3] = 0u;
-    }
-}
-
-struct FixSums {
-    float v[6];   // E', B contributions
-};
-
-// Pairs of a full brick whose slot the FP32 rule left undecided (non-lattice
-// geometry): exact slot in FP64, then the pair from the brick's buffer.  A
-// call of its own (rare), so its registers do not weigh on the brick loop.
-// The batched kernel's form: the point from global memory and a global
-// count (the batched item has no registers to spare for more).
-template <int BAND, bool DEBUG, bool INTERP>
-__device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char* bufp, int band_rel, float Px,
-                                             float Py, float Pz, float d32x, float d32y, float d32z, float K32,
-                                             float Ag, float A, float A_lo, float K32_lo, const double* obs_xyz,
-                                             int slot, double lox, double loy, double loz, double dx_, double dy_,
-                                             double dz_, int bx, int by, int bz, const double* s_th, int K,
-                                             unsigned long long* fallbacks, int32_t* status, int32_t* debug_slots,
-                                             size_t n_cells, int b, int64_t k0) {
-    using L = Layout<BAND>;
-    float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
-    while (mask) {
-        const int cl = __ffsll((long long)mask) - 1;
-        mask &= mask - 1;
-        const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
-        const float dx = fmaf(-(float)i, d32x, Px);
-        const float dy = fmaf(-(float)j, d32y, Py);
-        const float dz = fmaf(-(float)k, d32z, Pz);
-        const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-        const float ri = rsqrt_ftz(S);
-        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-        const int idx = slot_fallback_f32(obs_xyz, slot, lox, loy, loz, dx_, dy_, dz_, kBrick * bx + i,
-                                          kBrick * by + j, kBrick * bz + k, s_th, K, (int)(bits - kMagicBits),
-                                          fallbacks);
-        int row = idx - band_rel;
-        if (row < 0 || row >= BAND) {
-            atomicExch(status, kStatusInternal);
-            row = row < 0 ? 0 : BAND - 1;
-        }
-        if (DEBUG) debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
-        const uint32_t off = (uint32_t)cl * L::kCellBytes + (uint32_t)row * L::kRowBytes;
-        float4 v0 = *reinterpret_cast<const float4*>(bufp + off);
-        float4 v1 = *reinterpret_cast<const float4*>(bufp + off + 16u);
-        if (INTERP) {
-            const float4 u0 = *reinterpret_cast<const float4*>(bufp + off + 32u);
-            const float4 u1 = *reinterpret_cast<const float4*>(bufp + off + 48u);
-            lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
-        }
-        pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
-    }
-    return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
-}
-
-// The same, with the FP64 geometry and the count in shared memory (the
-// single-problem kernel).
-template <int BAND, bool DEBUG, bool INTERP>
-__device__ __noinline__ FixSums staged_fixup_geo(uint64_t mask, const unsigned char* bufp, int band_rel, float Px,
-                                             float Py, float Pz, float d32x, float d32y, float d32z, float K32,
-                                             float Ag, float A, float A_lo, float K32_lo, int slot, int bx,
-                                             int by, int bz, const double* s_th, int K, int32_t* status,
-                                             int32_t* debug_slots, size_t n_cells, int b, int64_t k0) {
-    using L = Layout<BAND>;
-    float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
-    while (mask) {
-        const int cl = __ffsll((long long)mask) - 1;
-        mask &= mask - 1;
-        const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
-        const float dx = fmaf(-(float)i, d32x, Px);
-        const float dy = fmaf(-(float)j, d32y, Py);
-        const float dz = fmaf(-(float)k, d32z, Pz);
-        const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-        const float ri = rsqrt_ftz(S);
-        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-        const int idx = staged_slot_fp64<BAND>(kBrick * bx + i, kBrick * by + j, kBrick * bz + k, s_th, K,
-                                               (int)(bits - kMagicBits));
-        int row = idx - band_rel;
-        if (row < 0 || row >= BAND) {
-            atomicExch(status, kStatusInternal);
-            row = row < 0 ? 0 : BAND - 1;
-        }
-        if (DEBUG) debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
-        const uint32_t off = (uint32_t)cl * L::kCellBytes + (uint32_t)row * L::kRowBytes;
-        float4 v0 = *reinterpret_cast<const float4*>(bufp + off);
-        float4 v1 = *reinterpret_cast<const float4*>(bufp + off + 16u);
-        if (INTERP) {
-            const float4 u0 = *reinterpret_cast<const float4*>(bufp + off + 32u);
-            const float4 u1 = *reinterpret_cast<const float4*>(bufp + off + 48u);
-            lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
-        }
-        pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
-    }
-    return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
-}
-
-// One work item: observation tile `tile` x source split `split` at time
-// index `ti` of problem p.  g_it counts the CTA's staged bricks across items
-// (it selects the buffer and the mbarrier phase).  Returns false if a copy
-// did not complete in time (the caller stops).  GEO: undecided pairs take
-// their FP64 geometry from shared memory and are counted there (the
-// single-problem kernel); otherwise from global memory (the batched kernel).
-template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool GEO>
-__device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const int comp,
-                                            const int tile, const int split, const int ti, uint32_t& g_it) {
-    using L = Layout<BAND>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int K = p.K;
-    const int KT = K + 2 * kTabGuard;
-    uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem + L::kCtrl);
-    int* s_band = reinterpret_cast<int*>(smem + L::kCtrl + 16);
-    float2* s_tab = reinterpret_cast<float2*>(smem + L::kTab);
-    double* s_th = reinterpret_cast<double*>(smem + L::kTab + (size_t)KT * sizeof(float2));
-    float* s_D = reinterpret_cast<float*>(s_th + K + 1);
-
-    const int tid = threadIdx.x;
-
-    const float2* g_tab = p.tab2 + (size_t)ti * KT;
-    for (int i = tid; i < KT; i += kTileThreads) s_tab[i] = g_tab[i];
-    const double* g_th = p.theta + (size_t)ti * (K + 1);
-    for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
-    const double* txyz = p.obs_xyz + (size_t)tile * kTileThreads * 3;
-    if constexpr (!EXACT && GEO)
-        staged_fill_geometry<BAND>(txyz, K, p.nbx + p.nby + p.nbz, p.npx, p.npy, p.npz, p.lo[0], p.lo[1], p.lo[2],
-                                   p.d[0], p.d[1], p.d[2]);
-    const double cox = txyz[0], coy = txyz[1], coz = txyz[2];
-    const int nbxy = p.nbx + p.nby;
-    for (int i = tid; i < nbxy + p.nbz; i += kTileThreads) {
-        const int a = i < p.nbx ? 0 : (i < nbxy ? 1 : 2);
-        const int b = a == 0 ? i : (a == 1 ? i - p.nbx : i - nbxy);
-        const double co = a == 0 ? cox : (a == 1 ? coy : coz);
-        s_D[i] = __double2float_rn(__dsub_rn(co, cell_center(p.lo[a], p.d[a], kBrick * b)));
-    }
-    __syncthreads();
-
-    ThreadCtx ctx;
-    ctx.slot = tile * kTileThreads + tid;
-    const double xo = txyz[3 * tid + 0], yo = txyz[3 * tid + 1], zo = txyz[3 * tid + 2];
-    const float oox = __double2float_rn(__dsub_rn(xo, cox));
-    const float ooy = __double2float_rn(__dsub_rn(yo, coy));
-    const float ooz = __double2float_rn(__dsub_rn(zo, coz));
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        ctx.rlo[a] = p.obs_scr[(2 * a) * p.n_slots + ctx.slot];
-        ctx.rhi[a] = p.obs_scr[(2 * a + 1) * p.n_slots + ctx.slot];
-    }
-    const TimeParams tp = p.times[ti];
-    const float K32 = p.K32;
-    const float Ag = tp.Ag;
-    const float A = tp.A, A_lo = tp.A_lo, K32_lo = p.K32_lo;   // interpolation weights only
-    const float d32x = p.d32[0], d32y = p.d32[1], d32z = p.d32[2];
-    const size_t n_cells = (size_t)p.n_bricks * kBrickCells;
-    const uint32_t mbar_u32[2] = {smem_u32(&s_mbar[0]), smem_u32(&s_mbar[1])};
-    const uint32_t buf_u32[2] = {smem_u32(smem), smem_u32(smem + L::kBufBytes)};
-
-    // Producer (thread 0): slot band of (this tile, brick b) and its TMA copy.
-    float tbox[6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) tbox[a] = tid == 0 ? p.tile_box[(size_t)tile * 6 + a] : 0.f;
-    auto issue = [&](int bx, int by, int bz, int b, int bufi) {
-        const float cb[3] = {-s_D[bx], -s_D[p.nbx + by], -s_D[nbxy + bz]};
-        const float dd[3] = {d32x, d32y, d32z};
-        float mn2 = 0.f, mx2 = 0.f, span = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            // pair offsets D = x_o - x_s span [box_lo - (cb + 3d), box_hi - cb]
-            const float lo = tbox[a] - (cb[a] + 3.f * dd[a]);
-            const float hi = tbox[3 + a] - cb[a];
-            const float mn = lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
-            const float mx = fmaxf(fabsf(lo), fabsf(hi));
-            mn2 = fmaf(mn, mn, mn2);
-            mx2 = fmaf(mx, mx, mx2);
-            span += fabsf(cb[a]) + fabsf(tbox[a]) + fabsf(tbox[3 + a]) + 3.f * dd[a];
-        }
-        const float slack = 1e-5f * span;
-        const float rmin = fmaxf(sqrtf(mn2) * (1.f - 1e-5f) - slack, 0.f);
-        const float rmax = sqrtf(mx2) * (1.f + 1e-5f) + slack;
-        const int hi_rel = (int)floorf(tp.A - rmin * K32) + 2;
-        const int lo_rel = (int)floorf(tp.A - rmax * K32) - 2;
-        const int band_rel = max(lo_rel, tp.oldest_rel);
-        if (hi_rel - band_rel + 1 > BAND) atomicExch(p.status, kStatusInternal);
-        s_band[bufi] = band_rel;
-        const long long band_abs = tp.k0 + band_rel;
-        int y0;
-        if (band_abs >= 0)
-            y0 = (int)(band_abs % p.H);
-        else
-            y0 = band_abs < -(1ll << 30) ? -(1 << 30) : (int)band_abs;   // rows < 0 read as zero
-        // the buffer was last read through the generic proxy: order those
-        // reads before the async-proxy write
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(mbar_u32[bufi], L::kBufBytes);
-        tma_load_3d(buf_u32[bufi], tmap_ptr, 0, y0, b * kBrickCells, mbar_u32[bufi]);
-    };
-
-    float se[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
-    float ce[3] = {0.f, 0.f, 0.f}, cb[3] = {0.f, 0.f, 0.f};
-    const int b_begin = split * p.bricks_per_split;
-    const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
-    const uint32_t tbase = L::kTab + (uint32_t)(kTabGuard - kMagicBits) * 8u;
-
-    if (tid == 0 && b_begin < b_end) {
-        const int rest = b_begin / p.nbx;
-        if constexpr (L::kBufs == 2)
-            issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, g_it & 1);
-        else
-            issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, 0);
-    }
-    int64_t aborted_at = -1;
-    // brick coordinates of b, advanced incrementally (no division per brick)
-    int bx = 0, by = 0, bz = 0;
-    if (b_begin < b_end) {
-        bx = b_begin % p.nbx;
-        const int rest = b_begin / p.nbx;
-        by = rest % p.nby;
-        bz = rest / p.nby;
-    }
-    for (int b = b_begin; b < b_end; ++b) {
-        const uint32_t it = g_it + (uint32_t)(b - b_begin);
-        // buffer and mbarrier phase of brick b (one phase per copy into a buffer)
-        int buf;
-        bool ready;
-        if constexpr (L::kBufs == 2) {
-            buf = it & 1;
-            if (tid == 0 && b + 1 < b_end) {
-                int nx = bx + 1, ny = by, nz = bz;
-                if (nx == p.nbx) {
-                    nx = 0;
-                    if (++ny == p.nby) { ny = 0; ++nz; }
-                }
-                issue(nx, ny, nz, b + 1, buf ^ 1);
-            }
-            ready = mbar_wait_bounded(mbar_u32[buf], (it >> 1) & 1);
-        } else {
-            buf = 0;
-            ready = mbar_wait_bounded(mbar_u32[0], it & 1);
-        }
-        if (ready) {
-            const int band_rel = s_band[buf];
-            const float Px = oox + s_D[bx];
-            const float Py = ooy + s_D[p.nbx + by];
-            const float Pz = ooz + s_D[nbxy + bz];
-            const uint32_t gbase = (uint32_t)buf * L::kBufBytes -
-                                   (uint32_t)(kMagicBits + band_rel) * L::kRowBytes;
-            const bool full = (bx < p.nfull[0]) & (by < p.nfull[1]) & (bz < p.nfull[2]);
-            const bool near = (ctx.rlo[0] <= kBrick * bx + 3) & (ctx.rhi[0] >= kBrick * bx) &
-                              (ctx.rlo[1] <= kBrick * by + 3) & (ctx.rhi[1] >= kBrick * by) &
-                              (ctx.rlo[2] <= kBrick * bz + 3) & (ctx.rhi[2] >= kBrick * bz);
-            float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
-            if (full && !__any_sync(kFull, near)) {
-                // Per-axis offsets and squares of the brick's 4 columns; the
-                // z slabs are a rolled loop (keeps the hot body small), the
-                // 16 cells of a slab are unrolled.
-                float ddx[4], ddy[4], sqx[4], sqy[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    ddx[i] = fmaf(-(float)i, d32x, Px);
-                    ddy[i] = fmaf(-(float)i, d32y, Py);
-                    sqx[i] = __fmul_rn(ddx[i], ddx[i]);
-                    sqy[i] = __fmul_rn(ddy[i], ddy[i]);
-                }
-                uint64_t mask = 0;
-                float2 acc_eyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
-                float acc_ex = 0.f, acc_bz = 0.f;
-#pragma unroll 1
-                for (int k = 0; k < 4; ++k) {
-                    const float dz = fmaf(-(float)k, d32z, Pz);
-                    const float sqz = __fmul_rn(dz, dz);
-                    const uint32_t gk = gbase + (uint32_t)(k * 16) * L::kCellBytes;
-                    float2 dyz[4], dzx[4];      // (dy_j, dz) and (dz, dx_i) operand pairs
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        dyz[i] = make_float2(ddy[i], dz);
-                        dzx[i] = make_float2(dz, ddx[i]);
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float syz = __fadd_rn(sqy[j], sqz);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int c16 = j * 4 + i;
-                            const float S = __fadd_rn(sqx[i], syz);
-                            float ri = rsqrt_ftz(S);
-                            const float u = fmaf(-(S * ri), K32, Ag);
-                            const uint32_t bits = __float_as_uint(__fadd_rd(u, kMagic));
-                            // row of candidate k' (bits), moved down one row when S is past
-                            // the threshold: lower = 0 or ~0u
-                            const uint32_t row_hi = gk + bits * L::kRowBytes;
-                            uint32_t lower;
-                            if (EXACT) {
-                                // T_hi == T_lo: one 32-bit threshold decides
-                                const float th = *reinterpret_cast<const float*>(smem + (tbase + 4u + bits * 8u));
-                                lower = gt_mask(S, th);
-                            } else {
-                                const float2 th = *reinterpret_cast<const float2*>(smem + (tbase + bits * 8u));
-                                lower = gt_mask(S, th.y);
-                                if (!(S <= th.x) && lower == 0u) {   // undecided: redo after the brick
-                                    mask |= 1ull << (k * 16 + c16);
-                                    ri = 0.f;
-                                }
-                            }
-                            if (DEBUG) {
-                                p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + k * 16 + c16] =
-                                    (int)(tp.k0 + (int)(bits + lower - kMagicBits));
-                            }
-                            const uint32_t off = row_hi + lower * L::kRowBytes + (uint32_t)c16 * L::kCellBytes;
-                            float4 v0 = *reinterpret_cast<const float4*>(smem + off);
-                            float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
-                            if (INTERP) {   // slot n+1 is the next row of the same cell
-                                const float4 u0 = *reinterpret_cast<const float4*>(smem + off + 32u);
-                                const float4 u1 = *reinterpret_cast<const float4*>(smem + off + 48u);
-                                const float nrel = __uint_as_float(bits + lower) - kMagic;
-                                lerp8(v0, v1, u0, u1, interp_weight(S, ri, nrel, A, A_lo, K32, K32_lo));
-                            }
-                            // Eqs. E-1/B-1 with packed pairs, r^-2 factored out:
-                            //   (q, Vx) = ((drho, dJx/c) + (c rho, Jx) r^-1) r^-2,  q the D-term of E
-                            //   (Vy, Vz) = ((dJy, dJz)/c + (Jy, Jz) r^-1) r^-2
-                            const float2 ri2 = make_float2(ri, ri);
-                            const float2 r2 = __fmul2_rn(ri2, ri2);
-                            const float2 qvx = __fmul2_rn(__ffma2_rn(make_float2(v0.x, v0.y), ri2,
-                                                                     make_float2(v1.x, v1.y)), r2);
-                            const float2 vyz = __fmul2_rn(__ffma2_rn(make_float2(v0.z, v0.w), ri2,
-                                                                     make_float2(v1.z, v1.w)), r2);
-                            const float q = qvx.x, vx = qvx.y;
-                            // E' += D q - (dJ/c) / R
-                            acc_ex = fmaf(ddx[i], q, acc_ex);
-                            acc_ex = fmaf(-v1.y, ri, acc_ex);
-                            acc_eyz = __ffma2_rn(dyz[j], make_float2(q, q), acc_eyz);
-                            acc_eyz = __ffma2_rn(make_float2(-v1.z, -v1.w), ri2, acc_eyz);
-                            // B += V x D
-                            acc_bxy = __ffma2_rn(vyz, dzx[i], acc_bxy);          // (Vy dz, Vz dx)
-                            acc_bxy.x = fmaf(-vyz.y, ddy[j], acc_bxy.x);         // - Vz dy
-                            acc_bxy.y = fmaf(-vx, dz, acc_bxy.y);                // - Vx dz
-                            acc_bz = fmaf(vx, ddy[j], acc_bz);
-                            acc_bz = fmaf(-vyz.x, ddx[i], acc_bz);
-                        }
-                    }
-                }
-                pe[0] += acc_ex;
-                pe[1] += acc_eyz.x;
-                pe[2] += acc_eyz.y;
-                pb[0] += acc_bxy.x;
-                pb[1] += acc_bxy.y;
-                pb[2] += acc_bz;
-                if (!EXACT) {
-                    if (__any_sync(kFull, mask != 0ull)) {
-                        FixSums f;
-                        if constexpr (GEO) {
-                            f = staged_fixup_geo<BAND, DEBUG, INTERP>(
-                                mask, smem + (uint32_t)buf * L::kBufBytes, band_rel, Px, Py, Pz, d32x, d32y, d32z,
-                                K32, Ag, A, A_lo, K32_lo, ctx.slot, bx, by, bz, s_th, K, p.status, p.debug_slots,
-                                n_cells, b, tp.k0);
-                        } else {
-                            f = staged_fixup<BAND, DEBUG, INTERP>(
-                                mask, smem + (uint32_t)buf * L::kBufBytes, band_rel, Px, Py, Pz, d32x, d32y, d32z,
-                                K32, Ag, A, A_lo, K32_lo, p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
-                                p.d[1], p.d[2], bx, by, bz, s_th, K, p.fallbacks, p.status, p.debug_slots, n_cells,
-                                b, tp.k0);
-                        }
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            pe[a] += f.v[a];
-                            pb[a] += f.v[3 + a];
-                        }
-                    }
-                }
-            } else {
-                // Bricks with padding cells or screened pairs: rolled loop with
-                // per-pair checks and clamped indices.
-                for (int cl = 0; cl < kBrickCells; ++cl) {
-                    const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
-                    const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
-                    const bool real = (ix < p.n_src_axis[0]) & (iy < p.n_src_axis[1]) & (iz < p.n_src_axis[2]);
-                    const bool scr = (ix >= ctx.rlo[0]) & (ix <= ctx.rhi[0]) & (iy >= ctx.rlo[1]) &
-                                     (iy <= ctx.rhi[1]) & (iz >= ctx.rlo[2]) & (iz <= ctx.rhi[2]);
-                    const bool use = real & !scr;
-                    const float dx = fmaf(-(float)i, d32x, Px);
-                    const float dy = fmaf(-(float)j, d32y, Py);
-                    const float dz = fmaf(-(float)k, d32z, Pz);
-                    const float S = __fadd_rn(__fmul_rn(dx, dx),
-                                              __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-                    float ri = rsqrt_ftz(S);
-                    const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-                    const uint32_t tix = min(bits - (uint32_t)kMagicBits + (uint32_t)kTabGuard, (uint32_t)(KT - 1));
-                    const float2 th = s_tab[tix];
-                    const bool lower = S > th.y;
-                    int idx = (int)tix - kTabGuard - (lower ? 1 : 0);
-                    if (use && !(S <= th.x) && !lower) {
-                        if constexpr (EXACT || !GEO) {
-                            idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
-                                                    p.d[1], p.d[2], ix, iy, iz, s_th, K, idx, p.fallbacks);
-                        } else {
-                            idx = staged_slot_fp64<BAND>(ix, iy, iz, s_th, K, idx);
-                        }
-                    }
-                    int row = idx - band_rel;
-                    if (!use) {
-                        ri = 0.f;
-                        row = 0;
-                    } else if (row < 0 || row >= BAND) {
-                        atomicExch(p.status, kStatusInternal);
-                        row = row < 0 ? 0 : BAND - 1;
-                    }
-                    if (DEBUG) {
-                        p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + cl] =
-                            scr ? INT32_MIN : (int)(tp.k0 + idx);
-                    }
-                    const uint32_t off = (uint32_t)buf * L::kBufBytes + (uint32_t)cl * L::kCellBytes +
-                                         (uint32_t)row * L::kRowBytes;
-                    float4 v0 = *reinterpret_cast<const float4*>(smem + off);
-                    float4 v1 = *reinterpret_cast<const float4*>(smem + off + 16u);
-                    if (INTERP) {   // row + 1 < BAND: the band covers slot n+1 of every pair
-                        const float4 u0 = *reinterpret_cast<const float4*>(smem + off + 32u);
-                        const float4 u1 = *reinterpret_cast<const float4*>(smem + off + 48u);
-                        lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
-                    }
-                    pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (comp) {
-                    kahan_add(se[a], ce[a], pe[a]);
-                    kahan_add(sb[a], cb[a], pb[a]);
-                } else {
-                    se[a] += pe[a];
-                    sb[a] += pb[a];
-                }
-            }
-        }
-        if (++bx == p.nbx) {
-            bx = 0;
-            if (++by == p.nby) { by = 0; ++bz; }
-        }
-        // every thread is done with this buffer before it is refilled
-        if (__syncthreads_or(!ready)) {
-            aborted_at = b - b_begin;
-            break;
-        }
-        if constexpr (L::kBufs == 1) {
-            // single buffer: the next brick's copy starts now (bx, by, bz already name it)
-            if (tid == 0 && b + 1 < b_end) issue(bx, by, bz, b + 1, 0);
-        }
-    }
-    if (aborted_at >= 0) {
-        // a copy did not complete in time: report, then wait (bounded) for
-        // the copies still in flight before the shared memory goes away
-        if (tid == 0) {
-            const uint32_t it = g_it + (uint32_t)aborted_at;
-            atomicExch(p.status, kStatusTimeout);
-            if constexpr (L::kBufs == 2) {
-                mbar_wait_bounded(mbar_u32[it & 1], (it >> 1) & 1);
-                if (b_begin + aborted_at + 1 < b_end)
-                    mbar_wait_bounded(mbar_u32[(it + 1) & 1], ((it + 1) >> 1) & 1);
-            } else {
-                mbar_wait_bounded(mbar_u32[0], it & 1);   // the next copy was never issued
-            }
-        }
-        __syncthreads();
-    }
-    g_it += (uint32_t)(b_end > b_begin ? b_end - b_begin : 0);
-    if constexpr (!EXACT && GEO) {
-        // every thread passed the loop's last barrier: the item's count is complete
-        const uint32_t n = reinterpret_cast<const uint32_t*>(smem + L::kGeo)[3];
-        if (tid == 0 && n) atomicAdd(p.fallbacks, (unsigned long long)n);
-    }
-
-    double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        out[(size_t)a * p.n_slots] = comp ? (double)se[a] - (double)ce[a] : (double)se[a];
-        out[(size_t)(3 + a) * p.n_slots] = comp ? (double)sb[a] - (double)cb[a] : (double)sb[a];
-    }
-    return aborted_at < 0;
-}
-
-template <int BAND, bool EXACT, bool DEBUG, bool INTERP>
-__global__ void __launch_bounds__(kTileThreads, 2)
-    sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p) {
-    staged_init_barriers<BAND>();
-    uint32_t g_it = 0;
-    staged_item<BAND, EXACT, DEBUG, INTERP, true>(&tmap, p, p.comp, blockIdx.x, blockIdx.y, blockIdx.z, g_it);
-}
-
-// One item of the batched kernel as a call of its own: the item body gets
-// the register budget of the single-problem kernel instead of sharing it
-// with the queue loop (the call happens once per item, thousands of pairs).
-template <int BAND, bool EXACT>
-__device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int split,
-                                               int ti, uint32_t& g_it) {
-    return staged_item<BAND, EXACT, false, false, false>(map, p, p.comp, tile, split, ti, g_it);
-}
-
-// Persistent batched kernel: CTAs take (problem, time, split, tile) items
-// from a queue until it is empty; each item runs the same code as the
-// single-problem kernel, so a problem's result does not depend on the batch.
-template <int BAND, bool EXACT>
-__global__ void __launch_bounds__(kTileThreads, 2) sum_f32_staged_batch(const __grid_constant__ StagedBatchArgs a) {
-    using L = Layout<BAND>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    int* s_item = reinterpret_cast<int*>(smem + L::kCtrl + 32);
-    __shared__ SumParams s_par;
-    staged_init_barriers<BAND>();
-    uint32_t g_it = 0;
-    for (;;) {
-        if (threadIdx.x == 0) *s_item = (int)atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const int item = *s_item;
-        __syncthreads();
-        if (item >= a.n_items) break;
-        int lo = 0, hi = a.n - 1;                 // problem: last start <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.item_start[mid] <= item) lo = mid; else hi = mid - 1;
-        }
-        // The item's parameters go to shared memory: read through a dynamic
-        // index into global memory, their loop invariants would be held in
-        // registers (the single-problem kernel reads them from the constant
-        // bank) and the batched kernel would spill.
-        {
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.params[lo]);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(&s_par);
-            for (int w = threadIdx.x; w < (int)(sizeof(SumParams) / 4); w += kTileThreads) dst[w] = src[w];
-        }
-        __syncthreads();
-        const SumParams& p = s_par;
-        const int local = item - a.item_start[lo];
-        const int per_t = p.n_tiles * p.n_split;
-        const int ti = local / per_t;
-        const int r = local - ti * per_t;
-        const int split = r / p.n_tiles;
-        const int tile = r - split * p.n_tiles;
-        if (!staged_batch_item<BAND, EXACT>(&a.maps[lo], p, tile, split, ti, g_it)) break;
-    }
-}
+namespace staged {
 
 // Diagnostic: wait on an mbarrier that nothing arrives at, with the same
 // bounded wait as the staged kernel, and report the outcome in *status.
@@ -718,75 +25,56 @@ __global__ void wait_timeout_probe(int32_t* status, uint64_t limit_ns) {
     if (threadIdx.x == 0) *status = ok ? 0 : kStatusTimeout;
 }
 
+}  // namespace staged
+
 cudaError_t launch_wait_timeout_probe(int32_t* status, uint64_t limit_ns, cudaStream_t s) {
-    wait_timeout_probe<<<1, 32, 0, s>>>(status, limit_ns);
+    staged::wait_timeout_probe<<<1, 32, 0, s>>>(status, limit_ns);
     return cudaGetLastError();
 }
 
-bool staged_band_supported(int band) { return band == 16 || band == 24 || band == 32 || band == 48; }
+bool staged_band_supported(int band) {
+    for (int b : kStagedBands)
+        if (b == band) return true;
+    return false;
+}
+
+size_t staged_buffer_bytes(int band) { return (size_t)staged_stage_cells(band) * band * 32; }
 
 size_t staged_smem_bytes(const SumParams& p, int band, bool batched) {
-    const size_t buf = (size_t)kBrickCells * band * 32;
-    const size_t tab = (band >= 32 ? 1 : 2) * buf + 64;   // brick buffers, mbarriers / band origins / item
+    // alignment pad, two stage buffers, mbarriers / band origins / item / tile box
+    const size_t tab = 2 * staged_buffer_bytes(band) + kStagedCtrlBytes;
     const int nb_sum = p.nbx + p.nby + p.nbz;
     size_t b = tab + (size_t)(p.K + 2 * kTabGuard) * sizeof(float2);
     b += (size_t)(p.K + 1) * sizeof(double);
     b += (size_t)nb_sum * sizeof(float);
     // non-lattice geometry: FP64 points of the tile and cell centres, for the fall-back
     if (!p.exact && !batched)
-        b = staged_geometry_offset((uint32_t)tab, p.K, nb_sum) + (size_t)(3 * kTileThreads + p.npx + p.npy + p.npz) * 8;
-    return b;
+        b = staged::staged_geometry_offset((uint32_t)tab, p.K, nb_sum) +
+            (size_t)(3 * kTileThreads + p.npx + p.npy + p.npz) * 8;
+    return kStagedAlignPad + b;
 }
 
-template <int BAND, bool EXACT, bool DEBUG, bool INTERP = false>
-static cudaError_t launch_variant(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
-    const dim3 grid(p.n_tiles, p.n_split, p.n_t);
-    const size_t smem = staged_smem_bytes(p, BAND, false);
-    auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG, INTERP>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tensor_map);
-    k<<<grid, kTileThreads, smem, s>>>(*tm, p);
-    return cudaGetLastError();
-}
-
-template <int BAND, bool EXACT>
-static cudaError_t launch_batch_variant(const StagedBatchArgs& a, size_t smem, int grid, cudaStream_t s) {
-    auto k = sum_f32_staged_batch<BAND, EXACT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kTileThreads, smem, s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_sum_f32_staged(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
+    switch (c.band) {
+        case 16: return staged_launch_16(p, c, s);
+        case 24: return staged_launch_24(p, c, s);
+        case 32: return staged_launch_32(p, c, s);
+        case 48: return staged_launch_48(p, c, s);
+        case 64: return staged_launch_64(p, c, s);
+        case 96: return staged_launch_96(p, c, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_sum_f32_staged_batch(const StagedBatchArgs& a, int band, bool exact, size_t smem,
                                         int grid, cudaStream_t s) {
     switch (band) {
-        case 16: return exact ? launch_batch_variant<16, true>(a, smem, grid, s) : launch_batch_variant<16, false>(a, smem, grid, s);
-        case 24: return exact ? launch_batch_variant<24, true>(a, smem, grid, s) : launch_batch_variant<24, false>(a, smem, grid, s);
-        case 32: return exact ? launch_batch_variant<32, true>(a, smem, grid, s) : launch_batch_variant<32, false>(a, smem, grid, s);
-        case 48: return exact ? launch_batch_variant<48, true>(a, smem, grid, s) : launch_batch_variant<48, false>(a, smem, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int BAND>
-static cudaError_t launch_band(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
-    const bool dbg = p.debug_slots != nullptr;
-    // the slot of every pair is the same with and without interpolation, so
-    // the slot-recording kernels exist only in the floor-rule form
-    if (!dbg && p.interp)
-        return c.exact ? launch_variant<BAND, true, false, true>(p, c, s) : launch_variant<BAND, false, false, true>(p, c, s);
-    if (c.exact) return dbg ? launch_variant<BAND, true, true>(p, c, s) : launch_variant<BAND, true, false>(p, c, s);
-    return dbg ? launch_variant<BAND, false, true>(p, c, s) : launch_variant<BAND, false, false>(p, c, s);
-}
-
-cudaError_t launch_sum_f32_staged(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
-    switch (c.band) {
-        case 16: return launch_band<16>(p, c, s);
-        case 24: return launch_band<24>(p, c, s);
-        case 32: return launch_band<32>(p, c, s);
-        case 48: return launch_band<48>(p, c, s);
+        case 16: return staged_launch_batch_16(a, exact, smem, grid, s);
+        case 24: return staged_launch_batch_24(a, exact, smem, grid, s);
+        case 32: return staged_launch_batch_32(a, exact, smem, grid, s);
+        case 48: return staged_launch_batch_48(a, exact, smem, grid, s);
+        case 64: return staged_launch_batch_64(a, exact, smem, grid, s);
+        case 96: return staged_launch_batch_96(a, exact, smem, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

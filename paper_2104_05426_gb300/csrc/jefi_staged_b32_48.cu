@@ -1,0 +1,9 @@
+// jefi_staged_b32_48.cu -- the TMA-staged FP32 sum compiled for bands of 32
+// and 48 slots (stages of two z slabs, 128-byte swizzled lines of 4 slots);
+// the kernels are the templates of jefi_staged.cuh.
+#include "jefi_staged.cuh"
+
+namespace jefi {
+JEFI_STAGED_BAND_LAUNCHERS(32)
+JEFI_STAGED_BAND_LAUNCHERS(48)
+}  // namespace jefi

@@ -32,23 +32,18 @@ from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
-from . import (JEFI_FLAG_SHARED_RING, JefiError, default_params, grid, jefi_batch_plan_create,
+from workloads import Blob, MovingGaussians
+
+from . import (JEFI_EEVICTED, JEFI_FLAG_SHARED_RING, JefiError, default_params, grid, jefi_batch_plan_create,
                jefi_batch_plan_destroy, jefi_batch_plan_launch, jefi_batch_plan_tune, jefi_create,
                jefi_create_view, jefi_destroy, jefi_eval_batch, jefi_get_info, jefi_push_sources,
                jefi_valid_window)
 
 
-@dataclass
-class Blob:
-    q: float
-    sigma: float
-    x0: Tuple[float, float, float]
-    v: Tuple[float, float, float]
-
-
 class ServedProblem:
-    """A resident source problem: a cube grid of Gaussian charges moving at constant
-    velocity, its base handle and a device-side slice generator."""
+    """A resident source problem: a cube grid of Gaussian charges moving at
+    constant velocity (the seeded source model of ``workloads``), its base
+    handle and a device-side slice generator."""
 
     def __init__(self, side: int, half_width: float, H: int, dt: float, blobs: List[Blob],
                  device="cuda", stream=None):
@@ -61,6 +56,7 @@ class ServedProblem:
         self.H = H
         self.dt = dt
         self.blobs = blobs
+        self.model = MovingGaussians(blobs)
         d = 2.0 * half_width / side
         self.grid = grid((side,) * 3, (-half_width,) * 3, (d,) * 3)
         prm = default_params(dt=dt, history_slots=H, precision="fp32c", flags=JEFI_FLAG_SHARED_RING)
@@ -68,29 +64,19 @@ class ServedProblem:
         # loop runs then cost no cudaMalloc / cudaFree (cudaFree waits for the device)
         self.handle = jefi_create(self.grid, obs_points=np.zeros((0, 3)), params=prm, stream=stream,
                                   torch_allocator=True)
+        # cell centres resident on the device: a slice is generated by device
+        # ops alone (a host-to-device copy per slice would block the host
+        # behind the push stream, which waits for the batches in flight)
         ax = -half_width + (torch.arange(side, dtype=torch.float64, device=self.device) + 0.5) * d
         z, y, x = torch.meshgrid(ax, ax, ax, indexing="ij")
         self.pts = torch.stack([x.reshape(-1), y.reshape(-1), z.reshape(-1)], dim=1)
-        # blob parameters resident on the device: a slice is generated by
-        # device ops alone (a host-to-device copy per slice would block the
-        # host behind the push stream, which waits for the batches in flight)
-        f64 = dict(dtype=torch.float64, device=self.device)
-        self.b_x0 = torch.tensor([b.x0 for b in blobs], **f64)
-        self.b_v = torch.tensor([b.v for b in blobs], **f64)
-        self.b_amp = torch.tensor([b.q / ((2.0 * math.pi) ** 1.5 * b.sigma ** 3) for b in blobs], **f64)
-        self.b_inv2s2 = torch.tensor([0.5 / b.sigma ** 2 for b in blobs], **f64)
         self.n_pushed = 0
         self.last_push = None               # event after the latest push
         self.readers: List = []             # events of batches reading the ring
 
     def slice_at(self, t: float):
         """rho = sum of the blobs' Gaussians at time t, J = sum of rho_blob v_blob."""
-        torch = self.torch
-        centres = self.b_x0 + self.b_v * t                                # [nb, 3]
-        r2 = ((self.pts[None, :, :] - centres[:, None, :]) ** 2).sum(dim=2)  # [nb, N]
-        g = self.b_amp[:, None] * torch.exp(-r2 * self.b_inv2s2[:, None])
-        rho = g.sum(dim=0)
-        J = torch.einsum("bn,ba->na", g, self.b_v)
+        rho, J = self.model.sample_torch(self.pts, t)
         return rho.contiguous(), J.contiguous()
 
     def push_next(self, stream):
@@ -129,6 +115,8 @@ class Request:
 class ServingStats:
     completed: int
     rejected: int
+    evicted: int
+    failed: int
     wall_s: float
     p50_ms: float
     p99_ms: float
@@ -150,7 +138,7 @@ class ServingStats:
 class ServingEngine:
     def __init__(self, problems: List[ServedProblem], obs_half_width: float, n_streams: int = 4,
                  memory_budget: float = 64e9, max_batch: int = 64, tick_s: Optional[float] = None,
-                 keep_outputs: bool = False):
+                 keep_outputs: bool = False, keep_ids=None):
         import torch
 
         self.torch = torch
@@ -162,30 +150,31 @@ class ServingEngine:
         self.max_batch = max_batch
         self.tick_s = tick_s
         self.keep_outputs = keep_outputs
+        self.keep_ids = set(keep_ids or ())     # request ids whose E and B are kept
         self.views: Dict[Tuple[int, int], List] = {}     # (problem, side) -> [[view, busy, bytes]]
+        self.view_bytes: Dict[Tuple[int, int], int] = {}  # measured device bytes of a view
         self.resident_bytes = sum(jefi_get_info(p.handle)["device_bytes"] for p in problems)
         self.used_bytes = self.resident_bytes
         self.peak_bytes = self.used_bytes
         self.views_created = 0
 
     # ------------------------------------------------------------------ views
-    def _acquire_view(self, req: Request):
-        key = (req.problem, req.obs_side)
-        for entry in self.views.setdefault(key, []):
+    def _free_view(self, key):
+        for entry in self.views.get(key, []):
             if not entry[1]:
-                entry[1] = True
                 return entry
+        return None
+
+    def _create_view(self, req: Request):
         p = self.problems[req.problem]
         s = req.obs_side
         d = 2.0 * self.obs_half_width / s
         g = grid((s,) * 3, (-self.obs_half_width,) * 3, (d,) * 3)
         view = jefi_create_view(p.handle, obs_grid=g)
         nbytes = jefi_get_info(view)["device_bytes"]
-        entry = [view, True, nbytes]
-        self.views[key].append(entry)
-        self.used_bytes += nbytes
+        self.view_bytes[(req.problem, s)] = nbytes
         self.views_created += 1
-        return entry
+        return [view, True, nbytes]
 
     def _evict_idle(self, need: int):
         """Destroy cached views that no batch is using until `need` bytes are freed."""
@@ -216,7 +205,9 @@ class ServingEngine:
         free_streams = list(range(len(self.streams)))
         done: List[Request] = []
         batch_sizes: List[int] = []
-        rejected = 0
+        rejected = 0            # refused by the memory budget
+        evicted = 0             # the time's slices were overwritten before the launch
+        failed = 0              # other errors of a batch
         torch.cuda.synchronize()
         start = time.perf_counter()
         next_tick = self.tick_s if self.tick_s else math.inf
@@ -231,14 +222,16 @@ class ServingEngine:
                     p.push_next(self.push_stream)
                 next_tick += self.tick_s
                 progressed = True
-            # admission, first in first out, by device memory
+            # admission, first in first out, by device memory (a view's real
+            # bytes once one of its kind has been created, else an estimate)
             while queue:
                 req = queue[0]
-                need = self._output_bytes(req.obs_side)
                 key = (req.problem, req.obs_side)
-                has_free = any(not e[1] for e in self.views.get(key, []))
-                if not has_free:
-                    need += self._estimate_view_bytes(req)
+                entry = self._free_view(key)
+                out_bytes = self._output_bytes(req.obs_side)
+                need = out_bytes
+                if entry is None:
+                    need += self.view_bytes.get(key, self._estimate_view_bytes(req))
                 if self.used_bytes + need > self.memory_budget:
                     self._evict_idle(self.used_bytes + need - self.memory_budget)
                 if self.used_bytes + need > self.memory_budget:
@@ -249,22 +242,37 @@ class ServingEngine:
                         progressed = True
                         continue
                     break
+                if entry is None:
+                    entry = self._create_view(req)
+                    if self.used_bytes + entry[2] + out_bytes > self.memory_budget:
+                        # the estimate was low: make room, or give the view back and wait
+                        self._evict_idle(self.used_bytes + entry[2] + out_bytes - self.memory_budget)
+                        if self.used_bytes + entry[2] + out_bytes > self.memory_budget:
+                            jefi_destroy(entry[0])
+                            if not inflight and not admitted:
+                                queue.popleft()
+                                req.error = -1
+                                rejected += 1
+                                progressed = True
+                                continue
+                            break
+                    self.views.setdefault(key, []).append(entry)
+                    self.used_bytes += entry[2]
+                else:
+                    entry[1] = True
                 queue.popleft()
-                entry = self._acquire_view(req)
                 req.view = entry
                 req.E = torch.empty((req.obs_side ** 3, 3), dtype=torch.float64, device="cuda")
                 req.B = torch.empty_like(req.E)
-                self.used_bytes += self._output_bytes(req.obs_side)
+                self.used_bytes += out_bytes
                 self.peak_bytes = max(self.peak_bytes, self.used_bytes)
-                p = self.problems[req.problem]
-                lo, hi = jefi_valid_window(entry[0])
-                if not math.isfinite(lo):
-                    lo = hi - 4 * p.dt
-                req.t = lo + (hi - lo) * req.frac
-                req.pairs = p.side ** 3 * req.obs_side ** 3
+                req.pairs = self.problems[req.problem].side ** 3 * req.obs_side ** 3
                 admitted.append(req)
                 progressed = True
-            # launch: one batch per free stream
+            # launch: one batch per free stream.  A request's time is placed in
+            # its problem's valid window now, after the pushes enqueued so far
+            # (the batch waits for them): a push between admission and launch
+            # moves the window.
             while admitted and free_streams:
                 si = free_streams.pop()
                 stream = self.streams[si]
@@ -273,13 +281,16 @@ class ServingEngine:
                 for p_idx in {r.problem for r in batch}:
                     if self.problems[p_idx].last_push is not None:
                         stream.wait_event(self.problems[p_idx].last_push)
+                for r in batch:
+                    lo, hi = jefi_valid_window(r.view[0])
+                    if not math.isfinite(lo):
+                        lo = hi - 4 * self.problems[r.problem].dt
+                    r.t = lo + (hi - lo) * r.frac
                 t_launch = time.perf_counter() - start
                 try:
                     jefi_eval_batch([r.view[0] for r in batch], [r.t for r in batch],
                                     [r.E for r in batch], [r.B for r in batch], stream=stream)
-                    ok = True
                 except JefiError as e:
-                    ok = False
                     for r in batch:
                         r.error = e.code
                 ev = torch.cuda.Event()
@@ -299,11 +310,13 @@ class ServingEngine:
                         r.done = t_done
                         r.view[1] = False
                         self.used_bytes -= self._output_bytes(r.obs_side)
-                        if r.error:
-                            rejected += 1
+                        if r.error == JEFI_EEVICTED:
+                            evicted += 1
+                        elif r.error:
+                            failed += 1
                         else:
                             done.append(r)
-                        if not self.keep_outputs:
+                        if not (self.keep_outputs or r.rid in self.keep_ids):
                             r.E = r.B = None
                     free_streams.append(si)
                     progressed = True
@@ -321,7 +334,7 @@ class ServingEngine:
                 return math.nan
             return float(np.percentile(np.asarray(lat), q))
 
-        return ServingStats(completed=len(done), rejected=rejected, wall_s=wall, p50_ms=pct(50),
+        return ServingStats(completed=len(done), rejected=rejected, evicted=evicted, failed=failed, wall_s=wall, p50_ms=pct(50),
                             p99_ms=pct(99), mean_ms=float(np.mean(lat)) if lat else math.nan,
                             requests_per_s=len(done) / wall, pairs_per_s=pairs / wall,
                             max_batch=max(batch_sizes) if batch_sizes else 0,
@@ -362,8 +375,9 @@ def make_problems(n: int, seed: int, sides=(16, 64), H_range=(64, 256), half_wid
         for _ in range(int(rng.integers(1, 5))):
             v = rng.standard_normal(3)
             v *= rng.uniform(0.0, 0.5) / np.linalg.norm(v)
-            blobs.append(Blob(float(rng.choice([-1.0, 1.0])), float(rng.uniform(0.15, 0.35)),
-                              tuple(rng.uniform(-0.2, 0.2, 3) - v * H * dt * 0.5), tuple(v)))
+            q = float(rng.choice([-1.0, 1.0]))
+            sigma = float(rng.uniform(0.15, 0.35))
+            blobs.append(Blob(q, (sigma,) * 3, tuple(rng.uniform(-0.2, 0.2, 3) - v * H * dt * 0.5), tuple(v)))
         p = ServedProblem(side, half_width, H, dt, blobs)
         out.append(p)
     import torch
@@ -396,14 +410,20 @@ def poisson_requests(n: int, rate: float, n_problems: int, obs_sides=(8, 48), se
 
 def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0), sides=(16, 64),
             H_range=(64, 256), obs_sides=(8, 48), seed: int = 11, tick_s: float = 0.02,
-            n_streams: int = 4, max_batch: int = 32, memory_budget: Optional[float] = None) -> dict:
+            n_streams: int = 4, max_batch: int = 32, memory_budget: Optional[float] = None,
+            n_samples: int = 0):
     """Latency of Poisson-arriving requests against resident problems.
 
     First the saturated throughput (every request arrives at once), then, for
     each load factor f, a fresh stream of requests arriving at f times that
     rate, with one slice pushed to every problem per tick.  Returns the
     percentiles per load and the resident memory.  The device-memory budget
-    (resident histories, cached views and outputs) defaults to 64 GB."""
+    (resident histories, cached views and outputs) defaults to 64 GB.
+
+    With n_samples > 0 the outputs of that many seeded requests of the last
+    load level are kept and (result, samples) is returned; each sample holds
+    what an independent check needs to recompute the request (see
+    ``served_sample``)."""
     import torch
 
     if memory_budget is None:
@@ -420,18 +440,40 @@ def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0)
            "saturated": {"requests_per_s": sat.requests_per_s, "pairs_per_s": sat.pairs_per_s,
                          "mean_batch": sat.mean_batch}, "loads": []}
     eng.tick_s = tick_s
+    samples = []
     for i, f in enumerate(loads):
         rate = f * sat.requests_per_s
-        st = eng.run(poisson_requests(n_requests, rate=rate, n_problems=n_problems, obs_sides=obs_sides,
-                                      seed=seed + 2 + i))
+        reqs = poisson_requests(n_requests, rate=rate, n_problems=n_problems, obs_sides=obs_sides,
+                                seed=seed + 2 + i)
+        if n_samples and i == len(loads) - 1:
+            pick = np.random.Generator(np.random.PCG64(seed + 99)).choice(len(reqs), n_samples, replace=False)
+            eng.keep_ids = {int(k) for k in pick}
+        st = eng.run(reqs)
         out["loads"].append({"load": f, "offered_requests_per_s": rate, "p50_ms": st.p50_ms,
                              "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
                              "requests_per_s": st.requests_per_s, "pairs_per_s": st.pairs_per_s,
-                             "completed": st.completed, "rejected": st.rejected,
-                             "mean_batch": st.mean_batch, "peak_device_bytes": st.peak_bytes})
+                             "completed": st.completed, "rejected": st.rejected, "evicted": st.evicted,
+                             "failed": st.failed, "mean_batch": st.mean_batch,
+                             "peak_device_bytes": st.peak_bytes})
+        if eng.keep_ids:
+            samples = [served_sample(eng, r) for r in reqs if r.rid in eng.keep_ids and r.E is not None
+                       and not r.error]
+            eng.keep_ids = set()
     eng.close()
     torch.cuda.synchronize()
-    return out
+    return (out, samples) if n_samples else out
+
+
+def served_sample(eng: "ServingEngine", req: Request) -> dict:
+    """What an independent check needs to recompute one served request: the
+    problem's source grid, source model and dt (slice n is the model at n dt,
+    t0 = 0), the observation grid, the time, and the result copied to the host."""
+    p = eng.problems[req.problem]
+    s = req.obs_side
+    L = eng.obs_half_width
+    return {"rid": req.rid, "src_side": p.side, "src_half_width": p.L, "dt": p.dt, "blobs": p.blobs,
+            "obs_side": s, "obs_half_width": L, "t": req.t, "n_pushed": p.n_pushed,
+            "E": req.E.cpu().numpy(), "B": req.B.cpu().numpy()}
 
 
 def measure_batch(n_problems: int = 256, sides=(8, 48), H_range=(32, 128), obs_sides=(8, 32), seed: int = 4,
@@ -541,7 +583,7 @@ def measure_single(src_side: int, obs_side: int, H: int, reps: int = 3, seed: in
     rmax = math.sqrt(3.0) * 3.0
     dt = rmax / (H - 8)
     rng = np.random.Generator(np.random.PCG64(seed))
-    blobs = [Blob(float(q), float(rng.uniform(0.2, 0.3)), tuple(rng.uniform(-0.2, 0.2, 3)),
+    blobs = [Blob(float(q), (float(rng.uniform(0.2, 0.3)),) * 3, tuple(rng.uniform(-0.2, 0.2, 3)),
                   tuple(rng.uniform(-0.3, 0.3, 3))) for q in (1.0, -1.0)]
     p = ServedProblem(src_side, 1.0, H, dt, blobs)
     s = torch.cuda.current_stream()

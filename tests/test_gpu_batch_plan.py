@@ -189,11 +189,72 @@ def test_tuner_keeps_parity(gpu, plan_problems):
         jefi.jefi_destroy(h)
 
 
-def test_plan_refuses_interpolated_handles(gpu, plan_problems):
+def test_plan_runs_interpolated_handles(gpu, plan_problems):
+    """Second-order (JEFI_FLAG_INTERP) and floor-rule handles in one plan:
+    replays equal jefi_eval_batch bit for bit, the interpolated entries match
+    the oracle's second-order sum."""
+    import torch
+
     probs, hists = plan_problems
-    h = create(probs[1], "fp32c", flags=jefi.JEFI_FLAG_INTERP)
-    E, B = _alloc(h)
-    with pytest.raises(jefi.JefiError) as e:
-        jefi.jefi_batch_plan_create([h], [E], [B])
-    assert e.value.code == jefi.JEFI_EUNSUPPORTED
-    jefi.jefi_destroy(h)
+    specs = [(1, "fp32c", jefi.JEFI_FLAG_INTERP), (2, "fp64", jefi.JEFI_FLAG_INTERP), (3, "fp64", 0),
+             (4, "fp32c", jefi.JEFI_FLAG_INTERP | jefi.JEFI_FLAG_DIRECT_GATHER)]
+    hs = []
+    for k, prec, flags in specs:
+        h = create(probs[k], prec, flags=flags)
+        push_all(h, hists[k], upto=probs[k].n_push)
+        hs.append(h)
+    ts = []
+    for h in hs:
+        lo, hi = jefi.jefi_valid_window(h)
+        ts.append(0.5 * (lo + hi) if np.isfinite(lo) else hi - 0.5 * probs[1].dt)
+    outs = [_alloc(h) for h in hs]
+    plan = jefi.jefi_batch_plan_create(hs, [o[0] for o in outs], [o[1] for o in outs])
+    jefi.jefi_batch_plan_launch(plan, ts)
+    torch.cuda.synchronize()
+    _assert_equal(outs, _batch_reference(hs, ts))
+    for (k, prec, flags), (E, B), t in zip(specs, outs, ts):
+        p = probs[k]
+        rho, J, _, _ = hists[k]
+        n = p.n_push
+        fn = oracle.fields_interp if flags & jefi.JEFI_FLAG_INTERP else oracle.fields
+        Er, Br = fn(p.src.n, p.src.lo, p.src.d, p.obs(), rho[:n], J[:n], dt=p.dt, t0=p.t0, t=t)
+        tol = 1e-12 if prec == "fp64" else 1e-5
+        assert rel_l2(E.cpu().numpy(), Er) <= tol and rel_l2(B.cpu().numpy(), Br) <= tol, k
+    jefi.jefi_batch_plan_destroy(plan)
+    for h in hs:
+        assert jefi.jefi_get_info(h)["device_status"] == 0
+        jefi.jefi_destroy(h)
+
+
+def test_tune_cache_round_trip(gpu, plan_problems, tmp_path, monkeypatch):
+    """With JEFI_TUNE_CACHE set, a tuning stores its choice under the plan's
+    geometry key; the same batch on fresh handles then takes the stored
+    choice without timing candidates (from_cache), gives the same kernels and
+    splits, and its results still match the oracle."""
+    import torch
+
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("JEFI_TUNE_CACHE", str(path))
+    probs, hists = plan_problems
+    ts = [p.times[0] for p in probs] + [probs[0].times[0]]
+    chosen = []
+    for round_ in range(2):
+        hs, view = _handles(probs, hists)
+        entries = hs + [view]
+        outs = [_alloc(h) for h in entries]
+        plan = jefi.jefi_batch_plan_create(entries, [o[0] for o in outs], [o[1] for o in outs])
+        rep = jefi.jefi_batch_plan_tune(plan, ts)
+        assert rep["from_cache"] == round_
+        if round_ == 1:
+            assert rep["candidates"] == 1
+        chosen.append([(jefi.jefi_get_info(h)["staged_band"], jefi.jefi_get_info(h)["n_split"]) for h in entries])
+        jefi.jefi_batch_plan_launch(plan, ts)
+        torch.cuda.synchronize()
+        _assert_equal(outs, _batch_reference(entries, ts))
+        for k in range(len(hs)):
+            _check_oracle(probs, hists, k, outs[k][0], outs[k][1], ts[k], probs[k].n_push)
+        jefi.jefi_batch_plan_destroy(plan)
+        for h in [view] + hs:
+            jefi.jefi_destroy(h)
+    assert chosen[0] == chosen[1]
+    assert len(path.read_text().strip().splitlines()) == 1

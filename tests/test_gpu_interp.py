@@ -69,9 +69,9 @@ def test_interp_matches_oracle(gpu, cases, prec, tol, supplied):
     times = [hi - 0.37, hi - 0.2, hi - 0.013, hi]
     check(h, p, hist, times, supplied, tol, (prec, supplied))
     if prec != "fp64":
-        # C1's lattice tiles take the staged kernel; the dipole's shell points
-        # are too spread for any band and take the direct-gather kernel
-        assert (jefi.jefi_get_info(h)["staged_band"] > 0) == (not supplied)
+        # both take the staged kernel: C1's lattice tiles by their boxes, the
+        # dipole's shell points (radial tile order) by their distance shells
+        assert jefi.jefi_get_info(h)["staged_band"] > 0
     jefi.jefi_destroy(h)
 
 
@@ -219,22 +219,43 @@ def test_interp_staged_and_direct_kernels_agree(gpu, lattice):
         jefi.jefi_destroy(h)
 
 
-def test_interp_refused_by_batched_launch(gpu, c1):
-    """The batched kernels run the floor rule only: a batch holding a handle
-    with interpolation is refused and nothing is written."""
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32c", FP32C_TOL)])
+def test_interp_in_batched_launch(gpu, c1, cases, prec, tol):
+    """The batched kernels run the second-order rule for the handles that ask
+    for it, beside floor-rule handles in the same batch: each result is
+    bit-identical to its single evaluation and within tolerance of the
+    oracle's second-order sum (staged kernel: C1 lattice; direct gather: the
+    same problem forced onto it; the dipole's supplied derivatives)."""
     import torch
 
     p, hist = c1
-    h = create(p, "fp64", flags=INTERP)
-    push_all(h, hist)
-    _, hi = jefi.jefi_valid_window(h)
-    E = torch.full((p.n_obs, 3), 7.0, dtype=torch.float64, device="cuda")
-    B = torch.full_like(E, 7.0)
-    with pytest.raises(jefi.JefiError) as e:
-        jefi.jefi_eval_batch([h], [hi - 0.1], [E], [B])
-    assert e.value.code == jefi.JEFI_EUNSUPPORTED
-    assert bool((E == 7.0).all()) and bool((B == 7.0).all())
-    jefi.jefi_destroy(h)
+    pd, hd = cases[True]
+    hs = [create(p, prec, flags=INTERP), create(p, prec, flags=INTERP | jefi.JEFI_FLAG_DIRECT_GATHER),
+          create(p, prec), create(pd, prec, supplied=True, flags=INTERP)]
+    for h in hs[:3]:
+        push_all(h, hist)
+    push_all(hs[3], hd, supplied=True)
+    ts = []
+    for h in hs:
+        lo, hi = jefi.jefi_valid_window(h)
+        ts.append(hi - 0.13)
+    Es = [torch.full((h.n_obs, 3), 7.0, dtype=torch.float64, device="cuda") for h in hs]
+    Bs = [torch.full_like(E, 7.0) for E in Es]
+    jefi.jefi_eval_batch(hs, ts, Es, Bs)
+    torch.cuda.synchronize()
+    for i, h in enumerate(hs):
+        E1, B1 = jefi.eval_fields(h, ts[i])
+        assert torch.equal(E1, Es[i]) and torch.equal(B1, Bs[i]), i
+    for i, (prob, hh, sup) in enumerate(((p, hist, False), (p, hist, False), (pd, hd, True))):
+        k = (0, 1, 3)[i]
+        rho, J, drho, dJ = hh
+        kw = dict(drho=drho, dJ=dJ) if sup else {}
+        Er, Br = oracle.fields_interp(prob.src.n, prob.src.lo, prob.src.d, prob.obs(), rho, J, c=prob.c,
+                                      k_e=prob.k_e, k_b=prob.k_b, dt=prob.dt, t0=prob.t0, t=ts[k], **kw)
+        assert rel_l2(Es[k].cpu().numpy(), Er) <= tol and rel_l2(Bs[k].cpu().numpy(), Br) <= tol
+    for h in hs:
+        assert jefi.jefi_get_info(h)["device_status"] == 0
+        jefi.jefi_destroy(h)
 
 
 def test_view_creation_keeps_the_base_central_difference_state(gpu, c1):

@@ -56,3 +56,18 @@ def test_dipole_supplied_derivatives_match_time_differences():
     rm, Jm, _, _ = model.sample(g, t - h)
     assert np.allclose(drho, (rp - rm) / (2 * h), rtol=1e-6, atol=1e-9 * np.abs(drho).max())
     assert np.allclose(dJ, (Jp - Jm) / (2 * h), rtol=1e-6, atol=1e-9 * np.abs(dJ).max())
+
+
+def test_device_form_of_moving_gaussians_matches_the_numpy_form():
+    """The serving loop generates its slices with ``sample_torch`` (on the
+    device); it is the same source model as ``sample`` (pinned above)."""
+    import torch
+
+    m = MovingGaussians([Blob(1.0, (0.2, 0.3, 0.25), (0.1, -0.2, 0.0), (0.3, 0.1, -0.2)),
+                         Blob(-0.5, (0.3, 0.3, 0.3), (-0.2, 0.1, 0.2), (0.0, 0.4, 0.1))])
+    g = Grid((7, 6, 5), (-1.0, -0.9, -0.8), (0.3, 0.31, 0.33))
+    for t in (0.0, 0.7, 2.5):
+        rho, J = m.sample(g, t)
+        rt, Jt = m.sample_torch(torch.from_numpy(g.points()), t)
+        assert np.allclose(rt.numpy(), rho, rtol=1e-13, atol=1e-300)
+        assert np.allclose(Jt.numpy(), J, rtol=1e-13, atol=1e-300)

@@ -165,6 +165,24 @@ class MovingGaussians(SourceModel):
             J += rng.uniform(-amp * vmax, amp * vmax, (grid.size, 3))
         return rho, J
 
+    def sample_torch(self, pts, t):
+        """The noise-free sample at time t for points ``pts`` ([N, 3] torch
+        float64 tensor, any device), by the same formula as ``sample``: a
+        slice generated where the points live (no host copy per slice)."""
+        import torch
+
+        rho = torch.zeros(pts.shape[0], dtype=pts.dtype, device=pts.device)
+        J = torch.zeros((pts.shape[0], 3), dtype=pts.dtype, device=pts.device)
+        for b in self.blobs:
+            s = torch.tensor(b.sigma, dtype=pts.dtype, device=pts.device)
+            c = torch.tensor([b.x0[a] + b.v[a] * t for a in range(3)], dtype=pts.dtype, device=pts.device)
+            u = (pts - c) / s
+            norm = 1.0 / ((2.0 * math.pi) ** 1.5 * b.sigma[0] * b.sigma[1] * b.sigma[2])
+            g = (b.q * norm) * torch.exp(-0.5 * (u * u).sum(dim=1))
+            rho += g
+            J += g[:, None] * torch.tensor(b.v, dtype=pts.dtype, device=pts.device)[None, :]
+        return rho, J
+
 
 @dataclass
 class Dipole(SourceModel):
