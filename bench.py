@@ -569,7 +569,7 @@ def served_oracle_check(samples, point_stride=1):
     model (slice n at n dt), on every point_stride-th observation point:
     rel-L2 per field, worst over the sample."""
     import oracle
-    from workloads import Grid, MovingGaussians
+    from workloads import Grid
 
     worst = {"E": 0.0, "B": 0.0}
     pairs = 0
@@ -579,7 +579,7 @@ def served_oracle_check(samples, point_stride=1):
         obs_all = Grid.cube(sm["obs_side"], -sm["obs_half_width"], sm["obs_half_width"]).points()
         idx = np.arange(0, len(obs_all), point_stride)
         dt, t = sm["dt"], sm["t"]
-        model = MovingGaussians(sm["blobs"])
+        model = sm["model"]
         rmax = math.sqrt(3.0) * (sm["src_half_width"] + sm["obs_half_width"])
         n_lo = max(0, int(math.floor((t - rmax) / dt)) - 2)
         n_hi = min(sm["n_pushed"] - 1, int(math.ceil(t / dt)) + 1)

@@ -606,27 +606,26 @@ void build_tables(jefi_problem* h, int ti, double t) {
     tp.oldest_rel = (int32_t)std::max<int64_t>(std::min<int64_t>(oldest_rel, INT32_MAX / 2), INT32_MIN / 2);
     tp.A_lo = (float)(A - (double)tp.A);
     tp.k0 = k0;
+    tp.k0_mod = (int32_t)(((k0 % h->P) + h->P) % h->P);
+    tp.pad = 0;
     tp.A64 = A;
     h->h_times[ti] = tp;
 }
 
-// TMA descriptor over the FP32 ring.  Narrow bands: the ring as [cells][Hp][8]
-// floats, box = 8 channels x band slots x the stage's cells, dense rows.
-// Swizzled bands: the ring as [cells][Hp/4][32] floats (128-byte lines of 4
-// slots), box = one line x band/4 lines x the stage's cells, 128-byte
-// swizzle.  Before any launch the box is checked against the stage buffer it
-// lands in: the bytes it writes must equal the buffer's size (the kernel
-// waits for exactly that many) and a swizzled box's inner extent must be the
-// full 128-byte swizzle span (a narrower one would not land densely).
-// JEFI_EINTERNAL otherwise.
+// TMA descriptor over the FP32 ring [cells][Hp][8]: box = 8 channels x band
+// slots x the stage's cells.  Wide bands use the 32-byte swizzle, whose span
+// is the box's inner extent (one 32-byte row), so the box lands densely.
+// Before any launch the box is checked against the stage buffer it lands
+// in: the bytes it writes must equal the buffer's size (the kernel waits for
+// exactly that many) and a swizzled box's inner extent must be the full
+// 32-byte swizzle span.  JEFI_EINTERNAL otherwise.
 int make_tensor_map(jefi_problem* h) {
     const bool swz = staged_swizzled(h->band);
-    const cuuint32_t box_inner = swz ? 32 : 8;                      // floats
-    const cuuint32_t box_rows = swz ? (cuuint32_t)h->band / 4 : (cuuint32_t)h->band;
+    const cuuint32_t box_inner = 8;                                 // floats: one row
+    const cuuint32_t box_rows = (cuuint32_t)h->band;
     const cuuint32_t box_cells = (cuuint32_t)staged_stage_cells(h->band);
     const size_t landed = (size_t)box_inner * sizeof(float) * box_rows * box_cells;
-    if (landed != staged_buffer_bytes(h->band) || (swz && box_inner * sizeof(float) != 128) ||
-        (swz && (h->band % 4 != 0 || h->Hp % 4 != 0 || h->P % 4 != 0 || h->mirror % 4 != 0)) || box_rows > 256 ||
+    if (landed != staged_buffer_bytes(h->band) || (swz && box_inner * sizeof(float) != 32) || box_rows > 256 ||
         box_cells > 256)
         return JEFI_EINTERNAL;
     void* fn = nullptr;
@@ -635,14 +634,13 @@ int make_tensor_map(jefi_problem* h) {
             cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess)
         return JEFI_ECUDA;
     auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    const cuuint64_t rows = swz ? (cuuint64_t)h->Hp / 4 : (cuuint64_t)h->Hp;
-    const cuuint64_t dims[3] = {box_inner, rows, (cuuint64_t)h->n_bricks * kBrickCells};
+    const cuuint64_t dims[3] = {box_inner, (cuuint64_t)h->Hp, (cuuint64_t)h->n_bricks * kBrickCells};
     const cuuint64_t strides[2] = {box_inner * sizeof(float), (cuuint64_t)h->Hp * 8 * sizeof(float)};
     const cuuint32_t box[3] = {box_inner, box_rows, box_cells};
     const cuuint32_t elem[3] = {1, 1, 1};
     const CUresult r = encode(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->ring, dims, strides, box, elem,
                               CU_TENSOR_MAP_INTERLEAVE_NONE,
-                              swz ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                              swz ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return JEFI_ECUDA;
     h->tmap_band = h->band;
@@ -1313,8 +1311,10 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     // tile the kernel bounds the pair distances two ways and keeps the
     // tighter: the tile's box against the stage's box, and the shell
     // [rho_lo, rho_hi] of the tile's distances from O (the source grid's
-    // centre) widened by the farthest source cell from O.  The host takes
-    // the widest band over tiles of the same bounds (plus one spare slot).
+    // centre) widened by the farthest source cell from O (only where the
+    // shell can be the tighter bound: rho_lo < 0 marks the others).  The host
+    // takes the widest band over tiles of the same bounds (plus one spare
+    // slot).
     std::vector<float> tile_box((size_t)h->n_tiles * kTileBoxFloats);
     if (!h->fp64 && h->any_pairs && !(p->flags & JEFI_FLAG_DIRECT_GATHER)) {
         double O[3], r_src, db;
@@ -1343,19 +1343,22 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
                 tb[6 + a] = (float)(O[a] - anchor[a]);
                 d2 += (mx[a] - mn[a]) * (mx[a] - mn[a]);
             }
-            tb[9] = round_down_f32(rho_lo * (1 - 1e-12));
-            tb[10] = round_up_f32(rho_hi * (1 + 1e-12));
-            tb[11] = 0.f;
             // widest distance range of any pair of this tile: box bound or shell bound
             const double ext_box = std::sqrt(d2) + db;
             const double ext_shell = (rho_hi - rho_lo) + 2 * r_src;
             ext_max = std::max(ext_max, std::min(ext_box, ext_shell));
+            // the kernel tries the shell only where it can beat the box (it
+            // costs the producing thread a few more operations per stage)
+            const bool shell = ext_shell < ext_box;
+            tb[9] = shell ? round_down_f32(rho_lo * (1 - 1e-12)) : -1.f;
+            tb[10] = round_up_f32(rho_hi * (1 + 1e-12));
+            tb[11] = 0.f;
         }
         const double Kd = 1.0 / (p->c * p->dt);
         const double need = std::ceil(ext_max * Kd * (1 + 1e-4) + 1e-3) + 7;
         int band = 0;
-        for (int b : kStagedBands)   // swizzled bands start on a 4-slot line: 3 more slots
-            if (need + (staged_swizzled(b) ? 3 : 0) <= b) { band = b; break; }
+        for (int b : kStagedBands)
+            if (need <= b) { band = b; break; }
         if (base && band > base->mirror) band = 0;      // a view fits the base ring's mirror
         if (band > 0) {
             SumParams probe{};

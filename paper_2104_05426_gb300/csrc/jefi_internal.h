@@ -12,8 +12,7 @@
 //             [P, P+M) mirror slots [0, M) so that any M consecutive slots are
 //             one contiguous TMA box; slots P+M .. P+M+3 are permanently zero
 //             (slot P+M stands for sources before slice 0).  M = 0 unless the
-//             staged kernel is used, and a multiple of 4, so the ring is also
-//             a whole number of 128-byte lines of 4 slots per cell.
+//             staged kernel is used, and a multiple of 4.
 //             Channels: c*rho, Jx, Jy, Jz, drho/dt, dJx/dt/c, dJy/dt/c, dJz/dt/c.
 //             With these, per pair
 //               E' += D (ch0/R^3 + ch4/R^2) - ch5..7/R   ->  E = (k_e dV / c) E'
@@ -46,10 +45,11 @@ constexpr int kZeroPadSlots = 4;    // the zero line after the P + M ring slots
 #endif
 
 // Staged FP32 kernel: compiled band heights (slots per staged cell), the
-// cells per stage of each, and whether its rows are copied as 128-byte
-// swizzled lines (bands of 32 slots and more, whose rows spread over many
-// shared-memory banks).  Stage buffers start on a 1024-byte boundary; the
-// dynamic shared memory gets kStagedAlignPad extra bytes for that.
+// cells per stage of each, and whether its rows are copied with the 32-byte
+// swizzle (bands of 32 slots and more, whose rows spread over many
+// shared-memory banks).  Swizzled stage buffers start on a 1024-byte
+// boundary; the dynamic shared memory gets kStagedAlignPad extra bytes for
+// that.
 constexpr int kStagedBands[6] = {16, 24, 32, 48, 64, 96};
 constexpr int kStagedMaxBand = 96;
 constexpr int kStagedAlignPad = 1024;
@@ -65,6 +65,8 @@ struct TimeParams {
     float A_lo;         // fp32(T/dt - k0 - A): A + A_lo carries T/dt - k0 to ~2^-48 (interpolation weights)
     int64_t k0;         // table origin slot
     double A64;         // T/dt - k0 in FP64 (interpolation weight of the FP64 kernel)
+    int32_t k0_mod;     // k0 mod P (the ring's period), in [0, P): physical rows without 64-bit division
+    int32_t pad;
 };
 
 constexpr int kTabGuard = 32;       // guard entries on each side of the staged kernel's table
@@ -106,6 +108,7 @@ struct SumParams {
     const float* tile_box;          // [n_tiles][kTileBoxFloats]: min xyz, max xyz of (x_o - anchor) and
                                     // O - anchor (O the source grid's centre), fp32; the range
                                     // [rho_lo, rho_hi] of |x_o - O| over the tile, fp32 outward
+                                    // (rho_lo < 0: the kernel uses the box alone)
     int32_t n_src_axis[3];          // real source cells per axis
     int32_t nfull[3];               // whole bricks per axis (bricks past them hold padding cells)
     int32_t H;                      // ring period P (physical slot of slice n is n mod P)

@@ -57,7 +57,7 @@ __device__ __noinline__ Fix6 direct_fixup(const SumParams& p, uint64_t mask, int
         const unsigned cand = candidate_index(S, ri, K32, A, K);
         const int idx = slot_fallback_f32(p.obs_xyz, slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
                                           p.org[0] + kBrick * bx + i, p.org[1] + kBrick * by + j,
-                                          p.org[2] + kBrick * bz + k, s_th, K, (int)cand, p.fallbacks);
+                                          p.org[2] + kBrick * bz + k, s_th, K, (int)cand, nullptr);
         if (DEBUG) p.debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
         const float4* q = cbase + (cl * Hp + __float_as_int(s_tab[idx].z)) * 2;
         float4 v0 = __ldg(q), v1 = __ldg(q + 1);
@@ -138,6 +138,9 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
 
     float se[3] = {0.f, 0.f, 0.f}, sb[3] = {0.f, 0.f, 0.f};
     float ce[3] = {0.f, 0.f, 0.f}, cb[3] = {0.f, 0.f, 0.f};
+    // pairs whose slot was recomputed in FP64, counted per thread and added
+    // once per warp (not one atomic per pair)
+    uint32_t n_fb = 0;
 
     const int b_begin = split * p.bricks_per_split;
     const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
@@ -176,7 +179,8 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                     if (!ok) {
                         idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2],
                                                 p.d[0], p.d[1], p.d[2], p.org[0] + ix, p.org[1] + iy,
-                                                p.org[2] + iz, s_th, K, (int)idx, p.fallbacks);
+                                                p.org[2] + iz, s_th, K, (int)idx, nullptr);
+                        ++n_fb;
                         e = s_tab[idx];
                     }
                 }
@@ -224,6 +228,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                     dyz[i] = make_float2(ddy[i], dz);
                     dzx[i] = make_float2(dz, ddx[i]);
                 }
+                uint32_t m16 = 0;           // undecided cells of this slab
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float syz = __fadd_rn(sqy[j], sqz);
@@ -238,7 +243,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                         if (!exact) {   // T_hi < S <= T_lo: undecided, redone after the brick
                             const float th_hi = *reinterpret_cast<const float*>(smem + (thbase + bits * 4u));
                             if (!(S <= th_hi) && !lower) {
-                                mask |= 1ull << (k * 16 + c16);
+                                m16 |= 1u << c16;   // c16 is a constant of the unrolled body
                                 ri = 0.f;
                             }
                         }
@@ -278,6 +283,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
                         acc_bz = fmaf(-vyz.x, ddx[i], acc_bz);
                     }
                 }
+                if (!exact) mask |= (uint64_t)m16 << (k * 16);
             }
             pe[0] += acc_ex;
             pe[1] += acc_eyz.x;
@@ -286,6 +292,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
             pb[1] += acc_bxy.y;
             pb[2] += acc_bz;
             if (__any_sync(kFull, mask != 0ull)) {
+                n_fb += (uint32_t)__popcll(mask);
                 const Fix6 f = direct_fixup<DEBUG, INTERP>(p, mask, ctx.slot, b, bx, by, bz, Px, Py, Pz, cbase,
                                                            s_tab, s_th, tp.k0, A, A_lo);
                 pe[0] += f.v[0];
@@ -308,6 +315,10 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
         }
     }
 
+    {
+        const uint32_t w = __reduce_add_sync(kFull, n_fb);
+        if ((tid & 31) == 0 && w) atomicAdd(p.fallbacks, (unsigned long long)w);
+    }
     double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

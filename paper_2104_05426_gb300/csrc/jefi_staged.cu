@@ -47,11 +47,13 @@ size_t staged_smem_bytes(const SumParams& p, int band, bool batched) {
     size_t b = tab + (size_t)(p.K + 2 * kTabGuard) * sizeof(float2);
     b += (size_t)(p.K + 1) * sizeof(double);
     b += (size_t)nb_sum * sizeof(float);
-    // non-lattice geometry: FP64 points of the tile and cell centres, for the fall-back
-    if (!p.exact && !batched)
+    // non-lattice geometry: FP64 points of the tile and cell centres, for the
+    // fall-back (single and batched kernels alike)
+    (void)batched;
+    if (!p.exact)
         b = staged::staged_geometry_offset((uint32_t)tab, p.K, nb_sum) +
             (size_t)(3 * kTileThreads + p.npx + p.npy + p.npz) * 8;
-    return kStagedAlignPad + b;
+    return (staged_swizzled(band) ? kStagedAlignPad : 0) + b;
 }
 
 cudaError_t launch_sum_f32_staged(const SumParams& p, const StagedConfig& c, cudaStream_t s) {

@@ -15,13 +15,12 @@
 // waits bounded in time).
 //
 // Shared-memory layout of a stage buffer: [cell][slot][8 channels] FP32,
-// 32 bytes per (cell, slot) row.  Bands of 32 rows and more are copied as
-// 128-byte lines of 4 slots with the tensor map's 128-byte swizzle: within
-// each 1024-byte group of 8 lines the 16-byte chunk index is XORed with the
-// line index, so rows whose slot is the same modulo 4 (same banks in the
-// dense layout) land on different banks when they sit in different lines.
-// The ring's period, mirror and every band start are then multiples of 4
-// slots.
+// 32 bytes per (cell, slot) row.  Bands of 32 rows and more are copied with
+// the tensor map's 32-byte swizzle: in every other group of four rows the
+// two 16-byte halves of each row trade places (address bit 4 XOR bit 7), so
+// the first halves of any eight consecutive rows fall on eight different
+// groups of banks.  The lanes of a quarter-warp read one cell at nearby
+// slots; in the dense layout rows four apart share banks.
 //
 // Slot selection per pair, exact with respect to the FP64 rule of Eq. tr-1:
 //   k' = floor(A + g - R32/(c dt)), g bounding the FP32 error of the
@@ -110,8 +109,8 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 }
 
 // Byte offset of a dense [cell][slot][8] offset inside a 1024-byte aligned
-// buffer written with the 128-byte swizzle: bits 4-6 XOR bits 7-9.
-__device__ __forceinline__ uint32_t swz128(uint32_t off) { return off ^ ((off >> 3) & 0x70u); }
+// buffer written with the 32-byte swizzle: bit 4 XOR bit 7.
+__device__ __forceinline__ uint32_t swz32(uint32_t off) { return off ^ ((off >> 3) & 0x10u); }
 
 template <int BAND>
 struct Layout {
@@ -132,13 +131,20 @@ struct Layout {
     static_assert(kBufBytes % 1024 == 0, "stage buffers keep the 1024-byte alignment of the swizzle");
 };
 
-// The staged region of dynamic shared memory starts at the first 1024-byte
-// boundary (the swizzle pattern follows address bits 4-9); the launch adds
-// kStagedAlignPad bytes for it.
+// The staged region of dynamic shared memory.  Swizzled bands start it at
+// the first 1024-byte boundary (the swizzle pattern follows the address
+// bits; the launch adds kStagedAlignPad bytes for it); dense bands use the
+// array itself (a TMA destination needs 128 bytes), so their offsets stay
+// compile-time relative to it.
+template <int BAND>
 __device__ __forceinline__ unsigned char* staged_base() {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t pad = (0u - smem_u32(smem)) & (kStagedAlignPad - 1);
-    return smem + pad;
+    if constexpr (staged_swizzled(BAND)) {
+        const uint32_t pad = (0u - smem_u32(smem)) & (kStagedAlignPad - 1);
+        return smem + pad;
+    } else {
+        return smem;
+    }
 }
 
 // Shared-memory offset of the FP64 geometry of one item: after the float2
@@ -154,7 +160,7 @@ __host__ __device__ __forceinline__ uint32_t staged_geometry_offset(uint32_t tab
 template <int BAND>
 __device__ __noinline__ int staged_slot_fp64(int ix, int iy, int iz, const double* s_th, int K, int guess) {
     using L = Layout<BAND>;
-    unsigned char* sb = staged_base();
+    unsigned char* sb = staged_base<BAND>();
     const uint32_t* g = reinterpret_cast<const uint32_t*>(sb + L::kGeo);
     const double* s_xo = reinterpret_cast<const double*>(sb + g[0]) + 3 * threadIdx.x;
     const double* s_cc = reinterpret_cast<const double*>(sb + g[0]) + 3 * kTileThreads;
@@ -167,7 +173,7 @@ template <int BAND>
 __device__ __forceinline__ void staged_init_barriers() {
     using L = Layout<BAND>;
     if (threadIdx.x == 0) {
-        uint64_t* s_mbar = reinterpret_cast<uint64_t*>(staged_base() + L::kCtrl);
+        uint64_t* s_mbar = reinterpret_cast<uint64_t*>(staged_base<BAND>() + L::kCtrl);
         mbar_init(smem_u32(&s_mbar[0]), 1);
         mbar_init(smem_u32(&s_mbar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -183,7 +189,7 @@ __device__ __noinline__ void staged_fill_geometry(const double* txyz, int K, int
                                                   double lox, double loy, double loz, double dx_, double dy_,
                                                   double dz_, const int32_t* org) {
     using L = Layout<BAND>;
-    unsigned char* sb = staged_base();
+    unsigned char* sb = staged_base<BAND>();
     const int tid = threadIdx.x;
     const uint32_t geo = staged_geometry_offset(L::kTab, K, nb_sum);
     double* s_xo = reinterpret_cast<double*>(sb + geo);
@@ -209,7 +215,7 @@ struct FixSums {
 template <int BAND>
 __device__ __forceinline__ void load_row(const unsigned char* bufp, uint32_t off, float4& v0, float4& v1) {
     if constexpr (Layout<BAND>::kSwz) {
-        const uint32_t a = swz128(off);
+        const uint32_t a = swz32(off);
         v0 = *reinterpret_cast<const float4*>(bufp + a);
         v1 = *reinterpret_cast<const float4*>(bufp + (a ^ 16u));
     } else {
@@ -231,8 +237,7 @@ __device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char*
                                              const double* obs_xyz, int slot, double lox, double loy, double loz,
                                              double dx_, double dy_, double dz_, const int32_t* org, int bx, int by,
                                              int bz,
-                                             const double* s_th, int K, unsigned long long* fallbacks,
-                                             int32_t* status, int32_t* debug_slots, size_t n_cells, int b,
+                                             const double* s_th, int K, int32_t* status, int32_t* debug_slots, size_t n_cells, int b,
                                              int64_t k0) {
     using L = Layout<BAND>;
     float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
@@ -248,7 +253,7 @@ __device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char*
         const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
         const int idx = slot_fallback_f32(obs_xyz, slot, lox, loy, loz, dx_, dy_, dz_, org[0] + kBrick * bx + i,
                                           org[1] + kBrick * by + j, org[2] + kBrick * bz + k, s_th, K,
-                                          (int)(bits - kMagicBits), fallbacks);
+                                          (int)(bits - kMagicBits), nullptr);
         int row = idx - band_rel;
         if (row < 0 || row >= BAND) {
             atomicExch(status, kStatusInternal);
@@ -319,7 +324,7 @@ template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool GEO>
 __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const int comp,
                                             const int tile, const int split, const int ti, uint32_t& g_it) {
     using L = Layout<BAND>;
-    unsigned char* const sb = staged_base();
+    unsigned char* const sb = staged_base<BAND>();
     const int K = p.K;
     const int KT = K + 2 * kTabGuard;
     uint64_t* s_mbar = reinterpret_cast<uint64_t*>(sb + L::kCtrl);
@@ -402,20 +407,16 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         const float slack = 1e-5f * span;
         float rmin = fmaxf(sqrtf(mn2) * (1.f - 1e-5f) - slack, 0.f);
         float rmax = sqrtf(mx2) * (1.f + 1e-5f) + slack;
-        const float odist = sqrtf(od2) * (1.f + 1e-5f) + 1e-5f * ospan;
-        const float oslack = 1e-5f * (tb[10] + odist);
-        rmin = fmaxf(rmin, tb[9] - odist - oslack);
-        rmax = fminf(rmax, tb[10] + odist + oslack);
+        if (tb[9] >= 0.f) {   // tiles whose shell can be tighter than their box (the host decides)
+            const float odist = sqrtf(od2) * (1.f + 1e-5f) + 1e-5f * ospan;
+            const float oslack = 1e-5f * (tb[10] + odist);
+            rmin = fmaxf(rmin, tb[9] - odist - oslack);
+            rmax = fminf(rmax, tb[10] + odist + oslack);
+        }
         const int hi_rel = (int)floorf(tp.A - rmin * K32) + 2;
         const int lo_rel = (int)floorf(tp.A - rmax * K32) - 2;
-        int band_rel = max(lo_rel, tp.oldest_rel);
-        long long band_abs = tp.k0 + band_rel;
-        if constexpr (L::kSwz) {
-            // lines of 4 slots: the band starts on a line (the ring's period is
-            // a multiple of 4, so the physical start is one too)
-            band_abs &= ~3ll;
-            band_rel = (int)(band_abs - tp.k0);
-        }
+        const int band_rel = max(lo_rel, tp.oldest_rel);
+        const long long band_abs = tp.k0 + band_rel;
         // A band that does not fit the buffer (never, if the creation-time
         // bound holds) is reported and its stage skipped: no pair then reads
         // past the buffer.
@@ -423,22 +424,26 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         if (!fits) atomicExch(p.status, kStatusInternal);
         s_band[bufi] = fits ? band_rel : kBandSkip;
         int y0;
-        if (band_abs >= 0)
-            y0 = (int)(band_abs % p.H);
-        else
+        if (band_abs >= 0) {
+            // (k0 mod P + band_rel) mod P, band_rel being small: no 64-bit division
+            y0 = tp.k0_mod + band_rel;
+            while (y0 >= p.H) y0 -= p.H;
+            while (y0 < 0) y0 += p.H;
+        } else {
             y0 = band_abs < -(1ll << 30) ? -(1 << 30) : (int)band_abs;   // rows < 0 read as zero
+        }
         // the buffer was last read through the generic proxy: order those
         // reads before the async-proxy write
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(mbar_u32[bufi], L::kBufBytes);
-        if constexpr (L::kSwz)
-            tma_load_3d(buf_u32[bufi], tmap_ptr, 0, y0 / 4, b * kBrickCells + q * L::kCells, mbar_u32[bufi]);
-        else
-            tma_load_3d(buf_u32[bufi], tmap_ptr, 0, y0, b * kBrickCells + q * L::kCells, mbar_u32[bufi]);
+        tma_load_3d(buf_u32[bufi], tmap_ptr, 0, y0, b * kBrickCells + q * L::kCells, mbar_u32[bufi]);
     };
 
     float se[3] = {0.f, 0.f, 0.f}, sbv[3] = {0.f, 0.f, 0.f};
     float ce[3] = {0.f, 0.f, 0.f}, cbv[3] = {0.f, 0.f, 0.f};
+    // pairs whose slot was recomputed in FP64 through global memory, counted
+    // per thread and added once per warp (not one atomic per pair)
+    uint32_t n_fb = 0;
     const int b_begin = split * p.bricks_per_split;
     const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
     const uint32_t n_stages = b_end > b_begin ? (uint32_t)(b_end - b_begin) * L::kParts : 0u;
@@ -468,8 +473,9 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         const float Pz = ooz + s_D[nbxy + bz];
         // the brick's sum over its stages (compensated once per brick)
         float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
-#pragma unroll 1
-        for (int q = 0; q < L::kParts; ++q) {
+        // One stage: q-th group of kCells cells of brick b.  False if its copy
+        // did not complete in time (the item then stops).
+        auto stage = [&](const int q) -> bool {
             const uint32_t it = g_it + (uint32_t)(b - b_begin) * L::kParts + (uint32_t)q;
             const int buf = it & 1;
             // the next stage's copy goes into the other buffer, whose last
@@ -503,9 +509,14 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         sqx[i] = __fmul_rn(ddx[i], ddx[i]);
                         sqy[i] = __fmul_rn(ddy[i], ddy[i]);
                     }
-                    // dense offset of row n (relative to k0) of the stage's first
-                    // cell: (n - band_rel) * 32, with n carried in the magic bits
-                    const uint32_t gbase = 0u - (uint32_t)(kMagicBits + band_rel) * L::kRowBytes;
+                    // offset of row n (relative to k0) of the stage's first cell,
+                    // (n - band_rel) * 32 with n carried in the magic bits: from
+                    // the buffer's start for swizzled rows (the swizzle acts on
+                    // it), from the shared array's for dense rows (one 32-bit
+                    // address per pair, the buffer folded in here)
+                    const unsigned char* const rows = L::kSwz ? bufp : sb;
+                    const uint32_t gbase = (L::kSwz ? 0u : (uint32_t)buf * L::kBufBytes) -
+                                           (uint32_t)(kMagicBits + band_rel) * L::kRowBytes;
                     uint64_t mask = 0;
                     float2 acc_eyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
                     float acc_ex = 0.f, acc_bz = 0.f;
@@ -521,6 +532,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                             dyz[i] = make_float2(ddy[i], dz);
                             dzx[i] = make_float2(dz, ddx[i]);
                         }
+                        uint32_t m16 = 0;           // undecided cells of this slab (non-lattice geometry)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const float syz = __fadd_rn(sqy[j], sqz);
@@ -542,7 +554,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                     const float2 th = *reinterpret_cast<const float2*>(sb + (tbase + bits * 8u));
                                     lower = gt_mask(S, th.y);
                                     if (!(S <= th.x) && lower == 0u) {   // undecided: redo after the stage
-                                        mask |= 1ull << (k * 16 + c16);
+                                        m16 |= 1u << c16;   // c16 is a constant of the unrolled body
                                         ri = 0.f;
                                     }
                                 }
@@ -550,12 +562,13 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                     p.debug_slots[(size_t)ctx.slot * n_cells + (size_t)b * kBrickCells + k * 16 +
                                                   c16] = (int)(tp.k0 + (int)(bits + lower - kMagicBits));
                                 }
-                                const uint32_t off = gk + (bits + lower) * L::kRowBytes + (uint32_t)c16 * L::kCellBytes;
+                                const uint32_t row_hi = gk + bits * L::kRowBytes;
+                                const uint32_t off = row_hi + lower * L::kRowBytes + (uint32_t)c16 * L::kCellBytes;
                                 float4 v0, v1;
-                                load_row<BAND>(bufp, off, v0, v1);
+                                load_row<BAND>(rows, off, v0, v1);
                                 if (INTERP) {   // slot n+1 is the next row of the same cell
                                     float4 u0, u1;
-                                    load_row<BAND>(bufp, off + L::kRowBytes, u0, u1);
+                                    load_row<BAND>(rows, off + L::kRowBytes, u0, u1);
                                     const float nrel = __uint_as_float(bits + lower) - kMagic;
                                     lerp8(v0, v1, u0, u1, interp_weight(S, ri, nrel, A, A_lo, K32, K32_lo));
                                 }
@@ -582,6 +595,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                 acc_bz = fmaf(-vyz.x, ddx[i], acc_bz);
                             }
                         }
+                        if (!EXACT) mask |= (uint64_t)m16 << (k * 16);
                     }
                     pe[0] += acc_ex;
                     pe[1] += acc_eyz.x;
@@ -598,10 +612,11 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                     K32_lo, ctx.slot, bx, by, bz, s_th, K, p.status, p.debug_slots, n_cells, b,
                                     tp.k0);
                             } else {
+                                n_fb += (uint32_t)__popcll(mask);
                                 f = staged_fixup<BAND, DEBUG, INTERP>(
                                     mask, bufp, cell0, band_rel, Px, Py, Pz, d32x, d32y, d32z, K32, Ag, A, A_lo,
                                     K32_lo, p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1],
-                                    p.d[2], p.org, bx, by, bz, s_th, K, p.fallbacks, p.status, p.debug_slots,
+                                    p.d[2], p.org, bx, by, bz, s_th, K, p.status, p.debug_slots,
                                     n_cells, b, tp.k0);
                             }
 #pragma unroll
@@ -636,7 +651,8 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                             if constexpr (EXACT || !GEO) {
                                 idx = slot_fallback_f32(p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0],
                                                         p.d[1], p.d[2], p.org[0] + ix, p.org[1] + iy, p.org[2] + iz,
-                                                        s_th, K, idx, p.fallbacks);
+                                                        s_th, K, idx, nullptr);
+                                if constexpr (!EXACT) ++n_fb;
                             } else {
                                 idx = staged_slot_fp64<BAND>(ix, iy, iz, s_th, K, idx);
                             }
@@ -668,8 +684,16 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
             // every thread is done with this buffer before it is refilled
             if (__syncthreads_or(!ready)) {
                 aborted_at = (int64_t)(it - g_it);
-                break;
+                return false;
             }
+            return true;
+        };
+        if constexpr (L::kParts == 1) {
+            stage(0);                      // whole-brick stages: q is the constant 0
+        } else {
+#pragma unroll 1
+            for (int q = 0; q < L::kParts; ++q)
+                if (!stage(q)) break;
         }
         if (aborted_at < 0) {
 #pragma unroll
@@ -701,6 +725,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         __syncthreads();
     }
     g_it += n_stages;
+    if constexpr (!EXACT) {   // exact lattices decide every pair in FP32
+        const uint32_t w = __reduce_add_sync(kFull, n_fb);
+        if ((tid & 31) == 0 && w) atomicAdd(p.fallbacks, (unsigned long long)w);
+    }
     if constexpr (!EXACT && GEO) {
         // every thread passed the loop's last barrier: the item's count is complete
         const uint32_t n = reinterpret_cast<const uint32_t*>(sb + L::kGeo)[3];
@@ -727,10 +755,12 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 // One item of the batched kernel as a call of its own: the item body gets
 // the register budget of the single-problem kernel instead of sharing it
 // with the queue loop (the call happens once per item, thousands of pairs).
+// Non-lattice items take the FP64 geometry of undecided pairs from shared
+// memory, as the single-problem kernel does.
 template <int BAND, bool EXACT, bool INTERP>
 __device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int split,
                                                int ti, uint32_t& g_it) {
-    return staged_item<BAND, EXACT, false, INTERP, false>(map, p, p.comp, tile, split, ti, g_it);
+    return staged_item<BAND, EXACT, false, INTERP, !EXACT>(map, p, p.comp, tile, split, ti, g_it);
 }
 
 // Persistent batched kernel: CTAs take (problem, time, split, tile) items
@@ -739,7 +769,7 @@ __device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const Sum
 template <int BAND, bool EXACT>
 __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_staged_batch(const __grid_constant__ StagedBatchArgs a) {
     using L = Layout<BAND>;
-    int* s_item = reinterpret_cast<int*>(staged_base() + L::kCtrl + 32);
+    int* s_item = reinterpret_cast<int*>(staged_base<BAND>() + L::kCtrl + 32);
     __shared__ SumParams s_par;
     staged_init_barriers<BAND>();
     uint32_t g_it = 0;

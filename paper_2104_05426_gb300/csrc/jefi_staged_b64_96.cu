@@ -1,5 +1,5 @@
 // jefi_staged_b64_96.cu -- the TMA-staged FP32 sum compiled for bands of 64
-// and 96 slots (stages of one z slab, 128-byte swizzled lines of 4 slots);
+// and 96 slots (stages of one z slab, rows copied with the 32-byte swizzle);
 // the kernels are the templates of jefi_staged.cuh.
 #include "jefi_staged.cuh"
 

@@ -32,7 +32,7 @@ from typing import Dict, List, Optional, Tuple
 
 import numpy as np
 
-from workloads import Blob, MovingGaussians
+from workloads import OscBlob, OscillatingGaussians
 
 from . import (JEFI_EEVICTED, JEFI_FLAG_SHARED_RING, JefiError, default_params, grid, jefi_batch_plan_create,
                jefi_batch_plan_destroy, jefi_batch_plan_launch, jefi_batch_plan_tune, jefi_create,
@@ -41,11 +41,12 @@ from . import (JEFI_EEVICTED, JEFI_FLAG_SHARED_RING, JefiError, default_params, 
 
 
 class ServedProblem:
-    """A resident source problem: a cube grid of Gaussian charges moving at
-    constant velocity (the seeded source model of ``workloads``), its base
-    handle and a device-side slice generator."""
+    """A resident source problem: a cube grid of Gaussian charges on bounded
+    oscillating paths (the seeded source model of ``workloads``: the charges
+    stay in the box however long the loop runs), its base handle and a
+    device-side slice generator."""
 
-    def __init__(self, side: int, half_width: float, H: int, dt: float, blobs: List[Blob],
+    def __init__(self, side: int, half_width: float, H: int, dt: float, blobs: List[OscBlob],
                  device="cuda", stream=None):
         import torch
 
@@ -56,7 +57,7 @@ class ServedProblem:
         self.H = H
         self.dt = dt
         self.blobs = blobs
-        self.model = MovingGaussians(blobs)
+        self.model = OscillatingGaussians(blobs)
         d = 2.0 * half_width / side
         self.grid = grid((side,) * 3, (-half_width,) * 3, (d,) * 3)
         prm = default_params(dt=dt, history_slots=H, precision="fp32c", flags=JEFI_FLAG_SHARED_RING)
@@ -365,6 +366,7 @@ def make_problems(n: int, seed: int, sides=(16, 64), H_range=(64, 256), half_wid
     moving Gaussian charges; dt chosen so H slices just cover the pairs of an
     observation grid over [-2L,2L]^3.  Pushes H slices into each."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    rng_path = np.random.Generator(np.random.PCG64([seed, 1]))   # path shapes, apart from the geometry draws
     out = []
     for _ in range(n):
         side = int(rng.integers(sides[0], sides[1] + 1))
@@ -373,11 +375,16 @@ def make_problems(n: int, seed: int, sides=(16, 64), H_range=(64, 256), half_wid
         dt = rmax / (H - 8)
         blobs = []
         for _ in range(int(rng.integers(1, 5))):
-            v = rng.standard_normal(3)
-            v *= rng.uniform(0.0, 0.5) / np.linalg.norm(v)
+            # speed up to 0.5c on a path of amplitude 0.2-0.5 around x0
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            speed = rng.uniform(0.0, 0.5)
             q = float(rng.choice([-1.0, 1.0]))
             sigma = float(rng.uniform(0.15, 0.35))
-            blobs.append(Blob(q, (sigma,) * 3, tuple(rng.uniform(-0.2, 0.2, 3) - v * H * dt * 0.5), tuple(v)))
+            x0 = rng.uniform(-0.2, 0.2, 3)
+            amp = rng_path.uniform(0.2, 0.5)
+            blobs.append(OscBlob(q, (sigma,) * 3, tuple(x0), tuple(amp * d), speed / amp,
+                                 float(rng_path.uniform(0.0, 2.0 * math.pi))))
         p = ServedProblem(side, half_width, H, dt, blobs)
         out.append(p)
     import torch
@@ -471,7 +478,7 @@ def served_sample(eng: "ServingEngine", req: Request) -> dict:
     p = eng.problems[req.problem]
     s = req.obs_side
     L = eng.obs_half_width
-    return {"rid": req.rid, "src_side": p.side, "src_half_width": p.L, "dt": p.dt, "blobs": p.blobs,
+    return {"rid": req.rid, "src_side": p.side, "src_half_width": p.L, "dt": p.dt, "model": p.model,
             "obs_side": s, "obs_half_width": L, "t": req.t, "n_pushed": p.n_pushed,
             "E": req.E.cpu().numpy(), "B": req.B.cpu().numpy()}
 
@@ -583,8 +590,8 @@ def measure_single(src_side: int, obs_side: int, H: int, reps: int = 3, seed: in
     rmax = math.sqrt(3.0) * 3.0
     dt = rmax / (H - 8)
     rng = np.random.Generator(np.random.PCG64(seed))
-    blobs = [Blob(float(q), (float(rng.uniform(0.2, 0.3)),) * 3, tuple(rng.uniform(-0.2, 0.2, 3)),
-                  tuple(rng.uniform(-0.3, 0.3, 3))) for q in (1.0, -1.0)]
+    blobs = [OscBlob(float(q), (float(rng.uniform(0.2, 0.3)),) * 3, tuple(rng.uniform(-0.2, 0.2, 3)),
+                     tuple(rng.uniform(-0.3, 0.3, 3)), 1.0) for q in (1.0, -1.0)]
     p = ServedProblem(src_side, 1.0, H, dt, blobs)
     s = torch.cuda.current_stream()
     for _ in range(H + 1):

@@ -55,7 +55,7 @@ def test_served_results_match_the_oracle(gpu):
 
     import oracle
     from paper_2104_05426_gb300.serving import served_sample
-    from workloads import Grid, MovingGaussians
+    from workloads import Grid
 
     probs = make_problems(2, seed=5, sides=(8, 12), H_range=(40, 48))
     eng = ServingEngine(probs, obs_half_width=2.0, n_streams=2, max_batch=6, tick_s=0.004,
@@ -69,7 +69,7 @@ def test_served_results_match_the_oracle(gpu):
         src = Grid.cube(sm["src_side"], -sm["src_half_width"], sm["src_half_width"])
         obs = Grid.cube(sm["obs_side"], -sm["obs_half_width"], sm["obs_half_width"]).points()
         dt, t = sm["dt"], sm["t"]
-        model = MovingGaussians(sm["blobs"])
+        model = sm["model"]
         n_hi = sm["n_pushed"] - 1
         rmax = math.sqrt(3.0) * (sm["src_half_width"] + sm["obs_half_width"])
         n_lo = max(0, int(math.floor((t - rmax) / dt)) - 2)

@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from workloads import Blob, Dipole, Grid, MovingGaussians, Sinusoidal
+from workloads import Blob, Dipole, Grid, MovingGaussians, OscBlob, OscillatingGaussians, Sinusoidal
 
 
 def _residual(model, n, lo, hi, t, ht=1e-5):
@@ -35,6 +35,11 @@ MODELS = {
                                           Blob(-0.5, (0.2, 0.2, 0.2), (-0.2, 0.1, 0.1), (0.0, 0.5, -0.1))]),
                          -1.5, 1.5, 0.3),
     "dipole": (Dipole(1.0, 2.0 * math.pi / 8.0, 0.1), -0.5, 0.5, 1.1),
+    "oscillating Gaussians": (OscillatingGaussians([OscBlob(1.0, (0.3, 0.25, 0.35), (0.1, -0.05, 0.0),
+                                                            (0.2, -0.1, 0.15), 2.0, 0.3),
+                                                    OscBlob(-0.5, (0.2, 0.2, 0.2), (-0.2, 0.1, 0.1),
+                                                            (0.0, 0.25, -0.05), 1.3, 1.1)]),
+                              -1.5, 1.5, 0.7),
 }
 
 
@@ -67,6 +72,18 @@ def test_device_form_of_moving_gaussians_matches_the_numpy_form():
                          Blob(-0.5, (0.3, 0.3, 0.3), (-0.2, 0.1, 0.2), (0.0, 0.4, 0.1))])
     g = Grid((7, 6, 5), (-1.0, -0.9, -0.8), (0.3, 0.31, 0.33))
     for t in (0.0, 0.7, 2.5):
+        rho, J = m.sample(g, t)
+        rt, Jt = m.sample_torch(torch.from_numpy(g.points()), t)
+        assert np.allclose(rt.numpy(), rho, rtol=1e-13, atol=1e-300)
+        assert np.allclose(Jt.numpy(), J, rtol=1e-13, atol=1e-300)
+
+
+def test_device_form_of_oscillating_gaussians_matches_the_numpy_form():
+    import torch
+
+    m = OscillatingGaussians([OscBlob(1.0, (0.2, 0.3, 0.25), (0.1, -0.2, 0.0), (0.3, 0.1, -0.2), 1.7, 0.4)])
+    g = Grid((7, 6, 5), (-1.0, -0.9, -0.8), (0.3, 0.31, 0.33))
+    for t in (0.0, 0.9, 31.5):
         rho, J = m.sample(g, t)
         rt, Jt = m.sample_torch(torch.from_numpy(g.points()), t)
         assert np.allclose(rt.numpy(), rho, rtol=1e-13, atol=1e-300)

@@ -185,6 +185,59 @@ class MovingGaussians(SourceModel):
 
 
 @dataclass
+class OscBlob:
+    """A Gaussian charge whose centre oscillates: c(t) = x0 + amp sin(omega t + phase)."""
+    q: float
+    sigma: Tuple[float, float, float]
+    x0: Tuple[float, float, float]
+    amp: Tuple[float, float, float]
+    omega: float
+    phase: float = 0.0
+
+
+@dataclass
+class OscillatingGaussians(SourceModel):
+    """Rigidly moving Gaussian charges on bounded paths: rho = sum q G(r - c(t)),
+    J = sum q G(r - c(t)) c'(t), which satisfies continuity like any rigid
+    motion.  The charges stay near x0 forever, so a long-running history
+    (the serving workload pushes a slice per tick) keeps its fields."""
+    blobs: List[OscBlob]
+
+    def _centre(self, b, t):
+        s = math.sin(b.omega * t + b.phase)
+        c = math.cos(b.omega * t + b.phase)
+        return ([b.x0[a] + b.amp[a] * s for a in range(3)], [b.amp[a] * b.omega * c for a in range(3)])
+
+    def sample(self, grid, t, slice_index=0):
+        p = grid.points()
+        rho = np.zeros(grid.size)
+        J = np.zeros((grid.size, 3))
+        for b in self.blobs:
+            c, v = self._centre(b, t)
+            g = b.q * gaussian3(p, c, b.sigma)
+            rho += g
+            J += g[:, None] * np.asarray(v)[None, :]
+        return rho, J
+
+    def sample_torch(self, pts, t):
+        """The sample at time t for points ``pts`` ([N, 3] torch float64,
+        any device), by the same formula as ``sample``."""
+        import torch
+
+        rho = torch.zeros(pts.shape[0], dtype=pts.dtype, device=pts.device)
+        J = torch.zeros((pts.shape[0], 3), dtype=pts.dtype, device=pts.device)
+        for b in self.blobs:
+            c, v = self._centre(b, t)
+            s = torch.tensor(b.sigma, dtype=pts.dtype, device=pts.device)
+            u = (pts - torch.tensor(c, dtype=pts.dtype, device=pts.device)) / s
+            norm = 1.0 / ((2.0 * math.pi) ** 1.5 * b.sigma[0] * b.sigma[1] * b.sigma[2])
+            g = (b.q * norm) * torch.exp(-0.5 * (u * u).sum(dim=1))
+            rho += g
+            J += g[:, None] * torch.tensor(v, dtype=pts.dtype, device=pts.device)[None, :]
+        return rho, J
+
+
+@dataclass
 class Dipole(SourceModel):
     """P(r, t) = p0 cos(omega t) g_sigma(r) z-hat; rho = -dP_z/dz, J = dP/dt."""
 
