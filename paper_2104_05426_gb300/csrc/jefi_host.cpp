@@ -296,6 +296,37 @@ constexpr int kTileShapes[9][3] = {{0, 0, 0}, {8, 8, 4}, {16, 4, 4}, {4, 8, 8}, 
                                    {4, 16, 4}, {16, 8, 2}, {8, 16, 2}, {4, 4, 16}};
 constexpr int kNumTileShapes = 8;
 
+// The widest pair-distance range over the tiles of shape s of an observation
+// grid, from each tile's box alone (the box of a tile's points is known from
+// its index ranges): the box bound as in tiles_extent, the shell bound with
+// the box's nearest and farthest distances from O (never narrower than the
+// points').  O(tiles): this only ranks the shapes.
+double grid_tiles_extent(const jefi_grid& g, int s, const double* O, double r_src, double db) {
+    const int64_t n[3] = {g.n[0], g.n[1], g.n[2]};
+    int64_t t[3];
+    for (int a = 0; a < 3; ++a) t[a] = (n[a] + kTileShapes[s][a] - 1) / kTileShapes[s][a];
+    double ext_max = 0;
+    for (int64_t tz = 0; tz < t[2]; ++tz)
+        for (int64_t ty = 0; ty < t[1]; ++ty)
+            for (int64_t tx = 0; tx < t[0]; ++tx) {
+                const int64_t ti[3] = {tx, ty, tz};
+                double d2 = 0, near2 = 0, far2 = 0;
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t i0 = ti[a] * kTileShapes[s][a];
+                    const int64_t i1 = std::min(i0 + kTileShapes[s][a], n[a]) - 1;
+                    const double lo = center(g.lo[a], g.d[a], i0), hi = center(g.lo[a], g.d[a], i1);
+                    d2 += (hi - lo) * (hi - lo);
+                    const double nr = O[a] < lo ? lo - O[a] : (O[a] > hi ? O[a] - hi : 0.0);
+                    const double fr = std::max(std::fabs(lo - O[a]), std::fabs(hi - O[a]));
+                    near2 += nr * nr;
+                    far2 += fr * fr;
+                }
+                ext_max = std::max(ext_max, std::min(std::sqrt(d2) + db,
+                                                     std::sqrt(far2) - std::sqrt(near2) + 2 * r_src));
+            }
+    return ext_max;
+}
+
 // Observation order of a gx x gy x gz grid in tiles of shape s: tile slot ->
 // point index (x fastest), -1 for padding.
 void grid_tile_order(int64_t gx, int64_t gy, int64_t gz, int s, std::vector<int64_t>& order) {
@@ -960,7 +991,10 @@ int batch_fill(BatchLayout* L, unsigned char* host, Params&& params) {
 cudaError_t batch_launch_group(const BatchLayout& L, size_t g, jefi_problem* const* hs, unsigned char* d,
                                int n_sm, cudaStream_t s) {
     const BatchGroup& G = L.groups[g];
-    const int per_sm = G.kind == 0 ? 1 : (L.smem[g] > 110 * 1024 ? 1 : 2);
+    // persistent CTAs on a work queue: two per SM for the FP32 kernels (CTAs
+    // beyond what the shared memory lets the SM hold start later, find the
+    // queue empty and exit), one for the FP64 kernel (its register budget)
+    const int per_sm = G.kind == 0 ? 1 : 2;
     const int grid = std::max(1, std::min(L.n_items[g], per_sm * n_sm));
     if (G.kind == 2) {
         StagedBatchArgs a;
@@ -1119,8 +1153,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
                 source_shell(*src, h->org, np3, O, &r_src, &db);
                 double best = INFINITY;
                 for (int s = 1; s <= kNumTileShapes; ++s) {
-                    grid_tile_order(gx, gy, gz, s, order);
-                    const double e = tiles_extent(order, pts.data(), O, r_src, db);
+                    const double e = grid_tiles_extent(*obs_grid, s, O, r_src, db);
                     if (e < best * (1 - 1e-9)) {
                         best = e;
                         shape = s;

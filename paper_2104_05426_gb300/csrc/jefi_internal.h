@@ -47,16 +47,16 @@ constexpr int kZeroPadSlots = 4;    // the zero line after the P + M ring slots
 // Staged FP32 kernel: compiled band heights (slots per staged cell), the
 // cells per stage of each, and whether its rows are copied with the 32-byte
 // swizzle (bands of 32 slots and more, whose rows spread over many
-// shared-memory banks).  Swizzled stage buffers start on a 1024-byte
-// boundary; the dynamic shared memory gets kStagedAlignPad extra bytes for
-// that.
+// shared-memory banks).  Swizzled stage buffers start on a 256-byte boundary
+// (the swizzle's period); the dynamic shared memory gets kStagedAlignPad
+// extra bytes for that.
 constexpr int kStagedBands[6] = {16, 24, 32, 48, 64, 96};
 constexpr int kStagedMaxBand = 96;
-constexpr int kStagedAlignPad = 1024;
+constexpr int kStagedAlignPad = 256;
 JEFI_HD constexpr bool staged_swizzled(int band) { return band >= 32; }
 JEFI_HD constexpr int staged_stage_cells(int band) { return band <= 24 ? 64 : (band <= 48 ? 32 : 16); }
 constexpr int kTileBoxFloats = 12;  // per tile: box lo xyz, hi xyz, O xyz, rho_lo, rho_hi, 0
-constexpr int kStagedCtrlBytes = 128;   // control block after the stage buffers
+constexpr int kStagedCtrlBytes = 128 + 2 * 256;   // control block after the stage buffers (with 256 stage bands)
 
 struct TimeParams {
     float A;            // fp32(T/dt - k0): candidate index ~ floor(A - R/(c dt))

@@ -47,7 +47,7 @@ using namespace dev;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // a bounded wait gives up after 2 s
 constexpr int kStatusTimeout = 6;                    // JEFI_ETIMEOUT
 constexpr int kStatusInternal = 7;                   // JEFI_EINTERNAL
-constexpr int kBandSkip = INT32_MIN;                 // a stage whose band did not fit: skipped
+constexpr int kBandSkip = -32768;                    // a stage whose band did not fit: skipped (fits int16)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -108,7 +108,7 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Byte offset of a dense [cell][slot][8] offset inside a 1024-byte aligned
+// Byte offset of a dense [cell][slot][8] offset inside a 256-byte aligned
 // buffer written with the 32-byte swizzle: bit 4 XOR bit 7.
 __device__ __forceinline__ uint32_t swz32(uint32_t off) { return off ^ ((off >> 3) & 0x10u); }
 
@@ -123,17 +123,19 @@ struct Layout {
     static constexpr uint32_t kBufBytes = kCells * kCellBytes;
     static constexpr uint32_t kCtrl = 2 * kBufBytes;            // mbarriers, band origins, item
     static constexpr uint32_t kTileBox = kCtrl + 64;            // the item's tile box (kTileBoxFloats)
+    static constexpr uint32_t kBands = kCtrl + 128;             // bands of 256 upcoming stages (int16)
     static constexpr uint32_t kTab = kCtrl + kStagedCtrlBytes;  // float2 table
     // control words of the non-lattice fall-back (one item): offset of the
     // FP64 geometry (the tile's points, then the cell centres of x, y, z),
     // the cell counts of x and y, and the pairs redone
     static constexpr uint32_t kGeo = kCtrl + 48;
-    static_assert(kBufBytes % 1024 == 0, "stage buffers keep the 1024-byte alignment of the swizzle");
+    static_assert(kBufBytes % kStagedAlignPad == 0, "stage buffers keep the alignment of the swizzle");
 };
 
 // The staged region of dynamic shared memory.  Swizzled bands start it at
-// the first 1024-byte boundary (the swizzle pattern follows the address
-// bits; the launch adds kStagedAlignPad bytes for it); dense bands use the
+// the first 256-byte boundary (the 32-byte swizzle pattern follows address
+// bits 4 and 7 and repeats every 256 bytes; the launch adds kStagedAlignPad
+// bytes for it); dense bands use the
 // array itself (a TMA destination needs 128 bytes), so their offsets stay
 // compile-time relative to it.
 template <int BAND>
@@ -380,9 +382,29 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     // tighter: the boxes of the tile and of the stage's cells, and the shell
     // [rho_lo, rho_hi] of the tile's distances from the point O (the source
     // grid's centre) widened by the stage's farthest distance from O.
-    auto issue = [&](int bx, int by, int bz, int b, int q, int bufi) {
+    float se[3] = {0.f, 0.f, 0.f}, sbv[3] = {0.f, 0.f, 0.f};
+    float ce[3] = {0.f, 0.f, 0.f}, cbv[3] = {0.f, 0.f, 0.f};
+    // pairs whose slot was recomputed in FP64 through global memory, counted
+    // per thread and added once per warp (not one atomic per pair)
+    uint32_t n_fb = 0;
+    const int b_begin = split * p.bricks_per_split;
+    const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
+    const uint32_t n_stages = b_end > b_begin ? (uint32_t)(b_end - b_begin) * L::kParts : 0u;
+    const uint32_t tbase = L::kTab + (uint32_t)(kTabGuard - kMagicBits) * 8u;
+
+    // Slot band of (this tile, item stage g): bounds every pair distance two
+    // ways and keeps the tighter: the boxes of the tile and of the stage's
+    // cells, and the shell [rho_lo, rho_hi] of the tile's distances from the
+    // point O (the source grid's centre) widened by the stage's farthest
+    // distance from O.  kBandSkip (and the status word set) for a band that
+    // does not fit the buffer (never, if the creation-time bound holds): its
+    // stage is skipped, so no pair reads past the buffer.
+    auto stage_band = [&](uint32_t g) -> int {
+        const int b = b_begin + (int)(g / L::kParts);
+        const int q = (int)(g % L::kParts);
+        const int bx_ = b % p.nbx, r_ = b / p.nbx, by_ = r_ % p.nby, bz_ = r_ / p.nby;
         const float* tb = s_tb;
-        const float cb[3] = {-s_D[bx], -s_D[p.nbx + by], -s_D[nbxy + bz]};
+        const float cb[3] = {-s_D[bx_], -s_D[p.nbx + by_], -s_D[nbxy + bz_]};
         const float dd[3] = {d32x, d32y, d32z};
         const float c_lo[3] = {0.f, 0.f, (float)(q * L::kSlabs)};
         const float c_hi[3] = {3.f, 3.f, (float)(q * L::kSlabs + L::kSlabs - 1)};
@@ -416,21 +438,37 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         const int hi_rel = (int)floorf(tp.A - rmin * K32) + 2;
         const int lo_rel = (int)floorf(tp.A - rmax * K32) - 2;
         const int band_rel = max(lo_rel, tp.oldest_rel);
-        const long long band_abs = tp.k0 + band_rel;
-        // A band that does not fit the buffer (never, if the creation-time
-        // bound holds) is reported and its stage skipped: no pair then reads
-        // past the buffer.
-        const bool fits = hi_rel - band_rel + 1 <= BAND;
-        if (!fits) atomicExch(p.status, kStatusInternal);
-        s_band[bufi] = fits ? band_rel : kBandSkip;
-        int y0;
-        if (band_abs >= 0) {
-            // (k0 mod P + band_rel) mod P, band_rel being small: no 64-bit division
-            y0 = tp.k0_mod + band_rel;
-            while (y0 >= p.H) y0 -= p.H;
-            while (y0 < 0) y0 += p.H;
-        } else {
-            y0 = band_abs < -(1ll << 30) ? -(1 << 30) : (int)band_abs;   // rows < 0 read as zero
+        if (hi_rel - band_rel + 1 > BAND) {
+            atomicExch(p.status, kStatusInternal);
+            return kBandSkip;
+        }
+        return band_rel;
+    };
+    // The bands of 256 stages at a time, one per thread: the copy issue on
+    // one thread then only reads its stage's band (the other warps do not
+    // wait at the stage barrier for that thread's arithmetic).
+    int16_t* s_bands = reinterpret_cast<int16_t*>(sb + L::kBands);   // bands relative to k0 fit 16 bits
+    auto fill_bands = [&](uint32_t g0) {
+        const uint32_t g = g0 + (uint32_t)tid;
+        if (g < n_stages) s_bands[tid] = (int16_t)stage_band(g);
+    };
+    // Producer (thread 0): TMA copy of item stage g into buffer bufi.
+    auto issue = [&](uint32_t g, int bufi) {
+        const int band_rel = s_bands[g & (kTileThreads - 1)];
+        s_band[bufi] = band_rel;
+        const int b = b_begin + (int)(g / L::kParts);
+        const int q = (int)(g % L::kParts);
+        int y0 = 0;   // a skipped stage still copies (rows 0..) to keep the phases in step
+        if (band_rel != kBandSkip) {
+            const long long band_abs = tp.k0 + band_rel;
+            if (band_abs >= 0) {
+                // (k0 mod P + band_rel) mod P, band_rel being small: no 64-bit division
+                y0 = tp.k0_mod + band_rel;
+                while (y0 >= p.H) y0 -= p.H;
+                while (y0 < 0) y0 += p.H;
+            } else {
+                y0 = band_abs < -(1ll << 30) ? -(1 << 30) : (int)band_abs;   // rows < 0 read as zero
+            }
         }
         // the buffer was last read through the generic proxy: order those
         // reads before the async-proxy write
@@ -439,19 +477,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         tma_load_3d(buf_u32[bufi], tmap_ptr, 0, y0, b * kBrickCells + q * L::kCells, mbar_u32[bufi]);
     };
 
-    float se[3] = {0.f, 0.f, 0.f}, sbv[3] = {0.f, 0.f, 0.f};
-    float ce[3] = {0.f, 0.f, 0.f}, cbv[3] = {0.f, 0.f, 0.f};
-    // pairs whose slot was recomputed in FP64 through global memory, counted
-    // per thread and added once per warp (not one atomic per pair)
-    uint32_t n_fb = 0;
-    const int b_begin = split * p.bricks_per_split;
-    const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
-    const uint32_t n_stages = b_end > b_begin ? (uint32_t)(b_end - b_begin) * L::kParts : 0u;
-    const uint32_t tbase = L::kTab + (uint32_t)(kTabGuard - kMagicBits) * 8u;
-
-    if (tid == 0 && n_stages > 0) {
-        const int rest = b_begin / p.nbx;
-        issue(b_begin % p.nbx, rest % p.nby, rest / p.nby, b_begin, 0, g_it & 1);
+    if (n_stages > 0) {
+        fill_bands(0);
+        __syncthreads();
+        if (tid == 0) issue(0, g_it & 1);
     }
     int64_t aborted_at = -1;
     // brick coordinates of b, advanced incrementally (no division per brick)
@@ -476,22 +505,12 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         // One stage: q-th group of kCells cells of brick b.  False if its copy
         // did not complete in time (the item then stops).
         auto stage = [&](const int q) -> bool {
-            const uint32_t it = g_it + (uint32_t)(b - b_begin) * L::kParts + (uint32_t)q;
+            const uint32_t g = (uint32_t)(b - b_begin) * L::kParts + (uint32_t)q;   // stage of the item
+            const uint32_t it = g_it + g;
             const int buf = it & 1;
             // the next stage's copy goes into the other buffer, whose last
             // readers passed the barrier at the end of the previous stage
-            if (tid == 0 && it + 1 < g_it + n_stages) {
-                if (q + 1 < L::kParts) {
-                    issue(bx, by, bz, b, q + 1, buf ^ 1);
-                } else {
-                    int nx = bx + 1, ny = by, nz = bz;
-                    if (nx == p.nbx) {
-                        nx = 0;
-                        if (++ny == p.nby) { ny = 0; ++nz; }
-                    }
-                    issue(nx, ny, nz, b + 1, 0, buf ^ 1);
-                }
-            }
+            if (tid == 0 && g + 1 < n_stages) issue(g + 1, buf ^ 1);
             const bool ready = mbar_wait_bounded(mbar_u32[buf], (it >> 1) & 1);
             const int band_rel = s_band[buf];
             if (ready && band_rel != kBandSkip) {
@@ -681,9 +700,12 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     }
                 }
             }
-            // every thread is done with this buffer before it is refilled
+            // the next 256 bands, before the stage that issues the first of them
+            if (((g + 2) & (kTileThreads - 1)) == 0 && g + 2 < n_stages) fill_bands(g + 2);
+            // every thread is done with this buffer (and s_bands is complete)
+            // before the next copy is issued
             if (__syncthreads_or(!ready)) {
-                aborted_at = (int64_t)(it - g_it);
+                aborted_at = (int64_t)g;
                 return false;
             }
             return true;
