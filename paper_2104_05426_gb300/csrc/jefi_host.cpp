@@ -503,6 +503,17 @@ int current_sm_count() {
     return n;
 }
 
+// Consecutive source splits one staged work item sums, given the launch's
+// items at one split each: enough that about four waves of two CTAs per SM
+// remain.  The partials are those of one item per split whatever the value,
+// so it changes the cost of a launch (its items' preambles and first copies),
+// never its result.
+int32_t split_merge_for(int64_t items, int32_t n_split) {
+    const int64_t target = 4 * 2 * (int64_t)current_sm_count();
+    const int64_t m = items / std::max<int64_t>(target, 1);
+    return (int32_t)std::max<int64_t>(1, std::min<int64_t>(m, n_split));
+}
+
 // Record that work on h's memory was enqueued on stream s (jefi_destroy waits for it).
 int mark_use(jefi_problem* h, cudaStream_t s) {
     if (!h->last_use) JEFI_CUDA(cudaEventCreateWithFlags(&h->last_use, cudaEventDisableTiming));
@@ -736,6 +747,7 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     p.interp = h->interp ? 1 : 0;
     p.n_split = h->n_split;
     p.bricks_per_split = h->bricks_per_split;
+    p.split_merge = 1;
     p.partials = h->partials + (size_t)slot0 * h->n_split * 6 * h->n_slots;
     p.fallbacks = h->fallbacks;
     p.debug_slots = debug_slots;
@@ -773,6 +785,7 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
     }
     SumParams p = make_params(h, n_t, 0, debug_slots);
     if (h->band == 0 && sum_smem_bytes(p) > 200 * 1024) return JEFI_EUNSUPPORTED;
+    if (h->band > 0) p.split_merge = split_merge_for((int64_t)h->n_tiles * h->n_split * n_t, h->n_split);
 
     const bool timed = (h->prm.flags & JEFI_FLAG_STATS) != 0 && !debug_slots;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -970,10 +983,16 @@ int batch_fill(BatchLayout* L, unsigned char* host, Params&& params) {
         SumParams* prm = reinterpret_cast<SumParams*>(host + L->off_params[g]);
         int32_t* start = reinterpret_cast<int32_t*>(host + L->off_start[g]);
         int32_t acc = 0;
+        int64_t items1 = 0;   // the group's items at one split each
         for (size_t m = 0; m < G.members.size(); ++m) {
             prm[m] = params(G.members[m]);
+            items1 += (int64_t)prm[m].n_tiles * prm[m].n_split;
+        }
+        for (size_t m = 0; m < G.members.size(); ++m) {
+            // staged items merge splits (same results, fewer preambles)
+            prm[m].split_merge = G.kind == 2 ? std::min(split_merge_for(items1, INT32_MAX), prm[m].n_split) : 1;
             start[m] = acc;
-            acc += prm[m].n_tiles * prm[m].n_split;
+            acc += prm[m].n_tiles * ((prm[m].n_split + prm[m].split_merge - 1) / prm[m].split_merge);
             L->smem[g] = std::max(L->smem[g], G.kind == 2 ? staged_smem_bytes(prm[m], G.band, true)
                                                             : sum_smem_bytes(prm[m]));
         }

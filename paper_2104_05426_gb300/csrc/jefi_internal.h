@@ -98,6 +98,8 @@ struct SumParams {
     // work split
     int32_t n_split;
     int32_t bricks_per_split;
+    int32_t split_merge;            // staged kernel: consecutive splits one work item sums (>= 1);
+                                    // each split's partials are written as if it were an item of its own
     // outputs
     double* partials;
     unsigned long long* fallbacks;  // pairs whose slot was recomputed in FP64

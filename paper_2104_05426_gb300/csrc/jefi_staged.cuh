@@ -316,15 +316,15 @@ __device__ __noinline__ FixSums staged_fixup_geo(uint64_t mask, const unsigned c
     return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
 }
 
-// One work item: observation tile `tile` x source split `split` at time
-// index `ti` of problem p.  g_it counts the CTA's stages across items (it
+// One work item: observation tile `tile` x source splits [group split_merge,
+// (group + 1) split_merge) at time index `ti` of problem p.  g_it counts the CTA's stages across items (it
 // selects the buffer and the mbarrier phase).  Returns false if a copy did
 // not complete in time (the caller stops).  GEO: undecided pairs take their
 // FP64 geometry from shared memory and are counted there (the single-problem
 // kernel); otherwise from global memory (the batched kernel).
 template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool GEO>
 __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const int comp,
-                                            const int tile, const int split, const int ti, uint32_t& g_it) {
+                                            const int tile, const int group, const int ti, uint32_t& g_it) {
     using L = Layout<BAND>;
     unsigned char* const sb = staged_base<BAND>();
     const int K = p.K;
@@ -377,18 +377,27 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     const uint32_t mbar_u32[2] = {smem_u32(&s_mbar[0]), smem_u32(&s_mbar[1])};
     const uint32_t buf_u32[2] = {smem_u32(sb), smem_u32(sb + L::kBufBytes)};
 
-    // Producer (thread 0): slot band of (this tile, stage q of brick b) and its
-    // TMA copy.  The band bounds every pair distance two ways and keeps the
-    // tighter: the boxes of the tile and of the stage's cells, and the shell
-    // [rho_lo, rho_hi] of the tile's distances from the point O (the source
-    // grid's centre) widened by the stage's farthest distance from O.
     float se[3] = {0.f, 0.f, 0.f}, sbv[3] = {0.f, 0.f, 0.f};
     float ce[3] = {0.f, 0.f, 0.f}, cbv[3] = {0.f, 0.f, 0.f};
     // pairs whose slot was recomputed in FP64 through global memory, counted
     // per thread and added once per warp (not one atomic per pair)
     uint32_t n_fb = 0;
-    const int b_begin = split * p.bricks_per_split;
-    const int b_end = min(b_begin + p.bricks_per_split, p.n_bricks);
+    // The item covers splits [split_lo, split_hi) (p.split_merge per item);
+    // each split's bricks are summed and its partials written as an item of
+    // its own would: the result does not depend on how many splits an item
+    // merges, while the preamble and the pipeline's first copy are paid once.
+    const int split_lo = group * p.split_merge;
+    const int split_hi = min(split_lo + p.split_merge, p.n_split);
+    const int b_begin = split_lo * p.bricks_per_split;
+    const int b_end = min(split_hi * p.bricks_per_split, p.n_bricks);
+    auto write_split = [&](int sp) {
+        double* out = p.partials + ((size_t)ti * p.n_split + sp) * 6 * p.n_slots + ctx.slot;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            out[(size_t)a * p.n_slots] = comp ? (double)se[a] - (double)ce[a] : (double)se[a];
+            out[(size_t)(3 + a) * p.n_slots] = comp ? (double)sbv[a] - (double)cbv[a] : (double)sbv[a];
+        }
+    };
     const uint32_t n_stages = b_end > b_begin ? (uint32_t)(b_end - b_begin) * L::kParts : 0u;
     const uint32_t tbase = L::kTab + (uint32_t)(kTabGuard - kMagicBits) * 8u;
 
@@ -492,11 +501,15 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         bz = rest / p.nby;
     }
     for (int b = b_begin; b < b_end && aborted_at < 0; ++b) {
-        const bool full = (bx < p.nfull[0]) & (by < p.nfull[1]) & (bz < p.nfull[2]);
         const bool near = (ctx.rlo[0] <= kBrick * bx + 3) & (ctx.rhi[0] >= kBrick * bx) &
                           (ctx.rlo[1] <= kBrick * by + 3) & (ctx.rhi[1] >= kBrick * by) &
                           (ctx.rlo[2] <= kBrick * bz + 3) & (ctx.rhi[2] >= kBrick * bz);
-        const bool fast = full && !__any_sync(kFull, near);
+        // Bricks with a screened pair take the checked path.  Padding cells
+        // (past the grid's last cell) take the fast one: their channels are
+        // zero in every slot, their distances are unscreened and bounded away
+        // from zero like every padded pair (creation checks it), and their
+        // slots fall in the stage's band (computed from the padded box).
+        const bool fast = !__any_sync(kFull, near);
         const float Px = oox + s_D[bx];
         const float Py = ooy + s_D[p.nbx + by];
         const float Pz = ooz + s_D[nbxy + bz];
@@ -646,8 +659,8 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         }
                     }
                 } else {
-                    // Bricks with padding cells or screened pairs: rolled loop with
-                    // per-pair checks and clamped indices.
+                    // Bricks with screened pairs: rolled loop with per-pair checks
+                    // and clamped indices.
                     for (int cl = cell0; cl < cell0 + L::kCells; ++cl) {
                         const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
                         const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
@@ -733,6 +746,12 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
             bx = 0;
             if (++by == p.nby) { by = 0; ++bz; }
         }
+        if ((b + 1) % p.bricks_per_split == 0 || b + 1 == b_end) {
+            // the split of brick b is complete: its partial sums
+            write_split(b / p.bricks_per_split);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) se[a] = sbv[a] = ce[a] = cbv[a] = 0.f;
+        }
     }
     if (aborted_at >= 0) {
         // a copy did not complete in time: report, then wait (bounded) for
@@ -757,12 +776,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         if (tid == 0 && n) atomicAdd(p.fallbacks, (unsigned long long)n);
     }
 
-    double* out = p.partials + ((size_t)ti * p.n_split + split) * 6 * p.n_slots + ctx.slot;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        out[(size_t)a * p.n_slots] = comp ? (double)se[a] - (double)ce[a] : (double)se[a];
-        out[(size_t)(3 + a) * p.n_slots] = comp ? (double)sbv[a] - (double)cbv[a] : (double)sbv[a];
-    }
+    // a split without bricks still gets its (zero) partials; after a copy
+    // timed out the status word reports the item as failed
+    for (int sp = split_lo; sp < split_hi; ++sp)
+        if (sp * p.bricks_per_split >= b_end) write_split(sp);
     return aborted_at < 0;
 }
 
@@ -780,12 +797,12 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 // Non-lattice items take the FP64 geometry of undecided pairs from shared
 // memory, as the single-problem kernel does.
 template <int BAND, bool EXACT, bool INTERP>
-__device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int split,
+__device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int group,
                                                int ti, uint32_t& g_it) {
-    return staged_item<BAND, EXACT, false, INTERP, !EXACT>(map, p, p.comp, tile, split, ti, g_it);
+    return staged_item<BAND, EXACT, false, INTERP, !EXACT>(map, p, p.comp, tile, group, ti, g_it);
 }
 
-// Persistent batched kernel: CTAs take (problem, time, split, tile) items
+// Persistent batched kernel: CTAs take (problem, time, split group, tile) items
 // from a queue until it is empty; each item runs the same code as the
 // single-problem kernel, so a problem's result does not depend on the batch.
 template <int BAND, bool EXACT>
@@ -818,21 +835,22 @@ __global__ void __launch_bounds__(kTileThreads, 2) sum_f32_staged_batch(const __
         __syncthreads();
         const SumParams& p = s_par;
         const int local = item - a.item_start[lo];
-        const int per_t = p.n_tiles * p.n_split;
+        const int n_groups = (p.n_split + p.split_merge - 1) / p.split_merge;
+        const int per_t = p.n_tiles * n_groups;
         const int ti = local / per_t;
         const int r = local - ti * per_t;
-        const int split = r / p.n_tiles;
-        const int tile = r - split * p.n_tiles;
+        const int group = r / p.n_tiles;
+        const int tile = r - group * p.n_tiles;
         // the retarded-time rule is a property of the problem (uniform per item)
-        const bool ok = p.interp ? staged_batch_item<BAND, EXACT, true>(&a.maps[lo], p, tile, split, ti, g_it)
-                                 : staged_batch_item<BAND, EXACT, false>(&a.maps[lo], p, tile, split, ti, g_it);
+        const bool ok = p.interp ? staged_batch_item<BAND, EXACT, true>(&a.maps[lo], p, tile, group, ti, g_it)
+                                 : staged_batch_item<BAND, EXACT, false>(&a.maps[lo], p, tile, group, ti, g_it);
         if (!ok) break;
     }
 }
 
 template <int BAND, bool EXACT, bool DEBUG, bool INTERP = false>
 cudaError_t launch_variant(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
-    const dim3 grid(p.n_tiles, p.n_split, p.n_t);
+    const dim3 grid(p.n_tiles, (p.n_split + p.split_merge - 1) / p.split_merge, p.n_t);
     const size_t smem = staged_smem_bytes(p, BAND, false);
     auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG, INTERP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
