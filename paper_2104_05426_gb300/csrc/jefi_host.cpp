@@ -503,15 +503,33 @@ int current_sm_count() {
     return n;
 }
 
-// Consecutive source splits one staged work item sums, given the launch's
-// items at one split each: enough that about four waves of two CTAs per SM
-// remain.  The partials are those of one item per split whatever the value,
-// so it changes the cost of a launch (its items' preambles and first copies),
-// never its result.
-int32_t split_merge_for(int64_t items, int32_t n_split) {
-    const int64_t target = 4 * 2 * (int64_t)current_sm_count();
-    const int64_t m = items / std::max<int64_t>(target, 1);
-    return (int32_t)std::max<int64_t>(1, std::min<int64_t>(m, n_split));
+// CTAs of a staged sum kernel resident at once: two per SM while two
+// fit the SM's shared memory (228 KB, 1 KB of it reserved per CTA).
+int64_t staged_resident_ctas(size_t smem_bytes) {
+    const int64_t per_sm = std::min<int64_t>(2, (int64_t)(233472 / (smem_bytes + 1024)));
+    return std::max<int64_t>(1, per_sm) * current_sm_count();
+}
+
+// Consecutive source splits one staged work item sums in a single-problem
+// launch of `units` (tile, time) pairs.  Items of equal work run in waves of
+// the resident CTAs; the merge is the one with the least predicted time:
+// waves x (bricks per item + a preamble of about half a brick's work).  The
+// partials are those of one item per split whatever the value, so it changes
+// the cost of a launch (its items' preambles and first copies, its last
+// wave), never its result.
+int32_t split_merge_for(int64_t units, int32_t n_split, int32_t bricks_per_split, int64_t resident) {
+    double best = 0.0;
+    int32_t best_m = 1;
+    for (int32_t m = 1; m <= std::max(n_split, 1); ++m) {
+        const int64_t items = units * ((n_split + m - 1) / m);
+        const int64_t waves = (items + resident - 1) / std::max<int64_t>(resident, 1);
+        const double cost = (double)waves * ((double)m * bricks_per_split + 0.5);
+        if (m == 1 || cost < best) {
+            best = cost;
+            best_m = m;
+        }
+    }
+    return best_m;
 }
 
 // Record that work on h's memory was enqueued on stream s (jefi_destroy waits for it).
@@ -785,7 +803,9 @@ int launch_chunk(jefi_problem* h, int n_t, const double* t, double* E, double* B
     }
     SumParams p = make_params(h, n_t, 0, debug_slots);
     if (h->band == 0 && sum_smem_bytes(p) > 200 * 1024) return JEFI_EUNSUPPORTED;
-    if (h->band > 0) p.split_merge = split_merge_for((int64_t)h->n_tiles * h->n_split * n_t, h->n_split);
+    if (h->band > 0)
+        p.split_merge = split_merge_for((int64_t)h->n_tiles * n_t, h->n_split, h->bricks_per_split,
+                                        staged_resident_ctas(staged_smem_bytes(p, h->band, false)));
 
     const bool timed = (h->prm.flags & JEFI_FLAG_STATS) != 0 && !debug_slots;
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -979,22 +999,52 @@ int batch_fill(BatchLayout* L, unsigned char* host, Params&& params) {
     L->n_items.assign(ng, 0);
     L->smem.assign(ng, 0);
     for (size_t g = 0; g < ng; ++g) {
-        const BatchGroup& G = L->groups[g];
+        BatchGroup& G = L->groups[g];
         SumParams* prm = reinterpret_cast<SumParams*>(host + L->off_params[g]);
         int32_t* start = reinterpret_cast<int32_t*>(host + L->off_start[g]);
-        int32_t acc = 0;
-        int64_t items1 = 0;   // the group's items at one split each
-        for (size_t m = 0; m < G.members.size(); ++m) {
-            prm[m] = params(G.members[m]);
-            items1 += (int64_t)prm[m].n_tiles * prm[m].n_split;
+        const size_t nm = G.members.size();
+        std::vector<SumParams> par(nm);
+        for (size_t m = 0; m < nm; ++m) {
+            par[m] = params(G.members[m]);
+            L->smem[g] = std::max(L->smem[g], G.kind == 2 ? staged_smem_bytes(par[m], G.band, true)
+                                                            : sum_smem_bytes(par[m]));
         }
-        for (size_t m = 0; m < G.members.size(); ++m) {
-            // staged items merge splits (same results, fewer preambles)
-            prm[m].split_merge = G.kind == 2 ? std::min(split_merge_for(items1, INT32_MAX), prm[m].n_split) : 1;
+        if (G.kind == 2) {
+            // Staged items merge a member's splits up to about an equal share
+            // of the group's work (4 waves of the resident CTAs; never finer
+            // than the member's own splits), and the members are queued by
+            // item work, largest first: the queue's last items, which set the
+            // launch's tail, are its smallest.  Neither changes a result
+            // (each split's partials are written as one item per split would).
+            int64_t work = 0;   // (tile, brick) units of the group
+            for (size_t m = 0; m < nm; ++m) work += (int64_t)par[m].n_tiles * par[m].n_bricks;
+            const int64_t per_item = std::max<int64_t>(1, work / (4 * staged_resident_ctas(L->smem[g])));
+            std::vector<int64_t> item_work(nm);
+            for (size_t m = 0; m < nm; ++m) {
+                const int64_t bps = std::max<int32_t>(par[m].bricks_per_split, 1);
+                par[m].split_merge = (int32_t)std::max<int64_t>(
+                    1, std::min<int64_t>((per_item + bps / 2) / bps, par[m].n_split));
+                item_work[m] = std::min<int64_t>((int64_t)par[m].split_merge * bps, par[m].n_bricks);
+            }
+            std::vector<size_t> order(nm);
+            for (size_t m = 0; m < nm; ++m) order[m] = m;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](size_t x, size_t y) { return item_work[x] > item_work[y]; });
+            std::vector<int> members(nm);
+            std::vector<SumParams> sorted(nm);
+            for (size_t m = 0; m < nm; ++m) {
+                members[m] = G.members[order[m]];
+                sorted[m] = par[order[m]];
+            }
+            G.members.swap(members);
+            par.swap(sorted);
+        }
+        int32_t acc = 0;
+        for (size_t m = 0; m < nm; ++m) {
+            prm[m] = par[m];
+            if (G.kind != 2) prm[m].split_merge = 1;
             start[m] = acc;
             acc += prm[m].n_tiles * ((prm[m].n_split + prm[m].split_merge - 1) / prm[m].split_merge);
-            L->smem[g] = std::max(L->smem[g], G.kind == 2 ? staged_smem_bytes(prm[m], G.band, true)
-                                                            : sum_smem_bytes(prm[m]));
         }
         start[G.members.size()] = acc;
         L->n_items[g] = acc;
