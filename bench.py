@@ -511,7 +511,8 @@ def dipole_leg(dev, reps=5):
         out[prec] = {"value": pairs / (ms / 1e3), "unit": UNIT, "kernel_ms": ms,
                      "kernel": (f"staged band {info['staged_band']}" if info["staged_band"] and prec != "fp64"
                                 else ("sum_f64_kernel" if prec == "fp64" else "sum_f32_kernel (direct gather)")),
-                     "device_status": info["device_status"]}
+                     "device_status": info["device_status"],
+                     "fallback_pairs_per_launch": info["slot_fallbacks"] / max(info["sum_launches"], 1)}
         fields[prec] = (E, B)
         jefi.jefi_destroy(h)
     peak = pipe_peak(device_sm_count(dev), FP32_LANES_PER_SM, DEFAULT_SM_MAX_MHZ)

@@ -109,11 +109,15 @@ typedef struct {
      * large grid's. */
     int32_t src_origin[3];
     /* Observation grids only: the shape of the 256-point tiles one CTA
-     * evaluates, JEFI_TILE_8x8x4 ... JEFI_TILE_4x4x16, or JEFI_TILE_AUTO (0):
-     * for FP32 problems the shape whose widest tile spans the narrowest range
-     * of pair distances (the slot band the staged kernel copies), else
-     * 8x8x4.  Point lists are tiled in Morton order (or by distance from the
-     * sources when that narrows the bands clearly). */
+     * evaluates, JEFI_TILE_8x8x4 ... JEFI_TILE_4x4x16 (boxes of the grid),
+     * JEFI_TILE_PACKED (4x4x2-point blocks of the grid in Morton order,
+     * eight per tile: fewer padding lanes where the grid's sides are not
+     * multiples of a box), or JEFI_TILE_AUTO (0): for FP32 problems the
+     * tiling with the least predicted time, tiles x the cost of the slot band
+     * its widest tile needs (the band the staged kernel copies), else 8x8x4.
+     * Point lists are tiled in Morton order (or by distance from the sources
+     * when that narrows the bands clearly).  The tiling changes which CTA
+     * sums a point, never the slots. */
     int32_t tile_shape;
 } jefi_params;
 
@@ -126,6 +130,7 @@ typedef struct {
 #define JEFI_TILE_16x8x2 6
 #define JEFI_TILE_8x16x2 7
 #define JEFI_TILE_4x4x16 8
+#define JEFI_TILE_PACKED 9
 
 #define JEFI_FLAG_STATS 1u    /* time the sum kernel with CUDA events on the call's stream */
 #define JEFI_FLAG_DIRECT_GATHER 2u  /* FP32: never use the TMA-staged kernel (for comparisons) */

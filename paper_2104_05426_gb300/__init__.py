@@ -50,9 +50,11 @@ JEFI_KERNEL_MEASURE = 0
 JEFI_KERNEL_DIRECT = 1
 JEFI_KERNEL_STAGED = 2
 
-# Observation-grid tile shapes (points per tile along x, y, z); 0 = chosen at creation
+# Observation-grid tile shapes (points per tile along x, y, z); 0 = chosen at
+# creation; 9 = packed (4x4x2-point blocks in Morton order, eight per tile)
 TILE_SHAPES = {0: None, 1: (8, 8, 4), 2: (16, 4, 4), 3: (4, 8, 8), 4: (8, 4, 8), 5: (4, 16, 4),
-               6: (16, 8, 2), 7: (8, 16, 2), 8: (4, 4, 16)}
+               6: (16, 8, 2), 7: (8, 16, 2), 8: (4, 4, 16), 9: "packed"}
+JEFI_TILE_PACKED = 9
 
 PRECISIONS = {"fp64": JEFI_FP64, "fp32": JEFI_FP32, "fp32c": JEFI_FP32_COMP}
 

@@ -294,7 +294,8 @@ double tiles_extent(const std::vector<int64_t>& order, const double* pts, const 
 // creation.  A tile's warps are laid out x fastest, then y, then z.
 constexpr int kTileShapes[9][3] = {{0, 0, 0}, {8, 8, 4}, {16, 4, 4}, {4, 8, 8}, {8, 4, 8},
                                    {4, 16, 4}, {16, 8, 2}, {8, 16, 2}, {4, 4, 16}};
-constexpr int kNumTileShapes = 8;
+constexpr int kNumTileShapes = 8;   // box shapes; JEFI_TILE_PACKED (9) is the packed tiling
+constexpr int kTilePacked = 9;
 
 // The widest pair-distance range over the tiles of shape s of an observation
 // grid, from each tile's box alone (the box of a tile's points is known from
@@ -344,6 +345,62 @@ void grid_tile_order(int64_t gx, int64_t gy, int64_t gz, int s, std::vector<int6
             if (i < gx && j < gy && k < gz) order[tile * kTileThreads + tid] = (k * gy + j) * gx + i;
         }
     }
+}
+
+// Packed tiling of an observation grid (JEFI_TILE_PACKED): the grid cut
+// into warp blocks of 4x4x2 points (every block holds at least one point),
+// the blocks in Morton order of their block coordinates, eight consecutive
+// blocks per tile (the last tile may hold fewer).  On grids whose sides are
+// not multiples of a box shape this leaves far fewer padding lanes (which do
+// a point's arithmetic too) than box tiles, at the price of less regular
+// tiles where the Morton order turns.
+void packed_tile_order(int64_t gx, int64_t gy, int64_t gz, std::vector<int64_t>& order) {
+    const int64_t nbx = (gx + 3) / 4, nby = (gy + 3) / 4, nbz = (gz + 1) / 2;
+    std::vector<std::pair<uint64_t, int64_t>> keys;
+    keys.reserve((size_t)(nbx * nby * nbz));
+    for (int64_t k = 0; k < nbz; ++k)
+        for (int64_t j = 0; j < nby; ++j)
+            for (int64_t i = 0; i < nbx; ++i) {
+                const uint64_t q[3] = {(uint64_t)i, (uint64_t)j, (uint64_t)k};
+                uint64_t key = 0;
+                for (int bit = 20; bit >= 0; --bit)
+                    for (int a = 2; a >= 0; --a) key = (key << 1) | ((q[a] >> bit) & 1u);
+                keys.push_back({key, (k * nby + j) * nbx + i});
+            }
+    std::sort(keys.begin(), keys.end());
+    const int64_t n_tiles = ((int64_t)keys.size() + 7) / 8;
+    order.assign((size_t)n_tiles * kTileThreads, -1);
+    for (size_t w = 0; w < keys.size(); ++w) {
+        const int64_t b = keys[w].second;
+        const int64_t bi = b % nbx, bj = (b / nbx) % nby, bk = b / (nbx * nby);
+        for (int l = 0; l < 32; ++l) {
+            const int64_t i = 4 * bi + (l & 3), j = 4 * bj + ((l >> 2) & 3), k = 2 * bk + (l >> 4);
+            if (i < gx && j < gy && k < gz) order[w * 32 + l] = (k * gy + j) * gx + i;
+        }
+    }
+}
+
+// Relative time per (tile, brick) of the FP32 sum at a staged band height
+// (0: the direct-gather kernel), measured on GB300 on wide-band problems;
+// only ranks tilings of one problem against each other.
+double band_cost(int band) {
+    switch (band) {
+        case 16: case 24: return 1.0;
+        case 32: return 1.2;
+        case 48: return 1.3;
+        case 64: return 1.5;
+        case 96: return 1.8;
+        default: return 3.0;
+    }
+}
+
+// The staged band height a widest pair-distance range `ext` needs (0 if
+// none fits, or none within `max_band`).
+int band_for_extent(double ext, double Kd, int max_band) {
+    const double need = std::ceil(ext * Kd * (1 + 1e-4) + 1e-3) + 7;
+    for (int b : kStagedBands)
+        if (need <= b) return b <= max_band ? b : 0;
+    return 0;
 }
 
 }  // namespace
@@ -1150,7 +1207,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     for (int a = 0; a < 3; ++a) {
         if (src->n[a] < 0 || !(src->d[a] > 0) || !std::isfinite(src->d[a]) ||
             !std::isfinite(src->lo[a]) || !std::isfinite(p->screen[a]) || p->src_origin[a] < 0 ||
-            p->tile_shape < 0 || p->tile_shape > kNumTileShapes ||
+            p->tile_shape < 0 || p->tile_shape > kTilePacked ||
             (int64_t)p->src_origin[a] + src->n[a] + 4 > ((int64_t)1 << 30))
             return JEFI_EINVAL;
     }
@@ -1212,25 +1269,46 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         if (n_obs > 0) {
             int shape = p->tile_shape > 0 ? p->tile_shape : 1;
             if (p->tile_shape == 0 && !h->fp64 && h->n_src > 0) {
-                // the shape whose widest tile spans the narrowest pair-distance
-                // range (the staged kernel's band); the first shape on ties.
+                // The tiling with the least predicted time: its tiles times the
+                // relative cost of the band height its widest tile needs (box
+                // shapes from their boxes, the packed tiling from its points);
+                // on equal cost the narrower widest tile, then the first.
                 // FP32 handles choose alike whichever kernel they start on, so
                 // a handle switched between kernels equals one created on the
                 // other (same tiles, same sums)
                 const int64_t np3[3] = {h->npx, h->npy, h->npz};
                 double O[3], r_src, db;
                 source_shell(*src, h->org, np3, O, &r_src, &db);
-                double best = INFINITY;
-                for (int s = 1; s <= kNumTileShapes; ++s) {
-                    const double e = grid_tiles_extent(*obs_grid, s, O, r_src, db);
-                    if (e < best * (1 - 1e-9)) {
-                        best = e;
-                        shape = s;
+                const double Kd = 1.0 / (p->c * p->dt);
+                const int max_band = base ? base->mirror : kStagedMaxBand;
+                double best_cost = INFINITY, best_ext = INFINITY;
+                auto consider = [&](int s_, int64_t tiles, double e) {
+                    const double cost = (double)tiles * band_cost(band_for_extent(e, Kd, max_band));
+                    const bool tie = std::fabs(cost - best_cost) <= 1e-9 * cost;
+                    if ((!tie && cost < best_cost) || (tie && e < best_ext * (1 - 1e-9))) {
+                        best_cost = cost;
+                        best_ext = e;
+                        shape = s_;
+                        return true;
                     }
+                    return false;
+                };
+                for (int s_ = 1; s_ <= kNumTileShapes; ++s_) {
+                    int64_t tiles = 1;
+                    for (int a = 0; a < 3; ++a) tiles *= (obs_grid->n[a] + kTileShapes[s_][a] - 1) / kTileShapes[s_][a];
+                    consider(s_, tiles, grid_tiles_extent(*obs_grid, s_, O, r_src, db));
                 }
+                std::vector<int64_t> packed;
+                packed_tile_order(gx, gy, gz, packed);
+                if (consider(kTilePacked, (int64_t)(packed.size() / kTileThreads),
+                             tiles_extent(packed, pts.data(), O, r_src, db)))
+                    order.swap(packed);
             }
             h->tile_shape = shape;
-            grid_tile_order(gx, gy, gz, shape, order);
+            if (shape != kTilePacked)
+                grid_tile_order(gx, gy, gz, shape, order);
+            else if (order.empty())
+                packed_tile_order(gx, gy, gz, order);
         }
     } else {
         std::memcpy(pts.data(), obs_points, sizeof(double) * 3 * (size_t)n_obs);
@@ -1377,9 +1455,16 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         h->K = 1;
     }
     {
-        const int64_t target = 2 * 2 * (int64_t)current_sm_count();  // two waves of two CTAs per SM
+        // Source splits: enough (tile, split) items for eight waves of two
+        // CTAs per SM at one evaluation time (four for views, whose partials
+        // count against a serving budget), so that a launch can merge them
+        // into items that fill its last wave (split_merge_for); at most one
+        // split per brick, and partials of at most 256 MB.
+        const int64_t target = (base ? 4 : 8) * 2 * (int64_t)current_sm_count();
         int64_t ns = std::max<int64_t>(1, (target + h->n_tiles - 1) / std::max<int32_t>(h->n_tiles, 1));
         ns = std::min<int64_t>(ns, std::max<int32_t>(h->n_bricks, 1));
+        const int64_t split_bytes = (int64_t)h->time_chunk * 6 * 8 * std::max<int32_t>(h->n_slots, 1);
+        ns = std::max<int64_t>(1, std::min<int64_t>(ns, ((int64_t)256 << 20) / split_bytes));
         h->bricks_per_split = (int32_t)((h->n_bricks + ns - 1) / ns);
         if (h->bricks_per_split < 1) h->bricks_per_split = 1;
         h->n_split = (int32_t)((h->n_bricks + h->bricks_per_split - 1) / h->bricks_per_split);

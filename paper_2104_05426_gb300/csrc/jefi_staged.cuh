@@ -550,31 +550,51 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     const uint32_t gbase = (L::kSwz ? 0u : (uint32_t)buf * L::kBufBytes) -
                                            (uint32_t)(kMagicBits + band_rel) * L::kRowBytes;
                     uint64_t mask = 0;
-                    float2 acc_eyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
-                    float acc_ex = 0.f, acc_bz = 0.f;
+                    // operands of the candidates of two cells at once (packed FP32
+                    // with the scalar roundings: the same bits as one cell at a time)
+                    const float2 nK2 = make_float2(-K32, -K32), Ag2 = make_float2(Ag, Ag);
+                    const float2 magic2 = make_float2(kMagic, kMagic);
+                    // E' = sum D q - sum (dJ/c) r^-1 and B = sum V x D: the
+                    // products with D in scalars (no operand pair to build per
+                    // pair), the dJ-terms of y and z packed and subtracted per
+                    // stage (no negated pair per pair)
+                    float acc_ex = 0.f, acc_ey = 0.f, acc_ez = 0.f, acc_bz = 0.f;
+                    float2 acc_jyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
 #pragma unroll 1
                     for (int kk = 0; kk < L::kSlabs; ++kk) {
                         const int k = q * L::kSlabs + kk;
                         const float dz = fmaf(-(float)k, d32z, Pz);
                         const float sqz = __fmul_rn(dz, dz);
                         const uint32_t gk = gbase + (uint32_t)(kk * 16) * L::kCellBytes;
-                        float2 dyz[4], dzx[4];      // (dy_j, dz) and (dz, dx_i) operand pairs
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            dyz[i] = make_float2(ddy[i], dz);
-                            dzx[i] = make_float2(dz, ddx[i]);
-                        }
                         uint32_t m16 = 0;           // undecided cells of this slab (non-lattice geometry)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
                             const float syz = __fadd_rn(sqy[j], sqz);
+                            const float2 syz2 = make_float2(syz, syz);
+                            float2 S2, R2, B2;   // S, r^-1 and candidate bits of cells i, i+1
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 const int c16 = j * 4 + i;
-                                const float S = __fadd_rn(sqx[i], syz);
-                                float ri = rsqrt_ftz(S);
-                                const float u = fmaf(-(S * ri), K32, Ag);
-                                const uint32_t bits = __float_as_uint(__fadd_rd(u, kMagic));
+                                float S, ri;
+                                uint32_t bits;
+                                if constexpr (EXACT) {
+                                    // lattice kernel: two cells' candidates at once,
+                                    // S*r^-1*(-K) + A + g rounded as fmaf(-(S*ri), K, Ag)
+                                    if ((i & 1) == 0) {
+                                        S2 = __fadd2_rn(make_float2(sqx[i], sqx[i + 1]), syz2);
+                                        R2 = make_float2(rsqrt_ftz(S2.x), rsqrt_ftz(S2.y));
+                                        B2 = __fadd2_rd(__ffma2_rn(__fmul2_rn(S2, R2), nK2, Ag2), magic2);
+                                    }
+                                    S = (i & 1) ? S2.y : S2.x;
+                                    ri = (i & 1) ? R2.y : R2.x;
+                                    bits = __float_as_uint((i & 1) ? B2.y : B2.x);
+                                } else {
+                                    // one cell at a time (the pairs cost the
+                                    // undecided test's registers)
+                                    S = __fadd_rn(sqx[i], syz);
+                                    ri = rsqrt_ftz(S);
+                                    bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
+                                }
                                 // row of candidate k' (bits), moved down one row when S is
                                 // past the threshold: lower = 0 or ~0u
                                 uint32_t lower;
@@ -614,13 +634,15 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                 const float2 vyz = __fmul2_rn(__ffma2_rn(make_float2(v0.z, v0.w), ri2,
                                                                          make_float2(v1.z, v1.w)), r2);
                                 const float qq = qvx.x, vx = qvx.y;
-                                // E' += D q - (dJ/c) / R
+                                // E' += D q - (dJ/c) r^-1
                                 acc_ex = fmaf(ddx[i], qq, acc_ex);
                                 acc_ex = fmaf(-v1.y, ri, acc_ex);
-                                acc_eyz = __ffma2_rn(dyz[j], make_float2(qq, qq), acc_eyz);
-                                acc_eyz = __ffma2_rn(make_float2(-v1.z, -v1.w), ri2, acc_eyz);
+                                acc_ey = fmaf(ddy[j], qq, acc_ey);
+                                acc_ez = fmaf(dz, qq, acc_ez);
+                                acc_jyz = __ffma2_rn(make_float2(v1.z, v1.w), ri2, acc_jyz);
                                 // B += V x D
-                                acc_bxy = __ffma2_rn(vyz, dzx[i], acc_bxy);          // (Vy dz, Vz dx)
+                                acc_bxy.x = fmaf(vyz.x, dz, acc_bxy.x);              // Vy dz
+                                acc_bxy.y = fmaf(vyz.y, ddx[i], acc_bxy.y);          // Vz dx
                                 acc_bxy.x = fmaf(-vyz.y, ddy[j], acc_bxy.x);         // - Vz dy
                                 acc_bxy.y = fmaf(-vx, dz, acc_bxy.y);                // - Vx dz
                                 acc_bz = fmaf(vx, ddy[j], acc_bz);
@@ -630,8 +652,8 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         if (!EXACT) mask |= (uint64_t)m16 << (k * 16);
                     }
                     pe[0] += acc_ex;
-                    pe[1] += acc_eyz.x;
-                    pe[2] += acc_eyz.y;
+                    pe[1] += acc_ey - acc_jyz.x;
+                    pe[2] += acc_ez - acc_jyz.y;
                     pb[0] += acc_bxy.x;
                     pb[1] += acc_bxy.y;
                     pb[2] += acc_bz;

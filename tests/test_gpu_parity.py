@@ -472,11 +472,12 @@ def test_wide_band_staged_kernel(gpu, src_side, dt, band):
     jefi.jefi_destroy(h)
 
 
-@pytest.mark.parametrize("shape", list(range(1, 9)))
+@pytest.mark.parametrize("shape", list(range(1, 10)))
 def test_tile_shapes(gpu, shape):
-    """Every observation tile shape (JEFI_TILE_8x8x4 ... JEFI_TILE_4x4x16) on
-    a ragged grid: slots bit-exact with the oracle and fields within
-    tolerance; the automatic choice reports one of the shapes."""
+    """Every observation tiling (the box shapes JEFI_TILE_8x8x4 ...
+    JEFI_TILE_4x4x16 and JEFI_TILE_PACKED) on a ragged grid: slots bit-exact
+    with the oracle and fields within tolerance; the automatic choice reports
+    one of them."""
     src = Grid((14, 11, 9), (-0.7, -0.55, -0.45), (0.1, 0.1, 0.1))
     obs = Grid((19, 13, 11), (0.9, -0.8, -0.6), (0.11, 0.12, 0.1))
     blob = Blob(1.0, (0.25, 0.2, 0.2), (0.0, 0.0, 0.0), (0.2, 0.1, 0.0))
@@ -499,5 +500,5 @@ def test_tile_shapes(gpu, shape):
     jefi.jefi_destroy(h)
     auto = jefi.jefi_create(jefi.grid_from(src), obs_grid=jefi.grid_from(obs),
                             params=jefi.default_params(dt=dt, history_slots=H, precision="fp32c"))
-    assert jefi.jefi_get_info(auto)["tile_shape"] in range(1, 9)
+    assert jefi.jefi_get_info(auto)["tile_shape"] in range(1, 10)
     jefi.jefi_destroy(auto)
