@@ -535,18 +535,19 @@ def serving_leg(n_problems=16, n_requests=600, seed=11, tick_s=0.02, n_samples=6
     """Continuous batching of Poisson-arriving requests against resident
     problems (source sides 16-48, histories 64-128 slices, observation sides
     8-48, one slice pushed to every problem per tick): saturated throughput
-    first (all requests at once), then p50/p99 latency at 0.8x that rate.
+    first (all requests at once, pushes running), then p50/p99 latency at
+    0.8x that rate.
     Returns the figures and a seeded sample of served requests (kept for the
     oracle check)."""
     from paper_2104_05426_gb300.serving import ServingEngine, make_problems, poisson_requests, served_sample
 
     probs = make_problems(n_problems, seed, sides=(16, 48), H_range=(64, 128))
     sides = [8, 16, 24, 32, 40, 48]
-    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=4, max_batch=32, tick_s=None)
+    # saturated under the same pushes as the measured load
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=4, max_batch=32, tick_s=tick_s)
     sat = eng.run(poisson_requests(n_requests, rate=1e9, n_problems=n_problems, seed=seed + 1,
                                    side_choices=sides))
     rate = 0.8 * sat.requests_per_s
-    eng.tick_s = tick_s
     reqs = poisson_requests(n_requests, rate=rate, n_problems=n_problems, seed=seed + 2, side_choices=sides)
     eng.keep_ids = {int(k) for k in np.random.Generator(np.random.PCG64(seed + 3)).choice(
         n_requests, n_samples, replace=False)}
@@ -818,6 +819,10 @@ def main(argv=None):
                          "level at 0.5/0.8/1.0x saturation, 64 GB budget) with an oracle check of a "
                          "sample of served requests, and print it")
     ap.add_argument("--serving-requests", type=int, default=10000)
+    ap.add_argument("--leg", default=None, choices=["dipole", "batch"],
+                    help="only run one leg (the dipole workload, or the 256-problem batch) and print it "
+                         "(for profiler captures of its kernels)")
+    ap.add_argument("--batch-problems", type=int, default=256, help="problems of the --leg batch run")
     ap.add_argument("--paper-tables", action="store_true",
                     help="only time the paper's own workloads (Tables 2 and 4) and print them")
     ap.add_argument("--precision", default="fp32c", choices=["fp32c", "fp32", "fp64"],
@@ -829,7 +834,17 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.paper_tables:
+    if args.leg == "dipole":
+        import torch
+
+        print(json.dumps(dipole_leg(torch.device("cuda", 0)), default=float))
+    elif args.leg == "batch":
+        from paper_2104_05426_gb300.serving import measure_batch
+
+        r = measure_batch(n_problems=args.batch_problems, reps=1)
+        print(json.dumps({k: r[k] for k in ("problems", "pairs", "ms_per_batch", "pairs_per_s", "by_kernel")},
+                         default=float))
+    elif args.paper_tables:
         print(json.dumps(paper_tables()))
     elif args.serving_c5:
         from paper_2104_05426_gb300.serving import measure

@@ -61,6 +61,61 @@ static __device__ __forceinline__ int slot_fp64_stored(const double* xo, double 
     return theta_search(th, K, guess, S);
 }
 
+// a + b as s + e exactly (Knuth's two-sum; no operation may be contracted).
+static __device__ __forceinline__ void two_sum_f32(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Exact slot of an undecided pair without FP64 arithmetic, where it is
+// clearly inside one slot (a cheap pre-check before the FP64 rule: FP64
+// instructions run at 1/64 of the FP32 rate on this GPU).
+//
+// The squared distance is formed in double-float arithmetic from the point
+// and the cell centre split into FP32 pairs (hi = nearest float, lo = nearest
+// float to the remainder; both within 2^-48 of the FP64 value), every
+// difference by two-sum, every square as hi^2 (exact, by fma) + 2 hi lo.  On
+// creation the host bounds |S_df - S64| <= B = b1 R + b2 S (S64 the FP64
+// rule's squared distance; R a distance within 1e-5 of the pair's).  With
+// the thresholds as FP32 pairs too, slot i (theta[i+1] < S64 <= theta[i]) is
+// certain when S_df - theta[i] <= -B and S_df - theta[i+1] > B.  Only the
+// candidate g (the FP32 rule's k') and g - 1 are tried: the exact slot is one
+// of them.  Returns the table index, or -1 if the pair is within B of a
+// threshold (an exact tie of the FP64 rule, typically): the caller then
+// takes the FP64 rule.
+static __device__ __forceinline__ int slot_double_float(const float* xo_hl, float2 cx, float2 cy, float2 cz,
+                                                        const float2* th_hl, int K, int g, float R, float b1,
+                                                        float b2) {
+    if (g < 1 || g > K - 1) return -1;
+    const float2 c[3] = {cx, cy, cz};
+    float ph[3], pl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float s, e;
+        two_sum_f32(xo_hl[2 * a], -c[a].x, s, e);
+        float dh, dl;
+        two_sum_f32(s, __fadd_rn(e, __fsub_rn(xo_hl[2 * a + 1], c[a].y)), dh, dl);
+        ph[a] = __fmul_rn(dh, dh);
+        pl[a] = fmaf(__fmul_rn(2.f, dh), dl, fmaf(dh, dh, -ph[a]));
+    }
+    float s1, e1, s2, e2;
+    two_sum_f32(ph[0], ph[1], s1, e1);
+    two_sum_f32(s1, ph[2], s2, e2);
+    const float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fadd_rn(pl[0], pl[1]), pl[2]));
+    const float Sh = __fadd_rn(s2, lo);
+    const float Sl = __fsub_rn(lo, __fsub_rn(Sh, s2));
+    const float B = fmaf(b1, R, __fmul_rn(b2, Sh));
+    auto diff = [&](int i) {   // S_df - theta[i]
+        const float2 t = th_hl[i];
+        return __fadd_rn(__fsub_rn(Sh, t.x), __fsub_rn(Sl, t.y));
+    };
+    const float d0 = diff(g);
+    if (d0 <= -B && diff(g + 1) > B) return g;
+    if (d0 > B && diff(g - 1) <= -B) return g - 1;
+    return -1;
+}
+
 static __device__ __forceinline__ unsigned candidate_index(float S, float ri, float K32, float A, int K) {
     const float R = S * ri;
     const float u = fmaf(-R, K32, A);

@@ -433,6 +433,11 @@ struct jefi_problem {
     // device memory
     void* ring = nullptr;
     double* obs_xyz = nullptr;
+    float* obs_hl = nullptr;         // FP32: per slot the point as FP32 pairs (x hi, x lo, y hi, ...)
+    float2* cc_hl = nullptr;         // FP32: padded cell centres per axis as FP32 pairs (x, y, z)
+    float df_b1 = 0.f, df_b2 = 0.f;  // FP32: bound on |S_df - S64| (slot_double_float)
+    std::vector<float> h_obs_hl;
+    std::vector<float2> h_cc_hl;
     int32_t* obs_scr = nullptr;
     int32_t* d_inv_perm = nullptr;
     double* prev = nullptr;
@@ -637,8 +642,20 @@ void build_tables(jefi_problem* h, int ti, double t) {
     const int64_t n_lo = slot_of(h->pad.s_max, T, c, dt);
     const int64_t k0 = n_lo - kTablePad;
     const int K = h->K;
-    double* th = h->h_theta.data() + (size_t)ti * (K + 1);
+    double* th = h->h_theta.data() + (size_t)ti * theta_stride(K);
     for (int i = 0; i <= K; ++i) th[i] = threshold(k0 + i, T, c, dt);
+    // the same thresholds as FP32 pairs: hi = the nearest float, lo = the
+    // nearest float to the (exact) remainder
+    float2* thl = reinterpret_cast<float2*>(th + K + 1);
+    for (int i = 0; i <= K; ++i) {
+        const double v = th[i];
+        if (!std::isfinite(v)) {
+            thl[i] = make_float2((float)v, 0.f);
+        } else {
+            const float hi = (float)v;
+            thl[i] = make_float2(hi, std::isfinite(hi) ? (float)(v - (double)hi) : 0.f);
+        }
+    }
     float4* tab = h->h_tab.data() + (size_t)ti * K;
     auto err = [&](double S) { return h->err_rel * S + h->err_lin * std::sqrt(S) + h->err_abs; };
     for (int i = 0; i < K; ++i) {
@@ -796,6 +813,10 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     p.n_slots = h->n_slots;
     p.n_tiles = h->n_tiles;
     p.obs_xyz = h->obs_xyz;
+    p.obs_hl = h->obs_hl;
+    p.cc_hl = h->cc_hl;
+    p.df_b1 = h->df_b1;
+    p.df_b2 = h->df_b2;
     p.obs_scr = h->obs_scr;
     p.ring = h->ring;
     p.Hp = h->Hp;
@@ -812,7 +833,7 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
         p.nfull[a] = h->src.n[a] / kBrick;
     }
     p.tab32 = h->tab32 + (size_t)slot0 * K;
-    p.theta = h->theta + (size_t)slot0 * (K + 1);
+    p.theta = h->theta + (size_t)slot0 * theta_stride(K);
     p.times = h->times + slot0;
     p.n_t = n_t;
     p.K = K;
@@ -835,7 +856,7 @@ int upload_tables(jefi_problem* h, int n_t, cudaStream_t s) {
     const int K = h->K;
     JEFI_CUDA(cudaMemcpyAsync(h->tab32, h->h_tab.data(), sizeof(float4) * K * n_t,
                               cudaMemcpyHostToDevice, s));
-    JEFI_CUDA(cudaMemcpyAsync(h->theta, h->h_theta.data(), sizeof(double) * (K + 1) * n_t,
+    JEFI_CUDA(cudaMemcpyAsync(h->theta, h->h_theta.data(), sizeof(double) * theta_stride(K) * n_t,
                               cudaMemcpyHostToDevice, s));
     JEFI_CUDA(cudaMemcpyAsync(h->times, h->h_times.data(), sizeof(TimeParams) * n_t,
                               cudaMemcpyHostToDevice, s));
@@ -1392,6 +1413,33 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
 
     h->obs_sig = fnv1a(kFnvBasis, slot_xyz.data(), sizeof(double) * slot_xyz.size());
 
+    // Double-float copies of the geometry for the FP32 kernels' check of
+    // undecided pairs, and its bound.  Every coordinate splits as hi + lo
+    // within 2^-48 of its FP64 value; with X the largest coordinate, each
+    // double-float difference is within 8 X 2^-48 of the exact one, which
+    // moves the squared distance by at most 2 sqrt(3) R 8 X 2^-48; the
+    // squares, sums and the comparison add at most 2^-42.3 S, the FP64
+    // rule's own roundings 5 S 2^-53 and the thresholds' split 2^-48 S.
+    // Four times that: B = 2^-41 X R + 2^-40 S.
+    if (!h->fp64) {
+        auto split = [](double v) {
+            const float hi = (float)v;
+            return make_float2(hi, (float)(v - (double)hi));
+        };
+        h->h_obs_hl.resize((size_t)6 * h->n_slots);
+        for (size_t q = 0; q < (size_t)h->n_slots * 3; ++q) {
+            const float2 v = split(slot_xyz[q]);
+            h->h_obs_hl[2 * q] = v.x;
+            h->h_obs_hl[2 * q + 1] = v.y;
+        }
+        h->h_cc_hl.clear();
+        for (int a = 0; a < 3; ++a)
+            for (int64_t i = 0; i < npad_axis[a]; ++i)
+                h->h_cc_hl.push_back(split(center(src->lo[a], src->d[a], h->org[a] + i)));
+        h->df_b1 = (float)(std::ldexp(1.0, -41) * Xmax);
+        h->df_b2 = (float)std::ldexp(1.0, -40);
+    }
+
     // ---------------------------------------------------------------- screening and extremes
     const int64_t nlim[3] = {src->n[0], src->n[1], src->n[2]};
     const int64_t npad[3] = {h->npx, h->npy, h->npz};
@@ -1456,15 +1504,17 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     }
     {
         // Source splits: enough (tile, split) items for eight waves of two
-        // CTAs per SM at one evaluation time (four for views, whose partials
-        // count against a serving budget), so that a launch can merge them
-        // into items that fill its last wave (split_merge_for); at most one
-        // split per brick, and partials of at most 256 MB.
+        // CTAs per SM at one evaluation time (four for views), so that a
+        // launch can merge them into items that fill its last wave
+        // (split_merge_for); at most one split per brick, and partials of at
+        // most 256 MB (32 MB for views, many of which are cached under a
+        // serving budget).
         const int64_t target = (base ? 4 : 8) * 2 * (int64_t)current_sm_count();
         int64_t ns = std::max<int64_t>(1, (target + h->n_tiles - 1) / std::max<int32_t>(h->n_tiles, 1));
         ns = std::min<int64_t>(ns, std::max<int32_t>(h->n_bricks, 1));
         const int64_t split_bytes = (int64_t)h->time_chunk * 6 * 8 * std::max<int32_t>(h->n_slots, 1);
-        ns = std::max<int64_t>(1, std::min<int64_t>(ns, ((int64_t)256 << 20) / split_bytes));
+        const int64_t cap = base ? ((int64_t)32 << 20) : ((int64_t)256 << 20);
+        ns = std::max<int64_t>(1, std::min<int64_t>(ns, cap / split_bytes));
         h->bricks_per_split = (int32_t)((h->n_bricks + ns - 1) / ns);
         if (h->bricks_per_split < 1) h->bricks_per_split = 1;
         h->n_split = (int32_t)((h->n_bricks + h->bricks_per_split - 1) / h->bricks_per_split);
@@ -1597,10 +1647,15 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
     h->partials = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * h->n_split * 6 * std::max<int32_t>(1, h->n_slots));
     h->out_stage = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * 6 * std::max<int64_t>(1, n_obs));
     h->tab32 = (float4*)dev_alloc(h, sizeof(float4) * h->time_chunk * h->K);
-    h->theta = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * (h->K + 1));
+    h->theta = (double*)dev_alloc(h, sizeof(double) * h->time_chunk * theta_stride(h->K));
     h->times = (TimeParams*)dev_alloc(h, sizeof(TimeParams) * h->time_chunk);
     h->fallbacks = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long));
     h->status = (int32_t*)dev_alloc(h, sizeof(int32_t));
+    if (!h->fp64) {
+        h->obs_hl = (float*)dev_alloc(h, sizeof(float) * h->h_obs_hl.size());
+        h->cc_hl = (float2*)dev_alloc(h, sizeof(float2) * h->h_cc_hl.size());
+        if (!h->obs_hl || !h->cc_hl) h->status = nullptr;
+    }
     if (!h->fp64 && h->any_pairs && h->band == 0 && !alloc_direct_tables(h)) h->status = nullptr;
     if (h->band > 0) {
         h->tile_box = (float*)dev_alloc(h, sizeof(float) * tile_box.size());
@@ -1616,7 +1671,7 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         return JEFI_ENOMEM;
     }
     h->h_tab.resize((size_t)h->time_chunk * h->K);
-    h->h_theta.resize((size_t)h->time_chunk * (h->K + 1));
+    h->h_theta.resize((size_t)h->time_chunk * theta_stride(h->K));
     h->h_times.resize(h->time_chunk);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess && !base) e = cudaMemsetAsync(h->ring, 0, ring_bytes, s);
@@ -1637,6 +1692,10 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         e = cudaMemcpyAsync(h->obs_xyz, slot_xyz.data(), sizeof(double) * slot_xyz.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !scr.empty())
         e = cudaMemcpyAsync(h->obs_scr, scr.data(), sizeof(int32_t) * scr.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h->obs_hl && !h->h_obs_hl.empty())
+        e = cudaMemcpyAsync(h->obs_hl, h->h_obs_hl.data(), sizeof(float) * h->h_obs_hl.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h->cc_hl && !h->h_cc_hl.empty())
+        e = cudaMemcpyAsync(h->cc_hl, h->h_cc_hl.data(), sizeof(float2) * h->h_cc_hl.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && !h->inv_perm.empty())
         e = cudaMemcpyAsync(h->d_inv_perm, h->inv_perm.data(), sizeof(int32_t) * h->inv_perm.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -2348,7 +2407,7 @@ int plan_build(jefi_batch_plan_s* p) {
             tb.tab32 = bytes;
             bytes = align256(bytes + sizeof(float4) * h->K);
             tb.theta = bytes;
-            bytes = align256(bytes + sizeof(double) * (h->K + 1));
+            bytes = align256(bytes + sizeof(double) * theta_stride(h->K));
             tb.times = bytes;
             bytes = align256(bytes + sizeof(TimeParams));
             if (h->band > 0) {
@@ -2494,7 +2553,7 @@ int plan_prepare(jefi_batch_plan_s* p, int j, const double* t) {
         const size_t K = (size_t)h->K, KT = K + 2 * kTabGuard;
         build_tables(h, o, t[i]);
         std::memcpy(host + tb.tab32, h->h_tab.data() + o * K, sizeof(float4) * K);
-        std::memcpy(host + tb.theta, h->h_theta.data() + o * (K + 1), sizeof(double) * (K + 1));
+        std::memcpy(host + tb.theta, h->h_theta.data() + o * theta_stride((int)K), sizeof(double) * theta_stride((int)K));
         std::memcpy(host + tb.times, &h->h_times[o], sizeof(TimeParams));
         if (tb.tab2) std::memcpy(host + tb.tab2, h->h_tab2.data() + o * KT, sizeof(float2) * KT);
         if (tb.tabg) {

@@ -24,7 +24,10 @@
 //             the screening box of each observation point (FP64 decision).
 //   tab32     [n_t][K] float4 {hi, lo, phys_slot (int bits), 0} per candidate
 //             slot k = k0 + i: S32 in (lo, hi] proves slot k exactly.
-//   theta     [n_t][K+1] FP64 exact thresholds: slot(S) >= k0+i iff S <= theta[i].
+//   theta     [n_t][theta_stride(K)]: K+1 FP64 exact thresholds (slot(S) >=
+//             k0+i iff S <= theta[i]), then the same thresholds as FP32 pairs
+//             (hi, lo), hi + lo = theta[i] to 2^-48 relative, bit-copied into
+//             the next K+1 doubles (the double-float check of undecided pairs).
 //   partials  [n_t][n_split][6][n_slots] FP64 per-split sums.
 #pragma once
 
@@ -43,6 +46,9 @@ constexpr int kZeroPadSlots = 4;    // the zero line after the P + M ring slots
 #else
 #define JEFI_HD
 #endif
+
+// Doubles per evaluation time in a threshold table (see SumParams::theta).
+JEFI_HD constexpr size_t theta_stride(int K) { return 2 * (size_t)(K + 1); }
 
 // Staged FP32 kernel: compiled band heights (slots per staged cell), the
 // cells per stage of each, and whether its rows are copied with the 32-byte
@@ -124,6 +130,13 @@ struct SumParams {
     // second-order retarded time: sources interpolated between slots n and n+1
     int32_t interp;
     float K32_lo;                   // fp32(1/(c dt) - K32)
+    // Double-float check of undecided pairs (FP32 kernels): per slot the
+    // point's coordinates as FP32 pairs (x hi, x lo, y hi, y lo, z hi, z lo),
+    // per padded cell of each axis its centre as an FP32 pair (x cells, then
+    // y, then z), and the bound B = df_b1 R + df_b2 S on |S_df - S64|.
+    const float* obs_hl;
+    const float2* cc_hl;
+    float df_b1, df_b2;
     double K64;                     // 1 / (c dt)
 };
 

@@ -35,12 +35,14 @@ struct Fix6 {
 };
 
 // Pairs of a far brick whose slot the FP32 rule left undecided: exact slot
-// in FP64, then the pair as usual.  A call of its own (rare), so that its
-// registers do not weigh on the brick loop.
+// by the double-float check (slot_double_float), else in FP64, then the pair
+// as usual.  A call of its own (rare), so that its registers do not weigh on
+// the brick loop.  th_hl: this time's thresholds as FP32 pairs.
 template <bool DEBUG, bool INTERP>
 __device__ __noinline__ Fix6 direct_fixup(const SumParams& p, uint64_t mask, int slot, int b, int bx, int by, int bz,
                                           float Px, float Py, float Pz, const float4* cbase, const float4* s_tab,
-                                          const double* s_th, int64_t k0, float A, float A_lo) {
+                                          const double* s_th, int64_t k0, float A, float A_lo,
+                                          const float2* th_hl) {
     float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
     const int K = p.K, Hp = p.Hp;
     const float K32 = p.K32, K32_lo = p.K32_lo;
@@ -55,9 +57,12 @@ __device__ __noinline__ Fix6 direct_fixup(const SumParams& p, uint64_t mask, int
         const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
         const float ri = rsqrt_ftz(S);
         const unsigned cand = candidate_index(S, ri, K32, A, K);
-        const int idx = slot_fallback_f32(p.obs_xyz, slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
-                                          p.org[0] + kBrick * bx + i, p.org[1] + kBrick * by + j,
-                                          p.org[2] + kBrick * bz + k, s_th, K, (int)cand, nullptr);
+        const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
+        int idx = slot_double_float(p.obs_hl + (size_t)6 * slot, p.cc_hl[ix], p.cc_hl[p.npx + iy],
+                                    p.cc_hl[p.npx + p.npy + iz], th_hl, K, (int)cand, S * ri, p.df_b1, p.df_b2);
+        if (idx < 0)
+            idx = slot_fallback_f32(p.obs_xyz, slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1], p.d[2],
+                                    p.org[0] + ix, p.org[1] + iy, p.org[2] + iz, s_th, K, (int)cand, nullptr);
         if (DEBUG) p.debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
         const float4* q = cbase + (cl * Hp + __float_as_int(s_tab[idx].z)) * 2;
         float4 v0 = __ldg(q), v1 = __ldg(q + 1);
@@ -86,7 +91,7 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
     const int tid = threadIdx.x;
 
     const float4* g_tab = p.tab32 + (size_t)ti * K;
-    const double* g_th = p.theta + (size_t)ti * (K + 1);
+    const double* g_th = p.theta + (size_t)ti * theta_stride(K);
     const float2* g_tabg = p.tabg + (size_t)ti * KT;
     const float* g_tabh = p.tabh + (size_t)ti * KT;
     for (int i = tid; i < KT; i += kTileThreads) {
@@ -293,8 +298,9 @@ __device__ __forceinline__ void direct_f32_item(const SumParams& p, const int ti
             pb[2] += acc_bz;
             if (__any_sync(kFull, mask != 0ull)) {
                 n_fb += (uint32_t)__popcll(mask);
-                const Fix6 f = direct_fixup<DEBUG, INTERP>(p, mask, ctx.slot, b, bx, by, bz, Px, Py, Pz, cbase,
-                                                           s_tab, s_th, tp.k0, A, A_lo);
+                const Fix6 f = direct_fixup<DEBUG, INTERP>(
+                    p, mask, ctx.slot, b, bx, by, bz, Px, Py, Pz, cbase, s_tab, s_th, tp.k0, A, A_lo,
+                    reinterpret_cast<const float2*>(p.theta + (size_t)ti * theta_stride(K) + (K + 1)));
                 pe[0] += f.v[0];
                 pe[1] += f.v[1];
                 pe[2] += f.v[2];
@@ -428,7 +434,7 @@ __device__ __forceinline__ void f64_item(const SumParams& p, const int tile, con
 
     const int tid = threadIdx.x;
     const float4* g_tab = p.tab32 + (size_t)ti * K;
-    const double* g_th = p.theta + (size_t)ti * (K + 1);
+    const double* g_th = p.theta + (size_t)ti * theta_stride(K);
     for (int i = tid; i < K; i += kTileThreads) s_tab[i] = g_tab[i];
     for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
     for (int i = tid; i < p.npx; i += kTileThreads) s_xs[i] = cell_center(p.lo[0], p.d[0], p.org[0] + i);

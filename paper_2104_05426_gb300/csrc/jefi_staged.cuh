@@ -157,7 +157,7 @@ __host__ __device__ __forceinline__ uint32_t staged_geometry_offset(uint32_t tab
 }
 
 // Exact slot of one undecided pair from the FP64 geometry in shared memory
-// (written by the item's preamble); counts the pair.  A call of its own, so
+// (written by the item's preamble).  A call of its own, so
 // the FP64 search does not weigh on the registers of the stage loop.
 template <int BAND>
 __device__ __noinline__ int staged_slot_fp64(int ix, int iy, int iz, const double* s_th, int K, int guess) {
@@ -166,7 +166,6 @@ __device__ __noinline__ int staged_slot_fp64(int ix, int iy, int iz, const doubl
     const uint32_t* g = reinterpret_cast<const uint32_t*>(sb + L::kGeo);
     const double* s_xo = reinterpret_cast<const double*>(sb + g[0]) + 3 * threadIdx.x;
     const double* s_cc = reinterpret_cast<const double*>(sb + g[0]) + 3 * kTileThreads;
-    atomicAdd(const_cast<uint32_t*>(g + 3), 1u);
     return slot_fp64_stored(s_xo, s_cc[ix], s_cc[g[1] + iy], s_cc[g[1] + g[2] + iz], s_th, K, guess);
 }
 
@@ -209,10 +208,6 @@ __device__ __noinline__ void staged_fill_geometry(const double* txyz, int K, int
     }
 }
 
-struct FixSums {
-    float v[6];   // E', B contributions
-};
-
 // Both 16-byte halves of the row at dense offset `off` of a stage buffer.
 template <int BAND>
 __device__ __forceinline__ void load_row(const unsigned char* bufp, uint32_t off, float4& v0, float4& v1) {
@@ -226,64 +221,40 @@ __device__ __forceinline__ void load_row(const unsigned char* bufp, uint32_t off
     }
 }
 
-// Pairs of a full stage whose slot the FP32 rule left undecided (non-lattice
-// geometry): exact slot in FP64, then the pair from the stage's buffer.  A
-// call of its own (rare), so its registers do not weigh on the stage loop.
-// `mask` holds brick cell indices; the stage's cells start at cell0.  The
-// batched kernel's form: the point from global memory and a global count
-// (the batched item has no registers to spare for more).
-template <int BAND, bool DEBUG, bool INTERP>
-__device__ __noinline__ FixSums staged_fixup(uint64_t mask, const unsigned char* bufp, int cell0, int band_rel,
-                                             float Px, float Py, float Pz, float d32x, float d32y, float d32z,
-                                             float K32, float Ag, float A, float A_lo, float K32_lo,
-                                             const double* obs_xyz, int slot, double lox, double loy, double loz,
-                                             double dx_, double dy_, double dz_, const int32_t* org, int bx, int by,
-                                             int bz,
-                                             const double* s_th, int K, int32_t* status, int32_t* debug_slots, size_t n_cells, int b,
-                                             int64_t k0) {
-    using L = Layout<BAND>;
-    float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
-    while (mask) {
-        const int cl = __ffsll((long long)mask) - 1;
-        mask &= mask - 1;
-        const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
-        const float dx = fmaf(-(float)i, d32x, Px);
-        const float dy = fmaf(-(float)j, d32y, Py);
-        const float dz = fmaf(-(float)k, d32z, Pz);
-        const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
-        const float ri = rsqrt_ftz(S);
-        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-        const int idx = slot_fallback_f32(obs_xyz, slot, lox, loy, loz, dx_, dy_, dz_, org[0] + kBrick * bx + i,
-                                          org[1] + kBrick * by + j, org[2] + kBrick * bz + k, s_th, K,
-                                          (int)(bits - kMagicBits), nullptr);
-        int row = idx - band_rel;
-        if (row < 0 || row >= BAND) {
-            atomicExch(status, kStatusInternal);
-            row = row < 0 ? 0 : BAND - 1;
-        }
-        if (DEBUG) debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
-        const uint32_t off = (uint32_t)(cl - cell0) * L::kCellBytes + (uint32_t)row * L::kRowBytes;
-        float4 v0, v1;
-        load_row<BAND>(bufp, off, v0, v1);
-        if (INTERP) {
-            float4 u0, u1;
-            load_row<BAND>(bufp, off + L::kRowBytes, u0, u1);
-            lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
-        }
-        pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
-    }
-    return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
-}
+struct FixSums {
+    float v[6];   // E', B contributions
+};
 
-// The same, with the FP64 geometry and the count in shared memory (the
-// single-problem kernel).
-template <int BAND, bool DEBUG, bool INTERP>
-__device__ __noinline__ FixSums staged_fixup_geo(uint64_t mask, const unsigned char* bufp, int cell0, int band_rel,
-                                                 float Px, float Py, float Pz, float d32x, float d32y, float d32z,
-                                                 float K32, float Ag, float A, float A_lo, float K32_lo, int slot,
-                                                 int bx, int by, int bz, const double* s_th, int K, int32_t* status,
-                                                 int32_t* debug_slots, size_t n_cells, int b, int64_t k0) {
+// Pairs of a full stage whose slot the FP32 rule left undecided (non-lattice
+// geometry): the exact slot by the double-float check (slot_double_float),
+// else by the FP64 rule, then the pair from the stage's buffer.  A call of
+// its own (rare), so its registers do not weigh on the stage loop, with few
+// arguments: everything the item does not vary comes from the parameters'
+// copy in shared memory (`sp`), so that the stage loop keeps no extra values
+// alive for the call.  `mask` holds brick cell indices; the stage's cells
+// start at cell0; buf_off is the stage buffer's offset in the staged region.
+// GEO: the FP64 geometry of the pair in shared memory and the count there
+// (the single-problem kernel); otherwise the point from global memory, the
+// centre computed, and the count the caller's.
+template <int BAND, bool DEBUG, bool INTERP, bool GEO>
+__device__ __noinline__ FixSums staged_fixup(uint64_t mask, uint32_t buf_off, int cell0, int band_rel, float Px,
+                                             float Py, float Pz, int bx, int by, int bz, int b, int slot, int ti,
+                                             const SumParams* sp) {
     using L = Layout<BAND>;
+    unsigned char* const sb = staged_base<BAND>();
+    const unsigned char* bufp = sb + buf_off;
+    const int K = sp->K;
+    const double* s_th = reinterpret_cast<const double*>(sb + L::kTab + (size_t)(K + 2 * kTabGuard) * sizeof(float2));
+    const TimeParams tp = sp->times[ti];
+    const float K32 = sp->K32, K32_lo = sp->K32_lo;
+    const float d32x = sp->d32[0], d32y = sp->d32[1], d32z = sp->d32[2];
+    const float* xo_hl = sp->obs_hl + (size_t)6 * slot;
+    const float2* cc_hl = sp->cc_hl;
+    const float2* th_hl = reinterpret_cast<const float2*>(sp->theta + (size_t)ti * theta_stride(K) + (K + 1));
+    const int npx = sp->npx, npy = sp->npy;
+    const size_t n_cells = (size_t)sp->n_bricks * kBrickCells;
+    // every undecided pair counts, whichever check decides it
+    if (GEO) atomicAdd(reinterpret_cast<uint32_t*>(sb + L::kGeo) + 3, (uint32_t)__popcll(mask));
     float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
     while (mask) {
         const int cl = __ffsll((long long)mask) - 1;
@@ -294,22 +265,33 @@ __device__ __noinline__ FixSums staged_fixup_geo(uint64_t mask, const unsigned c
         const float dz = fmaf(-(float)k, d32z, Pz);
         const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
         const float ri = rsqrt_ftz(S);
-        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
-        const int idx = staged_slot_fp64<BAND>(kBrick * bx + i, kBrick * by + j, kBrick * bz + k, s_th, K,
-                                               (int)(bits - kMagicBits));
+        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, tp.Ag), kMagic));
+        const int guess = (int)(bits - kMagicBits);
+        const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
+        int idx = slot_double_float(xo_hl, cc_hl[ix], cc_hl[npx + iy], cc_hl[npx + npy + iz], th_hl, K, guess,
+                                    S * ri, sp->df_b1, sp->df_b2);
+        if (idx < 0) {
+            if constexpr (GEO) {
+                idx = staged_slot_fp64<BAND>(ix, iy, iz, s_th, K, guess);
+            } else {
+                idx = slot_fallback_f32(sp->obs_xyz, slot, sp->lo[0], sp->lo[1], sp->lo[2], sp->d[0], sp->d[1],
+                                        sp->d[2], sp->org[0] + ix, sp->org[1] + iy, sp->org[2] + iz, s_th, K, guess,
+                                        nullptr);
+            }
+        }
         int row = idx - band_rel;
         if (row < 0 || row >= BAND) {
-            atomicExch(status, kStatusInternal);
+            atomicExch(sp->status, kStatusInternal);
             row = row < 0 ? 0 : BAND - 1;
         }
-        if (DEBUG) debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(k0 + idx);
+        if (DEBUG) sp->debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(tp.k0 + idx);
         const uint32_t off = (uint32_t)(cl - cell0) * L::kCellBytes + (uint32_t)row * L::kRowBytes;
         float4 v0, v1;
         load_row<BAND>(bufp, off, v0, v1);
         if (INTERP) {
             float4 u0, u1;
             load_row<BAND>(bufp, off + L::kRowBytes, u0, u1);
-            lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, A, A_lo, K32, K32_lo));
+            lerp8(v0, v1, u0, u1, interp_weight(S, ri, (float)idx, tp.A, tp.A_lo, K32, K32_lo));
         }
         pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
     }
@@ -323,8 +305,9 @@ __device__ __noinline__ FixSums staged_fixup_geo(uint64_t mask, const unsigned c
 // FP64 geometry from shared memory and are counted there (the single-problem
 // kernel); otherwise from global memory (the batched kernel).
 template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool GEO>
-__device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const int comp,
-                                            const int tile, const int group, const int ti, uint32_t& g_it) {
+__device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const SumParams* sp,
+                                            const int comp, const int tile, const int group, const int ti,
+                                            uint32_t& g_it) {
     using L = Layout<BAND>;
     unsigned char* const sb = staged_base<BAND>();
     const int K = p.K;
@@ -341,7 +324,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
 
     const float2* g_tab = p.tab2 + (size_t)ti * KT;
     for (int i = tid; i < KT; i += kTileThreads) s_tab[i] = g_tab[i];
-    const double* g_th = p.theta + (size_t)ti * (K + 1);
+    const double* g_th = p.theta + (size_t)ti * theta_stride(K);
     for (int i = tid; i <= K; i += kTileThreads) s_th[i] = g_th[i];
     const double* txyz = p.obs_xyz + (size_t)tile * kTileThreads * 3;
     if constexpr (!EXACT && GEO)
@@ -659,20 +642,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     pb[2] += acc_bz;
                     if (!EXACT) {
                         if (__any_sync(kFull, mask != 0ull)) {
-                            FixSums f;
-                            if constexpr (GEO) {
-                                f = staged_fixup_geo<BAND, DEBUG, INTERP>(
-                                    mask, bufp, cell0, band_rel, Px, Py, Pz, d32x, d32y, d32z, K32, Ag, A, A_lo,
-                                    K32_lo, ctx.slot, bx, by, bz, s_th, K, p.status, p.debug_slots, n_cells, b,
-                                    tp.k0);
-                            } else {
-                                n_fb += (uint32_t)__popcll(mask);
-                                f = staged_fixup<BAND, DEBUG, INTERP>(
-                                    mask, bufp, cell0, band_rel, Px, Py, Pz, d32x, d32y, d32z, K32, Ag, A, A_lo,
-                                    K32_lo, p.obs_xyz, ctx.slot, p.lo[0], p.lo[1], p.lo[2], p.d[0], p.d[1],
-                                    p.d[2], p.org, bx, by, bz, s_th, K, p.status, p.debug_slots,
-                                    n_cells, b, tp.k0);
-                            }
+                            if constexpr (!GEO) n_fb += (uint32_t)__popcll(mask);
+                            const FixSums f = staged_fixup<BAND, DEBUG, INTERP, GEO>(
+                                mask, (uint32_t)buf * L::kBufBytes, cell0, band_rel, Px, Py, Pz, bx, by, bz, b,
+                                ctx.slot, ti, sp);
 #pragma unroll
                             for (int a = 0; a < 3; ++a) {
                                 pe[a] += f.v[a];
@@ -708,6 +681,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                                         s_th, K, idx, nullptr);
                                 if constexpr (!EXACT) ++n_fb;
                             } else {
+                                atomicAdd(reinterpret_cast<uint32_t*>(sb + L::kGeo) + 3, 1u);
                                 idx = staged_slot_fp64<BAND>(ix, iy, iz, s_th, K, idx);
                             }
                         }
@@ -808,9 +782,14 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
 template <int BAND, bool EXACT, bool DEBUG, bool INTERP>
 __global__ void __launch_bounds__(kTileThreads, 2)
     sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p) {
+    // the parameters the fix-up of undecided pairs reads (the stage loop
+    // reads its own from the constant bank)
+    __shared__ SumParams s_par;
+    if (!EXACT && threadIdx.x == 0) s_par = p;
     staged_init_barriers<BAND>();
     uint32_t g_it = 0;
-    staged_item<BAND, EXACT, DEBUG, INTERP, true>(&tmap, p, p.comp, blockIdx.x, blockIdx.y, blockIdx.z, g_it);
+    staged_item<BAND, EXACT, DEBUG, INTERP, true>(&tmap, p, &s_par, p.comp, blockIdx.x, blockIdx.y, blockIdx.z,
+                                                  g_it);
 }
 
 // One item of the batched kernel as a call of its own: the item body gets
@@ -821,7 +800,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 template <int BAND, bool EXACT, bool INTERP>
 __device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int group,
                                                int ti, uint32_t& g_it) {
-    return staged_item<BAND, EXACT, false, INTERP, !EXACT>(map, p, p.comp, tile, group, ti, g_it);
+    return staged_item<BAND, EXACT, false, INTERP, !EXACT>(map, p, &p, p.comp, tile, group, ti, g_it);
 }
 
 // Persistent batched kernel: CTAs take (problem, time, split group, tile) items

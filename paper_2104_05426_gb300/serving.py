@@ -229,6 +229,8 @@ class ServingEngine:
                 req = queue[0]
                 key = (req.problem, req.obs_side)
                 entry = self._free_view(key)
+                if entry is not None:
+                    entry[1] = True              # reserved: the eviction below must not take it
                 out_bytes = self._output_bytes(req.obs_side)
                 need = out_bytes
                 if entry is None:
@@ -236,6 +238,8 @@ class ServingEngine:
                 if self.used_bytes + need > self.memory_budget:
                     self._evict_idle(self.used_bytes + need - self.memory_budget)
                 if self.used_bytes + need > self.memory_budget:
+                    if entry is not None:
+                        entry[1] = False         # not admitted: the view is idle again
                     if not inflight and not admitted:
                         queue.popleft()          # can never fit: reject
                         req.error = -1
@@ -259,8 +263,6 @@ class ServingEngine:
                             break
                     self.views.setdefault(key, []).append(entry)
                     self.used_bytes += entry[2]
-                else:
-                    entry[1] = True
                 queue.popleft()
                 req.view = entry
                 req.E = torch.empty((req.obs_side ** 3, 3), dtype=torch.float64, device="cuda")
@@ -423,7 +425,7 @@ def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0)
 
     First the saturated throughput (every request arrives at once), then, for
     each load factor f, a fresh stream of requests arriving at f times that
-    rate, with one slice pushed to every problem per tick.  Returns the
+    rate; one slice is pushed to every problem per tick throughout.  Returns the
     percentiles per load and the resident memory.  The device-memory budget
     (resident histories, cached views and outputs) defaults to 64 GB.
 
@@ -436,7 +438,10 @@ def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0)
     if memory_budget is None:
         memory_budget = 64e9
     probs = make_problems(n_problems, seed, sides=sides, H_range=H_range)
-    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=n_streams, max_batch=max_batch, tick_s=None,
+    # saturated throughput under the same slice pushes as the load levels
+    # (every request arrives at once; the pushes compete for the device and
+    # the host loop, so a rate measured without them overstates capacity)
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=n_streams, max_batch=max_batch, tick_s=tick_s,
                         memory_budget=memory_budget)
     sat = eng.run(poisson_requests(n_requests, rate=1e9, n_problems=n_problems, obs_sides=obs_sides,
                                    seed=seed + 1))
@@ -446,7 +451,6 @@ def measure(n_problems: int = 64, n_requests: int = 10000, loads=(0.5, 0.8, 1.0)
            "resident_ring_bytes": int(eng.resident_bytes),
            "saturated": {"requests_per_s": sat.requests_per_s, "pairs_per_s": sat.pairs_per_s,
                          "mean_batch": sat.mean_batch}, "loads": []}
-    eng.tick_s = tick_s
     samples = []
     for i, f in enumerate(loads):
         rate = f * sat.requests_per_s

@@ -190,6 +190,49 @@ def test_exact_ties_dyadic_geometry(gpu):
         jefi.jefi_destroy(h)
 
 
+@pytest.mark.parametrize("flags", [0, jefi.JEFI_FLAG_DIRECT_GATHER])
+def test_non_lattice_exact_ties_slots(gpu, flags):
+    """Decimal (non-dyadic) lattices with offsets that are exact multiples of
+    c dt in real arithmetic (axis offsets k 0.1, Pythagorean (0.3, 0.4, 0)
+    ...), evaluated at multiples of dt: many pairs sit on a slot boundary of
+    the FP64 rule, so the FP32 kernels leave them undecided, and their
+    double-float check must defer to the FP64 rule (it cannot separate S
+    from the threshold).  Slots identical to the oracle's; batched results
+    bit-identical to single evaluations."""
+    import torch
+
+    src = Grid((10, 10, 10), (0.0, 0.0, 0.0), (0.1, 0.1, 0.1))
+    obs = Grid((10, 10, 6), (0.0, 0.0, 1.2), (0.1, 0.1, 0.1))
+    dt, H = 0.05, 96
+    prob = Problem("decimal ties", src, obs, None, dt, H, H, [], MovingGaussians([]))
+    rng = np.random.Generator(np.random.PCG64(12))
+    hist = (rng.standard_normal((H, src.size)), rng.standard_normal((H, src.size, 3)), None, None)
+    h = create(prob, "fp32c", flags=flags | jefi.JEFI_FLAG_STATS)
+    push_all(h, hist)
+    info = jefi.jefi_get_info(h)
+    assert (info["staged_band"] > 0) == (flags == 0)
+    lo, hi = jefi.jefi_valid_window(h)
+    k_hi = math.floor(hi / dt)
+    times = [k * dt for k in (k_hi, k_hi - 3) if k * dt >= lo]
+    assert times
+    for t in times:
+        got = jefi.jefi_debug_slots(h, t)
+        ref = oracle.all_slots(src.n, src.lo, src.d, obs.points(), dt=dt, t=t)
+        sc = ref == oracle.SCREENED
+        assert np.array_equal(got[~sc].astype(np.int64), ref[~sc]), t
+    jefi.jefi_reset_stats(h)
+    E1 = torch.empty((obs.size, 3), dtype=torch.float64, device="cuda")
+    B1 = torch.empty_like(E1)
+    jefi.jefi_eval_fields(h, times[0], E1, B1)
+    assert jefi.jefi_get_info(h)["slot_fallbacks"] > 0      # the geometry does leave pairs undecided
+    E2, B2 = torch.empty_like(E1), torch.empty_like(E1)
+    jefi.jefi_eval_batch([h], [times[0]], [E2], [B2])
+    torch.cuda.synchronize()
+    assert torch.equal(E1, E2) and torch.equal(B1, B2)
+    assert jefi.jefi_get_info(h)["device_status"] == 0
+    jefi.jefi_destroy(h)
+
+
 def test_random_non_lattice_geometry_slots(gpu):
     """Non-dyadic spacings, offsets, c and dt with scattered points: the
     FP32 path's guarded slot selection still matches on ~3e7 pairs."""

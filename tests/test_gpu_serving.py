@@ -47,6 +47,33 @@ def test_serving_with_pushes_and_memory_budget(gpu):
     eng.close()
 
 
+def test_cached_view_is_not_evicted_under_its_own_request(gpu):
+    """A request whose cached view is idle, admitted when the budget needs an
+    eviction: the eviction must not take that view (the request would be
+    launched on a destroyed handle).  Three requests on one stream, one at a
+    time, under a budget that holds both views but only one output."""
+    from paper_2104_05426_gb300.serving import Request
+
+    probs = make_problems(1, seed=5, sides=(12, 12), H_range=(40, 40))
+    p = probs[0]
+    sizes = {}
+    for s in (8, 12):
+        v = jefi.jefi_create_view(p.handle, obs_grid=jefi.grid((s,) * 3, (-2.0,) * 3, (4.0 / s,) * 3))
+        sizes[s] = jefi.jefi_get_info(v)["device_bytes"]
+        jefi.jefi_destroy(v)
+    out = {s: s ** 3 * 6 * 8 for s in (8, 12)}
+    resident = jefi.jefi_get_info(p.handle)["device_bytes"]
+    budget = resident + sizes[8] + sizes[12] + out[12] + out[8] // 2
+    eng = ServingEngine(probs, obs_half_width=2.0, n_streams=1, max_batch=1, tick_s=None, memory_budget=budget)
+    eng.view_bytes.update({(0, 8): sizes[8], (0, 12): sizes[12]})
+    reqs = [Request(0, 0, 8, 0.5, 0.0), Request(1, 0, 12, 0.5, 0.0), Request(2, 0, 8, 0.5, 0.0)]
+    stats = eng.run(reqs)
+    assert stats.completed == 3 and stats.rejected == 0 and stats.failed == 0
+    assert stats.peak_bytes <= budget
+    assert eng.views_created == 2                    # the third request reused the first view
+    eng.close()
+
+
 def test_served_results_match_the_oracle(gpu):
     """A seeded sample of requests served under pushes, against the FP64 CPU
     oracle on the same history (slice n = the source model at n dt): the
