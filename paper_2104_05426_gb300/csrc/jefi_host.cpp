@@ -1376,6 +1376,39 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
             }
         }
     }
+    // Anchor of each tile (its slot 0, from which the FP32 kernels form their
+    // offsets): on non-lattice geometry the point nearest the centre of the
+    // tile's box, which halves the largest anchor offset and with it the
+    // FP32 squared-distance error bound (fewer undecided pairs).  Lattices
+    // keep their order: every offset is exact there, from any anchor.
+    if (!h->fp64 && h->n_src > 0 && n_obs > 0) {
+        const int64_t np3[3] = {h->npx, h->npy, h->npz};
+        if (!exact_lattice(pts, *src, h->org, np3)) {
+            for (size_t t0 = 0; t0 < order.size(); t0 += kTileThreads) {
+                double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                for (size_t q = t0; q < t0 + kTileThreads; ++q) {
+                    if (order[q] < 0) continue;
+                    for (int a = 0; a < 3; ++a) {
+                        lo[a] = std::min(lo[a], pts[3 * order[q] + a]);
+                        hi[a] = std::max(hi[a], pts[3 * order[q] + a]);
+                    }
+                }
+                size_t best = t0;
+                double best_d = INFINITY;
+                for (size_t q = t0; q < t0 + kTileThreads; ++q) {
+                    if (order[q] < 0) continue;
+                    double dm = 0;
+                    for (int a = 0; a < 3; ++a)
+                        dm = std::max(dm, std::fabs(pts[3 * order[q] + a] - 0.5 * (lo[a] + hi[a])));
+                    if (dm < best_d) {
+                        best_d = dm;
+                        best = q;
+                    }
+                }
+                std::swap(order[t0], order[best]);
+            }
+        }
+    }
     h->n_slots = (int32_t)order.size();
     h->n_tiles = h->n_slots / kTileThreads;
     h->slot_obs.resize(order.size());
