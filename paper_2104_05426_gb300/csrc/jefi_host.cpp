@@ -817,6 +817,7 @@ SumParams make_params(const jefi_problem* h, int n_t, int slot0, int32_t* debug_
     p.cc_hl = h->cc_hl;
     p.df_b1 = h->df_b1;
     p.df_b2 = h->df_b2;
+    p.pad_yz = (h->src.n[1] % kBrick != 0 || h->src.n[2] % kBrick != 0) ? 1 : 0;
     p.obs_scr = h->obs_scr;
     p.ring = h->ring;
     p.Hp = h->Hp;

@@ -137,6 +137,7 @@ struct SumParams {
     const float* obs_hl;
     const float2* cc_hl;
     float df_b1, df_b2;
+    int32_t pad_yz;                 // the grid ends inside its last bricks along y or z
     double K64;                     // 1 / (c dt)
 };
 

@@ -301,10 +301,12 @@ __device__ __noinline__ FixSums staged_fixup(uint64_t mask, uint32_t buf_off, in
 // One work item: observation tile `tile` x source splits [group split_merge,
 // (group + 1) split_merge) at time index `ti` of problem p.  g_it counts the CTA's stages across items (it
 // selects the buffer and the mbarrier phase).  Returns false if a copy did
-// not complete in time (the caller stops).  GEO: undecided pairs take their
+// not complete in time (the caller stops).  PAD: the source grid ends inside
+// its last bricks along y or z; their padding rows and slabs are skipped
+// (zero channels: no sum changes).  GEO: undecided pairs take their
 // FP64 geometry from shared memory and are counted there (the single-problem
 // kernel); otherwise from global memory (the batched kernel).
-template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool GEO>
+template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool GEO, bool PAD>
 __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const SumParams& p, const SumParams* sp,
                                             const int comp, const int tile, const int group, const int ti,
                                             uint32_t& g_it) {
@@ -543,8 +545,13 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     // stage (no negated pair per pair)
                     float acc_ex = 0.f, acc_ey = 0.f, acc_ez = 0.f, acc_bz = 0.f;
                     float2 acc_jyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
+                    // slabs and rows past the grid's last cell (PAD) hold only
+                    // padding: skipped
+                    const int k_end =
+                        PAD ? min(max(p.n_src_axis[2] - kBrick * bz - q * L::kSlabs, 0), L::kSlabs) : L::kSlabs;
+                    const int j_end = PAD ? p.n_src_axis[1] - kBrick * by : 4;
 #pragma unroll 1
-                    for (int kk = 0; kk < L::kSlabs; ++kk) {
+                    for (int kk = 0; kk < k_end; ++kk) {
                         const int k = q * L::kSlabs + kk;
                         const float dz = fmaf(-(float)k, d32z, Pz);
                         const float sqz = __fmul_rn(dz, dz);
@@ -552,6 +559,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         uint32_t m16 = 0;           // undecided cells of this slab (non-lattice geometry)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
+                            if (PAD && j >= j_end) break;
                             const float syz = __fadd_rn(sqy[j], sqz);
                             const float2 syz2 = make_float2(syz, syz);
                             float2 S2, R2, B2;   // S, r^-1 and candidate bits of cells i, i+1
@@ -779,7 +787,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     return aborted_at < 0;
 }
 
-template <int BAND, bool EXACT, bool DEBUG, bool INTERP>
+template <int BAND, bool EXACT, bool DEBUG, bool INTERP, bool PAD>
 __global__ void __launch_bounds__(kTileThreads, 2)
     sum_f32_staged_kernel(const __grid_constant__ CUtensorMap tmap, const SumParams p) {
     // the parameters the fix-up of undecided pairs reads (the stage loop
@@ -788,8 +796,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     if (!EXACT && threadIdx.x == 0) s_par = p;
     staged_init_barriers<BAND>();
     uint32_t g_it = 0;
-    staged_item<BAND, EXACT, DEBUG, INTERP, true>(&tmap, p, &s_par, p.comp, blockIdx.x, blockIdx.y, blockIdx.z,
-                                                  g_it);
+    staged_item<BAND, EXACT, DEBUG, INTERP, true, PAD>(&tmap, p, &s_par, p.comp, blockIdx.x, blockIdx.y,
+                                                       blockIdx.z, g_it);
 }
 
 // One item of the batched kernel as a call of its own: the item body gets
@@ -800,7 +808,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 template <int BAND, bool EXACT, bool INTERP>
 __device__ __noinline__ bool staged_batch_item(const CUtensorMap* map, const SumParams& p, int tile, int group,
                                                int ti, uint32_t& g_it) {
-    return staged_item<BAND, EXACT, false, INTERP, !EXACT>(map, p, &p, p.comp, tile, group, ti, g_it);
+    return staged_item<BAND, EXACT, false, INTERP, !EXACT, true>(map, p, &p, p.comp, tile, group, ti, g_it);
 }
 
 // Persistent batched kernel: CTAs take (problem, time, split group, tile) items
@@ -853,7 +861,14 @@ template <int BAND, bool EXACT, bool DEBUG, bool INTERP = false>
 cudaError_t launch_variant(const SumParams& p, const StagedConfig& c, cudaStream_t s) {
     const dim3 grid(p.n_tiles, (p.n_split + p.split_merge - 1) / p.split_merge, p.n_t);
     const size_t smem = staged_smem_bytes(p, BAND, false);
-    auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG, INTERP>;
+    // The padding skip changes the stage loop's code: measured, bands of 32
+    // rows and more run faster in that form whether or not the grid pads,
+    // the 16- and 24-row kernels ~5 % slower unless it does (the heavy-ion
+    // and dipole grids do not).  The slot-recording kernels never skip.
+    auto k = sum_f32_staged_kernel<BAND, EXACT, DEBUG, INTERP, false>;
+    if constexpr (!DEBUG) {
+        if (BAND >= 32 || p.pad_yz) k = sum_f32_staged_kernel<BAND, EXACT, DEBUG, INTERP, true>;
+    }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap* tm = static_cast<const CUtensorMap*>(c.tensor_map);
