@@ -543,8 +543,17 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     // products with D in scalars (no operand pair to build per
                     // pair), the dJ-terms of y and z packed and subtracted per
                     // stage (no negated pair per pair)
-                    float acc_ex = 0.f, acc_ey = 0.f, acc_ez = 0.f, acc_bz = 0.f;
-                    float2 acc_jyz = make_float2(0.f, 0.f), acc_bxy = make_float2(0.f, 0.f);
+                    // (the lattice kernel keeps two sets, for even and odd cells:
+                    // shorter dependency chains, measured 0.5 % faster there and
+                    // 1.7 % slower on the non-lattice kernels)
+                    constexpr int kAcc = EXACT ? 2 : 1;
+                    float acc_ex2[kAcc], acc_ey2[kAcc], acc_ez2[kAcc], acc_bz2[kAcc];
+                    float2 acc_jyz2[kAcc], acc_bxy2[kAcc];
+#pragma unroll
+                    for (int a = 0; a < kAcc; ++a) {
+                        acc_ex2[a] = acc_ey2[a] = acc_ez2[a] = acc_bz2[a] = 0.f;
+                        acc_jyz2[a] = acc_bxy2[a] = make_float2(0.f, 0.f);
+                    }
                     // slabs and rows past the grid's last cell (PAD) hold only
                     // padding: skipped
                     const int k_end =
@@ -625,6 +634,13 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                 const float2 vyz = __fmul2_rn(__ffma2_rn(make_float2(v0.z, v0.w), ri2,
                                                                          make_float2(v1.z, v1.w)), r2);
                                 const float qq = qvx.x, vx = qvx.y;
+                                const int ia = EXACT ? (i & 1) : 0;
+                                float& acc_ex = acc_ex2[ia];
+                                float& acc_ey = acc_ey2[ia];
+                                float& acc_ez = acc_ez2[ia];
+                                float& acc_bz = acc_bz2[ia];
+                                float2& acc_jyz = acc_jyz2[ia];
+                                float2& acc_bxy = acc_bxy2[ia];
                                 // E' += D q - (dJ/c) r^-1
                                 acc_ex = fmaf(ddx[i], qq, acc_ex);
                                 acc_ex = fmaf(-v1.y, ri, acc_ex);
@@ -642,12 +658,21 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         }
                         if (!EXACT) mask |= (uint64_t)m16 << (k * 16);
                     }
-                    pe[0] += acc_ex;
-                    pe[1] += acc_ey - acc_jyz.x;
-                    pe[2] += acc_ez - acc_jyz.y;
-                    pb[0] += acc_bxy.x;
-                    pb[1] += acc_bxy.y;
-                    pb[2] += acc_bz;
+                    if constexpr (kAcc == 2) {
+                        pe[0] += acc_ex2[0] + acc_ex2[1];
+                        pe[1] += (acc_ey2[0] + acc_ey2[1]) - (acc_jyz2[0].x + acc_jyz2[1].x);
+                        pe[2] += (acc_ez2[0] + acc_ez2[1]) - (acc_jyz2[0].y + acc_jyz2[1].y);
+                        pb[0] += acc_bxy2[0].x + acc_bxy2[1].x;
+                        pb[1] += acc_bxy2[0].y + acc_bxy2[1].y;
+                        pb[2] += acc_bz2[0] + acc_bz2[1];
+                    } else {
+                        pe[0] += acc_ex2[0];
+                        pe[1] += acc_ey2[0] - acc_jyz2[0].x;
+                        pe[2] += acc_ez2[0] - acc_jyz2[0].y;
+                        pb[0] += acc_bxy2[0].x;
+                        pb[1] += acc_bxy2[0].y;
+                        pb[2] += acc_bz2[0];
+                    }
                     if (!EXACT) {
                         if (__any_sync(kFull, mask != 0ull)) {
                             if constexpr (!GEO) n_fb += (uint32_t)__popcll(mask);
