@@ -543,10 +543,11 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     // products with D in scalars (no operand pair to build per
                     // pair), the dJ-terms of y and z packed and subtracted per
                     // stage (no negated pair per pair)
-                    // (the lattice kernel keeps two sets, for even and odd cells:
-                    // shorter dependency chains, measured 0.5 % faster there and
-                    // 1.7 % slower on the non-lattice kernels)
-                    constexpr int kAcc = EXACT ? 2 : 1;
+                    // (the floor-rule lattice kernel keeps two sets, for even and
+                    // odd cells: shorter dependency chains, measured 0.5 % faster
+                    // there, 1.7 % slower on the non-lattice kernels and 4 % on
+                    // the interpolating one)
+                    constexpr int kAcc = (EXACT && !INTERP) ? 2 : 1;
                     float acc_ex2[kAcc], acc_ey2[kAcc], acc_ez2[kAcc], acc_bz2[kAcc];
                     float2 acc_jyz2[kAcc], acc_bxy2[kAcc];
 #pragma unroll
@@ -634,7 +635,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                 const float2 vyz = __fmul2_rn(__ffma2_rn(make_float2(v0.z, v0.w), ri2,
                                                                          make_float2(v1.z, v1.w)), r2);
                                 const float qq = qvx.x, vx = qvx.y;
-                                const int ia = EXACT ? (i & 1) : 0;
+                                const int ia = kAcc == 2 ? (i & 1) : 0;
                                 float& acc_ex = acc_ex2[ia];
                                 float& acc_ey = acc_ey2[ia];
                                 float& acc_ez = acc_ez2[ia];
