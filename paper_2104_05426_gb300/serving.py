@@ -95,6 +95,62 @@ class ServedProblem:
         self.n_pushed += 1
 
 
+class SliceBatch:
+    """The next slice of many served problems at once, by the formula of
+    ``OscillatingGaussians.sample_torch`` (rho = sum q G(r - c(t)), J = sum
+    q G(r - c(t)) c'(t), blobs in order), with a few device operations per
+    blob slot for all problems together instead of a dozen per blob per
+    problem: the serving loop pushes to every problem every tick, and its
+    single host thread would otherwise spend most of a tick launching the
+    generator's small kernels.  Problems with fewer blobs carry zero-charge
+    blobs (they add exact zeros).  `pts` of each problem on one device."""
+
+    def __init__(self, problems):
+        import torch
+
+        self.torch = torch
+        self.problems = list(problems)
+        dev = self.problems[0].pts.device
+        self.counts = [p.pts.shape[0] for p in self.problems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.counts)]).astype(np.int64)
+        self.pts = torch.cat([p.pts for p in self.problems], dim=0)
+        self.pidx = torch.repeat_interleave(torch.arange(len(self.problems), device=dev),
+                                            torch.tensor(self.counts, device=dev))
+        self.nb = max(len(p.blobs) for p in self.problems)
+        P, B = len(self.problems), self.nb
+        sig = np.ones((P, B, 3))
+        coef = np.zeros((P, B))
+        for i, p in enumerate(self.problems):
+            for k, b in enumerate(p.blobs):
+                sig[i, k] = b.sigma
+                coef[i, k] = b.q * (1.0 / ((2.0 * math.pi) ** 1.5 * b.sigma[0] * b.sigma[1] * b.sigma[2]))
+        self.sig = torch.tensor(sig, dtype=torch.float64, device=dev)
+        self.coef = torch.tensor(coef, dtype=torch.float64, device=dev)
+
+    def sample(self, times):
+        """rho [N_total] and J [N_total, 3] of every problem at its time
+        (times[i] for problem i); problem i's rows start at offsets[i]."""
+        torch = self.torch
+        P, B = len(self.problems), self.nb
+        cv = np.zeros((2, P, B, 3))
+        for i, p in enumerate(self.problems):
+            for k, b in enumerate(p.blobs):
+                c, v = p.model._centre(b, times[i])
+                cv[0, i, k] = c
+                cv[1, i, k] = v
+        cv = torch.from_numpy(cv)
+        if self.pts.is_cuda:   # pinned and asynchronous: the host does not wait for the stream
+            cv = cv.pin_memory().to(self.pts.device, non_blocking=True)
+        rho = torch.zeros(self.pts.shape[0], dtype=torch.float64, device=self.pts.device)
+        J = torch.zeros((self.pts.shape[0], 3), dtype=torch.float64, device=self.pts.device)
+        for k in range(B):
+            u = (self.pts - cv[0, :, k][self.pidx]) / self.sig[:, k][self.pidx]
+            g = self.coef[:, k][self.pidx] * torch.exp(-0.5 * (u * u).sum(dim=1))
+            rho += g
+            J += g[:, None] * cv[1, :, k][self.pidx]
+        return rho, J
+
+
 @dataclass
 class Request:
     rid: int
@@ -147,6 +203,8 @@ class ServingEngine:
         self.obs_half_width = obs_half_width
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.push_stream = torch.cuda.Stream()
+        self.gen_stream = torch.cuda.Stream()   # slice generation, apart from the batches' order
+        self.slices = SliceBatch(problems)
         self.memory_budget = memory_budget
         self.max_batch = max_batch
         self.tick_s = tick_s
@@ -158,6 +216,32 @@ class ServingEngine:
         self.used_bytes = self.resident_bytes
         self.peak_bytes = self.used_bytes
         self.views_created = 0
+
+    # ------------------------------------------------------------------ pushes
+    def _push_all(self):
+        """One tick: the next slice of every problem, generated together on a
+        stream of its own (it does not wait for the batches in flight), then
+        pushed on the push stream, each problem's push after the batches still
+        reading its ring; later batches wait for the push (last_push)."""
+        torch = self.torch
+        with torch.cuda.stream(self.gen_stream):
+            rho, J = self.slices.sample([p.n_pushed * p.dt for p in self.problems])
+            gen_done = torch.cuda.Event()
+            gen_done.record(self.gen_stream)
+        s = self.push_stream
+        rho.record_stream(s)
+        J.record_stream(s)
+        s.wait_event(gen_done)
+        off = self.slices.offsets
+        for i, p in enumerate(self.problems):
+            for ev in p.readers:
+                s.wait_event(ev)
+            p.readers = []
+            jefi_push_sources(p.handle, rho[off[i]:off[i + 1]], J[off[i]:off[i + 1]], stream=s)
+            ev = torch.cuda.Event()
+            ev.record(s)
+            p.last_push = ev
+            p.n_pushed += 1
 
     # ------------------------------------------------------------------ views
     def _free_view(self, key):
@@ -219,8 +303,7 @@ class ServingEngine:
                 queue.append(pending.popleft())
                 progressed = True
             if now >= next_tick:
-                for p in self.problems:
-                    p.push_next(self.push_stream)
+                self._push_all()
                 next_tick += self.tick_s
                 progressed = True
             # admission, first in first out, by device memory (a view's real

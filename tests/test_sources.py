@@ -74,8 +74,10 @@ def test_device_form_of_moving_gaussians_matches_the_numpy_form():
     for t in (0.0, 0.7, 2.5):
         rho, J = m.sample(g, t)
         rt, Jt = m.sample_torch(torch.from_numpy(g.points()), t)
-        assert np.allclose(rt.numpy(), rho, rtol=1e-13, atol=1e-300)
-        assert np.allclose(Jt.numpy(), J, rtol=1e-13, atol=1e-300)
+        assert np.allclose(rt.numpy(), rho, rtol=1e-13, atol=1e-13 * np.abs(rho).max())
+        # components that cancel between blobs are compared at the field's scale
+        # (numpy's and torch's exp may differ by an ulp, on some hosts)
+        assert np.allclose(Jt.numpy(), J, rtol=1e-13, atol=1e-13 * np.abs(J).max())
 
 
 def test_device_form_of_oscillating_gaussians_matches_the_numpy_form():
@@ -86,5 +88,40 @@ def test_device_form_of_oscillating_gaussians_matches_the_numpy_form():
     for t in (0.0, 0.9, 31.5):
         rho, J = m.sample(g, t)
         rt, Jt = m.sample_torch(torch.from_numpy(g.points()), t)
-        assert np.allclose(rt.numpy(), rho, rtol=1e-13, atol=1e-300)
-        assert np.allclose(Jt.numpy(), J, rtol=1e-13, atol=1e-300)
+        assert np.allclose(rt.numpy(), rho, rtol=1e-13, atol=1e-13 * np.abs(rho).max())
+        # components that cancel between blobs are compared at the field's scale
+        # (numpy's and torch's exp may differ by an ulp, on some hosts)
+        assert np.allclose(Jt.numpy(), J, rtol=1e-13, atol=1e-13 * np.abs(J).max())
+
+
+def test_batched_slices_of_many_problems_match_each_model():
+    """The serving loop's batched slice generator (every problem's next slice
+    in a few device operations per blob slot) gives each problem exactly what
+    its own source model gives, blob counts differing between problems."""
+    torch = pytest.importorskip("torch")
+    from paper_2104_05426_gb300.serving import SliceBatch
+
+    class Stub:
+        def __init__(self, n, blobs):
+            ax = torch.linspace(-1.0, 1.0, n, dtype=torch.float64)
+            z, y, x = torch.meshgrid(ax, ax, ax, indexing="ij")
+            self.pts = torch.stack([x.reshape(-1), y.reshape(-1), z.reshape(-1)], dim=1)
+            self.blobs = blobs
+            self.model = OscillatingGaussians(blobs)
+
+    rng = np.random.Generator(np.random.PCG64(5))
+
+    def blob():
+        return OscBlob(float(rng.choice([-1.0, 1.0])), tuple(rng.uniform(0.15, 0.35, 3)),
+                       tuple(rng.uniform(-0.2, 0.2, 3)), tuple(rng.uniform(-0.5, 0.5, 3)),
+                       float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.0, 6.0)))
+
+    probs = [Stub(n, [blob() for _ in range(nb)]) for n, nb in ((5, 1), (7, 4), (4, 2), (6, 3))]
+    sb = SliceBatch(probs)
+    times = [0.0, 0.37, 1.9, 12.25]
+    rho, J = sb.sample(times)
+    for i, p in enumerate(probs):
+        r_ref, j_ref = p.model.sample_torch(p.pts, times[i])
+        a, b = int(sb.offsets[i]), int(sb.offsets[i + 1])
+        assert torch.equal(rho[a:b], r_ref), i
+        assert torch.equal(J[a:b], j_ref), i
