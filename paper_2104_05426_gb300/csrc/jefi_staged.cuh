@@ -578,8 +578,10 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                 const int c16 = j * 4 + i;
                                 float S, ri;
                                 uint32_t bits;
-                                if constexpr (EXACT) {
-                                    // lattice kernel: two cells' candidates at once,
+                                if constexpr (EXACT || BAND <= 24) {
+                                    // two cells' candidates at once (the lattice kernels and
+                                    // the narrow bands: measured faster there; the wide
+                                    // non-lattice kernels spill with it),
                                     // S*r^-1*(-K) + A + g rounded as fmaf(-(S*ri), K, Ag)
                                     if ((i & 1) == 0) {
                                         S2 = __fadd2_rn(make_float2(sqx[i], sqx[i + 1]), syz2);
@@ -590,8 +592,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                                     ri = (i & 1) ? R2.y : R2.x;
                                     bits = __float_as_uint((i & 1) ? B2.y : B2.x);
                                 } else {
-                                    // one cell at a time (the pairs cost the
-                                    // undecided test's registers)
+                                    // one cell at a time
                                     S = __fadd_rn(sqx[i], syz);
                                     ri = rsqrt_ftz(S);
                                     bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, Ag), kMagic));
