@@ -578,20 +578,64 @@ int64_t staged_resident_ctas(size_t smem_bytes) {
 // waves x (bricks per item + a preamble of about half a brick's work).  The
 // partials are those of one item per split whatever the value, so it changes
 // the cost of a launch (its items' preambles and first copies, its last
-// wave), never its result.
-int32_t split_merge_for(int64_t units, int32_t n_split, int32_t bricks_per_split, int64_t resident) {
+// wave), never its result.  Only the least merge of each item count is a
+// candidate (a larger one with as many items costs more), so the search
+// takes O(sqrt(n_split)) steps.  `cost`, if given, receives the prediction.
+int32_t split_merge_for(int64_t units, int32_t n_split, int32_t bricks_per_split, int64_t resident,
+                        double* cost = nullptr) {
+    const int64_t n = std::max(n_split, 1);
+    const int64_t r = std::max<int64_t>(resident, 1);
     double best = 0.0;
     int32_t best_m = 1;
-    for (int32_t m = 1; m <= std::max(n_split, 1); ++m) {
-        const int64_t items = units * ((n_split + m - 1) / m);
-        const int64_t waves = (items + resident - 1) / std::max<int64_t>(resident, 1);
-        const double cost = (double)waves * ((double)m * bricks_per_split + 0.5);
-        if (m == 1 || cost < best) {
-            best = cost;
-            best_m = m;
+    for (int64_t m = 1; m <= n;) {
+        const int64_t q = (n + m - 1) / m;   // items per (tile, time)
+        const int64_t waves = (units * q + r - 1) / r;
+        const double c = (double)waves * ((double)m * bricks_per_split + 0.5);
+        if (m == 1 || c < best) {
+            best = c;
+            best_m = (int32_t)m;
+        }
+        if (q == 1) break;
+        m = (n + q - 2) / (q - 1);   // least merge with fewer items
+    }
+    if (cost) *cost = best;
+    return best_m;
+}
+
+// Source splits of a staged handle with n_tiles tiles over n_bricks bricks,
+// at most ns_max: the count whose launches of 1, 2, 4, ... time_chunk
+// evaluation times fill their waves best (split_merge_for's prediction over
+// the ideal units x bricks / resident), the fewest splits among equals.
+// Whole waves of equal items matter most where the units are few: a view of
+// 128 tiles over 4096 bricks (at most 10 splits) at one time runs 3 waves of
+// 7 splits, 98 % full, where 10 splits ran as 2 groups of 5 in one wave 84 %
+// full.
+int64_t split_count_for(int64_t n_tiles, int64_t n_bricks, int64_t ns_max, int32_t time_chunk,
+                        int64_t resident) {
+    const int64_t nb = std::max<int64_t>(n_bricks, 1);
+    const int64_t nt = std::max<int64_t>(n_tiles, 1);
+    ns_max = std::max<int64_t>(1, std::min(ns_max, nb));
+    double best = 0.0;
+    int64_t best_ns = 1;
+    for (int64_t ns = 1; ns <= ns_max; ++ns) {
+        const int64_t bps = (nb + ns - 1) / ns;
+        if ((nb + bps - 1) / bps != ns) continue;   // the same splits as a smaller count
+        double score = 0.0;
+        int n_launch = 0;
+        for (int32_t t = 1;; t = std::min(2 * t, time_chunk)) {
+            double c = 0.0;
+            split_merge_for(nt * t, (int32_t)ns, (int32_t)bps, resident, &c);
+            score += c / ((double)(nt * t) * (double)nb / (double)std::max<int64_t>(resident, 1));
+            ++n_launch;
+            if (t >= time_chunk) break;
+        }
+        score /= n_launch;
+        if (ns == 1 || score < best - 1e-9) {
+            best = score;
+            best_ns = ns;
         }
     }
-    return best_m;
+    return best_ns;
 }
 
 // Record that work on h's memory was enqueued on stream s (jefi_destroy waits for it).
@@ -1537,18 +1581,20 @@ static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const do
         h->K = 1;
     }
     {
-        // Source splits: enough (tile, split) items for eight waves of two
-        // CTAs per SM at one evaluation time (four for views), so that a
-        // launch can merge them into items that fill its last wave
-        // (split_merge_for); at most one split per brick, and partials of at
-        // most 256 MB (32 MB for views, many of which are cached under a
-        // serving budget).
-        const int64_t target = (base ? 4 : 8) * 2 * (int64_t)current_sm_count();
+        // Source splits: at most twice the count that gives eight waves of
+        // (tile, split) items of two CTAs per SM at one evaluation time (four
+        // for views), at most one per brick, and partials of at most 256 MB
+        // (32 MB for views, many of which are cached under a serving
+        // budget); within that, the count whose launches fill their waves
+        // (split_count_for; a launch can still merge them, split_merge_for).
+        const int64_t resident = 2 * (int64_t)current_sm_count();
+        const int64_t target = (base ? 4 : 8) * resident;
         int64_t ns = std::max<int64_t>(1, (target + h->n_tiles - 1) / std::max<int32_t>(h->n_tiles, 1));
-        ns = std::min<int64_t>(ns, std::max<int32_t>(h->n_bricks, 1));
+        ns = std::min<int64_t>(2 * ns, std::max<int32_t>(h->n_bricks, 1));
         const int64_t split_bytes = (int64_t)h->time_chunk * 6 * 8 * std::max<int32_t>(h->n_slots, 1);
         const int64_t cap = base ? ((int64_t)32 << 20) : ((int64_t)256 << 20);
         ns = std::max<int64_t>(1, std::min<int64_t>(ns, cap / split_bytes));
+        ns = split_count_for(h->n_tiles, h->n_bricks, ns, h->time_chunk, resident);
         h->bricks_per_split = (int32_t)((h->n_bricks + ns - 1) / ns);
         if (h->bricks_per_split < 1) h->bricks_per_split = 1;
         h->n_split = (int32_t)((h->n_bricks + h->bricks_per_split - 1) / h->bricks_per_split);
