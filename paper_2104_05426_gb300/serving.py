@@ -429,7 +429,10 @@ class ServingEngine:
                             latencies_ms=lat)
 
     def _estimate_view_bytes(self, req: Request) -> int:
-        # partial sums dominate: 8 time slots x splits x 6 x points x 8 B, splits ~ 2 waves / tiles
+        # a generous guess, used until a view of this (problem, side) exists and
+        # its real bytes are known: partial sums dominate (a view holds 2 time
+        # slots x splits x 6 x points x 8 B, at most 32 MB); this counts 8 slots
+        # and about two waves of (tile, split) items
         n = req.obs_side ** 3
         tiles = max(1, (n + 255) // 256)
         splits = max(1, min(608 // tiles, 64))
