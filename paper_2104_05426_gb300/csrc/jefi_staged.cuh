@@ -298,6 +298,103 @@ __device__ __noinline__ FixSums staged_fixup(uint64_t mask, uint32_t buf_off, in
     return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
 }
 
+// Capacity of a thread's queue of undecided pairs (non-lattice geometry).
+constexpr int kFixQueue = 16;
+
+// Pairs whose slot the FP32 rule left undecided (non-lattice geometry): the
+// exact slot by the double-float check (slot_double_float), else by the FP64
+// rule, then the pair from the ring in global memory.  The stage loop queues
+// a thread's undecided pairs (`fq`, nf entries of (brick << 6) | cell) and
+// the warp redoes them together once per split, or when a queue would
+// overflow (then with the current stage's `mask`, cells of brick mb): one
+// pass of this call for many stages, with many lanes busy, where a call per
+// stage had one lane busy and held the other warps at the stage barrier.
+// A call of its own (rare), so its registers do not weigh on the stage loop;
+// what the item does not vary it reads from the parameters (`sp`).  The
+// FP64 geometry of the item is in shared memory and the pairs are counted
+// there.  (oox, ooy, ooz): the point's offset from the tile's anchor.
+template <int BAND, bool DEBUG, bool INTERP>
+__device__ __noinline__ FixSums staged_fix_deferred(const uint32_t* fq, int nf, uint64_t mask, int mb, float oox,
+                                                    float ooy, float ooz, int slot, int ti, const SumParams* sp) {
+    using L = Layout<BAND>;
+    unsigned char* const sb = staged_base<BAND>();
+    const int K = sp->K;
+    const double* s_th = reinterpret_cast<const double*>(sb + L::kTab + (size_t)(K + 2 * kTabGuard) * sizeof(float2));
+    const float* s_D = reinterpret_cast<const float*>(s_th + K + 1);
+    const TimeParams tp = sp->times[ti];
+    const float K32 = sp->K32, K32_lo = sp->K32_lo;
+    const float d32x = sp->d32[0], d32y = sp->d32[1], d32z = sp->d32[2];
+    const float* xo_hl = sp->obs_hl + (size_t)6 * slot;
+    const float2* cc_hl = sp->cc_hl;
+    const float2* th_hl = reinterpret_cast<const float2*>(sp->theta + (size_t)ti * theta_stride(K) + (K + 1));
+    const int npx = sp->npx, npy = sp->npy, nbx = sp->nbx, nby = sp->nby;
+    const int Hp = sp->Hp, P = sp->H, zero_slot = sp->zero_slot;
+    const float4* ring = reinterpret_cast<const float4*>(sp->ring);
+    const size_t n_cells = (size_t)sp->n_bricks * kBrickCells;
+    // every undecided pair counts, whichever check decides it
+    atomicAdd(reinterpret_cast<uint32_t*>(sb + L::kGeo) + 3, (uint32_t)(nf + __popcll(mask)));
+    // physical ring row of slot k0 + n (the zero line for slots before slice 0)
+    auto phys = [&](int n) -> int {
+        if (tp.k0 + n < 0) return zero_slot;
+        int r = tp.k0_mod + n;
+        while (r >= P) r -= P;
+        while (r < 0) r += P;
+        return r;
+    };
+    float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
+    for (int e = 0;; ++e) {
+        int b, cl;
+        if (e < nf) {
+            const uint32_t q = fq[e];
+            b = (int)(q >> 6);
+            cl = (int)(q & 63u);
+        } else if (mask) {
+            b = mb;
+            cl = __ffsll((long long)mask) - 1;
+            mask &= mask - 1;
+        } else {
+            break;
+        }
+        const int bx = b % nbx, r_ = b / nbx, by = r_ % nby, bz = r_ / nby;
+        const int i = cl & 3, j = (cl >> 2) & 3, k = cl >> 4;
+        // the stage loop's operations, so the same S and candidate
+        const float Px = oox + s_D[bx];
+        const float Py = ooy + s_D[nbx + by];
+        const float Pz = ooz + s_D[nbx + nby + bz];
+        const float dx = fmaf(-(float)i, d32x, Px);
+        const float dy = fmaf(-(float)j, d32y, Py);
+        const float dz = fmaf(-(float)k, d32z, Pz);
+        const float S = __fadd_rn(__fmul_rn(dx, dx), __fadd_rn(__fmul_rn(dy, dy), __fmul_rn(dz, dz)));
+        const float ri = rsqrt_ftz(S);
+        const uint32_t bits = __float_as_uint(__fadd_rd(fmaf(-(S * ri), K32, tp.Ag), kMagic));
+        const int guess = (int)(bits - kMagicBits);
+        const int ix = kBrick * bx + i, iy = kBrick * by + j, iz = kBrick * bz + k;
+        int idx = slot_double_float(xo_hl, cc_hl[ix], cc_hl[npx + iy], cc_hl[npx + npy + iz], th_hl, K, guess,
+                                    S * ri, sp->df_b1, sp->df_b2);
+        if (idx < 0) idx = staged_slot_fp64<BAND>(ix, iy, iz, s_th, K, guess);
+        if (DEBUG) sp->debug_slots[(size_t)slot * n_cells + (size_t)b * kBrickCells + cl] = (int)(tp.k0 + idx);
+        const size_t cell = (size_t)b * kBrickCells + cl;
+        int ps = phys(idx);
+        if (cell >= n_cells || ps < 0 || ps >= Hp) {   // never, for a consistent handle
+            atomicExch(sp->status, kStatusInternal);
+            continue;
+        }
+        const float4* q = ring + (cell * Hp + ps) * 2;
+        float4 v0 = __ldg(q), v1 = __ldg(q + 1);
+        if (INTERP) {   // slot n+1
+            ps = phys(idx + 1);
+            if (ps < 0 || ps >= Hp) {
+                atomicExch(sp->status, kStatusInternal);
+                continue;
+            }
+            const float4* u = ring + (cell * Hp + ps) * 2;
+            lerp8(v0, v1, __ldg(u), __ldg(u + 1), interp_weight(S, ri, (float)idx, tp.A, tp.A_lo, K32, K32_lo));
+        }
+        pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
+    }
+    return FixSums{{pe[0], pe[1], pe[2], pb[0], pb[1], pb[2]}};
+}
+
 // One work item: observation tile `tile` x source splits [group split_merge,
 // (group + 1) split_merge) at time index `ti` of problem p.  g_it counts the CTA's stages across items (it
 // selects the buffer and the mbarrier phase).  Returns false if a copy did
@@ -367,6 +464,11 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
     // pairs whose slot was recomputed in FP64 through global memory, counted
     // per thread and added once per warp (not one atomic per pair)
     uint32_t n_fb = 0;
+    // undecided pairs (non-lattice geometry) of the current split, queued
+    // until the split ends: (brick << 6) | cell
+    static_assert(EXACT || GEO, "non-lattice items keep their FP64 geometry in shared memory");
+    uint32_t fq[(EXACT || BAND > 24) ? 1 : kFixQueue];
+    int nf = 0;
     // The item covers splits [split_lo, split_hi) (p.split_merge per item);
     // each split's bricks are summed and its partials written as an item of
     // its own would: the result does not depend on how many splits an item
@@ -500,6 +602,8 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
         const float Pz = ooz + s_D[nbxy + bz];
         // the brick's sum over its stages (compensated once per brick)
         float pe[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
+        // brick b ends its split (whose partials are written after it)
+        const bool split_last = (b + 1) % p.bricks_per_split == 0 || b + 1 == b_end;
         // One stage: q-th group of kCells cells of brick b.  False if its copy
         // did not complete in time (the item then stops).
         auto stage = [&](const int q) -> bool {
@@ -514,6 +618,7 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
             if (ready && band_rel != kBandSkip) {
                 const int cell0 = q * L::kCells;
                 const unsigned char* bufp = sb + (uint32_t)buf * L::kBufBytes;
+                uint64_t mask = 0;   // undecided pairs of the stage (non-lattice geometry)
                 if (fast) {
                     // Per-axis offsets and squares of the brick's 4 columns; the
                     // z slabs are a rolled loop (keeps the hot body small), the
@@ -534,7 +639,6 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                     const unsigned char* const rows = L::kSwz ? bufp : sb;
                     const uint32_t gbase = (L::kSwz ? 0u : (uint32_t)buf * L::kBufBytes) -
                                            (uint32_t)(kMagicBits + band_rel) * L::kRowBytes;
-                    uint64_t mask = 0;
                     // operands of the candidates of two cells at once (packed FP32
                     // with the scalar roundings: the same bits as one cell at a time)
                     const float2 nK2 = make_float2(-K32, -K32), Ag2 = make_float2(Ag, Ag);
@@ -675,19 +779,6 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         pb[1] += acc_bxy2[0].y;
                         pb[2] += acc_bz2[0];
                     }
-                    if (!EXACT) {
-                        if (__any_sync(kFull, mask != 0ull)) {
-                            if constexpr (!GEO) n_fb += (uint32_t)__popcll(mask);
-                            const FixSums f = staged_fixup<BAND, DEBUG, INTERP, GEO>(
-                                mask, (uint32_t)buf * L::kBufBytes, cell0, band_rel, Px, Py, Pz, bx, by, bz, b,
-                                ctx.slot, ti, sp);
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) {
-                                pe[a] += f.v[a];
-                                pb[a] += f.v[3 + a];
-                            }
-                        }
-                    }
                 } else {
                     // Bricks with screened pairs: rolled loop with per-pair checks
                     // and clamped indices.
@@ -743,6 +834,43 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
                         pair_f32(dx, dy, dz, ri, v0, v1, pe, pb);
                     }
                 }
+                if constexpr (!EXACT && BAND > 24) {
+                    // wide bands: the stage's undecided pairs now, from the
+                    // stage buffer (a queue made their batched item spill)
+                    if (__any_sync(kFull, mask != 0ull)) {
+                        const FixSums f = staged_fixup<BAND, DEBUG, INTERP, GEO>(
+                            mask, (uint32_t)buf * L::kBufBytes, cell0, band_rel, Px, Py, Pz, bx, by, bz, b,
+                            ctx.slot, ti, sp);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            pe[a] += f.v[a];
+                            pb[a] += f.v[3 + a];
+                        }
+                    }
+                } else if constexpr (!EXACT) {
+                    // Undecided pairs join the thread's queue.  The warp redoes
+                    // the queued pairs (and this stage's) when a queue would
+                    // overflow and at the split's last stage, so that they join
+                    // their own split's sums; one call site keeps the stage
+                    // loop's registers as they were.
+                    const bool last = split_last && q == L::kParts - 1;
+                    if (__any_sync(kFull, nf + __popcll(mask) > kFixQueue || (last && (nf > 0 || mask != 0ull)))) {
+                        const FixSums f = staged_fix_deferred<BAND, DEBUG, INTERP>(fq, nf, mask, b, oox, ooy, ooz,
+                                                                                   ctx.slot, ti, sp);
+                        nf = 0;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            pe[a] += f.v[a];
+                            pb[a] += f.v[3 + a];
+                        }
+                    } else {
+                        while (mask) {
+                            const int cl = __ffsll((long long)mask) - 1;
+                            mask &= mask - 1;
+                            fq[nf++] = ((uint32_t)b << 6) | (uint32_t)cl;
+                        }
+                    }
+                }
             }
             // the next 256 bands, before the stage that issues the first of them
             if (((g + 2) & (kTileThreads - 1)) == 0 && g + 2 < n_stages) fill_bands(g + 2);
@@ -777,8 +905,9 @@ __device__ __forceinline__ bool staged_item(const CUtensorMap* tmap_ptr, const S
             bx = 0;
             if (++by == p.nby) { by = 0; ++bz; }
         }
-        if ((b + 1) % p.bricks_per_split == 0 || b + 1 == b_end) {
-            // the split of brick b is complete: its partial sums
+        if (split_last) {
+            // the split of brick b is complete (its queued pairs were redone
+            // in its last stage): its partial sums
             write_split(b / p.bricks_per_split);
 #pragma unroll
             for (int a = 0; a < 3; ++a) se[a] = sbv[a] = ce[a] = cbv[a] = 0.f;
