@@ -298,6 +298,27 @@ void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double 
                           double c, double dt, int64_t* out);
 
 /*
+ * Host rule of the source splits (no GPU needed).  The direct sum of
+ * Eqs. E-1/B-1 runs over every source cell for every observation tile; the
+ * library cuts the source bricks of a tile into splits whose FP64 partial
+ * sums the reduction adds in split order (the paper has no counterpart: its
+ * kernel sums all cells in one thread).  For n_tiles tiles of 256 points
+ * over n_bricks 4x4x4 source bricks, at most max_splits splits, launches of
+ * 1, 2, 4, ... times_per_launch evaluation times and resident_ctas CTAs
+ * resident at once, this returns the split count jefi_create picks for a
+ * staged FP32 handle (*n_split, the one whose launches fill their waves of
+ * equal work items best, the fewest among equals), its bricks per split
+ * (*bricks_per_split) and the consecutive splits one work item of a
+ * single-time launch merges (*merge).  jefi_create takes max_splits as
+ * twice the count that gives 8 waves (4 for a view) at one time, capped at
+ * one split per brick and 256 MB of partial sums (32 MB for a view), and
+ * resident_ctas as 2 per SM.  Returns JEFI_EINVAL for a non-positive size
+ * or a NULL output.
+ */
+int jefi_host_split_plan(int64_t n_tiles, int64_t n_bricks, int64_t max_splits, int32_t times_per_launch,
+                         int64_t resident_ctas, int32_t* n_split, int32_t* bricks_per_split, int32_t* merge);
+
+/*
  * Push one slice given as a region of larger arrays: rho, J (and drho, dJ
  * when supplied) cover full_n[0] x full_n[1] x full_n[2] cells, x fastest,
  * and the handle's cell (i, j, k) is their cell offset + (i, j, k).  The

@@ -66,7 +66,7 @@ EXPORTS = ("jefi_default_params", "jefi_create", "jefi_push_sources", "jefi_eval
            "jefi_debug_wait_timeout", "jefi_checkpoint_bytes", "jefi_checkpoint", "jefi_restore",
            "jefi_select_kernel", "jefi_batch_plan_create", "jefi_batch_plan_launch",
            "jefi_batch_plan_tune", "jefi_batch_plan_destroy", "jefi_push_sources_region",
-           "jefi_so_partition", "jefi_sum_fields")
+           "jefi_so_partition", "jefi_sum_fields", "jefi_host_split_plan")
 
 JEFI_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -153,6 +153,8 @@ def load(build_if_needed: bool = True):
         L.jefi_debug_slots.argtypes = [P, D, P, P]
         L.jefi_host_pair_slots.argtypes = [I64, P, P, D, D, D, D, P]
         L.jefi_host_pair_slots.restype = None
+        PI32 = ctypes.POINTER(I32)
+        L.jefi_host_split_plan.argtypes = [I64, I64, I64, I32, I64, PI32, PI32, PI32]
         L.jefi_destroy.argtypes = [P]
         L.jefi_eval_batch.argtypes = [P, P, P, P, I32, P]
         L.jefi_create_view.argtypes = [P, ctypes.POINTER(jefi_grid), P, I64, P, ctypes.POINTER(P)]
@@ -477,6 +479,16 @@ def jefi_host_pair_slots(xo, xs, t, t0, c, dt) -> np.ndarray:
     load().jefi_host_pair_slots(xo.shape[0], xo.ctypes.data, xs.ctypes.data, float(t), float(t0),
                                 float(c), float(dt), out.ctypes.data)
     return out
+
+
+def jefi_host_split_plan(n_tiles: int, n_bricks: int, max_splits: int, times_per_launch: int,
+                         resident_ctas: int):
+    """(n_split, bricks_per_split, merge) of the library's split rule (host only)."""
+    out = [ctypes.c_int32(0) for _ in range(3)]
+    _check(load().jefi_host_split_plan(int(n_tiles), int(n_bricks), int(max_splits), int(times_per_launch),
+                                       int(resident_ctas), *(ctypes.byref(o) for o in out)),
+           "jefi_host_split_plan")
+    return tuple(o.value for o in out)
 
 
 def jefi_destroy(h: Handle):

@@ -1260,6 +1260,19 @@ void jefi_host_pair_slots(int64_t n, const double* xo, const double* xs, double 
     }
 }
 
+int jefi_host_split_plan(int64_t n_tiles, int64_t n_bricks, int64_t max_splits, int32_t times_per_launch,
+                         int64_t resident_ctas, int32_t* n_split, int32_t* bricks_per_split, int32_t* merge) {
+    if (n_tiles < 1 || n_bricks < 1 || max_splits < 1 || times_per_launch < 1 || resident_ctas < 1 || !n_split ||
+        !bricks_per_split || !merge || n_bricks > INT32_MAX)
+        return JEFI_EINVAL;
+    const int64_t ns = split_count_for(n_tiles, n_bricks, max_splits, times_per_launch, resident_ctas);
+    const int64_t bps = (n_bricks + ns - 1) / ns;
+    *n_split = (int32_t)((n_bricks + bps - 1) / bps);
+    *bricks_per_split = (int32_t)bps;
+    *merge = split_merge_for(n_tiles, *n_split, *bricks_per_split, resident_ctas);
+    return JEFI_OK;
+}
+
 static int create_impl(const jefi_grid* src, const jefi_grid* obs_grid, const double* obs_points,
                        int64_t n_obs_in, const jefi_params* p, void* stream, jefi_problem* base,
                        jefi_handle* out) {

@@ -195,3 +195,61 @@ def test_noalloc_wrapper_checks_shapes_before_any_launch():
             jefi.jefi_eval_fields_noalloc(g, args["obs"], args["rho"], args["J"], prm, 1.0, args["E"], args["B"])
     with pytest.raises(ValueError, match="device"):     # right shapes, host buffers
         jefi.jefi_eval_fields_noalloc(g, obs, rho, J, prm, 1.0, E, B)
+
+
+def _wave_cost(units, n_split, bps, resident):
+    """Waves x (bricks per item + half a brick of preamble) of the least
+    costly merge, by brute force over every merge (the rule the library
+    searches in O(sqrt(n_split)) steps)."""
+    best = None
+    for m in range(1, n_split + 1):
+        items = units * -(-n_split // m)
+        c = -(-items // resident) * (m * bps + 0.5)
+        if best is None or c < best[0]:
+            best = (c, m)
+    return best
+
+
+def test_split_plan_fills_whole_waves():
+    """The dipole workload (16 tiles, 512 bricks, 4 times per launch) and a
+    64^3-source view of 32^3 points: creation picks the split counts whose
+    launches run whole waves of equal items on 304 CTA slots."""
+    assert jefi.jefi_host_split_plan(16, 512, 170, 8, 304) == (19, 27, 1)
+    n, bps, m = jefi.jefi_host_split_plan(128, 4096, 10, 2, 304)
+    assert (n, bps, m) == (7, 586, 1)
+    assert 128 * n / (-(-128 * n // 304) * 304) > 0.98     # items fill 98 % of their waves
+
+
+def test_split_plan_is_consistent_and_optimal():
+    rng = np.random.Generator(np.random.PCG64(21))
+    for _ in range(300):
+        tiles = int(rng.integers(1, 2000))
+        bricks = int(rng.integers(1, 5000))
+        cap = int(rng.integers(1, 300))
+        chunk = int(rng.choice([1, 2, 8]))
+        resident = int(rng.choice([152, 304, 456]))
+        n, bps, m = jefi.jefi_host_split_plan(tiles, bricks, cap, chunk, resident)
+        assert 1 <= n <= min(cap, bricks) and bps * (n - 1) < bricks <= bps * n
+        assert m == _wave_cost(tiles, n, bps, resident)[1]
+        # no other count within the cap predicts less time, averaged over
+        # launches of 1, 2, 4, ... chunk times
+        ts = [1]
+        while ts[-1] < chunk:
+            ts.append(min(2 * ts[-1], chunk))
+
+        def score(k):
+            b = -(-bricks // k)
+            kk = -(-bricks // b)
+            return sum(_wave_cost(tiles * t, kk, b, resident)[0] / (tiles * t * bricks / resident)
+                       for t in ts) / len(ts)
+
+        if cap <= 60:
+            chosen = score(n)
+            assert all(chosen <= score(k) + 1e-9 for k in range(1, min(cap, bricks) + 1))
+
+
+def test_split_plan_rejects_bad_arguments():
+    for args in ((0, 10, 5, 1, 304), (4, 0, 5, 1, 304), (4, 10, 0, 1, 304), (4, 10, 5, 0, 304),
+                 (4, 10, 5, 1, 0)):
+        with pytest.raises(jefi.JefiError):
+            jefi.jefi_host_split_plan(*args)
